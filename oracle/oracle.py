@@ -1,0 +1,225 @@
+"""ctypes harness around the FP64 CPU oracle (oracle/qmc_oracle.cpp).
+
+Test infrastructure only: tests/, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of bench.py may use it; the
+product library never does.  Every numerical step lives in the C++ source,
+which cites the passages of Sorella & Mazzola (arXiv:1605.08423) it follows.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qmc_oracle.cpp")
+_LIBDIR = os.path.join(_HERE, "lib")
+_LIB = os.path.join(_LIBDIR, "libqmc_oracle.so")
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/lib/libqmc_oracle.so (g++, OpenMP, IEEE FP64)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+           _SRC, "-o", tmp]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("N", C.c_int32), ("n_up", C.c_int32), ("n_dn", C.c_int32), ("n_orb", C.c_int32),
+        ("n_gauss", C.c_int32), ("periodic", C.c_int32), ("mmax", C.c_int32), ("pad_", C.c_int32),
+        ("L", C.c_double), ("b_ee", C.c_double), ("b_ep", C.c_double), ("Z", C.c_double),
+        ("Zj", C.c_double), ("kappa", C.c_double),
+        ("zeta", C.POINTER(C.c_double)), ("coeff", C.POINTER(C.c_double)),
+    ]
+
+
+class ChainArgs(C.Structure):
+    _fields_ = [
+        ("W", C.c_int32), ("n_sweeps", C.c_int32), ("n_warmup", C.c_int32),
+        ("measure_every", C.c_int32), ("init_walkers", C.c_int32), ("forces", C.c_int32),
+        ("md_step", C.c_uint32), ("pad_", C.c_int32), ("sigma", C.c_double), ("seed", C.c_uint64),
+    ]
+
+
+_dp = C.POINTER(C.c_double)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        L.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
+        L.orc_uniform.restype = C.c_double
+        L.orc_uniform.argtypes = [C.c_uint64] + [C.c_uint32] * 4
+        L.orc_normal.restype = C.c_double
+        L.orc_normal.argtypes = [C.c_uint64] + [C.c_uint32] * 4
+        L.orc_ewald.restype = C.c_double
+        L.orc_ewald.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_double, C.c_int, C.c_int]
+        L.orc_eval_config.restype = C.c_int
+        L.orc_eval_config.argtypes = [C.POINTER(Params), _dp, _dp, C.c_int, _dp, _dp, _dp, _dp]
+        L.orc_eval_configs.restype = C.c_int
+        L.orc_eval_configs.argtypes = [C.POINTER(Params), _dp, C.c_int, _dp, C.c_int, _dp, _dp, _dp, _dp]
+        L.orc_init_walkers.argtypes = [C.POINTER(Params), _dp, C.c_int, C.c_uint64, _dp]
+        L.orc_vmc.argtypes = [C.POINTER(Params), _dp, C.POINTER(ChainArgs), _dp, _dp,
+                              C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+        L.orc_reduce.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.orc_langevin.restype = C.c_int
+        L.orc_langevin.argtypes = [C.c_int, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
+                                   C.c_double, _dp, C.c_int, C.c_double, _dp]
+        L.orc_langevin_noise.argtypes = [C.c_uint64, C.c_uint32, C.c_int, _dp]
+        L.orc_num_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_dp)
+
+
+@dataclass
+class System:
+    """Wavefunction / Hamiltonian parameters of one system (oracle side)."""
+    N: int
+    L: float
+    zeta: np.ndarray          # [G]
+    coeff: np.ndarray         # [N*G][n_orb]
+    n_up: int | None = None
+    n_dn: int | None = None
+    b_ee: float = 1.0
+    b_ep: float = 1.0
+    Z: float = 1.0
+    Zj: float | None = None
+    kappa: float | None = None
+    mmax: int = 6
+    periodic: bool = True
+
+    def cparams(self) -> Params:
+        self._zeta = np.ascontiguousarray(self.zeta, dtype=np.float64)
+        self._coeff = np.ascontiguousarray(self.coeff, dtype=np.float64)
+        n_up = self.N // 2 if self.n_up is None else self.n_up
+        n_dn = self.N - n_up if self.n_dn is None else self.n_dn
+        kappa = 5.0 / self.L if self.kappa is None else self.kappa
+        return Params(self.N, n_up, n_dn, self._coeff.shape[1], len(self._zeta), int(self.periodic),
+                      self.mmax, 0, self.L, self.b_ee, self.b_ep, self.Z,
+                      self.Z if self.Zj is None else self.Zj, kappa,
+                      _ptr(self._zeta), _ptr(self._coeff))
+
+    @property
+    def n_elec(self) -> int:
+        n_up = self.N // 2 if self.n_up is None else self.n_up
+        n_dn = self.N - n_up if self.n_dn is None else self.n_dn
+        return n_up + n_dn
+
+
+def philox(ctr, key):
+    c = (C.c_uint32 * 4)(*ctr)
+    k = (C.c_uint32 * 2)(*key)
+    o = (C.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, o)
+    return list(o)
+
+
+def ewald(q, pos, L, kappa, mmax, background=False) -> float:
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    return lib().orc_ewald(len(q), _ptr(q), _ptr(pos), L, kappa, mmax, int(background))
+
+
+def eval_config(sys: System, R, X, derivs=False):
+    """Return dict(lnpsi, sign, el, ekin, epot, grad[Ne,3], dlnpsi[N,3], del[N,3])."""
+    p = sys.cparams()
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    sc = np.zeros(5)
+    grad = np.zeros((sys.n_elec, 3))
+    dl = np.zeros((sys.N, 3))
+    de = np.zeros((sys.N, 3))
+    rc = lib().orc_eval_config(C.byref(p), _ptr(R), _ptr(X), int(derivs), _ptr(sc), _ptr(grad), _ptr(dl), _ptr(de))
+    if rc != 0:
+        raise ValueError("singular Slater block")
+    out = dict(lnpsi=sc[0], sign=int(sc[1]), el=sc[2], ekin=sc[3], epot=sc[4], grad=grad)
+    if derivs:
+        out.update(dlnpsi=dl, del_=de)
+    return out
+
+
+def eval_configs(sys: System, R, X, derivs=True):
+    """Walker-parallel evaluation: X [nconf, Ne, 3] -> lnpsi, el, dlnpsi, del."""
+    p = sys.cparams()
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    n = X.shape[0]
+    lp = np.zeros(n); el = np.zeros(n)
+    dl = np.zeros((n, sys.N, 3)); de = np.zeros((n, sys.N, 3))
+    rc = lib().orc_eval_configs(C.byref(p), _ptr(R), n, _ptr(X), int(derivs), _ptr(lp), _ptr(el), _ptr(dl), _ptr(de))
+    if rc != 0:
+        raise ValueError("singular Slater block")
+    return lp, el, dl, de
+
+
+def init_walkers(sys: System, R, W, seed):
+    p = sys.cparams()
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    X = np.zeros((W, sys.n_elec, 3))
+    lib().orc_init_walkers(C.byref(p), _ptr(R), W, seed, _ptr(X))
+    return X
+
+
+def vmc(sys: System, R, *, W, n_sweeps, n_warmup, measure_every=1, sigma=0.3, seed=1, md_step=0,
+        X=None, forces=True):
+    """Run W Metropolis chains; returns (X, acc[W, 3+9N], accept_ratio)."""
+    p = sys.cparams()
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    init = X is None
+    Xa = np.zeros((W, sys.n_elec, 3)) if init else np.array(X, dtype=np.float64, copy=True)
+    acc = np.zeros((W, 3 + 9 * sys.N))
+    ca = ChainArgs(W, n_sweeps, n_warmup, measure_every, int(init), int(forces), md_step, 0, sigma, seed)
+    na = C.c_longlong(0); nt = C.c_longlong(0)
+    lib().orc_vmc(C.byref(p), _ptr(R), C.byref(ca), _ptr(Xa), _ptr(acc), C.byref(na), C.byref(nt))
+    return Xa, acc, (na.value / nt.value if nt.value else 0.0)
+
+
+def reduce(acc, N):
+    acc = np.ascontiguousarray(acc, dtype=np.float64)
+    W = acc.shape[0]
+    N3 = 3 * N
+    E = C.c_double(); Ee = C.c_double(); Nc = C.c_double()
+    f = np.zeros(N3); S = np.zeros((N3, N3))
+    lib().orc_reduce(W, N3, _ptr(acc), C.byref(E), C.byref(Ee), _ptr(f), _ptr(S), C.byref(Nc))
+    return dict(E=E.value, E_err=Ee.value, f=f, S=S, Nc=Nc.value)
+
+
+def langevin(R, Rprev, f, S, Sprev, T, delta, alpha, xi, noise_correction=False, box=0.0):
+    R = np.ascontiguousarray(R, dtype=np.float64).ravel()
+    n = R.size
+    arr = [np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (Rprev, f, S, Sprev, xi)]
+    out = np.zeros(n)
+    rc = lib().orc_langevin(n, _ptr(R), _ptr(arr[0]), _ptr(arr[1]), _ptr(arr[2]), _ptr(arr[3]), T, delta,
+                            alpha, _ptr(arr[4]), int(noise_correction), box, _ptr(out))
+    if rc != 0:
+        raise ValueError("S is not positive definite")
+    return out
+
+
+def langevin_noise(seed, md_step, n):
+    xi = np.zeros(n)
+    lib().orc_langevin_noise(seed, md_step, n, _ptr(xi))
+    return xi
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()

@@ -1,0 +1,817 @@
+// qmc_oracle.cpp -- plain, slow FP64 CPU oracle for the VMC energy / force /
+// force-covariance path and the accelerated Langevin step of Sorella & Mazzola,
+// "Accelerated ab-initio Molecular Dynamics" (arXiv:1605.08423).
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, import or
+// execute this file: it is used by tests/, by __graft_entry__.smoke() and by the
+// cpu_baseline leg of bench.py.  It shares no code, header, table or helper with
+// the CUDA library; the only common ground is the seeded synthetic inputs, which
+// are passed in as arguments.
+//
+// Every function below states the passage it follows.  Derivatives with respect
+// to the nuclear positions R are taken by forward-mode dual numbers (type D3),
+// never by hand, so that this file contains no adjoint code.
+//
+// Readings of passages that the paper leaves open are listed at each function
+// and collected in the design doc of the repository.
+//
+// Parity status (each function is pinned by a test under tests/ against a
+// closed form, a textbook constant, a finite difference or brute force):
+//   philox4x32_10 ........ published known-answer vectors
+//   ewald ................ NaCl and simple-cubic Madelung constants, kappa invariance
+//   wavefunction / E_L ... exact hydrogen atom, finite differences in r and R,
+//                          translation / permutation / coefficient invariances, cusps
+//   vmc chain ............ importance-sampled brute-force integral on a tiny system
+//   reduce ............... i.i.d. synthetic samples with known covariance
+//   langevin_step ........ harmonic closed forms (steepest descent, Newton step,
+//                          stationary covariance, autocorrelation)
+//   "parity unpinned": the statistical quality of the random-coefficient
+//   wavefunction itself (nothing in the paper fixes it).
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include <algorithm>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace orc {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 counter-based generator, from its published definition
+// (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+// SC'11): ten rounds of two 32x32->64 multiplies with the Weyl key schedule.
+// ---------------------------------------------------------------------------
+static void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// Counter layout shared by definition with the device library (each side has
+// its own implementation): ctr = {stream, md_step, index, purpose}.
+enum Purpose : uint32_t {
+    P_PROP_X = 0, P_PROP_Y = 1, P_PROP_Z = 2, P_ACCEPT = 3,
+    P_INIT_X = 4, P_INIT_Y = 5, P_INIT_Z = 6, P_LANGEVIN = 7
+};
+
+// 53-bit uniform in the open interval (0,1) from two 32-bit words.
+static double uniform53(uint32_t a, uint32_t b) {
+    uint64_t k = ((uint64_t)(a >> 5) << 26) | (uint64_t)(b >> 6);
+    return ((double)k + 0.5) * (1.0 / 9007199254740992.0);
+}
+
+struct Rng {
+    uint32_t key[2];
+    explicit Rng(uint64_t seed) { key[0] = (uint32_t)seed; key[1] = (uint32_t)(seed >> 32); }
+    void block(uint32_t s, uint32_t m, uint32_t idx, uint32_t purpose, uint32_t out[4]) const {
+        uint32_t ctr[4] = {s, m, idx, purpose};
+        philox4x32_10(ctr, key, out);
+    }
+    double uniform(uint32_t s, uint32_t m, uint32_t idx, uint32_t purpose) const {
+        uint32_t w[4]; block(s, m, idx, purpose, w);
+        return uniform53(w[0], w[1]);
+    }
+    // Box-Muller (cosine branch) on the two uniforms of one block.
+    double normal(uint32_t s, uint32_t m, uint32_t idx, uint32_t purpose) const {
+        uint32_t w[4]; block(s, m, idx, purpose, w);
+        double u1 = uniform53(w[0], w[1]), u2 = uniform53(w[2], w[3]);
+        return std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * M_PI * u2);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Dual number with three tangent components: d/dR_{a,x}, d/dR_{a,y}, d/dR_{a,z}
+// of one nucleus a.  Used only to differentiate with respect to R.
+// ---------------------------------------------------------------------------
+struct D3 {
+    double v; double d[3];
+    D3() : v(0), d{0, 0, 0} {}
+    D3(double x) : v(x), d{0, 0, 0} {}
+};
+static inline double val(double x) { return x; }
+static inline double val(const D3& x) { return x.v; }
+static inline D3 operator+(const D3& a, const D3& b) { D3 r(a.v + b.v); for (int k = 0; k < 3; ++k) r.d[k] = a.d[k] + b.d[k]; return r; }
+static inline D3 operator-(const D3& a, const D3& b) { D3 r(a.v - b.v); for (int k = 0; k < 3; ++k) r.d[k] = a.d[k] - b.d[k]; return r; }
+static inline D3 operator-(const D3& a) { D3 r(-a.v); for (int k = 0; k < 3; ++k) r.d[k] = -a.d[k]; return r; }
+static inline D3 operator*(const D3& a, const D3& b) { D3 r(a.v * b.v); for (int k = 0; k < 3; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k]; return r; }
+static inline D3 operator/(const D3& a, const D3& b) { D3 r(a.v / b.v); for (int k = 0; k < 3; ++k) r.d[k] = (a.d[k] * b.v - a.v * b.d[k]) / (b.v * b.v); return r; }
+static inline D3 operator+(const D3& a, double b) { return a + D3(b); }
+static inline D3 operator+(double a, const D3& b) { return D3(a) + b; }
+static inline D3 operator-(const D3& a, double b) { return a - D3(b); }
+static inline D3 operator-(double a, const D3& b) { return D3(a) - b; }
+static inline D3 operator*(const D3& a, double b) { D3 r(a.v * b); for (int k = 0; k < 3; ++k) r.d[k] = a.d[k] * b; return r; }
+static inline D3 operator*(double a, const D3& b) { return b * a; }
+static inline D3 operator/(const D3& a, double b) { return a * (1.0 / b); }
+static inline D3 operator/(double a, const D3& b) { return D3(a) / b; }
+static inline D3& operator+=(D3& a, const D3& b) { a = a + b; return a; }
+static inline D3& operator-=(D3& a, const D3& b) { a = a - b; return a; }
+static inline D3& operator*=(D3& a, const D3& b) { a = a * b; return a; }
+static inline D3 chain(const D3& x, double f, double fp) { D3 r(f); for (int k = 0; k < 3; ++k) r.d[k] = fp * x.d[k]; return r; }
+static inline D3 exp(const D3& x) { double e = std::exp(x.v); return chain(x, e, e); }
+static inline D3 sin(const D3& x) { return chain(x, std::sin(x.v), std::cos(x.v)); }
+static inline D3 cos(const D3& x) { return chain(x, std::cos(x.v), -std::sin(x.v)); }
+static inline D3 sqrt(const D3& x) { double s = std::sqrt(x.v); return chain(x, s, 0.5 / s); }
+static inline D3 log(const D3& x) { return chain(x, std::log(x.v), 1.0 / x.v); }
+static inline D3 erfc(const D3& x) { return chain(x, std::erfc(x.v), -2.0 / std::sqrt(M_PI) * std::exp(-x.v * x.v)); }
+using std::exp; using std::sin; using std::cos; using std::sqrt; using std::log; using std::erfc;
+
+// ---------------------------------------------------------------------------
+// System description.  Mirrors the C-ABI parameters of the library but is
+// declared independently here.
+// ---------------------------------------------------------------------------
+struct Params {
+    int32_t N;            // nuclei (protons)
+    int32_t n_up, n_dn;   // electrons of each spin
+    int32_t n_orb;        // orbitals (columns of coeff); >= max(n_up, n_dn)
+    int32_t n_gauss;      // s-Gaussians per nucleus
+    int32_t periodic;     // 1: periodic box (sin periodisation + Ewald); 0: open
+    int32_t mmax;         // reciprocal cutoff |m| <= mmax
+    int32_t pad_;
+    double  L;            // box side (bohr)
+    double  b_ee, b_ep;   // Pade Jastrow parameters
+    double  Z;            // nuclear charge (1 for hydrogen)
+    double  Zj;           // e-n Jastrow cusp amplitude (Z for the cusp; 0 switches U_1 off)
+    double  kappa;        // Ewald splitting parameter
+    const double* zeta;   // [n_gauss]
+    const double* coeff;  // [N*n_gauss][n_orb], row b = a*n_gauss + g
+};
+
+// ---------------------------------------------------------------------------
+// Periodised displacement (SI, "periodized with the trivial substitution"):
+// each Cartesian component r_mu -> (L/pi) sin(pi r_mu / L), applied to the raw
+// difference.  Reading: used for both the Jastrow and the determinant orbitals.
+// For each component returns d, its first and second derivatives with respect
+// to the electron coordinate.
+// ---------------------------------------------------------------------------
+template <class S>
+static void periodised(const Params& p, double x, const S& R, S& d, S& dd, S& ddd) {
+    if (p.periodic) {
+        S arg = (x - R) * (M_PI / p.L);
+        d = (p.L / M_PI) * sin(arg);
+        dd = cos(arg);
+        ddd = -(M_PI / p.L) * sin(arg);
+    } else {
+        d = x - R; dd = S(1.0); ddd = S(0.0);
+    }
+}
+
+// Gaussian basis function chi = exp(-zeta |d|^2) with gradient and Laplacian
+// in the electron coordinate (SI basis of s-Gaussians per nucleus).
+template <class S>
+static void gaussian(const Params& p, const double x[3], const S Rc[3], double zeta,
+                     S& chi, S grad[3], S& lap) {
+    S d[3], dd[3], ddd[3];
+    S t(0.0);
+    for (int mu = 0; mu < 3; ++mu) { periodised(p, x[mu], Rc[mu], d[mu], dd[mu], ddd[mu]); t += d[mu] * d[mu]; }
+    chi = exp(-zeta * t);
+    lap = S(0.0);
+    for (int mu = 0; mu < 3; ++mu) {
+        S dt = 2.0 * d[mu] * dd[mu];                    // d t / d x_mu
+        S d2t = 2.0 * (dd[mu] * dd[mu] + d[mu] * ddd[mu]);  // d^2 t / d x_mu^2
+        grad[mu] = -zeta * dt * chi;
+        lap += (zeta * zeta * dt * dt - zeta * d2t) * chi;
+    }
+}
+
+// Pade pair functions (SI, U_2 and the e-n term).  Reading of the sign garble:
+// the electron-electron term is +r/(2(1+b r)) (cusp +1/2 under J = e^U) and the
+// electron-nucleus term is -Z r/(1+b r) (cusp -Z).
+static void u_ee(double b, double r, double& u, double& up, double& upp) {
+    double q = 1.0 + b * r;
+    u = r / (2.0 * q); up = 1.0 / (2.0 * q * q); upp = -b / (q * q * q);
+}
+template <class S>
+static void u_ep(double b, double Z, const S& r, S& u, S& up, S& upp) {
+    S q = 1.0 + b * r;
+    u = -Z * r / q; up = -Z / (q * q); upp = 2.0 * Z * b / (q * q * q);
+}
+
+// Value, gradient and Laplacian (in the electron coordinate x) of a radial
+// pair function u(|d(x - c)|).
+template <class S, class F>
+static void pair_term(const Params& p, const double x[3], const S c[3], F ufun,
+                      S& u, S grad[3], S& lap) {
+    S d[3], dd[3], ddd[3];
+    S t(0.0);
+    for (int mu = 0; mu < 3; ++mu) { periodised(p, x[mu], c[mu], d[mu], dd[mu], ddd[mu]); t += d[mu] * d[mu]; }
+    S r = sqrt(t);
+    S up, upp;
+    ufun(r, u, up, upp);
+    lap = S(0.0);
+    for (int mu = 0; mu < 3; ++mu) {
+        S dt = 2.0 * d[mu] * dd[mu];
+        S d2t = 2.0 * (dd[mu] * dd[mu] + d[mu] * ddd[mu]);
+        S dr = dt / (2.0 * r);
+        S d2r = d2t / (2.0 * r) - dt * dt / (4.0 * r * r * r);
+        grad[mu] = up * dr;
+        lap += upp * dr * dr + up * d2r;
+    }
+}
+
+// LU factorisation with partial pivoting (Golub & Van Loan, Alg. 3.4.1) and
+// the inverse by forward / back substitution.  Returns log|det| and the sign.
+template <class S>
+static bool lu_inverse(int n, std::vector<S> A, std::vector<S>& inv, S& logdet, int& sign) {
+    std::vector<int> perm(n);
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    sign = 1;
+    logdet = S(0.0);
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < n; ++i)
+            if (std::fabs(val(A[i * n + k])) > std::fabs(val(A[piv * n + k]))) piv = i;
+        if (val(A[piv * n + k]) == 0.0) return false;
+        if (piv != k) {
+            for (int j = 0; j < n; ++j) std::swap(A[k * n + j], A[piv * n + j]);
+            std::swap(perm[k], perm[piv]);
+            sign = -sign;
+        }
+        S pivot = A[k * n + k];
+        if (val(pivot) < 0) sign = -sign;
+        logdet += log(val(pivot) < 0 ? -pivot : pivot);
+        for (int i = k + 1; i < n; ++i) {
+            A[i * n + k] = A[i * n + k] / pivot;
+            for (int j = k + 1; j < n; ++j) A[i * n + j] -= A[i * n + k] * A[k * n + j];
+        }
+    }
+    inv.assign((size_t)n * n, S(0.0));
+    for (int col = 0; col < n; ++col) {
+        std::vector<S> y(n);
+        for (int i = 0; i < n; ++i) {          // solve L y = P e_col
+            S s = (perm[i] == col) ? S(1.0) : S(0.0);
+            for (int j = 0; j < i; ++j) s -= A[i * n + j] * y[j];
+            y[i] = s;
+        }
+        for (int i = n - 1; i >= 0; --i) {     // solve U x = y
+            S s = y[i];
+            for (int j = i + 1; j < n; ++j) s -= A[i * n + j] * inv[j * n + col];
+            inv[i * n + col] = s / A[i * n + i];
+        }
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Ewald sum over point charges in the cubic box (reading of the paper's
+// periodic Coulomb Hamiltonian; the truncation is part of the definition):
+//   V = sum_{k<l} q_k q_l sum_{n : |r_kl + nL| < L} erfc(kappa |r_kl+nL|)/|r_kl+nL|
+//     + 1/2 sum_k q_k^2 sum_{0 < |nL| < L} erfc(kappa |n| L)/(|n| L)      (empty)
+//     + (4 pi / L^3) sum_{half space, 0 < |m| <= mmax} exp(-k^2/4kappa^2)/k^2 |rho(k)|^2
+//     - kappa/sqrt(pi) sum_k q_k^2
+//     [- pi Q^2 / (2 L^3 kappa^2)   neutralising background, only if requested]
+// with k = 2 pi m / L and rho(k) = sum_k q_k exp(i k.r_k).
+// ---------------------------------------------------------------------------
+template <class S>
+static S ewald(int nq, const double* q, const S* pos, double L, double kappa, int mmax, bool background) {
+    S V(0.0);
+    for (int k = 0; k < nq; ++k)
+        for (int l = k + 1; l < nq; ++l) {
+            S r[3];
+            for (int mu = 0; mu < 3; ++mu) r[mu] = pos[3 * k + mu] - pos[3 * l + mu];
+            for (int nx = -3; nx <= 3; ++nx)
+                for (int ny = -3; ny <= 3; ++ny)
+                    for (int nz = -3; nz <= 3; ++nz) {
+                        S a = r[0] + nx * L, b = r[1] + ny * L, c = r[2] + nz * L;
+                        S d = sqrt(a * a + b * b + c * c);
+                        if (val(d) < L) V += q[k] * q[l] * erfc(kappa * d) / d;
+                    }
+        }
+    for (int k = 0; k < nq; ++k)
+        for (int nx = -1; nx <= 1; ++nx)
+            for (int ny = -1; ny <= 1; ++ny)
+                for (int nz = -1; nz <= 1; ++nz) {
+                    int n2 = nx * nx + ny * ny + nz * nz;
+                    double d = std::sqrt((double)n2) * L;
+                    if (n2 > 0 && d < L) V += 0.5 * q[k] * q[k] * std::erfc(kappa * d) / d;
+                }
+    const double vol = L * L * L;
+    for (int mx = 0; mx <= mmax; ++mx)
+        for (int my = -mmax; my <= mmax; ++my)
+            for (int mz = -mmax; mz <= mmax; ++mz) {
+                bool half = (mx > 0) || (mx == 0 && my > 0) || (mx == 0 && my == 0 && mz > 0);
+                int m2 = mx * mx + my * my + mz * mz;
+                if (!half || m2 > mmax * mmax) continue;
+                double kx = 2 * M_PI * mx / L, ky = 2 * M_PI * my / L, kz = 2 * M_PI * mz / L;
+                double k2 = kx * kx + ky * ky + kz * kz;
+                S re(0.0), im(0.0);
+                for (int j = 0; j < nq; ++j) {
+                    S ph = kx * pos[3 * j] + ky * pos[3 * j + 1] + kz * pos[3 * j + 2];
+                    re += q[j] * cos(ph);
+                    im += q[j] * sin(ph);
+                }
+                V += (4 * M_PI / vol) * std::exp(-k2 / (4 * kappa * kappa)) / k2 * (re * re + im * im);
+            }
+    double q2 = 0, Q = 0;
+    for (int k = 0; k < nq; ++k) { q2 += q[k] * q[k]; Q += q[k]; }
+    V -= kappa / std::sqrt(M_PI) * q2;
+    if (background) V -= M_PI * Q * Q / (2 * vol * kappa * kappa);
+    return V;
+}
+
+// Bare Coulomb energy of point charges (open boundary; hydrogen atom pin).
+template <class S>
+static S coulomb_open(int nq, const double* q, const S* pos) {
+    S V(0.0);
+    for (int k = 0; k < nq; ++k)
+        for (int l = k + 1; l < nq; ++l) {
+            S a = pos[3 * k] - pos[3 * l], b = pos[3 * k + 1] - pos[3 * l + 1], c = pos[3 * k + 2] - pos[3 * l + 2];
+            V += q[k] * q[l] / sqrt(a * a + b * b + c * c);
+        }
+    return V;
+}
+
+// ---------------------------------------------------------------------------
+// Jastrow-Slater wavefunction psi = det(Phi_up) det(Phi_dn) exp(U) (Eq. for
+// V(R), SI Jastrow J = e^U with U = U_1 + U_2 restricted to the Pade e-n and
+// e-e terms) and its local energy
+//   E_L = -1/2 sum_i [ lap_i ln psi + |grad_i ln psi|^2 ] + V.
+// Electrons 0..n_up-1 carry spin up.  Orbital j of either spin is
+// phi_j(r) = sum_b C[b][j] chi_b(r) (same coefficients for both spins).
+// ---------------------------------------------------------------------------
+template <class S>
+struct WfOut {
+    S lnpsi;          // ln |psi|
+    int sign;
+    S ekin, epot, el;
+    std::vector<double> grad;  // grad_i ln psi, [Ne][3] (values only)
+    bool ok;
+};
+
+template <class S>
+static void slater_block(const Params& p, const S* R, const double* X, int i0, int ne,
+                         S& logdet, int& sign, std::vector<S>& g, std::vector<S>& l, bool& ok) {
+    const int G = p.n_gauss, nb = p.N * G, no = p.n_orb;
+    std::vector<S> A((size_t)ne * ne), D[3], Lp((size_t)ne * ne);
+    for (int mu = 0; mu < 3; ++mu) D[mu].assign((size_t)ne * ne, S(0.0));
+    for (int i = 0; i < ne; ++i) {
+        const double* x = X + 3 * (i0 + i);
+        std::vector<S> chi(nb), dchi[3], lchi(nb);
+        for (int mu = 0; mu < 3; ++mu) dchi[mu].resize(nb);
+        for (int a = 0; a < p.N; ++a)
+            for (int gg = 0; gg < G; ++gg) {
+                S c, gr[3], lp;
+                gaussian(p, x, R + 3 * a, p.zeta[gg], c, gr, lp);
+                int b = a * G + gg;
+                chi[b] = c; lchi[b] = lp;
+                for (int mu = 0; mu < 3; ++mu) dchi[mu][b] = gr[mu];
+            }
+        for (int j = 0; j < ne; ++j) {
+            S v(0.0), lv(0.0), dv[3] = {S(0.0), S(0.0), S(0.0)};
+            for (int b = 0; b < nb; ++b) {
+                double cbj = p.coeff[(size_t)b * no + j];
+                v += cbj * chi[b]; lv += cbj * lchi[b];
+                for (int mu = 0; mu < 3; ++mu) dv[mu] += cbj * dchi[mu][b];
+            }
+            A[i * ne + j] = v; Lp[i * ne + j] = lv;
+            for (int mu = 0; mu < 3; ++mu) D[mu][i * ne + j] = dv[mu];
+        }
+    }
+    std::vector<S> inv;
+    ok = lu_inverse(ne, A, inv, logdet, sign);
+    g.assign((size_t)ne * 3, S(0.0)); l.assign(ne, S(0.0));
+    if (!ok) return;
+    // grad_i ln det = sum_j dphi_j(r_i) G_ji ;  lap_i det / det = sum_j lap phi_j(r_i) G_ji
+    for (int i = 0; i < ne; ++i)
+        for (int j = 0; j < ne; ++j) {
+            for (int mu = 0; mu < 3; ++mu) g[i * 3 + mu] += D[mu][i * ne + j] * inv[j * ne + i];
+            l[i] += Lp[i * ne + j] * inv[j * ne + i];
+        }
+}
+
+template <class S>
+static WfOut<S> wavefunction(const Params& p, const S* R, const double* X) {
+    WfOut<S> out;
+    const int Ne = p.n_up + p.n_dn;
+    out.ok = true;
+    out.sign = 1;
+    out.lnpsi = S(0.0);
+    std::vector<S> g((size_t)Ne * 3, S(0.0)), l(Ne, S(0.0));
+    for (int s = 0; s < 2; ++s) {
+        int i0 = s ? p.n_up : 0, ne = s ? p.n_dn : p.n_up;
+        if (ne == 0) continue;
+        S ld; int sg; bool ok;
+        std::vector<S> gs, ls;
+        slater_block(p, R, X, i0, ne, ld, sg, gs, ls, ok);
+        if (!ok) { out.ok = false; return out; }
+        out.lnpsi += ld; out.sign *= sg;
+        for (int i = 0; i < ne; ++i) {
+            for (int mu = 0; mu < 3; ++mu) g[(i0 + i) * 3 + mu] = gs[i * 3 + mu];
+            l[i0 + i] = ls[i];
+        }
+    }
+    // Jastrow U, grad_i U, lap_i U
+    std::vector<S> gU((size_t)Ne * 3, S(0.0)), lU(Ne, S(0.0));
+    S U(0.0);
+    auto fee = [&](const S& r, S& u, S& up, S& upp) {
+        double uu, a, b; u_ee(p.b_ee, val(r), uu, a, b); u = S(uu); up = S(a); upp = S(b);
+    };
+    auto fep = [&](const S& r, S& u, S& up, S& upp) { u_ep(p.b_ep, p.Zj, r, u, up, upp); };
+    for (int i = 0; i < Ne; ++i) {
+        for (int j = 0; j < Ne; ++j) {
+            if (j == i) continue;
+            S cj[3] = {S(X[3 * j]), S(X[3 * j + 1]), S(X[3 * j + 2])};
+            S u, gr[3], lp;
+            pair_term(p, X + 3 * i, cj, fee, u, gr, lp);
+            if (j > i) U += u;
+            for (int mu = 0; mu < 3; ++mu) gU[i * 3 + mu] += gr[mu];
+            lU[i] += lp;
+        }
+        for (int a = 0; a < p.N; ++a) {
+            S u, gr[3], lp;
+            pair_term(p, X + 3 * i, R + 3 * a, fep, u, gr, lp);
+            U += u;
+            for (int mu = 0; mu < 3; ++mu) gU[i * 3 + mu] += gr[mu];
+            lU[i] += lp;
+        }
+    }
+    out.lnpsi += U;
+    // kinetic energy: lap_i ln psi = (l_i - |g_i|^2) + lap_i U ; grad_i ln psi = g_i + grad_i U
+    S kin(0.0);
+    out.grad.assign((size_t)Ne * 3, 0.0);
+    for (int i = 0; i < Ne; ++i) {
+        S g2(0.0), t2(0.0);
+        for (int mu = 0; mu < 3; ++mu) {
+            S t = g[i * 3 + mu] + gU[i * 3 + mu];
+            g2 += g[i * 3 + mu] * g[i * 3 + mu];
+            t2 += t * t;
+            out.grad[i * 3 + mu] = val(t);
+        }
+        S lap_lnpsi = l[i] - g2 + lU[i];
+        kin += lap_lnpsi + t2;
+    }
+    out.ekin = -0.5 * kin;
+    // potential energy of all 2N charges
+    std::vector<double> q;
+    std::vector<S> pos;
+    for (int i = 0; i < Ne; ++i) { q.push_back(-1.0); for (int mu = 0; mu < 3; ++mu) pos.push_back(S(X[3 * i + mu])); }
+    for (int a = 0; a < p.N; ++a) { q.push_back(p.Z); for (int mu = 0; mu < 3; ++mu) pos.push_back(R[3 * a + mu]); }
+    if (p.periodic) out.epot = ewald((int)q.size(), q.data(), pos.data(), p.L, p.kappa, p.mmax, false);
+    else out.epot = coulomb_open((int)q.size(), q.data(), pos.data());
+    out.el = out.ekin + out.epot;
+    return out;
+}
+
+// Value-only evaluation plus all R-derivatives by one D3 pass per nucleus.
+struct ConfigResult {
+    double lnpsi, el, ekin, epot; int sign; bool ok;
+    std::vector<double> grad, dlnpsi, del;
+};
+static ConfigResult eval_config(const Params& p, const double* R, const double* X, bool derivs) {
+    ConfigResult res;
+    WfOut<double> w = wavefunction<double>(p, R, X);
+    res.ok = w.ok; res.lnpsi = w.lnpsi; res.el = w.el; res.ekin = w.ekin; res.epot = w.epot;
+    res.sign = w.sign; res.grad = w.grad;
+    if (!derivs || !w.ok) return res;
+    res.dlnpsi.assign((size_t)3 * p.N, 0.0);
+    res.del.assign((size_t)3 * p.N, 0.0);
+    std::vector<D3> Rd((size_t)3 * p.N);
+    for (int a = 0; a < p.N; ++a) {
+        for (int k = 0; k < 3 * p.N; ++k) Rd[k] = D3(R[k]);
+        for (int mu = 0; mu < 3; ++mu) Rd[3 * a + mu].d[mu] = 1.0;
+        WfOut<D3> wd = wavefunction<D3>(p, Rd.data(), X);
+        for (int mu = 0; mu < 3; ++mu) {
+            res.dlnpsi[3 * a + mu] = wd.lnpsi.d[mu];
+            res.del[3 * a + mu] = wd.el.d[mu];
+        }
+    }
+    return res;
+}
+
+static double wrap(double x, double L) { return x - L * std::floor(x / L); }
+
+// ---------------------------------------------------------------------------
+// Metropolis VMC chain of one walker (standard single-electron Metropolis;
+// the paper defers the sampler to its references).  Readings:
+//   * walker start: up electron i at nucleus i, down electron i at nucleus
+//     n_up + i (modulo N), plus 0.5 bohr Gaussian noise;
+//   * sweep = electrons 0..Ne-1 in order; proposal r' = r + sigma xi;
+//   * accept when u < |psi'/psi|^2 (strict);
+//   * after sweep s >= n_warmup, a sample is taken when
+//     (s - n_warmup + 1) % measure_every == 0.
+// Per-walker accumulators (layout [cnt, sE, sE2, sO(3N), sEO(3N), sdE(3N)]).
+// The ratio is det(A')/det(A) from a fresh LU of the moved block; the Jastrow
+// ratio uses the pair terms containing electron i (all others cancel).
+// ---------------------------------------------------------------------------
+static void slater_row(const Params& p, const double* R, const double* x, int ne, double* row) {
+    const int G = p.n_gauss, no = p.n_orb;
+    for (int j = 0; j < ne; ++j) row[j] = 0;
+    for (int a = 0; a < p.N; ++a)
+        for (int gg = 0; gg < G; ++gg) {
+            double c, gr[3], lp;
+            gaussian<double>(p, x, R + 3 * a, p.zeta[gg], c, gr, lp);
+            int b = a * G + gg;
+            for (int j = 0; j < ne; ++j) row[j] += p.coeff[(size_t)b * no + j] * c;
+        }
+}
+
+static double pair_u(const Params& p, const double* x, const double* c, bool ee) {
+    double t = 0;
+    for (int mu = 0; mu < 3; ++mu) {
+        double d, dd, ddd;
+        periodised<double>(p, x[mu], c[mu], d, dd, ddd);
+        t += d * d;
+    }
+    double r = std::sqrt(t), u, up, upp;
+    if (ee) u_ee(p.b_ee, r, u, up, upp);
+    else u_ep<double>(p.b_ep, p.Zj, r, u, up, upp);
+    return u;
+}
+
+static double jastrow_delta(const Params& p, const double* R, const double* X, int i, const double* xn) {
+    const int Ne = p.n_up + p.n_dn;
+    double du = 0;
+    for (int j = 0; j < Ne; ++j) {
+        if (j == i) continue;
+        du += pair_u(p, xn, X + 3 * j, true) - pair_u(p, X + 3 * i, X + 3 * j, true);
+    }
+    for (int a = 0; a < p.N; ++a) du += pair_u(p, xn, R + 3 * a, false) - pair_u(p, X + 3 * i, R + 3 * a, false);
+    return du;
+}
+
+static double logdet_of(int n, const std::vector<double>& A, int& sign, bool& ok) {
+    std::vector<double> inv; double ld;
+    ok = lu_inverse<double>(n, A, inv, ld, sign);
+    return ld;
+}
+
+struct ChainArgs {
+    int32_t W, n_sweeps, n_warmup, measure_every;
+    int32_t init_walkers;   // 1: place walkers from Philox; 0: X holds them already
+    int32_t forces;         // 1: accumulate R-derivatives (D3 passes)
+    uint32_t md_step;
+    int32_t pad_;
+    double sigma;
+    uint64_t seed;
+};
+
+static void init_walker(const Params& p, const Rng& rng, uint32_t w, const double* R, double* X) {
+    const int Ne = p.n_up + p.n_dn;
+    for (int i = 0; i < Ne; ++i) {
+        int site = (i < p.n_up ? i : p.n_up + (i - p.n_up)) % p.N;
+        for (int mu = 0; mu < 3; ++mu) {
+            double z = rng.normal(w, 0u, (uint32_t)i, P_INIT_X + mu);
+            double x = R[3 * site + mu] + 0.5 * z;
+            X[3 * i + mu] = p.periodic ? wrap(x, p.L) : x;
+        }
+    }
+}
+
+static void run_walker(const Params& p, const ChainArgs& c, const Rng& rng, uint32_t w, const double* R,
+                       double* X, double* acc, long long* n_acc, long long* n_try) {
+    const int Ne = p.n_up + p.n_dn, N3 = 3 * p.N;
+    if (c.init_walkers) init_walker(p, rng, w, R, X);
+    // Slater matrices of both spin blocks, rows = electrons
+    std::vector<double> A[2];
+    double ld[2] = {0, 0}; int sg[2] = {1, 1};
+    for (int s = 0; s < 2; ++s) {
+        int i0 = s ? p.n_up : 0, ne = s ? p.n_dn : p.n_up;
+        A[s].assign((size_t)ne * ne, 0.0);
+        for (int i = 0; i < ne; ++i) slater_row(p, R, X + 3 * (i0 + i), ne, &A[s][(size_t)i * ne]);
+        bool ok = true;
+        if (ne) ld[s] = logdet_of(ne, A[s], sg[s], ok);
+    }
+    const int total = c.n_warmup + c.n_sweeps;
+    for (int sw = 0; sw < total; ++sw) {
+        for (int i = 0; i < Ne; ++i) {
+            const int s = i < p.n_up ? 0 : 1;
+            const int i0 = s ? p.n_up : 0, ne = s ? p.n_dn : p.n_up, il = i - i0;
+            const uint32_t idx = (uint32_t)(sw * Ne + i);
+            double xn[3];
+            for (int mu = 0; mu < 3; ++mu) xn[mu] = X[3 * i + mu] + c.sigma * rng.normal(w, c.md_step, idx, P_PROP_X + mu);
+            std::vector<double> An = A[s];
+            slater_row(p, R, xn, ne, &An[(size_t)il * ne]);
+            int sgn; bool ok;
+            double ldn = logdet_of(ne, An, sgn, ok);
+            double du = jastrow_delta(p, R, X, i, xn);
+            double prob = ok ? std::exp(2.0 * (ldn - ld[s]) + 2.0 * du) : 0.0;
+            double u = rng.uniform(w, c.md_step, idx, P_ACCEPT);
+            ++*n_try;
+            if (u < prob) {
+                ++*n_acc;
+                A[s] = An; ld[s] = ldn; sg[s] = sgn;
+                for (int mu = 0; mu < 3; ++mu) X[3 * i + mu] = p.periodic ? wrap(xn[mu], p.L) : xn[mu];
+            }
+        }
+        if (sw >= c.n_warmup && ((sw - c.n_warmup + 1) % c.measure_every) == 0) {
+            ConfigResult r = eval_config(p, R, X, c.forces != 0);
+            acc[0] += 1; acc[1] += r.el; acc[2] += r.el * r.el;
+            if (c.forces)
+                for (int k = 0; k < N3; ++k) {
+                    acc[3 + k] += r.dlnpsi[k];
+                    acc[3 + N3 + k] += r.el * r.dlnpsi[k];
+                    acc[3 + 2 * N3 + k] += r.del[k];
+                }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Statistics (covariance matrix definition of the paper):
+//   E = mean E_L;  f = -<dE_L/dR> - 2(<E_L dlnpsi/dR> - E <dlnpsi/dR>)
+//   per-walker block forces f_w (same formula with walker means and the global E)
+//   S = sum_w (f_w - f)(f_w - f)^T / (W (W-1))   (covariance of the mean)
+//   E_err^2 = sum_w (E_w - E)^2 / (W (W-1)),  N_c = number of samples.
+// ---------------------------------------------------------------------------
+static void reduce(int W, int N3, const double* acc, double* E, double* Eerr, double* f, double* S, double* Nc) {
+    const int stride = 3 + 3 * N3;
+    double cnt = 0, sE = 0;
+    std::vector<double> sO(N3, 0), sEO(N3, 0), sdE(N3, 0);
+    for (int w = 0; w < W; ++w) {
+        const double* a = acc + (size_t)w * stride;
+        cnt += a[0]; sE += a[1];
+        for (int k = 0; k < N3; ++k) { sO[k] += a[3 + k]; sEO[k] += a[3 + N3 + k]; sdE[k] += a[3 + 2 * N3 + k]; }
+    }
+    *Nc = cnt;
+    double Em = sE / cnt;
+    *E = Em;
+    for (int k = 0; k < N3; ++k) f[k] = -sdE[k] / cnt - 2.0 * (sEO[k] / cnt - Em * sO[k] / cnt);
+    std::vector<double> fw((size_t)W * N3);
+    double ve = 0;
+    for (int w = 0; w < W; ++w) {
+        const double* a = acc + (size_t)w * stride;
+        double c = a[0];
+        double ew = a[1] / c;
+        ve += (ew - Em) * (ew - Em);
+        for (int k = 0; k < N3; ++k)
+            fw[(size_t)w * N3 + k] = -a[3 + 2 * N3 + k] / c - 2.0 * (a[3 + N3 + k] / c - Em * a[3 + k] / c);
+    }
+    *Eerr = W > 1 ? std::sqrt(ve / ((double)W * (W - 1))) : 0.0;
+    for (int i = 0; i < N3; ++i)
+        for (int j = 0; j < N3; ++j) {
+            double s = 0;
+            for (int w = 0; w < W; ++w) s += (fw[(size_t)w * N3 + i] - f[i]) * (fw[(size_t)w * N3 + j] - f[j]);
+            S[(size_t)i * N3 + j] = W > 1 ? s / ((double)W * (W - 1)) : 0.0;
+        }
+}
+
+// ---------------------------------------------------------------------------
+// Adopted integrator (SI, "Better integration scheme, the adopted one"):
+//   R' = R + Dt S^{-1} [ f - (S_prev - S)(R_prev - R) / (2 Db) ] + sqrt(2 T Db) z,
+//   <z z^T> = S^{-1},  Dt = (1-e^{-a D})/a,  Db = (1-e^{-2 a D})/(2a)  (Dt = Db = D at a = 0).
+// z = L^{-T} xi with S = L L^T (Cholesky) and xi ~ N(0, I).  Optional noise
+// correction (SI "Noise correction"): T -> T - D/2.  box > 0 wraps R' into [0, box).
+// ---------------------------------------------------------------------------
+static int langevin(int n, const double* R, const double* Rprev, const double* f, const double* S,
+                    const double* Sprev, double T, double delta, double alpha, const double* xi,
+                    int noise_correction, double box, double* Rout) {
+    double Dt = delta, Db = delta;
+    if (alpha > 0) {
+        Dt = (1.0 - std::exp(-alpha * delta)) / alpha;
+        Db = (1.0 - std::exp(-2.0 * alpha * delta)) / (2.0 * alpha);
+    }
+    if (noise_correction) T = T - 0.5 * delta;
+    std::vector<double> Lc((size_t)n * n, 0.0);
+    for (int j = 0; j < n; ++j) {                       // Cholesky, S = L L^T
+        double s = S[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) s -= Lc[(size_t)j * n + k] * Lc[(size_t)j * n + k];
+        if (!(s > 0)) return -1;
+        Lc[(size_t)j * n + j] = std::sqrt(s);
+        for (int i = j + 1; i < n; ++i) {
+            double t = S[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) t -= Lc[(size_t)i * n + k] * Lc[(size_t)j * n + k];
+            Lc[(size_t)i * n + j] = t / Lc[(size_t)j * n + j];
+        }
+    }
+    std::vector<double> g(n), y(n), x(n), z(n);
+    for (int i = 0; i < n; ++i) {
+        double s = 0;
+        for (int j = 0; j < n; ++j) s += (Sprev[(size_t)i * n + j] - S[(size_t)i * n + j]) * (Rprev[j] - R[j]);
+        g[i] = f[i] - s / (2.0 * Db);
+    }
+    for (int i = 0; i < n; ++i) {                       // L y = g
+        double s = g[i];
+        for (int k = 0; k < i; ++k) s -= Lc[(size_t)i * n + k] * y[k];
+        y[i] = s / Lc[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {                  // L^T x = y
+        double s = y[i];
+        for (int k = i + 1; k < n; ++k) s -= Lc[(size_t)k * n + i] * x[k];
+        x[i] = s / Lc[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {                  // L^T z = xi
+        double s = xi[i];
+        for (int k = i + 1; k < n; ++k) s -= Lc[(size_t)k * n + i] * z[k];
+        z[i] = s / Lc[(size_t)i * n + i];
+    }
+    double amp = (T > 0) ? std::sqrt(2.0 * T * Db) : 0.0;
+    for (int i = 0; i < n; ++i) {
+        double r = R[i] + Dt * x[i] + amp * z[i];
+        Rout[i] = box > 0 ? wrap(r, box) : r;
+    }
+    return 0;
+}
+
+}  // namespace orc
+
+// ===========================================================================
+// extern "C" surface used by the Python test harness (oracle/oracle.py)
+// ===========================================================================
+extern "C" {
+
+void orc_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) { orc::philox4x32_10(ctr, key, out); }
+
+double orc_uniform(uint64_t seed, uint32_t s, uint32_t m, uint32_t idx, uint32_t purpose) {
+    return orc::Rng(seed).uniform(s, m, idx, purpose);
+}
+double orc_normal(uint64_t seed, uint32_t s, uint32_t m, uint32_t idx, uint32_t purpose) {
+    return orc::Rng(seed).normal(s, m, idx, purpose);
+}
+
+double orc_ewald(int nq, const double* q, const double* pos, double L, double kappa, int mmax, int background) {
+    return orc::ewald<double>(nq, q, pos, L, kappa, mmax, background != 0);
+}
+
+// One configuration X ([Ne][3]) at nuclei R ([N][3]).  out_scalars = {lnpsi,
+// sign, E_L, E_kin, E_pot}; grad = grad_i ln psi [Ne][3]; dlnpsi, del = d/dR
+// [N][3] (only when derivs != 0).  Returns 0, or -1 for a singular Slater block.
+int orc_eval_config(const orc::Params* p, const double* R, const double* X, int derivs,
+                    double* out_scalars, double* grad, double* dlnpsi, double* del) {
+    orc::ConfigResult r = orc::eval_config(*p, R, X, derivs != 0);
+    if (!r.ok) return -1;
+    out_scalars[0] = r.lnpsi; out_scalars[1] = r.sign; out_scalars[2] = r.el;
+    out_scalars[3] = r.ekin; out_scalars[4] = r.epot;
+    const int Ne = p->n_up + p->n_dn;
+    if (grad) std::memcpy(grad, r.grad.data(), sizeof(double) * 3 * Ne);
+    if (derivs) {
+        std::memcpy(dlnpsi, r.dlnpsi.data(), sizeof(double) * 3 * p->N);
+        std::memcpy(del, r.del.data(), sizeof(double) * 3 * p->N);
+    }
+    return 0;
+}
+
+// Many configurations at once (walker-parallel): X [nconf][Ne][3].
+int orc_eval_configs(const orc::Params* p, const double* R, int nconf, const double* X, int derivs,
+                     double* lnpsi, double* el, double* dlnpsi, double* del) {
+    const int Ne = p->n_up + p->n_dn, N3 = 3 * p->N;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic) reduction(+ : bad)
+    for (int c = 0; c < nconf; ++c) {
+        orc::ConfigResult r = orc::eval_config(*p, R, X + (size_t)c * 3 * Ne, derivs != 0);
+        if (!r.ok) { ++bad; continue; }
+        lnpsi[c] = r.lnpsi; el[c] = r.el;
+        if (derivs)
+            for (int k = 0; k < N3; ++k) { dlnpsi[(size_t)c * N3 + k] = r.dlnpsi[k]; del[(size_t)c * N3 + k] = r.del[k]; }
+    }
+    return bad ? -1 : 0;
+}
+
+// Walker start positions, X [W][Ne][3].
+void orc_init_walkers(const orc::Params* p, const double* R, int W, uint64_t seed, double* X) {
+    const int Ne = p->n_up + p->n_dn;
+    orc::Rng rng(seed);
+    for (int w = 0; w < W; ++w) orc::init_walker(*p, rng, (uint32_t)w, R, X + (size_t)w * 3 * Ne);
+}
+
+// VMC chains of W walkers; X [W][Ne][3] in/out; acc [W][3 + 9N] accumulated
+// (caller zeroes it); n_accept / n_try summed over walkers.
+void orc_vmc(const orc::Params* p, const double* R, const orc::ChainArgs* c, double* X, double* acc,
+             long long* n_accept, long long* n_try) {
+    const int Ne = p->n_up + p->n_dn, stride = 3 + 9 * p->N;
+    orc::Rng rng(c->seed);
+    long long na = 0, nt = 0;
+#pragma omp parallel for schedule(dynamic) reduction(+ : na, nt)
+    for (int w = 0; w < c->W; ++w) {
+        long long a = 0, t = 0;
+        orc::run_walker(*p, *c, rng, (uint32_t)w, R, X + (size_t)w * 3 * Ne, acc + (size_t)w * stride, &a, &t);
+        na += a; nt += t;
+    }
+    *n_accept = na; *n_try = nt;
+}
+
+void orc_reduce(int W, int N3, const double* acc, double* E, double* Eerr, double* f, double* S, double* Nc) {
+    orc::reduce(W, N3, acc, E, Eerr, f, S, Nc);
+}
+
+int orc_langevin(int n, const double* R, const double* Rprev, const double* f, const double* S,
+                 const double* Sprev, double T, double delta, double alpha, const double* xi,
+                 int noise_correction, double box, double* Rout) {
+    return orc::langevin(n, R, Rprev, f, S, Sprev, T, delta, alpha, xi, noise_correction, box, Rout);
+}
+
+// Langevin noise xi_c for component c of MD step m (Philox, purpose P_LANGEVIN).
+void orc_langevin_noise(uint64_t seed, uint32_t md_step, int n, double* xi) {
+    orc::Rng rng(seed);
+    for (int c = 0; c < n; ++c) xi[c] = rng.normal((uint32_t)c, md_step, 0u, orc::P_LANGEVIN);
+}
+
+int orc_num_threads() {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+}  // extern "C"
