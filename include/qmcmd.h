@@ -1,0 +1,174 @@
+/*
+ * qmcmd.h -- C ABI of the GB300 library for the data-parallel hot path of
+ * Sorella & Mazzola, "Accelerated ab-initio Molecular Dynamics" (arXiv:1605.08423):
+ * Variational Monte Carlo (VMC) evaluation of the Born-Oppenheimer energy, the
+ * nuclear forces and their covariance for N protons in a periodic cubic box,
+ * and the accelerated first-order Langevin step that consumes them.
+ *
+ * Conventions shared by every entry point
+ *   - Units: bohr, hartree.  Temperatures are given in kelvin and converted with
+ *     k_B = 3.166811563e-6 Ha/K.
+ *   - Arrays are dense, row-major, FP64 unless stated.  R is [N][3]; electron
+ *     configurations are [W][N][3] with electrons 0..N/2-1 spin up and
+ *     N/2..N-1 spin down.
+ *   - Ownership: the caller owns every pointer it passes.  The library copies
+ *     what it needs during the call and keeps no caller pointer afterwards.
+ *     All device state (walkers, inverses, tables) is owned by the handle and
+ *     released by qmc_destroy.
+ *   - "_device" variants take device pointers and are asynchronous on the
+ *     handle's stream (qmc_set_stream); errors they raise on the GPU are
+ *     reported by the next qmc_sync.  All other calls take host pointers and
+ *     return only after the result is on the host.
+ *   - Return value: QMC_OK (0) or a negative QMC_ERR_* code; qmc_strerror
+ *     gives its text.  A failed call leaves caller arrays unspecified.
+ *   - Threading: one handle per host thread at a time.
+ */
+#ifndef QMCMD_H
+#define QMCMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    QMC_OK = 0,
+    QMC_ERR_INVALID = -1,   /* bad argument (sizes, parity of N, null pointer) */
+    QMC_ERR_OOM = -2,       /* device allocation failed / footprint above the cap */
+    QMC_ERR_CUDA = -3,      /* CUDA runtime error (no device, launch failure) */
+    QMC_ERR_NOT_PD = -4,    /* S is not positive definite (Cholesky failed) */
+    QMC_ERR_NONFINITE = -5, /* a local energy, ratio or force was not finite */
+    QMC_ERR_TIMEOUT = -6,   /* a bounded device wait gave up */
+    QMC_ERR_SINGULAR = -7   /* a Slater matrix was exactly singular */
+};
+
+enum { QMC_FP64 = 0, QMC_MIXED = 1 };          /* precision forms */
+enum { QMC_S_IDENTITY = 0, QMC_S_COV = 1 };    /* acceleration matrix of langevin_step */
+
+/*
+ * System and sampler parameters (the wavefunction of the paper's Eq. for
+ * V(R) restricted to a Jastrow-Slater form: psi = det(Phi_up) det(Phi_dn) e^U,
+ * orbitals phi_j(r) = sum_b coeff[b][j] exp(-zeta_g |d(r - R_a)|^2), b = a*n_gauss + g,
+ * d the sin-periodised displacement of the SI, U = Pade e-e + e-n terms).
+ */
+typedef struct {
+    int32_t n_protons;        /* N, even, 2..256; N electrons, N/2 per spin             */
+    int32_t n_gauss;          /* Gaussians per proton, 1..8                              */
+    int32_t n_walkers;        /* W >= 2                                                  */
+    int32_t n_sweeps;         /* measured sweeps per qmc_energy_forces call              */
+    int32_t n_warmup;         /* sweeps before the first measurement of the first call   */
+    int32_t n_warmup_cont;    /* same, for later calls (walkers carried over)            */
+    int32_t measure_every;    /* sweeps between samples, >= 1                           */
+    int32_t recompute_every;  /* sweeps between full FP64 inverse recomputes, >= 1       */
+    int32_t precision;        /* QMC_FP64 or QMC_MIXED                                   */
+    int32_t ewald_mmax;       /* reciprocal cutoff |m| <= mmax (k = 2 pi m / L)          */
+    double L;                 /* box side, bohr                                          */
+    double b_ee, b_ep;        /* Pade Jastrow parameters                                 */
+    double ewald_kappa;       /* Ewald splitting parameter, bohr^-1 (e.g. 5/L)           */
+    double sigma;             /* Gaussian proposal width, bohr                           */
+    uint64_t seed;            /* Philox4x32-10 key                                       */
+    const double* zeta;       /* [n_gauss] exponents, bohr^-2 (copied)                   */
+    const double* coeff;      /* [N*n_gauss][N/2] orbital coefficients (copied)          */
+} qmc_params;
+
+/* Result of one energy/force evaluation.  f and cov are caller-allocated host
+ * arrays of 3N and 3N*3N doubles. */
+typedef struct {
+    double E;          /* VMC energy, hartree                                   */
+    double E_err;      /* its error bar (walker blocks)                         */
+    double* f;         /* [3N] mean force -dE/dR, Ha/bohr                       */
+    double* cov;       /* [3N][3N] covariance of the mean force (S)             */
+    double n_samples;  /* N_c = walkers x measured sweeps / measure_every       */
+    double accept;     /* Metropolis acceptance ratio of the call               */
+} qmc_result;
+
+typedef struct qmc_system qmc_system;
+
+/* Create a handle: validates p, allocates all device state on the current
+ * CUDA device, uploads R ([N][3], host) and places the walkers (each electron
+ * next to a proton plus 0.5 bohr Philox noise).  Errors: INVALID, OOM, CUDA. */
+int qmc_init(const qmc_params* p, const double* R, qmc_system** out);
+
+/* Release every device allocation of h (h may be NULL). */
+void qmc_destroy(qmc_system* h);
+
+/* Bytes of device memory a handle with parameters p holds (admission control). */
+size_t qmc_footprint_bytes(const qmc_params* p);
+
+/* Launch subsequent work of h on `stream` (a cudaStream_t; NULL = handle's own). */
+int qmc_set_stream(qmc_system* h, void* stream);
+
+/* Wait for h's stream and return the device-side error status (QMC_OK or a code). */
+int qmc_sync(qmc_system* h);
+
+/*
+ * The hot path.  For nuclei R (host [N][3]): full inverse recompute, n_warmup
+ * (first call) or n_warmup_cont sweeps, then n_sweeps Metropolis sweeps with a
+ * local-energy and force sample every measure_every sweeps, then the
+ * reductions of the paper's covariance-matrix definition:
+ *   E = <E_L>,  f = -<dE_L/dR> - 2(<E_L dlnpsi/dR> - E <dlnpsi/dR>)   (Hellmann-Feynman + Pulay)
+ *   S = Cov(f) of the mean, from walker blocks.
+ * Walkers carry over to the next call.  Errors: INVALID, CUDA, NONFINITE, SINGULAR.
+ */
+int qmc_energy_forces(qmc_system* h, const double* R, qmc_result* out);
+
+/* Same, device pointers, asynchronous: R_dev [N][3]; out_dev receives
+ * [E, E_err, n_samples, accept, f(3N), S(3N*3N)] as FP64. */
+int qmc_energy_forces_device(qmc_system* h, const double* R_dev, double* out_dev);
+
+/*
+ * Accelerated first-order Langevin step (SI, adopted integrator):
+ *   R' = R + Dt S^{-1} [ f - (S_prev - S)(R_prev - R) / (2 Db) ] + sqrt(2 T Db) z,  <z z^T> = S^{-1},
+ *   Dt = (1 - e^{-alpha Delta})/alpha,  Db = (1 - e^{-2 alpha Delta})/(2 alpha)
+ * with (R_prev, S_prev) the pair of the previous call kept in h (equal to the
+ * current pair on the first call).  s_mode QMC_S_IDENTITY: S = I, alpha = 0
+ * (conventional first-order Langevin); QMC_S_COV: S as given and
+ * alpha = 0.122 N_c of the last qmc_energy_forces call unless alpha > 0.
+ * R (host, [3N]) is updated in place and wrapped into [0, L).  Noise from
+ * Philox (key = seed, counter = (component, step, 0, 7)).
+ * Errors: INVALID, NOT_PD, CUDA.
+ */
+int langevin_step(qmc_system* h, double* R, const double* f, const double* S,
+                  double T_kelvin, double delta, int s_mode, double alpha);
+
+/* Same, device pointers, asynchronous (R_dev in/out). */
+int langevin_step_device(qmc_system* h, double* R_dev, const double* f_dev, const double* S_dev,
+                         double T_kelvin, double delta, int s_mode, double alpha);
+
+/*
+ * Per-configuration evaluation (parity checks): for n_conf <= n_walkers
+ * configurations X (host [n_conf][N][3]) at nuclei R, returns ln|psi|, E_L
+ * and the R-derivatives d ln|psi|/dR, dE_L/dR ([n_conf][N][3]) from the same
+ * kernels the sampler uses.  Overwrites the first n_conf walkers.
+ */
+int qmc_eval_config(qmc_system* h, int n_conf, const double* X, const double* R,
+                    double* logpsi, double* EL, double* dlogpsi_dR, double* dEL_dR);
+
+/* Copy walker positions out of / into the handle (host [n_walkers][N][3]). */
+int qmc_get_walkers(qmc_system* h, double* X);
+int qmc_set_walkers(qmc_system* h, const double* X);
+
+/* Per-walker accumulators of the last call, host [n_walkers][3 + 9N]:
+ * [count, sum E_L, sum E_L^2, sum dlnpsi/dR (3N), sum E_L dlnpsi/dR (3N), sum dE_L/dR (3N)]. */
+int qmc_get_accumulators(qmc_system* h, double* acc);
+
+/* Set the MD step counter used in the Philox counters of the next call. */
+int qmc_set_md_step(qmc_system* h, uint32_t md_step);
+
+/* Kernel timing: when enabled, CUDA events on h's stream bracket every kernel
+ * class; qmc_kernel_times fills ms[k] (total ms) and launches[k] for the
+ * n <= QMC_NKERNEL classes named by qmc_kernel_name(k), then resets them. */
+enum { QMC_NKERNEL = 8 };
+int qmc_set_profiling(qmc_system* h, int on);
+int qmc_kernel_times(qmc_system* h, int n, double* ms, long long* launches);
+const char* qmc_kernel_name(int k);
+
+/* Text of an error code. */
+const char* qmc_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QMCMD_H */

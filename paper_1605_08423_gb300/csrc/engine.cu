@@ -1,0 +1,509 @@
+// engine.cu -- the qmc_system handle: device state of one system (walkers,
+// inverses, tables), the schedule of one energy/force call and every entry
+// point of include/qmcmd.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/qmcmd.h"
+#include "common.cuh"
+#include "kernels.cuh"
+
+using namespace qmc;
+
+namespace {
+
+constexpr double kBoltzmannHaPerK = 3.166811563e-6;
+
+const char* kKernelNames[QMC_NKERNEL] = {"propose", "orbitals_prop", "sweep", "recompute",
+                                         "orbitals_meas", "measure", "reduce", "langevin"};
+enum { KC_PROPOSE = 0, KC_ORB_PROP, KC_SWEEP, KC_RECOMPUTE, KC_ORB_MEAS, KC_MEASURE, KC_REDUCE, KC_LANGEVIN };
+
+struct EventPair { cudaEvent_t a, b; int cls; };
+
+}  // namespace
+
+struct qmc_system {
+    qmc_params p;
+    std::vector<double> zeta_h, coeff_h;
+    int N, n, G, B, W, nk, mmax;
+    bool mixed;
+    cudaStream_t stream = nullptr, own_stream = nullptr;
+    // tables
+    double *d_R = nullptr, *d_zeta = nullptr, *d_C64 = nullptr, *d_kw = nullptr, *d_ptrig64 = nullptr;
+    float *d_C32 = nullptr, *d_ptrig32 = nullptr;
+    int4* d_kvec = nullptr;
+    double2 *d_eikR = nullptr, *d_rhop = nullptr;
+    double *d_vconst = nullptr, *d_dvpp = nullptr;
+    // walkers
+    double *d_X = nullptr, *d_Xp = nullptr;
+    void *d_uacc = nullptr, *d_Phi = nullptr, *d_Gt = nullptr, *d_D = nullptr, *d_Lp = nullptr;
+    double* d_logdet = nullptr;
+    double* d_acc = nullptr;
+    unsigned long long* d_nacc = nullptr;
+    // reductions and output
+    double *d_colsum = nullptr, *d_dev = nullptr, *d_out = nullptr;
+    double *d_eval = nullptr;  // eval_config outputs
+    // Langevin
+    double *d_Rl = nullptr, *d_Rprev = nullptr, *d_f = nullptr, *d_S = nullptr, *d_Sprev = nullptr, *d_Lwork = nullptr;
+    int* d_err = nullptr;
+    std::vector<void*> allocs;
+    uint32_t md_step = 0;
+    bool first_call = true;
+    bool langevin_first = true;
+    uint32_t langevin_step_no = 0;
+    double last_Nc = 0.0;
+    bool profiling = false;
+    std::vector<EventPair> events, free_events;
+    double ktime[QMC_NKERNEL] = {0};
+    long long klaunch[QMC_NKERNEL] = {0};
+};
+
+namespace {
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? QMC_OK : QMC_ERR_CUDA; }
+
+template <typename T>
+T* dalloc(qmc_system* h, size_t count, int* rc) {
+    void* p = nullptr;
+    if (*rc != QMC_OK) return nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+        *rc = QMC_ERR_OOM;
+        cudaGetLastError();
+        return nullptr;
+    }
+    h->allocs.push_back(p);
+    return (T*)p;
+}
+
+void enumerate_kvec(int mmax, std::vector<int4>& kv) {
+    // half space: mx > 0, or mx == 0 and my > 0, or mx == my == 0 and mz > 0; 0 < |m|^2 <= mmax^2
+    for (int mx = 0; mx <= mmax; ++mx)
+        for (int my = -mmax; my <= mmax; ++my)
+            for (int mz = -mmax; mz <= mmax; ++mz) {
+                const bool half = mx > 0 || (mx == 0 && my > 0) || (mx == 0 && my == 0 && mz > 0);
+                if (half && mx * mx + my * my + mz * mz <= mmax * mmax) kv.push_back(make_int4(mx, my, mz, 0));
+            }
+}
+
+int validate(const qmc_params* p) {
+    if (!p || !p->zeta || !p->coeff) return QMC_ERR_INVALID;
+    if (p->n_protons < 2 || p->n_protons > 128 || (p->n_protons & 1)) return QMC_ERR_INVALID;
+    if (p->n_gauss < 1 || p->n_gauss > 8) return QMC_ERR_INVALID;
+    if (p->n_walkers < 2 || p->n_sweeps < 1 || p->n_warmup < 0 || p->n_warmup_cont < 0) return QMC_ERR_INVALID;
+    if (p->measure_every < 1 || p->recompute_every < 1) return QMC_ERR_INVALID;
+    if (p->precision != QMC_FP64 && p->precision != QMC_MIXED) return QMC_ERR_INVALID;
+    if (p->ewald_mmax < 1 || p->ewald_mmax > 12) return QMC_ERR_INVALID;
+    if (!(p->L > 0) || !(p->ewald_kappa > 0) || !(p->sigma > 0) || p->b_ee < 0 || p->b_ep < 0) return QMC_ERR_INVALID;
+    if (p->n_sweeps / p->measure_every < 1) return QMC_ERR_INVALID;
+    return QMC_OK;
+}
+
+size_t footprint(const qmc_params* p) {
+    const size_t N = p->n_protons, n = N / 2, G = p->n_gauss, B = N * G, W = p->n_walkers;
+    const size_t t = p->precision == QMC_MIXED ? 4 : 8;
+    int nkc = 0;
+    for (int mx = 0; mx <= p->ewald_mmax; ++mx)
+        for (int my = -p->ewald_mmax; my <= p->ewald_mmax; ++my)
+            for (int mz = -p->ewald_mmax; mz <= p->ewald_mmax; ++mz) {
+                const bool half = mx > 0 || (mx == 0 && my > 0) || (mx == 0 && my == 0 && mz > 0);
+                if (half && mx * mx + my * my + mz * mz <= p->ewald_mmax * p->ewald_mmax) ++nkc;
+            }
+    const size_t nk = nkc;
+    size_t b = 0;
+    b += 8 * (3 * N + G + B * n + 6 * N + 3 * N + 2) + 4 * (B * n + 6 * N) + 16 * nk + 8 * nk + 16 * (N * nk + nk);
+    b += 8 * 2 * W * 3 * N;                          // X, Xp
+    b += t * (W * N + W * N * n + 2 * W * n * n + 3 * W * N * n + W * N * n);   // uacc, Phi, Gt, D, Lp
+    b += 8 * 2 * W + 8 * W * (3 + 9 * N) + 8 * W;   // logdet, acc, nacc
+    b += 8 * (4 + 9 * N) + 8 * W * (3 * N + 1) + 8 * (4 + 3 * N + 9 * N * N);   // colsum, dev, out
+    b += 8 * (2 * W + 6 * W * N);                    // eval outputs
+    b += 8 * (3 * 3 * N + 3 * 9 * N * N);           // Langevin
+    return b;
+}
+
+void prof_begin(qmc_system* h, int cls, EventPair& ep) {
+    if (!h->profiling) return;
+    if (!h->free_events.empty()) {
+        ep = h->free_events.back();
+        h->free_events.pop_back();
+    } else {
+        cudaEventCreate(&ep.a);
+        cudaEventCreate(&ep.b);
+    }
+    ep.cls = cls;
+    cudaEventRecord(ep.a, h->stream);
+}
+void prof_end(qmc_system* h, EventPair& ep) {
+    if (!h->profiling) return;
+    cudaEventRecord(ep.b, h->stream);
+    h->events.push_back(ep);
+    ++h->klaunch[ep.cls];
+}
+
+template <typename T>
+SysView<T> view(qmc_system* h, int W) {
+    SysView<T> s;
+    s.N = h->N; s.n = h->n; s.G = h->G; s.B = h->B; s.W = W;
+    s.L = h->p.L; s.ell = h->p.L / kPi;
+    s.b_ee = h->p.b_ee; s.b_ep = h->p.b_ep; s.Zj = 1.0; s.kappa = h->p.ewald_kappa;
+    s.zeta = h->d_zeta;
+    s.C = (const T*)(sizeof(T) == 8 ? (const void*)h->d_C64 : (const void*)h->d_C32);
+    s.R = h->d_R;
+    s.ptrig = (const T*)(sizeof(T) == 8 ? (const void*)h->d_ptrig64 : (const void*)h->d_ptrig32);
+    s.nk = h->nk; s.mmax = h->mmax;
+    s.kvec = h->d_kvec; s.kw = h->d_kw; s.eikR = h->d_eikR; s.rho_p = h->d_rhop;
+    s.vconst = h->d_vconst; s.dvpp = h->d_dvpp; s.err = h->d_err;
+    return s;
+}
+
+void setup_tables(qmc_system* h) {
+    launch_setup(h->N, h->p.L, h->p.ewald_kappa, h->nk, h->d_kvec, h->d_R, h->d_kw, h->d_ptrig64, h->d_ptrig32,
+                 h->d_eikR, h->d_rhop, h->d_vconst, h->d_dvpp, h->stream);
+}
+
+// Slater matrices at the current walker positions and their FP64 inverse.
+template <typename T>
+void recompute(qmc_system* h, int W) {
+    EventPair ep;
+    prof_begin(h, KC_RECOMPUTE, ep);
+    SysView<T> s = view<T>(h, W);
+    launch_orbitals<T>(s, h->d_X, W * h->N, (T*)h->d_Phi, nullptr, nullptr, h->stream);
+    launch_invert<T>(W, h->N, h->n, (const T*)h->d_Phi, (T*)h->d_Gt, h->d_logdet, h->d_err, h->stream);
+    prof_end(h, ep);
+}
+
+template <typename T>
+void measure(qmc_system* h, int W, double* el, double* lnpsi, double* dl, double* de) {
+    SysView<T> s = view<T>(h, W);
+    EventPair ep;
+    prof_begin(h, KC_ORB_MEAS, ep);
+    launch_orbitals<T>(s, h->d_X, W * h->N, (T*)h->d_Phi, (T*)h->d_D, (T*)h->d_Lp, h->stream);
+    prof_end(h, ep);
+    prof_begin(h, KC_MEASURE, ep);
+    launch_measure<T>(s, h->d_X, (const T*)h->d_D, (const T*)h->d_Lp, (const T*)h->d_Gt, h->d_logdet, h->d_acc, el,
+                      lnpsi, dl, de, h->stream);
+    prof_end(h, ep);
+}
+
+template <typename T>
+void run_call(qmc_system* h) {
+    const int W = h->W, N = h->N;
+    SysView<T> s = view<T>(h, W);
+    const Key key = make_key(h->p.seed);
+    const uint32_t md = h->md_step;
+    cudaMemsetAsync(h->d_acc, 0, sizeof(double) * (size_t)W * (3 + 9 * N), h->stream);
+    cudaMemsetAsync(h->d_nacc, 0, sizeof(unsigned long long) * W, h->stream);
+    recompute<T>(h, W);
+    const int nw = h->first_call ? h->p.n_warmup : h->p.n_warmup_cont;
+    const int total = nw + h->p.n_sweeps;
+    for (int sw = 0; sw < total; ++sw) {
+        EventPair ep;
+        prof_begin(h, KC_PROPOSE, ep);
+        launch_propose<T>(W, N, h->d_X, h->d_Xp, (T*)h->d_uacc, key, md, (uint32_t)sw, h->p.sigma, h->stream);
+        prof_end(h, ep);
+        prof_begin(h, KC_ORB_PROP, ep);
+        launch_orbitals<T>(s, h->d_Xp, W * N, (T*)h->d_Phi, nullptr, nullptr, h->stream);
+        prof_end(h, ep);
+        prof_begin(h, KC_SWEEP, ep);
+        launch_sweep<T>(s, h->d_X, h->d_Xp, (const T*)h->d_uacc, (const T*)h->d_Phi, (T*)h->d_Gt, h->d_nacc,
+                        h->stream);
+        prof_end(h, ep);
+        if ((sw + 1) % h->p.recompute_every == 0) recompute<T>(h, W);
+        if (sw >= nw && ((sw - nw + 1) % h->p.measure_every) == 0) measure<T>(h, W, nullptr, nullptr, nullptr, nullptr);
+    }
+    EventPair ep;
+    prof_begin(h, KC_REDUCE, ep);
+    const double moves = (double)W * total * N;
+    launch_reduce(W, N, moves, h->d_acc, h->d_nacc, h->d_colsum, h->d_dev, h->d_out, h->d_err, h->stream);
+    prof_end(h, ep);
+    h->last_Nc = (double)W * (h->p.n_sweeps / h->p.measure_every);
+    h->md_step++;
+    h->first_call = false;
+}
+
+int read_err(qmc_system* h) {
+    int e = 0;
+    if (cudaMemcpyAsync(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return QMC_ERR_CUDA;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return QMC_ERR_CUDA;
+    cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
+    if (e & kErrNotPD) return QMC_ERR_NOT_PD;
+    if (e & kErrSingular) return QMC_ERR_SINGULAR;
+    if (e & kErrNonfinite) return QMC_ERR_NONFINITE;
+    if (e & kErrTimeout) return QMC_ERR_TIMEOUT;
+    return QMC_OK;
+}
+
+int check_launch() { return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA; }
+
+}  // namespace
+
+extern "C" {
+
+size_t qmc_footprint_bytes(const qmc_params* p) { return validate(p) == QMC_OK ? footprint(p) : 0; }
+
+int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
+    if (!out || !R) return QMC_ERR_INVALID;
+    *out = nullptr;
+    int rc = validate(p);
+    if (rc != QMC_OK) return rc;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return QMC_ERR_CUDA; }
+    qmc_system* h = new (std::nothrow) qmc_system();
+    if (!h) return QMC_ERR_OOM;
+    h->p = *p;
+    h->N = p->n_protons; h->n = h->N / 2; h->G = p->n_gauss; h->B = h->N * h->G; h->W = p->n_walkers;
+    h->mmax = p->ewald_mmax;
+    h->mixed = p->precision == QMC_MIXED;
+    h->zeta_h.assign(p->zeta, p->zeta + h->G);
+    h->coeff_h.assign(p->coeff, p->coeff + (size_t)h->B * h->n);
+    h->p.zeta = h->zeta_h.data();
+    h->p.coeff = h->coeff_h.data();
+    std::vector<int4> kv;
+    enumerate_kvec(h->mmax, kv);
+    h->nk = (int)kv.size();
+    if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete h;
+        return QMC_ERR_CUDA;
+    }
+    h->stream = h->own_stream;
+    const int N = h->N, n = h->n, W = h->W, B = h->B, nk = h->nk;
+    const size_t t = h->mixed ? sizeof(float) : sizeof(double);
+    h->d_R = dalloc<double>(h, 3 * N, &rc);
+    h->d_zeta = dalloc<double>(h, h->G, &rc);
+    h->d_C64 = dalloc<double>(h, (size_t)B * n, &rc);
+    h->d_C32 = dalloc<float>(h, (size_t)B * n, &rc);
+    h->d_ptrig64 = dalloc<double>(h, 6 * N, &rc);
+    h->d_ptrig32 = dalloc<float>(h, 6 * N, &rc);
+    h->d_kvec = dalloc<int4>(h, nk, &rc);
+    h->d_kw = dalloc<double>(h, nk, &rc);
+    h->d_eikR = dalloc<double2>(h, (size_t)N * nk, &rc);
+    h->d_rhop = dalloc<double2>(h, nk, &rc);
+    h->d_vconst = dalloc<double>(h, 1, &rc);
+    h->d_dvpp = dalloc<double>(h, 3 * N, &rc);
+    h->d_X = dalloc<double>(h, (size_t)W * 3 * N, &rc);
+    h->d_Xp = dalloc<double>(h, (size_t)W * 3 * N, &rc);
+    h->d_uacc = dalloc<unsigned char>(h, t * W * N, &rc);
+    h->d_Phi = dalloc<unsigned char>(h, t * W * N * n, &rc);
+    h->d_Gt = dalloc<unsigned char>(h, t * W * 2 * n * n, &rc);
+    h->d_D = dalloc<unsigned char>(h, t * W * N * 3 * n, &rc);
+    h->d_Lp = dalloc<unsigned char>(h, t * W * N * n, &rc);
+    h->d_logdet = dalloc<double>(h, 2 * (size_t)W, &rc);
+    h->d_acc = dalloc<double>(h, (size_t)W * (3 + 9 * N), &rc);
+    h->d_nacc = dalloc<unsigned long long>(h, W, &rc);
+    h->d_colsum = dalloc<double>(h, 4 + 9 * N, &rc);
+    h->d_dev = dalloc<double>(h, (size_t)W * (3 * N + 1), &rc);
+    h->d_out = dalloc<double>(h, 4 + 3 * N + 9 * (size_t)N * N, &rc);
+    h->d_eval = dalloc<double>(h, (size_t)W * (2 + 6 * N), &rc);
+    h->d_Rl = dalloc<double>(h, 3 * N, &rc);
+    h->d_Rprev = dalloc<double>(h, 3 * N, &rc);
+    h->d_f = dalloc<double>(h, 3 * N, &rc);
+    h->d_S = dalloc<double>(h, 9 * (size_t)N * N, &rc);
+    h->d_Sprev = dalloc<double>(h, 9 * (size_t)N * N, &rc);
+    h->d_Lwork = dalloc<double>(h, 9 * (size_t)N * N, &rc);
+    h->d_err = dalloc<int>(h, 1, &rc);
+    if (rc != QMC_OK) { qmc_destroy(h); return rc; }
+    std::vector<float> c32(h->coeff_h.begin(), h->coeff_h.end());
+    cudaStream_t st = h->stream;
+    cudaMemcpyAsync(h->d_R, R, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(h->d_zeta, h->zeta_h.data(), sizeof(double) * h->G, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(h->d_C64, h->coeff_h.data(), sizeof(double) * B * n, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(h->d_C32, c32.data(), sizeof(float) * B * n, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(h->d_kvec, kv.data(), sizeof(int4) * nk, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
+    cudaMemsetAsync(h->d_nacc, 0, sizeof(unsigned long long) * W, st);
+    setup_tables(h);
+    launch_init_walkers(W, N, p->L, h->d_R, h->d_X, make_key(p->seed), st);
+    rc = check_launch();
+    if (rc == QMC_OK) rc = cuda_rc(cudaStreamSynchronize(st));
+    if (rc != QMC_OK) { qmc_destroy(h); return rc; }
+    *out = h;
+    return QMC_OK;
+}
+
+void qmc_destroy(qmc_system* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (void* a : h->allocs) cudaFree(a);
+    for (auto& e : h->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+    for (auto& e : h->free_events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    delete h;
+}
+
+int qmc_set_stream(qmc_system* h, void* stream) {
+    if (!h) return QMC_ERR_INVALID;
+    h->stream = stream ? (cudaStream_t)stream : h->own_stream;
+    return QMC_OK;
+}
+
+int qmc_sync(qmc_system* h) {
+    if (!h) return QMC_ERR_INVALID;
+    return read_err(h);
+}
+
+int qmc_set_md_step(qmc_system* h, uint32_t md_step) {
+    if (!h) return QMC_ERR_INVALID;
+    h->md_step = md_step;
+    return QMC_OK;
+}
+
+int qmc_energy_forces_device(qmc_system* h, const double* R_dev, double* out_dev) {
+    if (!h || !R_dev || !out_dev) return QMC_ERR_INVALID;
+    const int N = h->N;
+    cudaMemcpyAsync(h->d_R, R_dev, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, h->stream);
+    setup_tables(h);
+    if (h->mixed) run_call<float>(h);
+    else run_call<double>(h);
+    cudaMemcpyAsync(out_dev, h->d_out, sizeof(double) * (4 + 3 * N + 9 * (size_t)N * N), cudaMemcpyDeviceToDevice,
+                    h->stream);
+    return check_launch();
+}
+
+int qmc_energy_forces(qmc_system* h, const double* R, qmc_result* out) {
+    if (!h || !R || !out || !out->f || !out->cov) return QMC_ERR_INVALID;
+    const int N = h->N;
+    cudaMemcpyAsync(h->d_R, R, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, h->stream);
+    setup_tables(h);
+    if (h->mixed) run_call<float>(h);
+    else run_call<double>(h);
+    int rc = check_launch();
+    if (rc != QMC_OK) return rc;
+    std::vector<double> o(4 + 3 * N + 9 * (size_t)N * N);
+    cudaMemcpyAsync(o.data(), h->d_out, sizeof(double) * o.size(), cudaMemcpyDeviceToHost, h->stream);
+    rc = read_err(h);
+    if (rc != QMC_OK) return rc;
+    out->E = o[0]; out->E_err = o[1]; out->n_samples = o[2]; out->accept = o[3];
+    std::memcpy(out->f, o.data() + 4, sizeof(double) * 3 * N);
+    std::memcpy(out->cov, o.data() + 4 + 3 * N, sizeof(double) * 9 * (size_t)N * N);
+    return QMC_OK;
+}
+
+int langevin_step_device(qmc_system* h, double* R_dev, const double* f_dev, const double* S_dev, double T_kelvin,
+                         double delta, int s_mode, double alpha) {
+    if (!h || !R_dev || !f_dev || (!S_dev && s_mode == QMC_S_COV)) return QMC_ERR_INVALID;
+    if (s_mode != QMC_S_IDENTITY && s_mode != QMC_S_COV) return QMC_ERR_INVALID;
+    if (!(delta > 0) || T_kelvin < 0) return QMC_ERR_INVALID;
+    const int n3 = 3 * h->N;
+    cudaStream_t st = h->stream;
+    const int identity = s_mode == QMC_S_IDENTITY;
+    if (!identity)
+        cudaMemcpyAsync(h->d_S, S_dev, sizeof(double) * n3 * n3, cudaMemcpyDeviceToDevice, st);
+    if (h->langevin_first) {
+        cudaMemcpyAsync(h->d_Rprev, R_dev, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st);
+        if (!identity) cudaMemcpyAsync(h->d_Sprev, h->d_S, sizeof(double) * n3 * n3, cudaMemcpyDeviceToDevice, st);
+        else cudaMemsetAsync(h->d_Sprev, 0, sizeof(double) * n3 * n3, st);
+        h->langevin_first = false;
+    }
+    double a = 0.0;
+    if (!identity) a = alpha > 0 ? alpha : 0.122 * h->last_Nc;
+    EventPair ep;
+    prof_begin(h, KC_LANGEVIN, ep);
+    launch_langevin(n3, R_dev, h->d_Rprev, f_dev, h->d_S, h->d_Sprev, h->d_Lwork, T_kelvin * kBoltzmannHaPerK, delta,
+                    a, make_key(h->p.seed), h->langevin_step_no, h->p.L, identity, h->d_err, st);
+    prof_end(h, ep);
+    h->langevin_step_no++;
+    return check_launch();
+}
+
+int langevin_step(qmc_system* h, double* R, const double* f, const double* S, double T_kelvin, double delta,
+                  int s_mode, double alpha) {
+    if (!h || !R || !f || (!S && s_mode == QMC_S_COV)) return QMC_ERR_INVALID;
+    const int n3 = 3 * h->N;
+    cudaStream_t st = h->stream;
+    cudaMemcpyAsync(h->d_Rl, R, sizeof(double) * n3, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(h->d_f, f, sizeof(double) * n3, cudaMemcpyHostToDevice, st);
+    if (s_mode == QMC_S_COV) cudaMemcpyAsync(h->d_S, S, sizeof(double) * n3 * n3, cudaMemcpyHostToDevice, st);
+    int rc = langevin_step_device(h, h->d_Rl, h->d_f, s_mode == QMC_S_COV ? h->d_S : nullptr, T_kelvin, delta, s_mode,
+                                  alpha);
+    if (rc != QMC_OK) return rc;
+    cudaMemcpyAsync(R, h->d_Rl, sizeof(double) * n3, cudaMemcpyDeviceToHost, st);
+    return read_err(h);
+}
+
+int qmc_eval_config(qmc_system* h, int n_conf, const double* X, const double* R, double* logpsi, double* EL,
+                    double* dlogpsi_dR, double* dEL_dR) {
+    if (!h || !X || !R || !logpsi || !EL || !dlogpsi_dR || !dEL_dR) return QMC_ERR_INVALID;
+    if (n_conf < 1 || n_conf > h->W) return QMC_ERR_INVALID;
+    const int N = h->N, N3 = 3 * N;
+    cudaStream_t st = h->stream;
+    cudaMemcpyAsync(h->d_R, R, sizeof(double) * N3, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(h->d_X, X, sizeof(double) * (size_t)n_conf * N3, cudaMemcpyHostToDevice, st);
+    setup_tables(h);
+    cudaMemsetAsync(h->d_acc, 0, sizeof(double) * (size_t)n_conf * (3 + 9 * N), st);
+    double* el = h->d_eval;
+    double* lp = el + n_conf;
+    double* dl = lp + n_conf;
+    double* de = dl + (size_t)n_conf * N3;
+    if (h->mixed) { recompute<float>(h, n_conf); measure<float>(h, n_conf, el, lp, dl, de); }
+    else { recompute<double>(h, n_conf); measure<double>(h, n_conf, el, lp, dl, de); }
+    int rc = check_launch();
+    if (rc != QMC_OK) return rc;
+    cudaMemcpyAsync(EL, el, sizeof(double) * n_conf, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(logpsi, lp, sizeof(double) * n_conf, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(dlogpsi_dR, dl, sizeof(double) * n_conf * N3, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(dEL_dR, de, sizeof(double) * n_conf * N3, cudaMemcpyDeviceToHost, st);
+    return read_err(h);
+}
+
+int qmc_get_walkers(qmc_system* h, double* X) {
+    if (!h || !X) return QMC_ERR_INVALID;
+    cudaMemcpyAsync(X, h->d_X, sizeof(double) * (size_t)h->W * 3 * h->N, cudaMemcpyDeviceToHost, h->stream);
+    return read_err(h);
+}
+
+int qmc_set_walkers(qmc_system* h, const double* X) {
+    if (!h || !X) return QMC_ERR_INVALID;
+    cudaMemcpyAsync(h->d_X, X, sizeof(double) * (size_t)h->W * 3 * h->N, cudaMemcpyHostToDevice, h->stream);
+    return read_err(h);
+}
+
+int qmc_get_accumulators(qmc_system* h, double* acc) {
+    if (!h || !acc) return QMC_ERR_INVALID;
+    cudaMemcpyAsync(acc, h->d_acc, sizeof(double) * (size_t)h->W * (3 + 9 * h->N), cudaMemcpyDeviceToHost, h->stream);
+    return read_err(h);
+}
+
+int qmc_set_profiling(qmc_system* h, int on) {
+    if (!h) return QMC_ERR_INVALID;
+    h->profiling = on != 0;
+    return QMC_OK;
+}
+
+int qmc_kernel_times(qmc_system* h, int n, double* ms, long long* launches) {
+    if (!h || n < 0) return QMC_ERR_INVALID;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return QMC_ERR_CUDA;
+    for (auto& e : h->events) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e.a, e.b);
+        h->ktime[e.cls] += t;
+        h->free_events.push_back(e);
+    }
+    h->events.clear();
+    for (int k = 0; k < n && k < QMC_NKERNEL; ++k) {
+        if (ms) ms[k] = h->ktime[k];
+        if (launches) launches[k] = h->klaunch[k];
+    }
+    for (int k = 0; k < QMC_NKERNEL; ++k) { h->ktime[k] = 0; h->klaunch[k] = 0; }
+    return QMC_OK;
+}
+
+const char* qmc_kernel_name(int k) { return (k >= 0 && k < QMC_NKERNEL) ? kKernelNames[k] : "?"; }
+
+const char* qmc_strerror(int code) {
+    switch (code) {
+        case QMC_OK: return "ok";
+        case QMC_ERR_INVALID: return "invalid argument";
+        case QMC_ERR_OOM: return "out of device memory";
+        case QMC_ERR_CUDA: return "CUDA runtime error";
+        case QMC_ERR_NOT_PD: return "acceleration matrix S is not positive definite";
+        case QMC_ERR_NONFINITE: return "non-finite local energy, ratio or force";
+        case QMC_ERR_TIMEOUT: return "bounded device wait gave up";
+        case QMC_ERR_SINGULAR: return "singular Slater matrix";
+        default: return "unknown error";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// k_langevin.cu -- accelerated first-order Langevin step (SI, adopted integrator):
+//   R' = R + Dt S^{-1} [ f - (S_prev - S)(R_prev - R) / (2 Db) ] + sqrt(2 T Db) z,   <z z^T> = S^{-1}
+//   Dt = (1 - e^{-alpha D}) / alpha,  Db = (1 - e^{-2 alpha D}) / (2 alpha)   (both D at alpha = 0)
+// with S = L L^T (Cholesky), x = S^{-1} g by two triangular solves and z = L^{-T} xi,
+// xi ~ N(0, I) from Philox (counter = (component, md step, 0, 7)).  One CTA, FP64.
+// identity != 0 runs the conventional dynamics (S = I, alpha = 0).
+// On exit (R_prev, S_prev) hold the pair of this step for the next call.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace qmc {
+
+__global__ void __launch_bounds__(1024) langevin_kernel(int n, double* R, double* Rprev, const double* __restrict__ f,
+                                                        const double* __restrict__ S, double* Sprev, double* Lc,
+                                                        double T, double delta, double alpha, Key key, uint32_t md,
+                                                        double box, int identity, int* err) {
+    extern __shared__ double v[];
+    double* g = v;          // [n]
+    double* x = g + n;      // [n]
+    double* z = x + n;      // [n]
+    double* r0 = z + n;     // [n]
+    __shared__ double red[32];
+    __shared__ int notpd;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double Dt = delta, Db = delta;
+    if (!identity && alpha > 0.0) {
+        Dt = (1.0 - exp(-alpha * delta)) / alpha;
+        Db = (1.0 - exp(-2.0 * alpha * delta)) / (2.0 * alpha);
+    }
+    if (tid == 0) notpd = 0;
+    // Cholesky (left-looking, column by column)
+    if (!identity) {
+        for (int j = 0; j < n; ++j) {
+            double p = 0.0;
+            for (int k = tid; k < j; k += nt) p += Lc[(size_t)j * n + k] * Lc[(size_t)j * n + k];
+            p = block_sum(p, red);
+            const double d = S[(size_t)j * n + j] - p;
+            if (!(d > 0.0)) {
+                if (tid == 0) notpd = 1;
+                break;
+            }
+            const double ljj = sqrt(d);
+            if (tid == 0) Lc[(size_t)j * n + j] = ljj;
+            for (int i = j + 1 + tid; i < n; i += nt) {
+                double t = S[(size_t)i * n + j];
+                for (int k = 0; k < j; ++k) t -= Lc[(size_t)i * n + k] * Lc[(size_t)j * n + k];
+                Lc[(size_t)i * n + j] = t / ljj;
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+        if (notpd) {
+            if (tid == 0) raise_err(err, kErrNotPD);
+            return;
+        }
+    }
+    // g = f - (S_prev - S)(R_prev - R) / (2 Db);  xi;  keep R
+    for (int i = tid; i < n; i += nt) {
+        double t = f[i];
+        if (!identity) {
+            double s = 0.0;
+            for (int j = 0; j < n; ++j) s += (Sprev[(size_t)i * n + j] - S[(size_t)i * n + j]) * (Rprev[j] - R[j]);
+            t -= s / (2.0 * Db);
+        }
+        g[i] = t;
+        const uint4 w = philox((uint32_t)i, md, 0u, kLangevin, key);
+        z[i] = Draw<double>::normal(w);
+        r0[i] = R[i];
+    }
+    __syncthreads();
+    if (!identity) {
+        // forward solve L y = g (column oriented), y stored in g
+        for (int k = 0; k < n; ++k) {
+            const double yk = g[k] / Lc[(size_t)k * n + k];
+            __syncthreads();
+            if (tid == 0) g[k] = yk;
+            for (int i = k + 1 + tid; i < n; i += nt) g[i] -= Lc[(size_t)i * n + k] * yk;
+            __syncthreads();
+        }
+        // back solves L^T x = y and L^T z = xi
+        for (int k = n - 1; k >= 0; --k) {
+            const double xk = g[k] / Lc[(size_t)k * n + k];
+            const double zk = z[k] / Lc[(size_t)k * n + k];
+            __syncthreads();
+            if (tid == 0) { x[k] = xk; z[k] = zk; }
+            for (int i = tid; i < k; i += nt) {
+                g[i] -= Lc[(size_t)k * n + i] * xk;
+                z[i] -= Lc[(size_t)k * n + i] * zk;
+            }
+            __syncthreads();
+        }
+    } else {
+        for (int i = tid; i < n; i += nt) x[i] = g[i];
+        __syncthreads();
+    }
+    const double amp = T > 0.0 ? sqrt(2.0 * T * Db) : 0.0;
+    for (int i = tid; i < n; i += nt) {
+        double r = r0[i] + Dt * x[i] + amp * z[i];
+        if (box > 0.0) r -= box * floor(r / box);
+        Rprev[i] = r0[i];
+        R[i] = r;
+    }
+    for (size_t idx = tid; idx < (size_t)n * n; idx += nt) Sprev[idx] = identity ? (idx % (n + 1) == 0 ? 1.0 : 0.0) : S[idx];
+}
+
+void launch_langevin(int n3, double* R, double* Rprev, const double* f, const double* S, double* Sprev,
+                     double* Lwork, double T_ha, double delta, double alpha, Key key, uint32_t md, double box,
+                     int identity, int* err, cudaStream_t st) {
+    const size_t smem = 4 * (size_t)n3 * sizeof(double);
+    langevin_kernel<<<1, 1024, smem, st>>>(n3, R, Rprev, f, S, Sprev, Lwork, T_ha, delta, alpha, key, md, box,
+                                           identity, err);
+}
+
+}  // namespace qmc

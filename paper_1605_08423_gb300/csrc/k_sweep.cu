@@ -1,0 +1,170 @@
+// k_sweep.cu -- one Metropolis sweep of every walker (single-electron moves).
+//
+// One warp per walker.  For electron i (up block first, then down) with
+// proposal r'_i (precomputed by the proposal kernel) and its orbital row
+// phi'_j = phi_j(r'_i) (precomputed by the orbital kernel for the whole sweep):
+//   ratio   R  = sum_j phi'_j G_{j,i}                     (determinant ratio)
+//   Jastrow dU = sum_{j != i} [u_ee(r'_i,r_j) - u_ee(r_i,r_j)] + sum_a [u_en(r'_i,R_a) - u_en(r_i,R_a)]
+//   accept if u < R^2 exp(2 dU)
+// and on acceptance the Sherman-Morrison rank-1 update of the inverse of the
+// spin block:  G' = G - G_{:,i} (phi'^T G - e_i^T) / R.
+// The inverse of the moving spin block is staged in shared memory (row stride
+// n+1: conflict-free per-lane rows) for the n moves of that block.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace qmc {
+
+template <typename T>
+struct SweepSmem {
+    // per warp: G^T [n][n+1], old row [n], phi' [n], positions [3N] (double), trig [6N]
+    __host__ __device__ static size_t warp_bytes(int N, int n) {
+        size_t b = (size_t)n * (n + 1) * sizeof(T) + 2 * (size_t)n * sizeof(T);
+        b = (b + 7) & ~size_t(7);
+        b += (size_t)3 * N * sizeof(double) + (size_t)6 * N * sizeof(T);
+        return (b + 15) & ~size_t(15);
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ T pair_dist(const T* a, const T* b, T ell) {
+    // |d| for the periodised displacement between two points given by their
+    // (sin, cos)(pi x / L) triples
+    T t = 0;
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) {
+        const T sd = a[mu] * b[3 + mu] - a[3 + mu] * b[mu];
+        t += sd * sd;
+    }
+    return ell * qsqrt(t);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) sweep_kernel(SysView<T> s, double* __restrict__ X, const double* __restrict__ Xp,
+                                                    const T* __restrict__ uacc, const T* __restrict__ Phi,
+                                                    T* __restrict__ Gt, unsigned long long* __restrict__ nacc) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = s.N, n = s.n, ld = n + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    T* ptr_s = (T*)smraw;                                    // [N][6] proton trig
+    size_t off = ((size_t)6 * N * sizeof(T) + 15) & ~size_t(15);
+    unsigned char* mine = smraw + off + (size_t)warp * SweepSmem<T>::warp_bytes(N, n);
+    T* Gs = (T*)mine;
+    T* rowb = Gs + (size_t)n * ld;
+    T* phi = rowb + n;
+    size_t o2 = ((size_t)n * ld + 2 * (size_t)n) * sizeof(T);
+    o2 = (o2 + 7) & ~size_t(7);
+    double* xs = (double*)(mine + o2);
+    T* et = (T*)(xs + 3 * N);
+
+    for (int idx = threadIdx.x; idx < 6 * N; idx += blockDim.x) ptr_s[idx] = s.ptrig[idx];
+    __syncthreads();
+    const int w = blockIdx.x * wpb + warp;
+    if (w >= s.W) return;
+
+    const T ell = (T)s.ell, bee = (T)s.b_ee, bep = (T)s.b_ep, Zj = (T)s.Zj;
+    const double L = s.L;
+    for (int idx = lane; idx < 3 * N; idx += 32) xs[idx] = X[(size_t)w * 3 * N + idx];
+    __syncwarp();
+    for (int idx = lane; idx < 3 * N; idx += 32) {
+        const int i = idx / 3, mu = idx % 3;
+        T sn, cs;
+        qsincospi((T)(xs[idx] / L), &sn, &cs);
+        et[6 * i + mu] = sn;
+        et[6 * i + 3 + mu] = cs;
+    }
+    __syncwarp();
+    unsigned long long naccept = 0;
+    for (int sp = 0; sp < 2; ++sp) {
+        T* G = Gt + ((size_t)w * 2 + sp) * n * n;
+        for (int idx = lane; idx < n * n; idx += 32) Gs[(idx / n) * ld + idx % n] = G[idx];
+        __syncwarp();
+        for (int il = 0; il < n; ++il) {
+            const int i = sp * n + il;
+            const size_t row = (size_t)w * N + i;
+            double xp[3];
+            T pt[6];
+#pragma unroll
+            for (int mu = 0; mu < 3; ++mu) {
+                xp[mu] = Xp[row * 3 + mu];
+                qsincospi((T)(xp[mu] / L), &pt[mu], &pt[3 + mu]);
+            }
+            for (int j = lane; j < n; j += 32) phi[j] = Phi[row * n + j];
+            __syncwarp();
+            T part = 0;
+            for (int j = lane; j < n; j += 32) part += phi[j] * Gs[il * ld + j];
+            const T ratio = warp_sum(part);
+            T du = 0;
+            const T* ei = et + 6 * i;
+            for (int j = lane; j < N; j += 32) {
+                if (j == i) continue;
+                const T* ej = et + 6 * j;
+                T u1, u0, d1, d2;
+                pade_ee(bee, pair_dist(pt, ej, ell), u1, d1, d2);
+                pade_ee(bee, pair_dist(ei, ej, ell), u0, d1, d2);
+                du += u1 - u0;
+            }
+            for (int a = lane; a < N; a += 32) {
+                const T* pa = ptr_s + 6 * a;
+                T u1, u0, d1, d2, d3;
+                pade_ep(bep, Zj, pair_dist(pt, pa, ell), u1, d1, d2, d3);
+                pade_ep(bep, Zj, pair_dist(ei, pa, ell), u0, d1, d2, d3);
+                du += u1 - u0;
+            }
+            du = warp_sum(du);
+            const T prob = ratio * ratio * qexp(T(2) * du);
+            const T u = uacc[row];
+            if (u < prob) {
+                for (int j = lane; j < n; j += 32) rowb[j] = Gs[il * ld + j];
+                __syncwarp();
+                const T ir = T(1) / ratio;
+                for (int l = lane; l < n; l += 32) {
+                    T wl = 0;
+                    T* gl = Gs + l * ld;
+                    for (int j = 0; j < n; ++j) wl += phi[j] * gl[j];
+                    const T coef = (wl - (l == il ? T(1) : T(0))) * ir;
+                    for (int j = 0; j < n; ++j) gl[j] -= coef * rowb[j];
+                }
+                if (lane < 3) {
+                    const double x = xp[lane] - L * floor(xp[lane] / L);
+                    xs[3 * i + lane] = x;
+                    T sn, cs;
+                    qsincospi((T)(x / L), &sn, &cs);
+                    et[6 * i + lane] = sn;
+                    et[6 * i + 3 + lane] = cs;
+                }
+                ++naccept;
+            }
+            __syncwarp();
+        }
+        for (int idx = lane; idx < n * n; idx += 32) G[idx] = Gs[(idx / n) * ld + idx % n];
+        __syncwarp();
+    }
+    for (int idx = lane; idx < 3 * N; idx += 32) X[(size_t)w * 3 * N + idx] = xs[idx];
+    if (lane == 0) nacc[w] += naccept;
+}
+
+template <typename T>
+void launch_sweep(const SysView<T>& s, double* X, const double* Xp, const T* uacc, const T* Phi, T* Gt,
+                  unsigned long long* nacc, cudaStream_t st) {
+    const size_t wb = SweepSmem<T>::warp_bytes(s.N, s.n);
+    const size_t head = ((size_t)6 * s.N * sizeof(T) + 15) & ~size_t(15);
+    int wpb = (int)((200 * 1024 - head) / wb);
+    if (wpb > 8) wpb = 8;
+    if (wpb < 1) wpb = 1;
+    const size_t smem = head + wpb * wb;
+    static bool attr_set[2] = {false, false};
+    const int which = sizeof(T) == 8;
+    if (!attr_set[which]) {
+        cudaFuncSetAttribute(sweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        attr_set[which] = true;
+    }
+    sweep_kernel<T><<<(s.W + wpb - 1) / wpb, 32 * wpb, smem, st>>>(s, X, Xp, uacc, Phi, Gt, nacc);
+}
+
+template void launch_sweep<double>(const SysView<double>&, double*, const double*, const double*, const double*,
+                                   double*, unsigned long long*, cudaStream_t);
+template void launch_sweep<float>(const SysView<float>&, double*, const double*, const float*, const float*,
+                                  float*, unsigned long long*, cudaStream_t);
+
+}  // namespace qmc

@@ -1,0 +1,53 @@
+// kernels.cuh -- host-side launchers of the qmcmd kernels (one per kernel class).
+#pragma once
+#include "common.cuh"
+
+namespace qmc {
+
+// k_orbitals.cu
+template <typename T>
+void launch_orbitals(const SysView<T>& s, const double* pos, int nrows, T* val, T* grad, T* lap, cudaStream_t st);
+template <typename T>
+void launch_propose(int W, int N, const double* X, double* Xp, T* uacc, Key key, uint32_t md, uint32_t sweep,
+                    double sigma, cudaStream_t st);
+void launch_init_walkers(int W, int N, double L, const double* R, double* X, Key key, cudaStream_t st);
+
+// k_orbitals_tc.cu (tensor-core form of the value-only contraction)
+bool tc_orbitals_supported(int n, int B);
+void launch_orbitals_tc(const SysView<float>& s, const void* chat, const double* pos, int nrows, float* val,
+                        cudaStream_t st);
+void prepare_tc_coeff(const float* C, int B, int n, void* chat, cudaStream_t st);
+size_t tc_coeff_bytes(int B, int n);
+
+// k_invert.cu: FP64 Gauss-Jordan inverse of each walker's two Slater blocks.
+template <typename T>
+void launch_invert(int W, int N, int n, const T* Phi, T* Gt, double* logdet, int* err, cudaStream_t st);
+
+// k_sweep.cu: one Metropolis sweep per walker (warp per walker).
+template <typename T>
+void launch_sweep(const SysView<T>& s, double* X, const double* Xp, const T* uacc, const T* Phi, T* Gt,
+                  unsigned long long* nacc, cudaStream_t st);
+
+// k_measure.cu: local energy, d ln psi / dR and dE_L / dR per walker.
+template <typename T>
+void launch_measure(const SysView<T>& s, const double* X, const T* D, const T* Lp, const T* Gt,
+                    const double* logdet, double* acc, double* out_el, double* out_lnpsi, double* out_dl,
+                    double* out_de, cudaStream_t st);
+template <typename T>
+size_t measure_smem_bytes(int N, int n, int nk, int mmax);
+
+// k_setup.cu: per-R tables (proton trig, structure factors, p-p Ewald terms).
+void launch_setup(int N, double L, double kappa, int nk, const int4* kvec, const double* R, double* kw,
+                  double* ptrig64, float* ptrig32, double2* eikR, double2* rho_p, double* vconst, double* dvpp,
+                  cudaStream_t st);
+
+// k_reduce.cu: walker reductions and the covariance matrix.
+void launch_reduce(int W, int N, double moves, const double* acc, const unsigned long long* nacc,
+                   double* colsum, double* dev, double* out, int* err, cudaStream_t st);
+
+// k_langevin.cu
+void launch_langevin(int n3, double* R, double* Rprev, const double* f, const double* S, double* Sprev,
+                     double* Lwork, double T_ha, double delta, double alpha, Key key, uint32_t md, double box,
+                     int identity, int* err, cudaStream_t st);
+
+}  // namespace qmc

@@ -1,0 +1,262 @@
+"""Python binding of libqmcmd.so (include/qmcmd.h): argument marshalling only.
+
+Every step of the energy / force / covariance path and of the Langevin step
+runs in the library's CUDA kernels; this module converts numpy arrays and
+torch tensors to pointers and turns error codes into exceptions.  There is
+no CPU fallback: if the compiled library is missing or no GPU is present,
+the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import synth
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libqmcmd.so")
+
+QMC_FP64, QMC_MIXED = 0, 1
+QMC_S_IDENTITY, QMC_S_COV = 0, 1
+NKERNEL = 8
+
+
+class QMCError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("n_protons", C.c_int32), ("n_gauss", C.c_int32), ("n_walkers", C.c_int32), ("n_sweeps", C.c_int32),
+        ("n_warmup", C.c_int32), ("n_warmup_cont", C.c_int32), ("measure_every", C.c_int32),
+        ("recompute_every", C.c_int32), ("precision", C.c_int32), ("ewald_mmax", C.c_int32),
+        ("L", C.c_double), ("b_ee", C.c_double), ("b_ep", C.c_double), ("ewald_kappa", C.c_double),
+        ("sigma", C.c_double), ("seed", C.c_uint64),
+        ("zeta", C.POINTER(C.c_double)), ("coeff", C.POINTER(C.c_double)),
+    ]
+
+
+class Result(C.Structure):
+    _fields_ = [("E", C.c_double), ("E_err", C.c_double), ("f", C.POINTER(C.c_double)),
+                ("cov", C.POINTER(C.c_double)), ("n_samples", C.c_double), ("accept", C.c_double)]
+
+
+_dp = C.POINTER(C.c_double)
+_lib = None
+
+
+def lib():
+    """Load libqmcmd.so (built by __graft_entry__.build() / paper_1605_08423_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1605_08423_gb300.build` "
+                               "(the CUDA library is the only implementation of this path)")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.qmc_init.argtypes = [C.POINTER(Params), _dp, C.POINTER(vp)]
+        L.qmc_destroy.argtypes = [vp]
+        L.qmc_destroy.restype = None
+        L.qmc_footprint_bytes.argtypes = [C.POINTER(Params)]
+        L.qmc_footprint_bytes.restype = C.c_size_t
+        L.qmc_set_stream.argtypes = [vp, vp]
+        L.qmc_sync.argtypes = [vp]
+        L.qmc_energy_forces.argtypes = [vp, _dp, C.POINTER(Result)]
+        L.qmc_energy_forces_device.argtypes = [vp, vp, vp]
+        L.langevin_step.argtypes = [vp, _dp, _dp, _dp, C.c_double, C.c_double, C.c_int, C.c_double]
+        L.langevin_step_device.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, C.c_int, C.c_double]
+        L.qmc_eval_config.argtypes = [vp, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.qmc_get_walkers.argtypes = [vp, _dp]
+        L.qmc_set_walkers.argtypes = [vp, _dp]
+        L.qmc_get_accumulators.argtypes = [vp, _dp]
+        L.qmc_set_md_step.argtypes = [vp, C.c_uint32]
+        L.qmc_set_profiling.argtypes = [vp, C.c_int]
+        L.qmc_kernel_times.argtypes = [vp, C.c_int, _dp, C.POINTER(C.c_longlong)]
+        L.qmc_kernel_name.argtypes = [C.c_int]
+        L.qmc_kernel_name.restype = C.c_char_p
+        L.qmc_strerror.argtypes = [C.c_int]
+        L.qmc_strerror.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().qmc_strerror(code).decode()
+
+
+def _chk(rc: int, what: str):
+    if rc != 0:
+        raise QMCError(rc, what)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+@dataclass
+class Config:
+    """Parameters of one system handle (mirrors qmc_params)."""
+    N: int
+    L: float
+    zeta: np.ndarray
+    coeff: np.ndarray
+    walkers: int
+    sweeps: int
+    warmup: int = 20
+    warmup_cont: int = 5
+    measure_every: int = 1
+    recompute_every: int = 1
+    precision: int = QMC_FP64
+    mmax: int = 6
+    b_ee: float = 1.0
+    b_ep: float = 1.0
+    kappa: float | None = None
+    sigma: float = 0.3
+    seed: int = 1
+
+    @classmethod
+    def from_workload(cls, wl: "synth.Workload", precision=QMC_FP64, **over):
+        kw = dict(N=wl.N, L=wl.L, zeta=np.array(wl.zeta), coeff=wl.C, walkers=wl.walkers, sweeps=wl.sweeps,
+                  warmup=wl.warmup, measure_every=wl.measure_every, recompute_every=wl.recompute_every,
+                  precision=precision, sigma=wl.sigma, seed=wl.seed)
+        kw.update(over)
+        return cls(**kw)
+
+    def cparams(self) -> Params:
+        self._z = _f64(self.zeta)
+        self._c = _f64(self.coeff)
+        kappa = 5.0 / self.L if self.kappa is None else self.kappa
+        return Params(self.N, len(self._z), self.walkers, self.sweeps, self.warmup, self.warmup_cont,
+                      self.measure_every, self.recompute_every, self.precision, self.mmax, self.L, self.b_ee,
+                      self.b_ep, kappa, self.sigma, self.seed, _p(self._z), _p(self._c))
+
+
+def footprint_bytes(cfg: Config) -> int:
+    p = cfg.cparams()
+    return int(lib().qmc_footprint_bytes(C.byref(p)))
+
+
+class QMCSystem:
+    """One handle of libqmcmd: resident walkers + tables of one system."""
+
+    def __init__(self, cfg: Config, R):
+        self.cfg = cfg
+        self.N = cfg.N
+        self._h = C.c_void_p()
+        p = cfg.cparams()
+        _chk(lib().qmc_init(C.byref(p), _p(_f64(R)), C.byref(self._h)), "qmc_init")
+
+    def close(self):
+        if self._h:
+            lib().qmc_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ host API
+    def energy_forces(self, R) -> dict:
+        N3 = 3 * self.N
+        f = np.zeros(N3)
+        S = np.zeros((N3, N3))
+        r = Result(0.0, 0.0, _p(f), _p(S), 0.0, 0.0)
+        _chk(lib().qmc_energy_forces(self._h, _p(_f64(R)), C.byref(r)), "qmc_energy_forces")
+        return dict(E=r.E, E_err=r.E_err, f=f, S=S, Nc=r.n_samples, accept=r.accept)
+
+    def langevin_step(self, R, f, S, T_kelvin, delta, s_mode=QMC_S_COV, alpha=0.0) -> np.ndarray:
+        Rn = _f64(R).copy().ravel()
+        Sa = _f64(S) if S is not None else np.zeros(1)
+        _chk(lib().langevin_step(self._h, _p(Rn), _p(_f64(f)), _p(Sa), T_kelvin, delta, s_mode, alpha),
+             "langevin_step")
+        return Rn
+
+    def eval_config(self, X, R) -> dict:
+        X = _f64(X)
+        nc = X.shape[0]
+        lp = np.zeros(nc); el = np.zeros(nc)
+        dl = np.zeros((nc, self.N, 3)); de = np.zeros((nc, self.N, 3))
+        _chk(lib().qmc_eval_config(self._h, nc, _p(X), _p(_f64(R)), _p(lp), _p(el), _p(dl), _p(de)),
+             "qmc_eval_config")
+        return dict(lnpsi=lp, el=el, dlnpsi=dl, del_=de)
+
+    def walkers(self) -> np.ndarray:
+        X = np.zeros((self.cfg.walkers, self.N, 3))
+        _chk(lib().qmc_get_walkers(self._h, _p(X)), "qmc_get_walkers")
+        return X
+
+    def set_walkers(self, X):
+        _chk(lib().qmc_set_walkers(self._h, _p(_f64(X))), "qmc_set_walkers")
+
+    def accumulators(self) -> np.ndarray:
+        a = np.zeros((self.cfg.walkers, 3 + 9 * self.N))
+        _chk(lib().qmc_get_accumulators(self._h, _p(a)), "qmc_get_accumulators")
+        return a
+
+    def set_md_step(self, m: int):
+        _chk(lib().qmc_set_md_step(self._h, m), "qmc_set_md_step")
+
+    # ------------------------------------------------------------------ device API (torch tensors)
+    def set_stream(self, stream_handle: int | None):
+        _chk(lib().qmc_set_stream(self._h, C.c_void_p(stream_handle or 0)), "qmc_set_stream")
+
+    def energy_forces_device(self, R_dev, out_dev):
+        """R_dev: float64 cuda tensor [N,3]; out_dev: float64 cuda tensor [4+3N+9N^2] (asynchronous)."""
+        _chk(lib().qmc_energy_forces_device(self._h, C.c_void_p(R_dev.data_ptr()), C.c_void_p(out_dev.data_ptr())),
+             "qmc_energy_forces_device")
+
+    def langevin_step_device(self, R_dev, f_dev, S_dev, T_kelvin, delta, s_mode=QMC_S_COV, alpha=0.0):
+        _chk(lib().langevin_step_device(self._h, C.c_void_p(R_dev.data_ptr()), C.c_void_p(f_dev.data_ptr()),
+                                        C.c_void_p(S_dev.data_ptr() if S_dev is not None else 0), T_kelvin, delta,
+                                        s_mode, alpha), "langevin_step_device")
+
+    def sync(self):
+        _chk(lib().qmc_sync(self._h), "qmc_sync")
+
+    def set_profiling(self, on: bool):
+        _chk(lib().qmc_set_profiling(self._h, int(on)), "qmc_set_profiling")
+
+    def kernel_times(self) -> dict:
+        ms = np.zeros(NKERNEL)
+        ln = (C.c_longlong * NKERNEL)()
+        _chk(lib().qmc_kernel_times(self._h, NKERNEL, _p(ms), ln), "qmc_kernel_times")
+        return {lib().qmc_kernel_name(k).decode(): (float(ms[k]), int(ln[k])) for k in range(NKERNEL)}
+
+
+def unpack_out(out: np.ndarray, N: int) -> dict:
+    """Split the device output vector [E, E_err, N_c, accept, f(3N), S(3N*3N)]."""
+    N3 = 3 * N
+    return dict(E=out[0], E_err=out[1], Nc=out[2], accept=out[3], f=out[4:4 + N3],
+                S=out[4 + N3:4 + N3 + N3 * N3].reshape(N3, N3))
+
+
+def energy_forces_function():
+    """torch.autograd.Function whose forward is the VMC energy E(R) and whose
+    backward returns dE/dR = -f (the library's Hellmann-Feynman + Pulay force)."""
+    import torch
+
+    class EnergyForces(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, R, system):
+            out = system.energy_forces(R.detach().cpu().numpy().reshape(-1, 3))
+            f = torch.as_tensor(out["f"], dtype=R.dtype, device=R.device).reshape(R.shape)
+            ctx.save_for_backward(f)
+            return torch.as_tensor(out["E"], dtype=R.dtype, device=R.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (f,) = ctx.saved_tensors
+            return -f * grad_out, None
+
+    return EnergyForces

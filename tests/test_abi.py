@@ -1,0 +1,61 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads and exports
+every function declared in include/qmcmd.h, struct layouts agree with the
+binding, and argument validation happens before any device work."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_1605_08423_gb300 import build as gbuild
+from paper_1605_08423_gb300 import qmcmd as q
+from paper_1605_08423_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "qmcmd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gbuild.build()
+    return q.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert "qmc_init" in names and "langevin_step" in names and "qmc_energy_forces" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_struct_layouts_match_header(lib):
+    # qmc_params: 10 int32, 5 double, uint64, 2 pointers
+    assert C.sizeof(q.Params) == 10 * 4 + 5 * 8 + 8 + 2 * 8
+    assert C.sizeof(q.Result) == 6 * 8
+
+
+def test_invalid_parameters_rejected_without_gpu(lib):
+    wl = synth.workload("h16", walkers=2)
+    cfg = q.Config.from_workload(wl, walkers=1)
+    assert q.footprint_bytes(cfg) == 0            # invalid -> 0
+    cfg_ok = q.Config.from_workload(wl)
+    assert q.footprint_bytes(cfg_ok) > 0
+    odd = q.Config.from_workload(wl)
+    odd.N = 15
+    h = C.c_void_p()
+    rc = lib.qmc_init(C.byref(odd.cparams()), (C.c_double * 48)(), C.byref(h))
+    assert rc == -1
+    assert q.strerror(-7) == "singular Slater matrix"
+
+
+def test_footprint_scales_with_walkers(lib):
+    wl = synth.workload("h64")
+    a = q.footprint_bytes(q.Config.from_workload(wl, walkers=1000))
+    b = q.footprint_bytes(q.Config.from_workload(wl, walkers=2000))
+    assert 1.8 < b / a < 2.1

@@ -1,0 +1,156 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: FP64 form 1e-10 relative, mixed form 1e-4 relative (E_L and
+ln|psi| relative to their own magnitude; force vectors relative to the
+largest component of the oracle's vector).  Chains on the same Philox
+streams must reproduce the oracle's walker positions and accumulators.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1605_08423_gb300 import qmcmd as q
+from paper_1605_08423_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {q.QMC_FP64: 1e-10, q.QMC_MIXED: 1e-4}
+
+
+def _oracle_sys(wl):
+    return orc.System(N=wl.N, L=wl.L, zeta=np.array(wl.zeta), coeff=wl.C)
+
+
+def _configs(wl, n, seed):
+    half = n // 2
+    X1 = synth.near_protons(half, wl.R, wl.N // 2, 0.7, wl.L, seed)
+    X2 = synth.random_electrons(n - half, wl.N, wl.L, seed)
+    return np.concatenate([X1, X2])
+
+
+def _rel_vec(a, b):
+    return np.max(np.abs(a - b), axis=(-1, -2)) / np.max(np.abs(b), axis=(-1, -2))
+
+
+@pytest.mark.parametrize("name,nconf,prec", [
+    ("h16", 12, q.QMC_FP64), ("h16", 12, q.QMC_MIXED),
+    ("h64", 4, q.QMC_FP64), ("h64", 4, q.QMC_MIXED),
+])
+def test_eval_config_matches_oracle(name, nconf, prec):
+    wl = synth.workload(name)
+    X = _configs(wl, nconf, 5)
+    sysg = q.QMCSystem(q.Config.from_workload(wl, precision=prec, walkers=max(nconf, 2)), wl.R)
+    g = sysg.eval_config(X, wl.R)
+    lp, el, dl, de = orc.eval_configs(_oracle_sys(wl), wl.R, X, derivs=True)
+    tol = TOL[prec]
+    assert np.all(np.abs(g["el"] - el) <= tol * np.abs(el)), (g["el"], el)
+    assert np.all(np.abs(g["lnpsi"] - lp) <= tol * np.maximum(np.abs(lp), 1.0)), (g["lnpsi"], lp)
+    assert np.all(_rel_vec(g["dlnpsi"], dl) <= tol), _rel_vec(g["dlnpsi"], dl)
+    assert np.all(_rel_vec(g["del_"], de) <= tol), _rel_vec(g["del_"], de)
+
+
+@pytest.mark.parametrize("prec", [q.QMC_FP64, q.QMC_MIXED])
+def test_eval_config_full_size_sampled(prec):
+    """The N=128, 4-Gaussian headline system: sampled configurations."""
+    wl = synth.workload("h128", walkers=2)
+    X = _configs(wl, 2, 17)
+    sysg = q.QMCSystem(q.Config.from_workload(wl, precision=prec), wl.R)
+    g = sysg.eval_config(X, wl.R)
+    lp, el, dl, de = orc.eval_configs(_oracle_sys(wl), wl.R, X, derivs=True)
+    tol = TOL[prec]
+    assert np.all(np.abs(g["el"] - el) <= tol * np.abs(el)), (g["el"], el)
+    assert np.all(np.abs(g["lnpsi"] - lp) <= tol * np.abs(lp))
+    assert np.all(_rel_vec(g["dlnpsi"], dl) <= tol), _rel_vec(g["dlnpsi"], dl)
+    assert np.all(_rel_vec(g["del_"], de) <= tol), _rel_vec(g["del_"], de)
+
+
+def test_walker_start_matches_oracle():
+    wl = synth.workload("h16", walkers=32)
+    sysg = q.QMCSystem(q.Config.from_workload(wl), wl.R)
+    Xo = orc.init_walkers(_oracle_sys(wl), wl.R, 32, wl.seed)
+    assert np.allclose(sysg.walkers(), Xo, atol=1e-12, rtol=0)
+
+
+def test_fp64_chain_reproduces_oracle():
+    """Same Philox streams: identical accept sequences, positions and sums."""
+    wl = synth.workload("h16", walkers=16, sweeps=3, warmup=2)
+    cfg = q.Config.from_workload(wl, recompute_every=1)
+    sysg = q.QMCSystem(cfg, wl.R)
+    res = sysg.energy_forces(wl.R)
+    Xg, accg = sysg.walkers(), sysg.accumulators()
+    Xo, acco, ar = orc.vmc(_oracle_sys(wl), wl.R, W=16, n_sweeps=3, n_warmup=2, sigma=wl.sigma, seed=wl.seed)
+    assert np.allclose(Xg, Xo, atol=1e-9, rtol=0)
+    scale = np.maximum(np.abs(acco), 1.0)
+    assert np.max(np.abs(accg - acco) / scale) < 1e-8
+    ro = orc.reduce(acco, wl.N)
+    assert abs(res["E"] - ro["E"]) < 1e-10 * abs(ro["E"])
+    assert np.max(np.abs(res["f"] - ro["f"])) < 1e-8 * np.max(np.abs(ro["f"]))
+    assert np.max(np.abs(res["S"] - ro["S"])) < 1e-8 * np.max(np.abs(ro["S"]))
+    assert abs(res["accept"] - ar) < 1e-12
+
+
+def test_mixed_chain_statistically_matches_fp64():
+    wl = synth.workload("h16", walkers=256, sweeps=120, warmup=30)
+    r64 = q.QMCSystem(q.Config.from_workload(wl, precision=q.QMC_FP64), wl.R).energy_forces(wl.R)
+    r32 = q.QMCSystem(q.Config.from_workload(wl, precision=q.QMC_MIXED), wl.R).energy_forces(wl.R)
+    err = np.hypot(r64["E_err"], r32["E_err"])
+    assert abs(r64["E"] - r32["E"]) < 4 * err, (r64["E"], r32["E"], err)
+    sig = np.sqrt(np.diag(r64["S"]) + np.diag(r32["S"]))
+    z = np.abs(r64["f"] - r32["f"]) / sig
+    assert np.mean(z < 3) > 0.95 and np.max(z) < 5.5, z
+
+
+def _spd(n, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n))
+    return A @ A.T / n + 0.3 * np.eye(n)
+
+
+@pytest.mark.parametrize("mode", [q.QMC_S_IDENTITY, q.QMC_S_COV])
+def test_langevin_step_matches_oracle(mode):
+    wl = synth.workload("h16", walkers=2)
+    sysg = q.QMCSystem(q.Config.from_workload(wl), wl.R)
+    n = 3 * wl.N
+    rng = np.random.default_rng(4)
+    R0 = wl.R.ravel().copy()
+    T = 1000.0 * synth.K_B_HARTREE_PER_KELVIN
+    alpha = 0.0 if mode == q.QMC_S_IDENTITY else 37.0
+    Rprev, Sprev = R0.copy(), None
+    R = R0.copy()
+    for step in range(3):
+        f = rng.standard_normal(n)
+        S = np.eye(n) if mode == q.QMC_S_IDENTITY else _spd(n, 10 + step) * 1e-3
+        if Sprev is None:
+            Sprev = S
+        xi = orc.langevin_noise(wl.seed, step, n)
+        Ro = orc.langevin(R, Rprev, f, S, Sprev, T, 0.1, alpha, xi, box=wl.L)
+        Rg = sysg.langevin_step(R, f, S if mode == q.QMC_S_COV else None, 1000.0, 0.1, s_mode=mode, alpha=alpha)
+        assert np.max(np.abs(Rg - Ro)) < 1e-10, (step, np.max(np.abs(Rg - Ro)))
+        Rprev, Sprev, R = R, S, Ro
+
+
+def test_autograd_function_backward_is_minus_force():
+    import torch
+    wl = synth.workload("h16", walkers=64, sweeps=10, warmup=5)
+    sysg = q.QMCSystem(q.Config.from_workload(wl), wl.R)
+    EF = q.energy_forces_function()
+    R = torch.tensor(wl.R, dtype=torch.float64, requires_grad=True)
+    E = EF.apply(R, sysg)
+    E.backward()
+    sys2 = q.QMCSystem(q.Config.from_workload(wl), wl.R)
+    ref = sys2.energy_forces(wl.R)
+    assert abs(float(E) - ref["E"]) < 1e-12 * abs(ref["E"])
+    assert np.allclose(R.grad.numpy().ravel(), -ref["f"], rtol=0, atol=1e-12 * np.max(np.abs(ref["f"])))
+
+
+def test_errors_are_reported():
+    wl = synth.workload("h16", walkers=2)
+    sysg = q.QMCSystem(q.Config.from_workload(wl), wl.R)
+    n = 3 * wl.N
+    S = -np.eye(n)
+    with pytest.raises(q.QMCError) as e:
+        sysg.langevin_step(wl.R, np.zeros(n), S, 1000.0, 0.1, s_mode=q.QMC_S_COV, alpha=1.0)
+    assert e.value.code == -4
+    with pytest.raises(q.QMCError) as e:
+        q.QMCSystem(q.Config.from_workload(wl, walkers=1), wl.R)
+    assert e.value.code == -1
