@@ -1,0 +1,336 @@
+"""Throughput benchmark of the VMC energy / force / covariance hot path plus the
+accelerated Langevin step on GB300.
+
+One step = one qmc_energy_forces call (warm-up continuation sweeps, measured
+sweeps with a local-energy and adjoint-force sample each sweep, reductions to
+E, f and S) followed by one langevin_step with S = Cov(f).  The default
+workload is the N=128 dense-hydrogen system (r_s = 1.2, 4 s-Gaussians per
+proton, 16384 walkers, 1000 sweeps) in the mixed-precision form.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs an independent replica (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VMC electron moves/s and force-evals/s at N=128 vs FP64 form; p50/p99 latency"
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="h128")
+    ap.add_argument("--rs", type=float, default=1.2)
+    ap.add_argument("--walkers", type=int, default=None)
+    ap.add_argument("--sweeps", type=int, default=None)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--recompute-every", type=int, default=8)
+    ap.add_argument("--fp64-sweeps", type=int, default=4, help="sweeps per step of the FP64-form comparison (0: skip)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return d, "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-i", str(index), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _flops_per_launch(cls: str, W, N, n, B, G, acc_ratio):
+    """Algorithmic FLOPs of one launch of a kernel class (dense multiply-adds x 2)."""
+    if cls == "orbitals_prop":
+        return 2.0 * W * N * B * n
+    if cls == "orbitals_meas":
+        return 10.0 * W * N * B * n
+    if cls == "measure":
+        return 2.0 * W * (4.0 * n ** 3 + 4.0 * N * G * n * n)
+    if cls == "sweep":
+        return 2.0 * W * N * (n + acc_ratio * 2.0 * n * n)
+    return None
+
+
+def _cpu_baseline(wl, walkers_per_core=1):
+    """The FP64 oracle on the host cores: one sweep plus one local-energy and
+    force sample per walker, W = threads x walkers_per_core."""
+    import numpy as np
+    from oracle import oracle as orc
+    threads = orc.num_threads()
+    W = threads * walkers_per_core
+    osys = orc.System(N=wl.N, L=wl.L, zeta=np.array(wl.zeta), coeff=wl.C)
+    t0 = time.perf_counter()
+    orc.vmc(osys, wl.R, W=W, n_sweeps=1, n_warmup=0, sigma=wl.sigma, seed=wl.seed, forces=True)
+    dt = time.perf_counter() - t0
+    moves = W * wl.N
+    return {"value": moves / dt, "unit": "electron moves/s", "cores": threads, "kind": "oracle",
+            "sample": f"{W} walkers x 1 sweep of N={wl.N} (each sweep followed by one E_L + 3N-force sample), "
+                      f"{dt:.1f} s", "force_evals_per_s": W / dt, "seconds": dt, "moves": moves}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from paper_1605_08423_gb300 import synth
+    wl = synth.workload(args.workload, rs=args.rs)
+    times = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        r = _cpu_baseline(wl)
+        if i >= args.warmup:
+            times.append(r)
+        last = r
+    tot_moves = sum(t["moves"] for t in times)
+    tot_time = sum(t["seconds"] for t in times)
+    value = tot_moves / tot_time
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "electron moves/s", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_time / len(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": f"{args.workload} (N={wl.N}, r_s={wl.rs}, {wl.n_gauss} s-Gaussians/proton); "
+                                  "each step a bounded sample on the host cores"},
+           "cpu_baseline": {"value": value, "unit": "electron moves/s", "cores": last["cores"], "kind": "oracle",
+                            "sample": last["sample"]},
+           "e2e": {"value": value, "unit": "electron moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    from paper_1605_08423_gb300 import qmcmd as q
+    from paper_1605_08423_gb300 import synth
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    over = {"rs": args.rs, "seed": 1002 + rank}
+    if args.walkers:
+        over["walkers"] = args.walkers
+    if args.sweeps:
+        over["sweeps"] = args.sweeps
+    wl = synth.workload(args.workload, **over)
+    prec = q.QMC_MIXED if args.precision == "mixed" else q.QMC_FP64
+    cfg = q.Config.from_workload(wl, precision=prec, warmup=20, warmup_cont=5, measure_every=1,
+                                 recompute_every=args.recompute_every)
+    N, n, G = wl.N, wl.N // 2, wl.n_gauss
+    B, W, N3 = N * G, wl.walkers, 3 * wl.N
+    system = q.QMCSystem(cfg, wl.R)
+    # a dedicated stream: the library launches on it and the timing events are recorded on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    system.set_stream(stream.cuda_stream)
+    R_dev = torch.tensor(wl.R, dtype=torch.float64, device="cuda")
+    out_dev = torch.zeros(4 + N3 + N3 * N3, dtype=torch.float64, device="cuda")
+    T_K, delta = wl.T_kelvin, wl.delta
+
+    def step():
+        system.energy_forces_device(R_dev, out_dev)
+        system.langevin_step_device(R_dev, out_dev[4:4 + N3], out_dev[4 + N3:], T_K, delta, q.QMC_S_COV)
+
+    for _ in range(args.warmup):
+        step()
+    system.sync()
+    system.kernel_times()          # reset
+    system.set_profiling(True)
+    n0 = system.launch_count()
+    clocks = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    system.sync()
+    launches = system.launch_count() - n0
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    kt = system.kernel_times()
+    system.set_profiling(False)
+    res = q.unpack_out(out_dev.cpu().numpy(), N)
+    sweeps_per_step = cfg.warmup_cont + cfg.sweeps
+    moves_per_step = W * N * sweeps_per_step
+    fevals_per_step = W * (cfg.sweeps // cfg.measure_every)
+    value = ws * moves_per_step * args.steps / (ms / 1e3)
+    fevals = ws * fevals_per_step * args.steps / (ms / 1e3)
+
+    # end to end through the host-pointer C ABI (R, f, S host buffers; copies inside)
+    Rh = wl.R.copy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        r = system.energy_forces(Rh)
+        Rh = system.langevin_step(Rh, r["f"], r["S"], T_K, delta, q.QMC_S_COV).reshape(N, 3)
+    t_e2e = time.perf_counter() - t0
+    e2e = ws * moves_per_step * args.e2e_steps / t_e2e
+    h2d = 8 * (N3 + N3 + N3 + N3 * N3)
+    d2h = 8 * (4 + N3 + N3 * N3 + N3)
+
+    # roofline of the dominant kernel class
+    peaks, peak_kind = _peaks()
+    dom = max(kt, key=lambda k: kt[k][0])
+    dms, dl = kt[dom]
+    fl = _flops_per_launch(dom, W, N, n, B, G, float(res["accept"]))
+    sm_clock = (clk.get("sm_max_mhz") or 2070.0) * 1e6
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_clock / 1e12
+    if fl is not None and dl > 0:
+        achieved = fl / (dms / dl / 1e3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock",
+                "flops_per_launch": fl, "avg_launch_ms": dms / dl}
+    else:
+        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": None, "traffic": None}
+    breakdown = {k: {"ms": v[0] / args.steps, "launches": v[1] // max(args.steps, 1)} for k, v in kt.items()}
+
+    # FP64 form on the same system (short burst) for the "vs FP64 form" comparison
+    fp64 = None
+    if args.fp64_sweeps > 0 and prec == q.QMC_MIXED and rank == 0:
+        wl64 = synth.workload(args.workload, **{**over, "sweeps": args.fp64_sweeps})
+        cfg64 = q.Config.from_workload(wl64, precision=q.QMC_FP64, warmup=0, warmup_cont=0, measure_every=1,
+                                       recompute_every=args.recompute_every)
+        s64 = q.QMCSystem(cfg64, wl.R)
+        s64.set_stream(stream.cuda_stream)
+        out64 = torch.zeros_like(out_dev)
+        s64.energy_forces_device(R_dev, out64)       # first call (warms code paths)
+        s64.sync()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        s64.energy_forces_device(R_dev, out64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        s64.sync()
+        t64 = f0.elapsed_time(f1) / 1e3
+        fp64 = {"value": W * N * args.fp64_sweeps / t64, "unit": "electron moves/s",
+                "force_evals_per_s": W * args.fp64_sweeps / t64,
+                "sample": f"{args.fp64_sweeps} sweeps + {args.fp64_sweeps} samples, {W} walkers",
+                "mixed_over_fp64": value / (W * N * args.fp64_sweeps / t64)}
+        s64.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = _cpu_baseline(wl)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "electron moves/s", "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32" if prec == q.QMC_MIXED else "f64", "data": "synthetic",
+               "config": {"workload": f"{args.workload}: N={N} H, r_s={wl.rs}, L={wl.L:.3f} bohr, "
+                                      f"{G} s-Gaussians/proton, {W} walkers x {cfg.sweeps} sweeps "
+                                      f"(+{cfg.warmup_cont} continuation), sample every sweep, "
+                                      f"{'mixed' if prec == q.QMC_MIXED else 'FP64'} form, "
+                                      f"FP64 inverse every {cfg.recompute_every} sweeps, "
+                                      "adjoint forces, Langevin step with S = Cov(f)",
+                          "walkers": W, "sweeps": cfg.sweeps, "parallelism": f"replicas x{ws}",
+                          "l2": "inputs larger than L2 (walker state "
+                                f"{q.footprint_bytes(cfg) / 1e9:.1f} GB per replica)"},
+               "force_evals_per_s": fevals,
+               "clocks": clk,
+               "e2e": {"value": e2e, "unit": "electron moves/s", "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
+               "gpu_launches": launches,
+               "roofline": roof,
+               "kernel_ms_per_step": breakdown,
+               "fp64_form": fp64,
+               "cpu_baseline": cpu,
+               "peaks": peak_kind,
+               "result": {"E": res["E"], "E_err": res["E_err"], "accept": res["accept"], "Nc": res["Nc"]}}
+        print(json.dumps(out), flush=True)
+    system.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = _args()
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

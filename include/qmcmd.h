@@ -165,6 +165,9 @@ int qmc_set_profiling(qmc_system* h, int on);
 int qmc_kernel_times(qmc_system* h, int n, double* ms, long long* launches);
 const char* qmc_kernel_name(int k);
 
+/* Number of CUDA kernels this handle has launched so far (monotonic). */
+long long qmc_launch_count(qmc_system* h);
+
 /* Text of an error code. */
 const char* qmc_strerror(int code);
 

@@ -99,6 +99,8 @@ __device__ __forceinline__ void raise_err(int* err, int bit) { atomicOr(err, bit
 // ---------------------------------------------------------------------------
 // Read-only view of one system on the device (passed by value to kernels).
 // ---------------------------------------------------------------------------
+template <typename T> struct V2 { T x, y; };
+
 template <typename T>
 struct SysView {
     int N, n, G, B, W;
@@ -108,12 +110,15 @@ struct SysView {
     const double* zeta;     // [G]
     const T* C;             // [B][n]
     const double* R;        // [N][3]
+    const T* RT;            // [N][3] in the working precision
     const T* ptrig;         // [N][6]: sin(pi R/L) xyz, cos(pi R/L) xyz
     int nk;                 // half-space reciprocal vectors
     int mmax;               // reciprocal cutoff |m| <= mmax
     const int4* kvec;       // [nk] (mx, my, mz, 0)
     const double* kw;       // [nk] (4 pi / L^3) exp(-k^2/4 kappa^2) / k^2
     const double2* eikR;    // [N][nk] exp(i k.R_a)
+    const V2<T>* eikRt;     // the same in the working precision
+    const T* kwt;           // kw in the working precision
     const double2* rho_p;   // [nk] sum_a Z exp(i k.R_a)
     const double* vconst;   // [1] proton-proton real-space + self energy
     const double* dvpp;     // [3N] d(proton-proton real-space energy)/dR
@@ -183,10 +188,10 @@ __device__ __forceinline__ void rho_to_t(T r, T u1, T u2, T u3, T& f1, T& f2, T&
 // minimum-image vector r0, phi(r) = erfc(kappa r)/r; optionally the gradient
 // with respect to r0.
 template <typename T>
-__device__ __forceinline__ T ewald_real(double dx, double dy, double dz, double L, T kappa, T* grad) {
-    dx -= L * rint(dx / L); dy -= L * rint(dy / L); dz -= L * rint(dz / L);
-    const T r0[3] = {(T)dx, (T)dy, (T)dz};
-    const T Lt = (T)L;
+__device__ __forceinline__ T ewald_real(T dx, T dy, T dz, T Lt, T kappa, T* grad) {
+    const T iL = T(1) / Lt;
+    dx -= Lt * rint(dx * iL); dy -= Lt * rint(dy * iL); dz -= Lt * rint(dz * iL);
+    const T r0[3] = {dx, dy, dz};
     T sh[3];
 #pragma unroll
     for (int m = 0; m < 3; ++m) sh[m] = r0[m] >= T(0) ? -Lt : Lt;

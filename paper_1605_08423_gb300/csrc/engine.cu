@@ -37,6 +37,8 @@ struct qmc_system {
     int4* d_kvec = nullptr;
     double2 *d_eikR = nullptr, *d_rhop = nullptr;
     double *d_vconst = nullptr, *d_dvpp = nullptr;
+    float *d_R32 = nullptr, *d_kw32 = nullptr;
+    float2* d_eikR32 = nullptr;
     // walkers
     double *d_X = nullptr, *d_Xp = nullptr;
     void *d_uacc = nullptr, *d_Phi = nullptr, *d_Gt = nullptr, *d_D = nullptr, *d_Lp = nullptr;
@@ -55,6 +57,7 @@ struct qmc_system {
     bool langevin_first = true;
     uint32_t langevin_step_no = 0;
     double last_Nc = 0.0;
+    long long nlaunch = 0;  // kernels launched by this handle
     bool profiling = false;
     std::vector<EventPair> events, free_events;
     double ktime[QMC_NKERNEL] = {0};
@@ -152,6 +155,9 @@ SysView<T> view(qmc_system* h, int W) {
     s.zeta = h->d_zeta;
     s.C = (const T*)(sizeof(T) == 8 ? (const void*)h->d_C64 : (const void*)h->d_C32);
     s.R = h->d_R;
+    s.RT = (const T*)(sizeof(T) == 8 ? (const void*)h->d_R : (const void*)h->d_R32);
+    s.eikRt = (const V2<T>*)(sizeof(T) == 8 ? (const void*)h->d_eikR : (const void*)h->d_eikR32);
+    s.kwt = (const T*)(sizeof(T) == 8 ? (const void*)h->d_kw : (const void*)h->d_kw32);
     s.ptrig = (const T*)(sizeof(T) == 8 ? (const void*)h->d_ptrig64 : (const void*)h->d_ptrig32);
     s.nk = h->nk; s.mmax = h->mmax;
     s.kvec = h->d_kvec; s.kw = h->d_kw; s.eikR = h->d_eikR; s.rho_p = h->d_rhop;
@@ -160,8 +166,9 @@ SysView<T> view(qmc_system* h, int W) {
 }
 
 void setup_tables(qmc_system* h) {
+    h->nlaunch += 5;
     launch_setup(h->N, h->p.L, h->p.ewald_kappa, h->nk, h->d_kvec, h->d_R, h->d_kw, h->d_ptrig64, h->d_ptrig32,
-                 h->d_eikR, h->d_rhop, h->d_vconst, h->d_dvpp, h->stream);
+                 h->d_eikR, h->d_rhop, h->d_vconst, h->d_dvpp, h->d_R32, h->d_eikR32, h->d_kw32, h->stream);
 }
 
 // Slater matrices at the current walker positions and their FP64 inverse.
@@ -170,6 +177,7 @@ void recompute(qmc_system* h, int W) {
     EventPair ep;
     prof_begin(h, KC_RECOMPUTE, ep);
     SysView<T> s = view<T>(h, W);
+    h->nlaunch += 2;
     launch_orbitals<T>(s, h->d_X, W * h->N, (T*)h->d_Phi, nullptr, nullptr, h->stream);
     launch_invert<T>(W, h->N, h->n, (const T*)h->d_Phi, (T*)h->d_Gt, h->d_logdet, h->d_err, h->stream);
     prof_end(h, ep);
@@ -179,6 +187,7 @@ template <typename T>
 void measure(qmc_system* h, int W, double* el, double* lnpsi, double* dl, double* de) {
     SysView<T> s = view<T>(h, W);
     EventPair ep;
+    h->nlaunch += 2;
     prof_begin(h, KC_ORB_MEAS, ep);
     launch_orbitals<T>(s, h->d_X, W * h->N, (T*)h->d_Phi, (T*)h->d_D, (T*)h->d_Lp, h->stream);
     prof_end(h, ep);
@@ -201,6 +210,7 @@ void run_call(qmc_system* h) {
     const int total = nw + h->p.n_sweeps;
     for (int sw = 0; sw < total; ++sw) {
         EventPair ep;
+        h->nlaunch += 3;
         prof_begin(h, KC_PROPOSE, ep);
         launch_propose<T>(W, N, h->d_X, h->d_Xp, (T*)h->d_uacc, key, md, (uint32_t)sw, h->p.sigma, h->stream);
         prof_end(h, ep);
@@ -217,6 +227,7 @@ void run_call(qmc_system* h) {
     EventPair ep;
     prof_begin(h, KC_REDUCE, ep);
     const double moves = (double)W * total * N;
+    h->nlaunch += 5;
     launch_reduce(W, N, moves, h->d_acc, h->d_nacc, h->d_colsum, h->d_dev, h->d_out, h->d_err, h->stream);
     prof_end(h, ep);
     h->last_Nc = (double)W * (h->p.n_sweeps / h->p.measure_every);
@@ -283,6 +294,9 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
     h->d_rhop = dalloc<double2>(h, nk, &rc);
     h->d_vconst = dalloc<double>(h, 1, &rc);
     h->d_dvpp = dalloc<double>(h, 3 * N, &rc);
+    h->d_R32 = dalloc<float>(h, 3 * N, &rc);
+    h->d_kw32 = dalloc<float>(h, nk, &rc);
+    h->d_eikR32 = dalloc<float2>(h, (size_t)N * nk, &rc);
     h->d_X = dalloc<double>(h, (size_t)W * 3 * N, &rc);
     h->d_Xp = dalloc<double>(h, (size_t)W * 3 * N, &rc);
     h->d_uacc = dalloc<unsigned char>(h, t * W * N, &rc);
@@ -401,6 +415,7 @@ int langevin_step_device(qmc_system* h, double* R_dev, const double* f_dev, cons
     if (!identity) a = alpha > 0 ? alpha : 0.122 * h->last_Nc;
     EventPair ep;
     prof_begin(h, KC_LANGEVIN, ep);
+    h->nlaunch += 1;
     launch_langevin(n3, R_dev, h->d_Rprev, f_dev, h->d_S, h->d_Sprev, h->d_Lwork, T_kelvin * kBoltzmannHaPerK, delta,
                     a, make_key(h->p.seed), h->langevin_step_no, h->p.L, identity, h->d_err, st);
     prof_end(h, ep);
@@ -489,6 +504,8 @@ int qmc_kernel_times(qmc_system* h, int n, double* ms, long long* launches) {
     for (int k = 0; k < QMC_NKERNEL; ++k) { h->ktime[k] = 0; h->klaunch[k] = 0; }
     return QMC_OK;
 }
+
+long long qmc_launch_count(qmc_system* h) { return h ? h->nlaunch : -1; }
 
 const char* qmc_kernel_name(int k) { return (k >= 0 && k < QMC_NKERNEL) ? kKernelNames[k] : "?"; }
 

@@ -21,15 +21,14 @@
 
 namespace qmc {
 
-template <typename T> struct V2 { T x, y; };
-
 template <typename T>
 struct MLayout {
-    size_t xs, et, gU, lU, Ui, gi, li, facc, rho, red, uni, total;
+    size_t xs, xt, et, gU, lU, Ui, gi, li, facc, rho, red, uni, total;
     __host__ __device__ MLayout(int N, int n, int nk, int mmax) {
         size_t o = 0;
         auto take = [&](size_t bytes) { size_t r = o; o = (o + bytes + 15) & ~size_t(15); return r; };
         xs = take(sizeof(double) * 3 * N);
+        xt = take(sizeof(T) * 3 * N);
         et = take(sizeof(T) * 6 * N);
         gU = take(sizeof(T) * 3 * N);
         lU = take(sizeof(T) * N);
@@ -46,6 +45,34 @@ struct MLayout {
     }
 };
 
+// One electron-proton pair: real-space Ewald value v = phi(r) summed over
+// images and its gradient g with respect to the electron-proton vector; the
+// e-n Jastrow contributions dl (to d ln psi/dR_a) and de (to dE_L/dR_a, given
+// vv = g_i + grad_i U).  sd, cd: sin, cos(pi (x - R_a)/L) per component.
+template <typename S>
+__device__ __forceinline__ void ep_pair(const S sd[3], const S cd[3], S ell, S k2, S bep, S Zj, S dx, S dy, S dz, S L,
+                                        S kap, const S vv[3], S& v, S g[3], S dl[3], S de[3]) {
+    S p[3], q[3], t = 0;
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) {
+        p[mu] = ell * sd[mu] * cd[mu];
+        q[mu] = cd[mu] * cd[mu] - sd[mu] * sd[mu];
+        t += sd[mu] * sd[mu];
+    }
+    t *= ell * ell;
+    const S r = qsqrt(t);
+    S u, u1, u2, u3, f1, f2, f3;
+    pade_ep(bep, Zj, r, u, u1, u2, u3);
+    rho_to_t(r, u1, u2, u3, f1, f2, f3);
+    RadialDerivs<S> rd;
+    radial_chain(p, q, f1, f2, f3, k2, rd);
+    S hv[3];
+    hess_mul(rd.h, vv, hv);
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) { dl[mu] = -rd.g[mu]; de[mu] = hv[mu] + S(0.5) * rd.tl[mu]; }
+    v = ewald_real<S>(dx, dy, dz, L, kap, g);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, const double* __restrict__ X,
                                                       const T* __restrict__ D, const T* __restrict__ Lp,
@@ -57,6 +84,7 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
     const int N = s.N, n = s.n, G = s.G, nk = s.nk;
     const MLayout<T> lay(N, n, nk, mmax);
     double* xs = (double*)(sm + lay.xs);
+    T* xt = (T*)(sm + lay.xt);
     T* et = (T*)(sm + lay.et);
     T* gU = (T*)(sm + lay.gU);
     T* lU = (T*)(sm + lay.lU);
@@ -81,6 +109,7 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
     for (int idx = tid; idx < 3 * N; idx += nt) {
         const double x = X[(size_t)w * 3 * N + idx];
         xs[idx] = x;
+        xt[idx] = (T)x;
         T sn, cs;
         qsincospi((T)(x / L), &sn, &cs);
         et[6 * (idx / 3) + idx % 3] = sn;
@@ -165,24 +194,62 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
 
     // ---- P4a: electron-electron real-space Ewald
     double vee_p = 0.0;
-    for (int i = tid; i < N; i += nt)
+    const T Lt = (T)L;
+    for (int i = tid; i < N; i += nt) {
+        T v = 0;
         for (int j = i + 1; j < N; ++j)
-            vee_p += (double)ewald_real<T>(xs[3 * i] - xs[3 * j], xs[3 * i + 1] - xs[3 * j + 1],
-                                           xs[3 * i + 2] - xs[3 * j + 2], L, kap, nullptr);
-    // ---- P4b: electron-proton real-space Ewald and its R-gradient (warp per proton)
+            v += ewald_real<T>(xt[3 * i] - xt[3 * j], xt[3 * i + 1] - xt[3 * j + 1], xt[3 * i + 2] - xt[3 * j + 2], Lt,
+                               kap, nullptr);
+        vee_p += (double)v;
+    }
+    // ---- P4b: electron-proton pairs (warp per proton, lanes over electrons): the
+    // real-space Ewald energy and its R-gradient (Hellmann-Feynman) together with
+    // the e-n Jastrow terms of d ln psi/dR and dE_L/dR.  In the mixed form, pairs
+    // closer than 0.3 bohr are evaluated and summed in FP64: there the 1/r^2
+    // Coulomb force and the 1/r^2 part of grad lap u_en cancel (cusp condition),
+    // and FP32 rounding of either term would survive the cancellation.
     double vep_p = 0.0;
     for (int a = warp; a < N; a += nw) {
-        T v = 0, gx = 0, gy = 0, gz = 0;
+        T v = 0, gv[3] = {0, 0, 0}, dl[3] = {0, 0, 0}, de[3] = {0, 0, 0};
+        double vC = 0, gC[3] = {0, 0, 0}, dlC[3] = {0, 0, 0}, deC[3] = {0, 0, 0};
+        const T* pa = s.ptrig + 6 * a;
         for (int i = lane; i < N; i += 32) {
-            T gr[3];
-            v += ewald_real<T>(xs[3 * i] - s.R[3 * a], xs[3 * i + 1] - s.R[3 * a + 1], xs[3 * i + 2] - s.R[3 * a + 2],
-                               L, kap, gr);
-            gx += gr[0]; gy += gr[1]; gz += gr[2];
+            const double dx = xs[3 * i] - s.R[3 * a], dy = xs[3 * i + 1] - s.R[3 * a + 1],
+                         dz = xs[3 * i + 2] - s.R[3 * a + 2];
+            T sd[3], cd[3], t;
+            disp_trig(et + 6 * i, pa, ell, sd, cd, t);
+            if (sizeof(T) == 4 && t < T(0.09)) {
+                double sdd[3], cdd[3], vv[3], pv, pg[3], pl[3], pe[3];
+                sincospi(dx / L, &sdd[0], &cdd[0]);
+                sincospi(dy / L, &sdd[1], &cdd[1]);
+                sincospi(dz / L, &sdd[2], &cdd[2]);
+                for (int mu = 0; mu < 3; ++mu) vv[mu] = (double)gi[3 * i + mu] + (double)gU[3 * i + mu];
+                ep_pair<double>(sdd, cdd, s.ell, (double)k2, s.b_ep, s.Zj, dx, dy, dz, L, s.kappa, vv, pv, pg, pl, pe);
+                vC += pv;
+                for (int mu = 0; mu < 3; ++mu) { gC[mu] += pg[mu]; dlC[mu] += pl[mu]; deC[mu] += pe[mu]; }
+            } else {
+                T vv[3], pv, pg[3], pl[3], pe[3];
+                for (int mu = 0; mu < 3; ++mu) vv[mu] = gi[3 * i + mu] + gU[3 * i + mu];
+                const T* ra = s.RT + 3 * a;
+                ep_pair<T>(sd, cd, ell, k2, bep, Zj, xt[3 * i] - ra[0], xt[3 * i + 1] - ra[1], xt[3 * i + 2] - ra[2],
+                           Lt, kap, vv, pv, pg, pl, pe);
+                v += pv;
+                for (int mu = 0; mu < 3; ++mu) { gv[mu] += pg[mu]; dl[mu] += pl[mu]; de[mu] += pe[mu]; }
+            }
         }
-        v = warp_sum(v); gx = warp_sum(gx); gy = warp_sum(gy); gz = warp_sum(gz);
+        v = warp_sum(v); vC = warp_sum(vC);
+#pragma unroll
+        for (int mu = 0; mu < 3; ++mu) {
+            gv[mu] = warp_sum(gv[mu]); dl[mu] = warp_sum(dl[mu]); de[mu] = warp_sum(de[mu]);
+            gC[mu] = warp_sum(gC[mu]); dlC[mu] = warp_sum(dlC[mu]); deC[mu] = warp_sum(deC[mu]);
+        }
         if (lane == 0) {
-            vep_p += -Zn * (double)v;
-            f_dv[3 * a] += Zn * (double)gx; f_dv[3 * a + 1] += Zn * (double)gy; f_dv[3 * a + 2] += Zn * (double)gz;
+            vep_p += -Zn * ((double)v + vC);
+            for (int mu = 0; mu < 3; ++mu) {
+                f_dv[3 * a + mu] += Zn * ((double)gv[mu] + gC[mu]);
+                f_dl[3 * a + mu] += (double)dl[mu] + dlC[mu];
+                f_de[3 * a + mu] += (double)de[mu] + deC[mu];
+            }
         }
     }
     // ---- P4c: reciprocal space: electron structure factor from per-electron phase tables
@@ -222,9 +289,9 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
     for (int a = warp; a < N; a += nw) {
         T gx = 0, gy = 0, gz = 0;
         for (int k = lane; k < nk; k += 32) {
-            const double2 e = s.eikR[(size_t)a * nk + k];
-            const double2 r = rho[k];
-            const T c = (T)(2.0 * Zn * s.kw[k] * (r.y * e.x - r.x * e.y));
+            const V2<T> e = s.eikRt[(size_t)a * nk + k];
+            const double2 rd = rho[k];
+            const T c = T(2) * (T)Zn * s.kwt[k] * ((T)rd.y * e.x - (T)rd.x * e.y);
             const int4 m = s.kvec[k];
             gx += c * twopiL * (T)m.x; gy += c * twopiL * (T)m.y; gz += c * twopiL * (T)m.z;
         }
@@ -235,33 +302,6 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
     const double vep = block_sum(vep_p, red + 32);
     const double vrec = block_sum(vrec_p, red);
 
-    // ---- P5: e-n Jastrow terms of d ln psi / dR and dE_L / dR (warp per proton)
-    for (int a = warp; a < N; a += nw) {
-        T dl[3] = {0, 0, 0}, de[3] = {0, 0, 0};
-        const T* pa = s.ptrig + 6 * a;
-        for (int i = lane; i < N; i += 32) {
-            T sd[3], cd[3], t, p[3], q[3];
-            disp_trig(et + 6 * i, pa, ell, sd, cd, t);
-#pragma unroll
-            for (int mu = 0; mu < 3; ++mu) { p[mu] = ell * sd[mu] * cd[mu]; q[mu] = cd[mu] * cd[mu] - sd[mu] * sd[mu]; }
-            const T r = qsqrt(t);
-            T u, u1, u2, u3, f1, f2, f3;
-            pade_ep(bep, Zj, r, u, u1, u2, u3);
-            rho_to_t(r, u1, u2, u3, f1, f2, f3);
-            RadialDerivs<T> rd;
-            radial_chain(p, q, f1, f2, f3, k2, rd);
-            T v[3], hv[3];
-#pragma unroll
-            for (int mu = 0; mu < 3; ++mu) v[mu] = gi[3 * i + mu] + gU[3 * i + mu];
-            hess_mul(rd.h, v, hv);
-#pragma unroll
-            for (int mu = 0; mu < 3; ++mu) { dl[mu] -= rd.g[mu]; de[mu] += hv[mu] + T(0.5) * rd.tl[mu]; }
-        }
-#pragma unroll
-        for (int mu = 0; mu < 3; ++mu) { dl[mu] = warp_sum(dl[mu]); de[mu] = warp_sum(de[mu]); }
-        if (lane == 0)
-            for (int mu = 0; mu < 3; ++mu) { f_dl[3 * a + mu] += (double)dl[mu]; f_de[3 * a + mu] += (double)de[mu]; }
-    }
     __syncthreads();
 
     // ---- P6: orbital (Pulay) terms, one spin block at a time

@@ -10,9 +10,11 @@
 
 namespace qmc {
 
-__global__ void ptrig_kernel(int N, double L, const double* __restrict__ R, double* ptrig64, float* ptrig32) {
+__global__ void ptrig_kernel(int N, double L, const double* __restrict__ R, double* ptrig64, float* ptrig32,
+                             float* R32) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * N) return;
+    R32[t] = (float)R[t];
     const int a = t / 3, mu = t % 3;
     double sn, cs;
     sincospi(R[t] / L, &sn, &cs);
@@ -21,7 +23,7 @@ __global__ void ptrig_kernel(int N, double L, const double* __restrict__ R, doub
 }
 
 __global__ void eikr_kernel(int N, int nk, double L, const int4* __restrict__ kvec, const double* __restrict__ R,
-                            double2* eikR) {
+                            double2* eikR, float2* eikR32) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N * nk) return;
     const int a = t / nk, k = t - a * nk;
@@ -30,6 +32,7 @@ __global__ void eikr_kernel(int N, int nk, double L, const int4* __restrict__ kv
     double sn, cs;
     sincospi(ph, &sn, &cs);
     eikR[t] = make_double2(cs, sn);
+    eikR32[t] = make_float2((float)cs, (float)sn);
 }
 
 __global__ void rhop_kernel(int N, int nk, const double2* __restrict__ eikR, double2* rho_p) {
@@ -61,21 +64,22 @@ __global__ void pp_kernel(int N, double L, double kappa, const double* __restric
 }
 
 // Reciprocal weights (4 pi / L^3) exp(-k^2 / 4 kappa^2) / k^2 of the half-space vectors.
-__global__ void kw_kernel(int nk, double L, double kappa, const int4* __restrict__ kvec, double* kw) {
+__global__ void kw_kernel(int nk, double L, double kappa, const int4* __restrict__ kvec, double* kw, float* kw32) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nk) return;
     const int4 m = kvec[k];
     const double tp = 2.0 * kPi / L;
     const double k2 = tp * tp * (double)(m.x * m.x + m.y * m.y + m.z * m.z);
     kw[k] = 4.0 * kPi / (L * L * L) * exp(-k2 / (4.0 * kappa * kappa)) / k2;
+    kw32[k] = (float)kw[k];
 }
 
 void launch_setup(int N, double L, double kappa, int nk, const int4* kvec, const double* R, double* kw,
                   double* ptrig64, float* ptrig32, double2* eikR, double2* rho_p, double* vconst, double* dvpp,
-                  cudaStream_t st) {
-    kw_kernel<<<(nk + 127) / 128, 128, 0, st>>>(nk, L, kappa, kvec, kw);
-    ptrig_kernel<<<(3 * N + 127) / 128, 128, 0, st>>>(N, L, R, ptrig64, ptrig32);
-    eikr_kernel<<<(N * nk + 255) / 256, 256, 0, st>>>(N, nk, L, kvec, R, eikR);
+                  float* R32, float2* eikR32, float* kw32, cudaStream_t st) {
+    kw_kernel<<<(nk + 127) / 128, 128, 0, st>>>(nk, L, kappa, kvec, kw, kw32);
+    ptrig_kernel<<<(3 * N + 127) / 128, 128, 0, st>>>(N, L, R, ptrig64, ptrig32, R32);
+    eikr_kernel<<<(N * nk + 255) / 256, 256, 0, st>>>(N, nk, L, kvec, R, eikR, eikR32);
     rhop_kernel<<<(nk + 127) / 128, 128, 0, st>>>(N, nk, eikR, rho_p);
     pp_kernel<<<1, 256, 0, st>>>(N, L, kappa, R, vconst, dvpp);
 }

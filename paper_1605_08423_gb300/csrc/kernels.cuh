@@ -39,7 +39,7 @@ size_t measure_smem_bytes(int N, int n, int nk, int mmax);
 // k_setup.cu: per-R tables (proton trig, structure factors, p-p Ewald terms).
 void launch_setup(int N, double L, double kappa, int nk, const int4* kvec, const double* R, double* kw,
                   double* ptrig64, float* ptrig32, double2* eikR, double2* rho_p, double* vconst, double* dvpp,
-                  cudaStream_t st);
+                  float* R32, float2* eikR32, float* kw32, cudaStream_t st);
 
 // k_reduce.cu: walker reductions and the covariance matrix.
 void launch_reduce(int W, int N, double moves, const double* acc, const unsigned long long* nacc,

@@ -77,6 +77,8 @@ def lib():
         L.qmc_set_md_step.argtypes = [vp, C.c_uint32]
         L.qmc_set_profiling.argtypes = [vp, C.c_int]
         L.qmc_kernel_times.argtypes = [vp, C.c_int, _dp, C.POINTER(C.c_longlong)]
+        L.qmc_launch_count.argtypes = [vp]
+        L.qmc_launch_count.restype = C.c_longlong
         L.qmc_kernel_name.argtypes = [C.c_int]
         L.qmc_kernel_name.restype = C.c_char_p
         L.qmc_strerror.argtypes = [C.c_int]
@@ -226,6 +228,9 @@ class QMCSystem:
 
     def set_profiling(self, on: bool):
         _chk(lib().qmc_set_profiling(self._h, int(on)), "qmc_set_profiling")
+
+    def launch_count(self) -> int:
+        return int(lib().qmc_launch_count(self._h))
 
     def kernel_times(self) -> dict:
         ms = np.zeros(NKERNEL)
