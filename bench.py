@@ -105,12 +105,12 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def _flops_per_launch(cls: str, W, N, n, B, G, acc_ratio):
+def _flops_per_launch(cls: str, W, N, n, B, G, acc_ratio, use_tc):
     """Algorithmic FLOPs of one launch of a kernel class (dense multiply-adds x 2)."""
     if cls == "orbitals_prop":
         return 2.0 * W * N * B * n
-    if cls == "orbitals_meas":
-        return 10.0 * W * N * B * n
+    if cls == "orbitals_meas":   # grad (3) + Laplacian on the tensor cores; SIMT also forms the values
+        return (8.0 if use_tc else 10.0) * W * N * B * n
     if cls == "measure":
         return 2.0 * W * (4.0 * n ** 3 + 4.0 * N * G * n * n)
     if cls == "sweep":
@@ -246,22 +246,33 @@ def run_ours(args, ws, rank, local):
     h2d = 8 * (N3 + N3 + N3 + N3 * N3)
     d2h = 8 * (4 + N3 + N3 * N3 + N3)
 
-    # roofline of the dominant kernel class
+    # roofline of every kernel class with an algorithmic FLOP count; the dominant one is "roofline"
     peaks, peak_kind = _peaks()
-    dom = max(kt, key=lambda k: kt[k][0])
-    dms, dl = kt[dom]
-    fl = _flops_per_launch(dom, W, N, n, B, G, float(res["accept"]))
     sm_clock = (clk.get("sm_max_mhz") or 2070.0) * 1e6
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_clock / 1e12
-    if fl is not None and dl > 0:
-        achieved = fl / (dms / dl / 1e3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None,
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock",
-                "flops_per_launch": fl, "avg_launch_ms": dms / dl}
-    else:
-        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": None, "traffic": None}
+    bf16_sust = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    tf32_peak = bf16_sust * (1.1 / 2.25)      # nominal TF32 / BF16 dense ratio
+    use_tc = prec == q.QMC_MIXED
+    roofs = {}
+    for cls, (cms, cl) in kt.items():
+        fl = _flops_per_launch(cls, W, N, n, B, G, float(res["accept"]), use_tc)
+        if fl is None or cl == 0:
+            continue
+        avg = cms / cl
+        ach = fl / (avg / 1e3) / 1e12
+        if use_tc and cls.startswith("orbitals"):
+            roofs[cls] = {"kernel": cls, "bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
+                          "frac": ach / tf32_peak, "traffic": None,
+                          "peak_source": f"TF32 = {peak_kind} bf16 sustained x 1.1/2.25 (nominal ratio)",
+                          "flops_per_launch": fl, "tensor_pipe_flops_per_launch": 6 * fl, "avg_launch_ms": avg}
+        else:
+            roofs[cls] = {"kernel": cls, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                          "frac": ach / fp32_peak, "traffic": None,
+                          "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock",
+                          "flops_per_launch": fl, "avg_launch_ms": avg}
+    dom = max(kt, key=lambda k: kt[k][0])
+    roof = roofs.get(dom, {"kernel": dom, "bound": "alu", "achieved": None, "peak": fp32_peak,
+                           "unit": "TFLOP/s", "frac": None, "traffic": None})
     breakdown = {k: {"ms": v[0] / args.steps, "launches": v[1] // max(args.steps, 1)} for k, v in kt.items()}
 
     # FP64 form on the same system (short burst) for the "vs FP64 form" comparison
@@ -312,6 +323,7 @@ def run_ours(args, ws, rank, local):
                        "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
                "gpu_launches": launches,
                "roofline": roof,
+               "rooflines": roofs,
                "kernel_ms_per_step": breakdown,
                "fp64_form": fp64,
                "cpu_baseline": cpu,

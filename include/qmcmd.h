@@ -154,6 +154,13 @@ int qmc_set_walkers(qmc_system* h, const double* X);
  * [count, sum E_L, sum E_L^2, sum dlnpsi/dR (3N), sum E_L dlnpsi/dR (3N), sum dE_L/dR (3N)]. */
 int qmc_get_accumulators(qmc_system* h, double* acc);
 
+/* Handle options.  QMC_OPT_TENSOR_CORES (mixed form only, default 1): evaluate
+ * the orbital contractions with the tcgen05 tensor-core kernel (3xTF32 split,
+ * FP32-level accuracy); 0 selects the SIMT FP32 kernel.  INVALID for an
+ * unknown option or when the form has no tensor-core kernel. */
+enum { QMC_OPT_TENSOR_CORES = 1 };
+int qmc_set_option(qmc_system* h, int option, int value);
+
 /* Set the MD step counter used in the Philox counters of the next call. */
 int qmc_set_md_step(qmc_system* h, uint32_t md_step);
 

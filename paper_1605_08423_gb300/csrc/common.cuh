@@ -104,6 +104,7 @@ template <typename T> struct V2 { T x, y; };
 template <typename T>
 struct SysView {
     int N, n, G, B, W;
+    int np;                 // n padded to a power of two >= 4 (tiled products)
     double L, ell;          // box side, L/pi
     double b_ee, b_ep, Zj;  // Jastrow parameters (Zj = e-n cusp amplitude)
     double kappa;           // Ewald splitting

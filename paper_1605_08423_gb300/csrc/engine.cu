@@ -39,6 +39,8 @@ struct qmc_system {
     double *d_vconst = nullptr, *d_dvpp = nullptr;
     float *d_R32 = nullptr, *d_kw32 = nullptr;
     float2* d_eikR32 = nullptr;
+    void* d_chat = nullptr;    // C^T chunks, TF32 hi/lo, swizzled (tensor-core orbital kernel)
+    bool use_tc = false;
     // walkers
     double *d_X = nullptr, *d_Xp = nullptr;
     void *d_uacc = nullptr, *d_Phi = nullptr, *d_Gt = nullptr, *d_D = nullptr, *d_Lp = nullptr;
@@ -150,6 +152,8 @@ template <typename T>
 SysView<T> view(qmc_system* h, int W) {
     SysView<T> s;
     s.N = h->N; s.n = h->n; s.G = h->G; s.B = h->B; s.W = W;
+    s.np = 4;
+    while (s.np < s.n) s.np *= 2;
     s.L = h->p.L; s.ell = h->p.L / kPi;
     s.b_ee = h->p.b_ee; s.b_ep = h->p.b_ep; s.Zj = 1.0; s.kappa = h->p.ewald_kappa;
     s.zeta = h->d_zeta;
@@ -171,6 +175,16 @@ void setup_tables(qmc_system* h) {
                  h->d_eikR, h->d_rhop, h->d_vconst, h->d_dvpp, h->d_R32, h->d_eikR32, h->d_kw32, h->stream);
 }
 
+// Orbital rows at `pos`: tensor-core kernel in the mixed form, SIMT otherwise.
+template <typename T>
+void orbitals(qmc_system* h, const SysView<T>& s, const double* pos, int nrows, T* val, T* grad, T* lap) {
+    if (sizeof(T) == 4 && h->use_tc)
+        launch_orbitals_tc(*(const SysView<float>*)&s, h->d_chat, pos, nrows, (float*)val, (float*)grad, (float*)lap,
+                           h->stream);
+    else
+        launch_orbitals<T>(s, pos, nrows, val, grad, lap, h->stream);
+}
+
 // Slater matrices at the current walker positions and their FP64 inverse.
 template <typename T>
 void recompute(qmc_system* h, int W) {
@@ -178,7 +192,7 @@ void recompute(qmc_system* h, int W) {
     prof_begin(h, KC_RECOMPUTE, ep);
     SysView<T> s = view<T>(h, W);
     h->nlaunch += 2;
-    launch_orbitals<T>(s, h->d_X, W * h->N, (T*)h->d_Phi, nullptr, nullptr, h->stream);
+    orbitals<T>(h, s, h->d_X, W * h->N, (T*)h->d_Phi, nullptr, nullptr);
     launch_invert<T>(W, h->N, h->n, (const T*)h->d_Phi, (T*)h->d_Gt, h->d_logdet, h->d_err, h->stream);
     prof_end(h, ep);
 }
@@ -189,7 +203,7 @@ void measure(qmc_system* h, int W, double* el, double* lnpsi, double* dl, double
     EventPair ep;
     h->nlaunch += 2;
     prof_begin(h, KC_ORB_MEAS, ep);
-    launch_orbitals<T>(s, h->d_X, W * h->N, (T*)h->d_Phi, (T*)h->d_D, (T*)h->d_Lp, h->stream);
+    orbitals<T>(h, s, h->d_X, W * h->N, (T*)h->d_Phi, (T*)h->d_D, (T*)h->d_Lp);
     prof_end(h, ep);
     prof_begin(h, KC_MEASURE, ep);
     launch_measure<T>(s, h->d_X, (const T*)h->d_D, (const T*)h->d_Lp, (const T*)h->d_Gt, h->d_logdet, h->d_acc, el,
@@ -215,7 +229,7 @@ void run_call(qmc_system* h) {
         launch_propose<T>(W, N, h->d_X, h->d_Xp, (T*)h->d_uacc, key, md, (uint32_t)sw, h->p.sigma, h->stream);
         prof_end(h, ep);
         prof_begin(h, KC_ORB_PROP, ep);
-        launch_orbitals<T>(s, h->d_Xp, W * N, (T*)h->d_Phi, nullptr, nullptr, h->stream);
+        orbitals<T>(h, s, h->d_Xp, W * N, (T*)h->d_Phi, nullptr, nullptr);
         prof_end(h, ep);
         prof_begin(h, KC_SWEEP, ep);
         launch_sweep<T>(s, h->d_X, h->d_Xp, (const T*)h->d_uacc, (const T*)h->d_Phi, (T*)h->d_Gt, h->d_nacc,
@@ -318,6 +332,10 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
     h->d_Sprev = dalloc<double>(h, 9 * (size_t)N * N, &rc);
     h->d_Lwork = dalloc<double>(h, 9 * (size_t)N * N, &rc);
     h->d_err = dalloc<int>(h, 1, &rc);
+    if (h->mixed && tc_orbitals_supported(n, B)) {
+        h->d_chat = dalloc<unsigned char>(h, tc_coeff_bytes(B, n), &rc);
+        h->use_tc = true;
+    }
     if (rc != QMC_OK) { qmc_destroy(h); return rc; }
     std::vector<float> c32(h->coeff_h.begin(), h->coeff_h.end());
     cudaStream_t st = h->stream;
@@ -328,6 +346,7 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
     cudaMemcpyAsync(h->d_kvec, kv.data(), sizeof(int4) * nk, cudaMemcpyHostToDevice, st);
     cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
     cudaMemsetAsync(h->d_nacc, 0, sizeof(unsigned long long) * W, st);
+    if (h->d_chat) prepare_tc_coeff(h->d_C32, B, n, h->d_chat, st);
     setup_tables(h);
     launch_init_walkers(W, N, p->L, h->d_R, h->d_X, make_key(p->seed), st);
     rc = check_launch();
@@ -479,6 +498,16 @@ int qmc_get_accumulators(qmc_system* h, double* acc) {
     if (!h || !acc) return QMC_ERR_INVALID;
     cudaMemcpyAsync(acc, h->d_acc, sizeof(double) * (size_t)h->W * (3 + 9 * h->N), cudaMemcpyDeviceToHost, h->stream);
     return read_err(h);
+}
+
+int qmc_set_option(qmc_system* h, int option, int value) {
+    if (!h) return QMC_ERR_INVALID;
+    if (option == QMC_OPT_TENSOR_CORES) {
+        if (value && !h->d_chat) return QMC_ERR_INVALID;
+        h->use_tc = value != 0;
+        return QMC_OK;
+    }
+    return QMC_ERR_INVALID;
 }
 
 int qmc_set_profiling(qmc_system* h, int on) {

@@ -23,7 +23,7 @@ namespace qmc {
 
 template <typename T>
 struct MLayout {
-    size_t xs, xt, et, gU, lU, Ui, gi, li, facc, rho, red, uni, total;
+    size_t xs, xt, et, gU, lU, Ui, gi, li, facc, rho, red, stage, uni, total;
     __host__ __device__ MLayout(int N, int n, int nk, int mmax) {
         size_t o = 0;
         auto take = [&](size_t bytes) { size_t r = o; o = (o + bytes + 15) & ~size_t(15); return r; };
@@ -38,9 +38,14 @@ struct MLayout {
         facc = take(sizeof(double) * 9 * N);
         rho = take(sizeof(double2) * nk);
         red = take(sizeof(double) * 64);
+        stage = take(sizeof(double) * 64 * 6);
         const size_t etab = sizeof(V2<T>) * (size_t)N * 3 * (2 * mmax + 1);
-        const size_t spin = sizeof(T) * 3 * (size_t)n * (n + 1);
-        uni = take(etab > spin ? etab : spin);
+        int np = 4;
+        while (np < n) np *= 2;
+        const size_t spin = sizeof(T) * (size_t)np * (3 * (np + 4) + 68);
+        const size_t jpart = sizeof(T) * 5 * 256;   // P1 partials: nparts * N <= 256 rows of 5
+        size_t u = etab > spin ? etab : spin;
+        uni = take(u > jpart ? u : jpart);
         total = o;
     }
 };
@@ -96,6 +101,7 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
     double* f_dv = f_de + 3 * N;
     double2* rho = (double2*)(sm + lay.rho);
     double* red = (double*)(sm + lay.red);
+    double* stage = (double*)(sm + lay.stage);
     unsigned char* uni = sm + lay.uni;
 
     const int w = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
@@ -118,11 +124,17 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
     for (int idx = tid; idx < 9 * N; idx += nt) f_dl[idx] = 0.0;
     __syncthreads();
 
-    // ---- P1: Jastrow gradient / Laplacian per electron, U partial sums
-    for (int i = tid; i < N; i += nt) {
+    // ---- P1: Jastrow gradient / Laplacian per electron, U partial sums.  The
+    // partner range is split into nparts slices so that every thread works;
+    // the slices are summed in order afterwards.
+    const int nparts = nt >= N ? nt / N : 1;
+    T* jpart = (T*)uni;
+    for (int tt = tid; tt < nparts * N; tt += nt) {
+        const int i = tt % N, pi = tt / N;
+        const int j0 = (N * pi) / nparts, j1 = (N * (pi + 1)) / nparts;
         T g[3] = {0, 0, 0}, lp = 0, ui = 0;
         const T* ei = et + 6 * i;
-        for (int j = 0; j < N; ++j) {
+        for (int j = j0; j < j1; ++j) {
             if (j == i) continue;
             T sd[3], cd[3], t;
             disp_trig(ei, et + 6 * j, ell, sd, cd, t);
@@ -140,7 +152,7 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
             lp += T(4) * f2 * pp + T(2) * f1 * sq;
             if (j > i) ui += u;
         }
-        for (int a = 0; a < N; ++a) {
+        for (int a = j0; a < j1; ++a) {
             T sd[3], cd[3], t;
             disp_trig(ei, s.ptrig + 6 * a, ell, sd, cd, t);
             const T r = qsqrt(t);
@@ -157,8 +169,17 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
             lp += T(4) * f2 * pp + T(2) * f1 * sq;
             ui += u;
         }
-        gU[3 * i] = g[0]; gU[3 * i + 1] = g[1]; gU[3 * i + 2] = g[2];
-        lU[i] = lp; Ui[i] = ui;
+        T* o = jpart + ((size_t)pi * N + i) * 5;
+        o[0] = g[0]; o[1] = g[1]; o[2] = g[2]; o[3] = lp; o[4] = ui;
+    }
+    __syncthreads();
+    for (int i = tid; i < N; i += nt) {
+        T v[5] = {0, 0, 0, 0, 0};
+        for (int pi = 0; pi < nparts; ++pi)
+#pragma unroll
+            for (int c = 0; c < 5; ++c) v[c] += jpart[((size_t)pi * N + i) * 5 + c];
+        gU[3 * i] = v[0]; gU[3 * i + 1] = v[1]; gU[3 * i + 2] = v[2];
+        lU[i] = v[3]; Ui[i] = v[4];
     }
 
     // ---- P2: g_i = sum_j D_ij G_ji, l_i = sum_j Lp_ij G_ji
@@ -195,11 +216,18 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
     // ---- P4a: electron-electron real-space Ewald
     double vee_p = 0.0;
     const T Lt = (T)L;
-    for (int i = tid; i < N; i += nt) {
+    // balanced cyclic pairing: electron i with i+d (mod N), d = 1..N/2 (d = N/2 only for i < N/2),
+    // the distance range split into nparts slices
+    for (int tt = tid; tt < nparts * N; tt += nt) {
+        const int i = tt % N, pi = tt / N, half = N / 2;
+        const int d0 = 1 + (half * pi) / nparts, d1 = 1 + (half * (pi + 1)) / nparts;
         T v = 0;
-        for (int j = i + 1; j < N; ++j)
+        for (int d = d0; d < d1; ++d) {
+            if (2 * d == N && i >= half) continue;
+            const int j = (i + d) % N;
             v += ewald_real<T>(xt[3 * i] - xt[3 * j], xt[3 * i + 1] - xt[3 * j + 1], xt[3 * i + 2] - xt[3 * j + 2], Lt,
                                kap, nullptr);
+        }
         vee_p += (double)v;
     }
     // ---- P4b: electron-proton pairs (warp per proton, lanes over electrons): the
@@ -304,75 +332,158 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
 
     __syncthreads();
 
-    // ---- P6: orbital (Pulay) terms, one spin block at a time
-    const int ld = n + 1;
-    T* Gs = (T*)uni;
-    T* Ys = Gs + (size_t)n * ld;
-    T* Ks = Ys + (size_t)n * ld;
+    // ---- P6: orbital (Pulay) terms, one spin block at a time.  All n x n and
+    // B x n products are register-tiled 4 x 4 per thread on a zero-padded
+    // np x np block (np = padded n, a power of two >= 4):
+    //   M1 = Y G,  K = G M1  (= G Y G),  Z = C G,  P = C K  (per 64-row tile of C)
+    // and the basis-derivative contraction is fused onto each Z/P tile.
+    const int np = s.np, ldt = np + 4, ng = np / 4;
+    T* bufA = (T*)uni;                       // Y^T [j][i], later K [j][i]
+    T* bufG = bufA + (size_t)np * ldt;       // G   [j][i] = G_{j,i}
+    T* bufS = bufG + (size_t)np * ldt;       // G^T [i][j], later C^T tile [j][b] (stride 68)
+    T* bufM = bufS + (size_t)np * 68;        // M1  [i][i']
     for (int sp = 0; sp < 2; ++sp) {
         const T* Gsp = Gt + ((size_t)w * 2 + sp) * n * n;
-        for (int idx = tid; idx < n * n; idx += nt) {
-            const int il = idx / n, j = idx - il * n, i = sp * n + il;
-            Gs[il * ld + j] = Gsp[idx];
-            const size_t rr = (size_t)w * N + i;
-            const T* dr = D + rr * 3 * n;
-            Ys[il * ld + j] = T(-0.5) * Lp[rr * n + j] -
-                              (gU[3 * i] * dr[j] + gU[3 * i + 1] * dr[n + j] + gU[3 * i + 2] * dr[2 * n + j]);
-        }
-        __syncthreads();
-        for (int idx = tid; idx < n * n; idx += nt) {          // M1 = Y G  ->  Ks
-            const int il = idx / n, ip = idx - il * n;
-            T acc_ = 0;
-            for (int j = 0; j < n; ++j) acc_ += Ys[il * ld + j] * Gs[ip * ld + j];
-            Ks[il * ld + ip] = acc_;
-        }
-        __syncthreads();
-        for (int idx = tid; idx < n * n; idx += nt) {          // (G M1)^T -> Ys : Kt[ip][j] = sum_i G_ji M1[i][ip]
-            const int ip = idx / n, j = idx - ip * n;
-            T acc_ = 0;
-            for (int i = 0; i < n; ++i) acc_ += Gs[i * ld + j] * Ks[i * ld + ip];
-            Ys[ip * ld + j] = acc_;
-        }
-        __syncthreads();
-        for (int a = warp; a < N; a += nw) {
-            T dl[3] = {0, 0, 0}, de[3] = {0, 0, 0};
-            const T* pa = s.ptrig + 6 * a;
-            for (int il = lane; il < n; il += 32) {
+        for (int idx = tid; idx < np * np; idx += nt) {
+            const int il = idx / np, j = idx - il * np;
+            T g = 0, y = 0;
+            if (il < n && j < n) {
                 const int i = sp * n + il;
-                T sd[3], cd[3], t, p[3], q[3];
-                disp_trig(et + 6 * i, pa, ell, sd, cd, t);
+                g = Gsp[il * n + j];
+                const size_t rr = (size_t)w * N + i;
+                const T* dr = D + rr * 3 * n;
+                y = T(-0.5) * Lp[rr * n + j] - (gU[3 * i] * dr[j] + gU[3 * i + 1] * dr[n + j] + gU[3 * i + 2] * dr[2 * n + j]);
+            }
+            bufS[il * ldt + j] = g;
+            bufG[j * ldt + il] = g;
+            bufA[j * ldt + il] = y;
+        }
+        __syncthreads();
+        if (tid < ng * ng) {                     // M1[i][i'] = sum_j Y[i][j] G[j][i']
+            const int r0 = 4 * (tid / ng), c0 = 4 * (tid % ng);
+            T acc4[4][4] = {};
+            for (int j = 0; j < np; ++j) {
+                T y4[4], g4[4];
 #pragma unroll
-                for (int mu = 0; mu < 3; ++mu) { p[mu] = ell * sd[mu] * cd[mu]; q[mu] = cd[mu] * cd[mu] - sd[mu] * sd[mu]; }
-                const T* gu = gU + 3 * i;
-                const T* grow = Gs + il * ld;
-                const T* krow = Ys + il * ld;
-                for (int g = 0; g < G; ++g) {
-                    const T* cb = s.C + ((size_t)a * G + g) * n;
-                    T zb = 0, pb = 0;
-                    for (int j = 0; j < n; ++j) {
-                        const T c = cb[j];
-                        zb += c * grow[j];
-                        pb += c * krow[j];
+                for (int q = 0; q < 4; ++q) { y4[q] = bufA[j * ldt + r0 + q]; g4[q] = bufG[j * ldt + c0 + q]; }
+#pragma unroll
+                for (int a_ = 0; a_ < 4; ++a_)
+#pragma unroll
+                    for (int b_ = 0; b_ < 4; ++b_) acc4[a_][b_] += y4[a_] * g4[b_];
+            }
+#pragma unroll
+            for (int a_ = 0; a_ < 4; ++a_)
+#pragma unroll
+                for (int b_ = 0; b_ < 4; ++b_) bufM[(r0 + a_) * ldt + c0 + b_] = acc4[a_][b_];
+        }
+        __syncthreads();
+        if (tid < ng * ng) {                     // K[j][i'] = sum_i G[j][i] M1[i][i']
+            const int r0 = 4 * (tid / ng), c0 = 4 * (tid % ng);
+            T acc4[4][4] = {};
+            for (int i = 0; i < np; ++i) {
+                T g4[4], m4[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) { g4[q] = bufS[i * ldt + r0 + q]; m4[q] = bufM[i * ldt + c0 + q]; }
+#pragma unroll
+                for (int a_ = 0; a_ < 4; ++a_)
+#pragma unroll
+                    for (int b_ = 0; b_ < 4; ++b_) acc4[a_][b_] += g4[a_] * m4[b_];
+            }
+#pragma unroll
+            for (int a_ = 0; a_ < 4; ++a_)
+#pragma unroll
+                for (int b_ = 0; b_ < 4; ++b_) bufA[(r0 + a_) * ldt + c0 + b_] = acc4[a_][b_];
+        }
+        __syncthreads();
+        const int B = s.B;
+        for (int b0 = 0; b0 < B; b0 += 64) {
+            for (int idx = tid; idx < 64 * np; idx += nt) {   // C^T tile
+                const int bl = idx / np, j = idx - bl * np;
+                bufS[j * 68 + bl] = (b0 + bl < B && j < n) ? s.C[(size_t)(b0 + bl) * n + j] : T(0);
+            }
+            __syncthreads();
+            const bool act = tid < 16 * ng;
+            const int bg = tid / ng, ig = tid % ng;
+            T z4[4][4] = {}, p4[4][4] = {};
+            if (act) {
+                for (int j = 0; j < np; ++j) {
+                    T c4[4], g4[4], k4[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        c4[q] = bufS[j * 68 + 4 * bg + q];
+                        g4[q] = bufG[j * ldt + 4 * ig + q];
+                        k4[q] = bufA[j * ldt + 4 * ig + q];
                     }
-                    const T z = (T)s.zeta[g];
+#pragma unroll
+                    for (int a_ = 0; a_ < 4; ++a_)
+#pragma unroll
+                        for (int b_ = 0; b_ < 4; ++b_) {
+                            z4[a_][b_] += c4[a_] * g4[b_];
+                            p4[a_][b_] += c4[a_] * k4[b_];
+                        }
+                }
+            }
+            T fl[4][3] = {}, fe[4][3] = {};
+#pragma unroll
+            for (int bb = 0; bb < 4; ++bb) {
+                const int b = b0 + 4 * bg + bb;
+                if (!act || b >= B) continue;
+                const int a = b / G, g = b - a * G;
+                const T z = (T)s.zeta[g];
+                const T* pa = s.ptrig + 6 * a;
+#pragma unroll
+                for (int ii = 0; ii < 4; ++ii) {
+                    const int il = 4 * ig + ii;
+                    if (il >= n) continue;
+                    const int i = sp * n + il;
+                    T sd[3], cd[3], t, pv[3], qv[3];
+                    disp_trig(et + 6 * i, pa, ell, sd, cd, t);
+#pragma unroll
+                    for (int mu = 0; mu < 3; ++mu) { pv[mu] = ell * sd[mu] * cd[mu]; qv[mu] = cd[mu] * cd[mu] - sd[mu] * sd[mu]; }
                     const T e = qexp(-z * t);
                     RadialDerivs<T> rd;
-                    radial_chain(p, q, -z * e, z * z * e, -z * z * z * e, k2, rd);
+                    radial_chain(pv, qv, -z * e, z * z * e, -z * z * z * e, k2, rd);
                     T hv[3];
-                    hess_mul(rd.h, gu, hv);
+                    hess_mul(rd.h, gU + 3 * i, hv);
+                    const T zb = z4[bb][ii], pb = p4[bb][ii];
 #pragma unroll
                     for (int mu = 0; mu < 3; ++mu) {
-                        dl[mu] -= zb * rd.g[mu];
-                        de[mu] += pb * rd.g[mu] + zb * (hv[mu] + T(0.5) * rd.tl[mu]);
+                        fl[bb][mu] -= zb * rd.g[mu];
+                        fe[bb][mu] += pb * rd.g[mu] + zb * (hv[mu] + T(0.5) * rd.tl[mu]);
                     }
                 }
             }
+            // reduce over the ng threads that share these four basis functions
 #pragma unroll
-            for (int mu = 0; mu < 3; ++mu) { dl[mu] = warp_sum(dl[mu]); de[mu] = warp_sum(de[mu]); }
-            if (lane == 0)
-                for (int mu = 0; mu < 3; ++mu) { f_dl[3 * a + mu] += (double)dl[mu]; f_de[3 * a + mu] += (double)de[mu]; }
+            for (int bb = 0; bb < 4; ++bb)
+#pragma unroll
+                for (int mu = 0; mu < 3; ++mu)
+                    for (int o = 1; o < ng; o <<= 1) {
+                        fl[bb][mu] += __shfl_xor_sync(0xffffffffu, fl[bb][mu], o);
+                        fe[bb][mu] += __shfl_xor_sync(0xffffffffu, fe[bb][mu], o);
+                    }
+            if (act && ig == 0)
+                for (int bb = 0; bb < 4; ++bb)
+                    for (int mu = 0; mu < 3; ++mu) {
+                        stage[(4 * bg + bb) * 6 + mu] = (double)fl[bb][mu];
+                        stage[(4 * bg + bb) * 6 + 3 + mu] = (double)fe[bb][mu];
+                    }
+            __syncthreads();
+            {   // one thread per nucleus of this tile sums its basis functions in order
+                const int bend = (b0 + 64 < B) ? b0 + 64 : B;
+                const int a_first = b0 / G, a_last = (bend - 1) / G;
+                const int a = a_first + tid;
+                if (a <= a_last) {
+                    const int lo = (a * G > b0) ? a * G : b0, hi = ((a + 1) * G < bend) ? (a + 1) * G : bend;
+                    for (int b = lo; b < hi; ++b)
+                        for (int mu = 0; mu < 3; ++mu) {
+                            f_dl[3 * a + mu] += stage[(b - b0) * 6 + mu];
+                            f_de[3 * a + mu] += stage[(b - b0) * 6 + 3 + mu];
+                        }
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 
     // ---- P7: accumulate the sample

@@ -1,0 +1,244 @@
+// k_orbitals_tc.cu -- tensor-core (tcgen05) form of the walker-batched
+// molecular-orbital contraction for the mixed-precision path.
+//
+//   phi_j(r) = sum_b C[b][j] chi_b(r)   (and grad, Laplacian for Q = 5)
+//
+// A CTA owns 128 rows (electron positions).  For each chunk of 32 basis
+// functions the threads evaluate the periodised Gaussians (value, or
+// gradient and Laplacian) of the 128 rows straight into shared memory, in the
+// K-major 128-byte-swizzled layout the tensor core reads, split into three
+// exact TF32 pieces x = x0 + x1 + x2 (representation error ~2^-35).  One thread
+// then issues, per quantity, the six products with i + j <= 2
+//   D += A0 B0 + A0 B1 + A1 B0 + A0 B2 + A1 B1 + A2 B0   (tcgen05.mma kind::tf32)
+// accumulating in tensor memory (FP32).  The dropped products are below 2^-33
+// relative, so the contraction is at least as accurate as FP32 arithmetic.
+// B = C^T chunk, prepared once per handle in the same swizzled layout.  After
+// the last chunk the accumulators go TMEM -> registers -> shared -> HBM.
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tc.cuh"
+
+namespace qmc {
+
+namespace {
+constexpr int kRows = 128;     // MMA M
+constexpr int kKc = 32;        // basis functions per chunk (128 bytes of FP32 per row)
+constexpr int kTileA = kRows * kKc * 4;   // 16 KB
+}
+
+constexpr int kPieces = 3;   // TF32 pieces per operand
+
+__host__ __device__ inline int tc_nm(int n) { return n <= 16 ? 16 : ((n + 15) / 16) * 16; }
+
+size_t tc_coeff_bytes(int B, int n) {
+    const int nch = (B + kKc - 1) / kKc;
+    return (size_t)nch * kPieces * tc_nm(n) * 128;
+}
+
+bool tc_orbitals_supported(int n, int B) { (void)B; return n >= 1 && n <= 64; }
+
+// C^T chunks, three TF32 pieces, swizzled: chunk c at c * 3 * NM * 128 bytes, piece p at p * NM * 128.
+__global__ void prepare_coeff_kernel(const float* __restrict__ C, int B, int n, int NM, unsigned char* chat) {
+    const int nch = (B + kKc - 1) / kKc;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nch * NM * kKc) return;
+    const int c = t / (NM * kKc), rem = t - c * NM * kKc, j = rem / kKc, k = rem - j * kKc;
+    const int b = c * kKc + k;
+    const float x = (b < B && j < n) ? C[(size_t)b * n + j] : 0.f;
+    float x0, x1, x2;
+    tc::split3_tf32(x, x0, x1, x2);
+    unsigned char* base = chat + (size_t)c * kPieces * NM * 128;
+    *(float*)(base + tc::sw128_off(j, k)) = x0;
+    *(float*)(base + (size_t)NM * 128 + tc::sw128_off(j, k)) = x1;
+    *(float*)(base + (size_t)2 * NM * 128 + tc::sw128_off(j, k)) = x2;
+}
+
+void prepare_tc_coeff(const float* C, int B, int n, void* chat, cudaStream_t st) {
+    const int NM = tc_nm(n), nch = (B + kKc - 1) / kKc;
+    const int tot = nch * NM * kKc;
+    prepare_coeff_kernel<<<(tot + 255) / 256, 256, 0, st>>>(C, B, n, NM, (unsigned char*)chat);
+}
+
+// Q = 1: values (Slater rows / proposals).  Q = 4: d/dx, d/dy, d/dz and the
+// Laplacian (local energy; the values are not needed there).
+template <int Q>
+__global__ void __launch_bounds__(Q == 1 ? 256 : 512, 1)
+    orbitals_tc_kernel(SysView<float> s, const unsigned char* __restrict__ chat, const double* __restrict__ pos,
+                       int nrows, int NM, float* __restrict__ val, float* __restrict__ grad, float* __restrict__ lap) {
+    extern __shared__ unsigned char smraw[];
+    unsigned char* base = (unsigned char*)((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+    unsigned char* sA = base;                                    // [Q][piece] tiles of 16 KB
+    unsigned char* sB = base + (size_t)Q * kPieces * kTileA;     // [piece] tiles of NM * 128 bytes
+    float* ptr_s = (float*)(sB + (size_t)kPieces * NM * 128);    // [N][6] proton trig
+    __shared__ float rtrig[kRows][6];
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tbase;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nt = blockDim.x;
+    const int row0 = blockIdx.x * kRows;
+    const int n = s.n, B = s.B, G = s.G, N = s.N;
+    const float ell = (float)s.ell;
+    constexpr uint32_t kCols = (Q == 1) ? 64u : 256u;      // TMEM columns (power of two >= Q * NM)
+
+    if (warp == 0) { tc::tmem_alloc(&tbase, kCols); tc::tmem_relinquish(); }
+    if (tid == 0) tc::mbar_init(&mbar, 1);
+    for (int idx = tid; idx < kRows * 3; idx += nt) {
+        const int r = idx / 3, mu = idx % 3, row = row0 + r;
+        float sn = 0.f, cs = 1.f;
+        if (row < nrows) sincospif((float)(pos[(size_t)row * 3 + mu] / s.L), &sn, &cs);
+        rtrig[r][mu] = sn;
+        rtrig[r][3 + mu] = cs;
+    }
+    for (int idx = tid; idx < 6 * N; idx += nt) ptr_s[idx] = s.ptrig[idx];
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tbase;
+    const uint32_t idesc = tc::idesc_tf32(kRows, NM);
+    const int nch = (B + kKc - 1) / kKc;
+    const size_t chunk_bytes = (size_t)kPieces * NM * 128;
+    bool ok = true;
+
+    for (int c = 0; c < nch; ++c) {
+        // B operand: the prepared C^T chunk (16-byte vectors)
+        const uint4* src = (const uint4*)(chat + (size_t)c * chunk_bytes);
+        uint4* dst = (uint4*)sB;
+        for (int idx = tid; idx < (int)(chunk_bytes / 16); idx += nt) dst[idx] = src[idx];
+        // A operand: one item = (row, 4 consecutive basis functions); the
+        // displacement to a nucleus is computed once for its Gaussians
+        for (int item = tid; item < kRows * (kKc / 4); item += nt) {
+            const int r = item / (kKc / 4), k0 = 4 * (item - r * (kKc / 4));
+            float v[Q][4];
+            int a_prev = -1;
+            float t = 0.f, pp = 0.f, sq = 0.f, pv[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const int b = c * kKc + k0 + kk;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) v[q][kk] = 0.f;
+                if (b >= B || row0 + r >= nrows) continue;
+                const int a = b / G, g = b - a * G;
+                if (a != a_prev) {
+                    a_prev = a;
+                    const float* pt = ptr_s + 6 * a;
+                    t = 0.f; pp = 0.f; sq = 0.f;
+#pragma unroll
+                    for (int mu = 0; mu < 3; ++mu) {
+                        const float sx = rtrig[r][mu], cx = rtrig[r][3 + mu];
+                        const float sd = sx * pt[3 + mu] - cx * pt[mu];
+                        const float cd = cx * pt[3 + mu] + sx * pt[mu];
+                        t += sd * sd;
+                        pv[mu] = ell * sd * cd;
+                        pp += pv[mu] * pv[mu];
+                        sq += cd * cd - sd * sd;
+                    }
+                    t *= ell * ell;
+                }
+                const float z = (float)s.zeta[g];
+                const float e = expf(-z * t);
+                if (Q == 1) {
+                    v[0][kk] = e;
+                } else {
+                    const float f1 = -z * e, f2 = z * z * e;
+#pragma unroll
+                    for (int mu = 0; mu < 3; ++mu) v[mu][kk] = 2.f * f1 * pv[mu];
+                    v[Q - 1][kk] = 4.f * f2 * pp + 2.f * f1 * sq;
+                }
+            }
+            const uint32_t off = tc::sw128_off(r, k0);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                float4 x0, x1, x2;
+                tc::split3_tf32(v[q][0], x0.x, x1.x, x2.x);
+                tc::split3_tf32(v[q][1], x0.y, x1.y, x2.y);
+                tc::split3_tf32(v[q][2], x0.z, x1.z, x2.z);
+                tc::split3_tf32(v[q][3], x0.w, x1.w, x2.w);
+                unsigned char* tq = sA + (size_t)(kPieces * q) * kTileA + off;
+                *(float4*)(tq) = x0;
+                *(float4*)(tq + kTileA) = x1;
+                *(float4*)(tq + 2 * kTileA) = x2;
+            }
+        }
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t b0 = tc::smem_addr(sB), bstep = (uint32_t)NM * 128;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const uint32_t a0 = tc::smem_addr(sA + (size_t)(kPieces * q) * kTileA);
+                const uint32_t d = tmem + (uint32_t)(q * NM);
+#pragma unroll
+                for (int ks = 0; ks < kKc / 8; ++ks) {
+                    const uint32_t o = 32u * ks;
+                    // products A_i B_j with i + j <= 2, smallest first
+                    const int pi[6] = {2, 1, 0, 1, 0, 0}, pj[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+                    for (int m = 0; m < 6; ++m)
+                        tc::mma_tf32(d, tc::desc_sw128(a0 + pi[m] * kTileA + o), tc::desc_sw128(b0 + pj[m] * bstep + o),
+                                     idesc, (c > 0 || ks > 0 || m > 0) ? 1u : 0u);
+                }
+            }
+            tc::mma_commit(&mbar);
+        }
+        if (!tc::mbar_wait(&mbar, (uint32_t)(c & 1), 1ll << 26)) ok = false;
+        tc::fence_after_sync();
+        __syncthreads();
+    }
+    if (!ok && lane == 0) raise_err(s.err, kErrTimeout);
+
+    // Epilogue, one quantity at a time: TMEM -> registers -> shared staging
+    // tile [128][NM + 4] (the A tiles are free now) -> coalesced HBM stores.
+    float* stage = (float*)sA;
+    const int lds = NM + 4;
+    const int quarter = warp & 3, cgroup = warp >> 2, ngroups = nt / 128;
+    const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
+    const int r = quarter * 32 + lane;
+    const int rows_here = (nrows - row0) < kRows ? (nrows - row0) : kRows;
+    for (int q = 0; q < Q; ++q) {
+        for (int c0 = cgroup * 16; c0 < NM; c0 += 16 * ngroups) {
+            float v[16];
+            tc::tmem_ld16(taddr + (uint32_t)(q * NM + c0), v);
+#pragma unroll
+            for (int j = 0; j < 16; j += 4)
+                *(float4*)(stage + (size_t)r * lds + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+        __syncthreads();
+        for (int idx = tid; idx < rows_here * n; idx += nt) {
+            const int rr = idx / n, j = idx - rr * n, row = row0 + rr;
+            const float x = stage[(size_t)rr * lds + j];
+            if (Q == 1) val[(size_t)row * n + j] = x;
+            else if (q == Q - 1) lap[(size_t)row * n + j] = x;
+            else grad[((size_t)row * 3 + q) * n + j] = x;
+        }
+        __syncthreads();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kCols);
+}
+
+void launch_orbitals_tc(const SysView<float>& s, const void* chat, const double* pos, int nrows, float* val,
+                        float* grad, float* lap, cudaStream_t st) {
+    const int NM = tc_nm(s.n);
+    const int grid = (nrows + kRows - 1) / kRows;
+    // the dynamic shared-memory limit is raised to what a launch needs (the
+    // kernel also holds static shared memory, so the opt-in maximum minus that)
+    static size_t set4 = 0, set1 = 0;
+    if (grad) {
+        const size_t smem = 1024 + (size_t)4 * kPieces * kTileA + (size_t)kPieces * NM * 128 + 24 * (size_t)s.N;
+        if (smem > set4 && cudaFuncSetAttribute(orbitals_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem) == cudaSuccess)
+            set4 = smem;
+        orbitals_tc_kernel<4><<<grid, 512, smem, st>>>(s, (const unsigned char*)chat, pos, nrows, NM, val, grad, lap);
+    } else {
+        const size_t smem = 1024 + (size_t)kPieces * kTileA + (size_t)kPieces * NM * 128 + 24 * (size_t)s.N;
+        if (smem > set1 && cudaFuncSetAttribute(orbitals_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem) == cudaSuccess)
+            set1 = smem;
+        orbitals_tc_kernel<1><<<grid, 256, smem, st>>>(s, (const unsigned char*)chat, pos, nrows, NM, val, nullptr,
+                                                       nullptr);
+    }
+}
+
+}  // namespace qmc

@@ -15,7 +15,7 @@ void launch_init_walkers(int W, int N, double L, const double* R, double* X, Key
 // k_orbitals_tc.cu (tensor-core form of the value-only contraction)
 bool tc_orbitals_supported(int n, int B);
 void launch_orbitals_tc(const SysView<float>& s, const void* chat, const double* pos, int nrows, float* val,
-                        cudaStream_t st);
+                        float* grad, float* lap, cudaStream_t st);
 void prepare_tc_coeff(const float* C, int B, int n, void* chat, cudaStream_t st);
 size_t tc_coeff_bytes(int B, int n);
 

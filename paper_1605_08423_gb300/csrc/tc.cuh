@@ -1,0 +1,125 @@
+// tc.cuh -- thin inline-PTX wrappers for the sm_100-family tensor-core path:
+// tensor memory (TMEM) allocation, shared-memory matrix descriptors,
+// tcgen05.mma (kind::tf32, one CTA), commit to an mbarrier, bounded mbarrier
+// waits and TMEM loads.  Written from the public PTX ISA description of
+// tcgen05; no library code.
+#pragma once
+#include <cstdint>
+
+namespace qmc {
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// One warp allocates `ncols` TMEM columns (power of two >= 32); the base
+// address is written to shared memory at `dst`.
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(dst)), "r"(ncols));
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols));
+}
+
+// Shared-memory descriptor of a K-major operand tile stored with the 128-byte
+// swizzle: rows of 128 bytes, 8-row groups of 1024 bytes (stride-dimension
+// offset), tile base 1024-byte aligned.  Bits: [0,14) address>>4,
+// [16,30) leading offset>>4 (unused for this layout), [32,46) stride offset>>4,
+// [46,48) descriptor version 1, [61,64) layout 2 = 128-byte swizzle.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)2u << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::tf32, FP32 accumulator, both operands K-major:
+// [4,6) D format (1 = F32), [7,10) A format (2 = TF32), [10,13) B format,
+// [17,23) N >> 3, [24,29) M >> 4.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+// Arrive on `mbar` when all tcgen05.mma issued so far by this thread are complete.
+__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_addr(mbar)));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(mbar)), "r"(count));
+}
+
+// Wait for phase `parity` of `mbar` to complete; gives up after max_iter polls
+// and returns false (the caller records the timeout and leaves cleanly).
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long long max_iter) {
+    const uint32_t a = smem_addr(mbar);
+    for (long long it = 0; it < max_iter; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity));
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane (32x32b shape).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Byte offset of element (r, k) (4-byte elements, 32 per row) in a K-major
+// tile stored with the 128-byte swizzle.
+__host__ __device__ __forceinline__ uint32_t sw128_off(int r, int k) {
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 2) ^ (r & 7)) & 7) << 4) + (k & 3) * 4);
+}
+
+// Round an FP32 value to the nearest TF32 value (10 explicit mantissa bits;
+// the 13 dropped bits rounded half away from zero in magnitude).
+__device__ __forceinline__ float round_tf32(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// x = hi + mid + lo + O(2^-35 |x|), each piece an exact TF32 value.
+__device__ __forceinline__ void split3_tf32(float x, float& hi, float& mid, float& lo) {
+    hi = round_tf32(x);
+    const float r = x - hi;
+    mid = round_tf32(r);
+    lo = round_tf32(r - mid);
+}
+
+// x = hi + lo + O(2^-24 |x|) with hi and lo both exact TF32 values, so the
+// tensor core (which reads only the TF32 bits) sees them unchanged and the
+// representation error is unbiased.
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+    hi = round_tf32(x);
+    lo = round_tf32(x - hi);
+}
+
+}  // namespace tc
+}  // namespace qmc

@@ -76,6 +76,7 @@ def lib():
         L.qmc_get_accumulators.argtypes = [vp, _dp]
         L.qmc_set_md_step.argtypes = [vp, C.c_uint32]
         L.qmc_set_profiling.argtypes = [vp, C.c_int]
+        L.qmc_set_option.argtypes = [vp, C.c_int, C.c_int]
         L.qmc_kernel_times.argtypes = [vp, C.c_int, _dp, C.POINTER(C.c_longlong)]
         L.qmc_launch_count.argtypes = [vp]
         L.qmc_launch_count.restype = C.c_longlong
@@ -225,6 +226,9 @@ class QMCSystem:
 
     def sync(self):
         _chk(lib().qmc_sync(self._h), "qmc_sync")
+
+    def set_tensor_cores(self, on: bool):
+        _chk(lib().qmc_set_option(self._h, 1, int(on)), "qmc_set_option")
 
     def set_profiling(self, on: bool):
         _chk(lib().qmc_set_profiling(self._h, int(on)), "qmc_set_profiling")

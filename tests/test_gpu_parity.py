@@ -75,6 +75,21 @@ def test_eval_config_full_size_sampled(prec):
     assert np.all(_rel_vec(g["del_"], de) <= tol), _rel_vec(g["del_"], de)
 
 
+@pytest.mark.parametrize("name", ["h16", "h64"])
+def test_tensor_core_orbitals_match_simt(name):
+    """The tcgen05 (3xTF32) orbital contraction agrees with the SIMT FP32 one."""
+    wl = synth.workload(name)
+    X = _sampled(wl, 6, 21, sweeps=6)
+    s = q.QMCSystem(q.Config.from_workload(wl, precision=q.QMC_MIXED, walkers=6), wl.R)
+    tc = s.eval_config(X, wl.R)
+    s.set_tensor_cores(False)
+    simt = s.eval_config(X, wl.R)
+    assert np.all(np.abs(tc["el"] - simt["el"]) <= 2e-5 * np.abs(simt["el"]))
+    assert np.all(np.abs(tc["lnpsi"] - simt["lnpsi"]) <= 2e-5 * np.abs(simt["lnpsi"]))
+    assert np.all(_rel_vec(tc["del_"], simt["del_"]) <= 2e-5)
+    assert np.all(_rel_vec(tc["dlnpsi"], simt["dlnpsi"]) <= 2e-5)
+
+
 def test_walker_start_matches_oracle():
     wl = synth.workload("h16", walkers=32)
     sysg = q.QMCSystem(q.Config.from_workload(wl), wl.R)
