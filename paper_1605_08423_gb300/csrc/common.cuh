@@ -67,8 +67,20 @@ __device__ __forceinline__ double qsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float qsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double qerfc(double x) { return erfc(x); }
 __device__ __forceinline__ float qerfc(float x) { return erfcf(x); }
+__device__ __forceinline__ double qrint(double x) { return rint(x); }
+__device__ __forceinline__ float qrint(float x) { return rintf(x); }
 __device__ __forceinline__ void qsincospi(double x, double* s, double* c) { sincospi(x, s, c); }
 __device__ __forceinline__ void qsincospi(float x, float* s, float* c) { sincospif(x, s, c); }
+
+// Four consecutive elements from 16-byte-aligned shared memory.
+__device__ __forceinline__ void load4(const float* p, float o[4]) {
+    const float4 v = *(const float4*)p;
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void load4(const double* p, double o[4]) {
+    const double2 a = *(const double2*)p, b = *(const double2*)(p + 2);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -109,6 +121,7 @@ struct SysView {
     double b_ee, b_ep, Zj;  // Jastrow parameters (Zj = e-n cusp amplitude)
     double kappa;           // Ewald splitting
     const double* zeta;     // [G]
+    const T* zetat;         // [G] in the working precision
     const T* C;             // [B][n]
     const double* R;        // [N][3]
     const T* RT;            // [N][3] in the working precision
@@ -191,7 +204,7 @@ __device__ __forceinline__ void rho_to_t(T r, T u1, T u2, T u3, T& f1, T& f2, T&
 template <typename T>
 __device__ __forceinline__ T ewald_real(T dx, T dy, T dz, T Lt, T kappa, T* grad) {
     const T iL = T(1) / Lt;
-    dx -= Lt * rint(dx * iL); dy -= Lt * rint(dy * iL); dz -= Lt * rint(dz * iL);
+    dx -= Lt * qrint(dx * iL); dy -= Lt * qrint(dy * iL); dz -= Lt * qrint(dz * iL);
     const T r0[3] = {dx, dy, dz};
     T sh[3];
 #pragma unroll
@@ -199,21 +212,31 @@ __device__ __forceinline__ T ewald_real(T dx, T dy, T dz, T Lt, T kappa, T* grad
     T v = 0;
     if (grad) grad[0] = grad[1] = grad[2] = 0;
     const T c2 = T(1.1283791670955126);  // 2 / sqrt(pi)
+    // the (at most 8) candidate images inside the cutoff, compacted into a bit
+    // mask so that a warp runs the erfc body only max(popcount) times
+    unsigned mask = 0;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const T a = r0[0] + ((c & 1) ? sh[0] : T(0));
         const T b = r0[1] + ((c & 2) ? sh[1] : T(0));
         const T e = r0[2] + ((c & 4) ? sh[2] : T(0));
         const T r2 = a * a + b * b + e * e;
-        if (r2 < Lt * Lt && r2 > T(0)) {
-            const T r = qsqrt(r2), ir = T(1) / r;
-            const T ec = qerfc(kappa * r);
-            v += ec * ir;
-            if (grad) {
-                const T dphi = -(ec * ir + c2 * kappa * qexp(-kappa * kappa * r2)) * ir;  // phi'(r)
-                const T s = dphi * ir;
-                grad[0] += s * a; grad[1] += s * b; grad[2] += s * e;
-            }
+        if (r2 < Lt * Lt && r2 > T(0)) mask |= 1u << c;
+    }
+    while (mask) {
+        const int c = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const T a = r0[0] + ((c & 1) ? sh[0] : T(0));
+        const T b = r0[1] + ((c & 2) ? sh[1] : T(0));
+        const T e = r0[2] + ((c & 4) ? sh[2] : T(0));
+        const T r2 = a * a + b * b + e * e;
+        const T r = qsqrt(r2), ir = T(1) / r;
+        const T ec = qerfc(kappa * r);
+        v += ec * ir;
+        if (grad) {
+            const T dphi = -(ec * ir + c2 * kappa * qexp(-kappa * kappa * r2)) * ir;  // phi'(r)
+            const T s = dphi * ir;
+            grad[0] += s * a; grad[1] += s * b; grad[2] += s * e;
         }
     }
     return v;

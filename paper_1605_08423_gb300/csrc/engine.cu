@@ -37,7 +37,8 @@ struct qmc_system {
     int4* d_kvec = nullptr;
     double2 *d_eikR = nullptr, *d_rhop = nullptr;
     double *d_vconst = nullptr, *d_dvpp = nullptr;
-    float *d_R32 = nullptr, *d_kw32 = nullptr;
+    float *d_R32 = nullptr, *d_kw32 = nullptr, *d_zeta32 = nullptr;
+    void* d_ptp = nullptr;     // (sin, cos)(pi x'/L) of the proposals of the current sweep
     float2* d_eikR32 = nullptr;
     void* d_chat = nullptr;    // C^T chunks, TF32 hi/lo, swizzled (tensor-core orbital kernel)
     bool use_tc = false;
@@ -157,6 +158,7 @@ SysView<T> view(qmc_system* h, int W) {
     s.L = h->p.L; s.ell = h->p.L / kPi;
     s.b_ee = h->p.b_ee; s.b_ep = h->p.b_ep; s.Zj = 1.0; s.kappa = h->p.ewald_kappa;
     s.zeta = h->d_zeta;
+    s.zetat = (const T*)(sizeof(T) == 8 ? (const void*)h->d_zeta : (const void*)h->d_zeta32);
     s.C = (const T*)(sizeof(T) == 8 ? (const void*)h->d_C64 : (const void*)h->d_C32);
     s.R = h->d_R;
     s.RT = (const T*)(sizeof(T) == 8 ? (const void*)h->d_R : (const void*)h->d_R32);
@@ -226,14 +228,15 @@ void run_call(qmc_system* h) {
         EventPair ep;
         h->nlaunch += 3;
         prof_begin(h, KC_PROPOSE, ep);
-        launch_propose<T>(W, N, h->d_X, h->d_Xp, (T*)h->d_uacc, key, md, (uint32_t)sw, h->p.sigma, h->stream);
+        launch_propose<T>(W, N, h->p.L, h->d_X, h->d_Xp, (T*)h->d_ptp, (T*)h->d_uacc, key, md, (uint32_t)sw,
+                          h->p.sigma, h->stream);
         prof_end(h, ep);
         prof_begin(h, KC_ORB_PROP, ep);
         orbitals<T>(h, s, h->d_Xp, W * N, (T*)h->d_Phi, nullptr, nullptr);
         prof_end(h, ep);
         prof_begin(h, KC_SWEEP, ep);
-        launch_sweep<T>(s, h->d_X, h->d_Xp, (const T*)h->d_uacc, (const T*)h->d_Phi, (T*)h->d_Gt, h->d_nacc,
-                        h->stream);
+        launch_sweep<T>(s, h->d_X, h->d_Xp, (const T*)h->d_ptp, (const T*)h->d_uacc, (const T*)h->d_Phi,
+                        (T*)h->d_Gt, h->d_nacc, h->stream);
         prof_end(h, ep);
         if ((sw + 1) % h->p.recompute_every == 0) recompute<T>(h, W);
         if (sw >= nw && ((sw - nw + 1) % h->p.measure_every) == 0) measure<T>(h, W, nullptr, nullptr, nullptr, nullptr);
@@ -309,6 +312,8 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
     h->d_vconst = dalloc<double>(h, 1, &rc);
     h->d_dvpp = dalloc<double>(h, 3 * N, &rc);
     h->d_R32 = dalloc<float>(h, 3 * N, &rc);
+    h->d_zeta32 = dalloc<float>(h, h->G, &rc);
+    h->d_ptp = dalloc<unsigned char>(h, t * (size_t)W * N * 6, &rc);
     h->d_kw32 = dalloc<float>(h, nk, &rc);
     h->d_eikR32 = dalloc<float2>(h, (size_t)N * nk, &rc);
     h->d_X = dalloc<double>(h, (size_t)W * 3 * N, &rc);
@@ -338,11 +343,13 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
     }
     if (rc != QMC_OK) { qmc_destroy(h); return rc; }
     std::vector<float> c32(h->coeff_h.begin(), h->coeff_h.end());
+    std::vector<float> z32(h->zeta_h.begin(), h->zeta_h.end());
     cudaStream_t st = h->stream;
     cudaMemcpyAsync(h->d_R, R, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(h->d_zeta, h->zeta_h.data(), sizeof(double) * h->G, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(h->d_C64, h->coeff_h.data(), sizeof(double) * B * n, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(h->d_C32, c32.data(), sizeof(float) * B * n, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(h->d_zeta32, z32.data(), sizeof(float) * h->G, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(h->d_kvec, kv.data(), sizeof(int4) * nk, cudaMemcpyHostToDevice, st);
     cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
     cudaMemsetAsync(h->d_nacc, 0, sizeof(unsigned long long) * W, st);

@@ -23,7 +23,7 @@ namespace qmc {
 
 template <typename T>
 struct MLayout {
-    size_t xs, xt, et, gU, lU, Ui, gi, li, facc, rho, red, stage, uni, total;
+    size_t xs, xt, et, gU, lU, Ui, gi, li, facc, rho, rhot, red, stage, cmask, uni, total;
     __host__ __device__ MLayout(int N, int n, int nk, int mmax) {
         size_t o = 0;
         auto take = [&](size_t bytes) { size_t r = o; o = (o + bytes + 15) & ~size_t(15); return r; };
@@ -37,8 +37,10 @@ struct MLayout {
         li = take(sizeof(T) * N);
         facc = take(sizeof(double) * 9 * N);
         rho = take(sizeof(double2) * nk);
+        rhot = take(sizeof(V2<T>) * nk);
         red = take(sizeof(double) * 64);
         stage = take(sizeof(double) * 64 * 6);
+        cmask = take(sizeof(unsigned) * (size_t)N * ((N + 31) / 32));
         const size_t etab = sizeof(V2<T>) * (size_t)N * 3 * (2 * mmax + 1);
         int np = 4;
         while (np < n) np *= 2;
@@ -100,8 +102,10 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
     double* f_de = f_dl + 3 * N;
     double* f_dv = f_de + 3 * N;
     double2* rho = (double2*)(sm + lay.rho);
+    V2<T>* rhot = (V2<T>*)(sm + lay.rhot);
     double* red = (double*)(sm + lay.red);
     double* stage = (double*)(sm + lay.stage);
+    unsigned* cmask = (unsigned*)(sm + lay.cmask);
     unsigned char* uni = sm + lay.uni;
 
     const int w = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
@@ -111,17 +115,19 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
     const T twopiL = T(2.0 * kPi / L), k2 = twopiL * twopiL;
     const double Zn = 1.0;  // proton charge
 
+    const double iL = 1.0 / L;
     // ---- P0: positions and their (sin, cos)(pi x / L)
     for (int idx = tid; idx < 3 * N; idx += nt) {
         const double x = X[(size_t)w * 3 * N + idx];
         xs[idx] = x;
         xt[idx] = (T)x;
         T sn, cs;
-        qsincospi((T)(x / L), &sn, &cs);
+        qsincospi((T)(x * iL), &sn, &cs);
         et[6 * (idx / 3) + idx % 3] = sn;
         et[6 * (idx / 3) + 3 + idx % 3] = cs;
     }
     for (int idx = tid; idx < 9 * N; idx += nt) f_dl[idx] = 0.0;
+    for (int idx = tid; idx < N * ((N + 31) / 32); idx += nt) cmask[idx] = 0u;
     __syncthreads();
 
     // ---- P1: Jastrow gradient / Laplacian per electron, U partial sums.  The
@@ -233,50 +239,74 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
     // ---- P4b: electron-proton pairs (warp per proton, lanes over electrons): the
     // real-space Ewald energy and its R-gradient (Hellmann-Feynman) together with
     // the e-n Jastrow terms of d ln psi/dR and dE_L/dR.  In the mixed form, pairs
-    // closer than 0.3 bohr are evaluated and summed in FP64: there the 1/r^2
-    // Coulomb force and the 1/r^2 part of grad lap u_en cancel (cusp condition),
-    // and FP32 rounding of either term would survive the cancellation.
+    // closer than 0.3 bohr are only flagged here and evaluated afterwards in FP64
+    // (one thread per proton, electrons in increasing order): there the 1/r^2
+    // Coulomb force and the 1/r^2 part of grad lap u_en cancel (cusp
+    // condition), and FP32 rounding of either term would survive the
+    // cancellation.  Deferring them keeps FP64 off the common path.
     double vep_p = 0.0;
+    const int nwords = (N + 31) / 32;
     for (int a = warp; a < N; a += nw) {
         T v = 0, gv[3] = {0, 0, 0}, dl[3] = {0, 0, 0}, de[3] = {0, 0, 0};
-        double vC = 0, gC[3] = {0, 0, 0}, dlC[3] = {0, 0, 0}, deC[3] = {0, 0, 0};
         const T* pa = s.ptrig + 6 * a;
+        const T* ra = s.RT + 3 * a;
         for (int i = lane; i < N; i += 32) {
-            const double dx = xs[3 * i] - s.R[3 * a], dy = xs[3 * i + 1] - s.R[3 * a + 1],
-                         dz = xs[3 * i + 2] - s.R[3 * a + 2];
             T sd[3], cd[3], t;
             disp_trig(et + 6 * i, pa, ell, sd, cd, t);
             if (sizeof(T) == 4 && t < T(0.09)) {
-                double sdd[3], cdd[3], vv[3], pv, pg[3], pl[3], pe[3];
-                sincospi(dx / L, &sdd[0], &cdd[0]);
-                sincospi(dy / L, &sdd[1], &cdd[1]);
-                sincospi(dz / L, &sdd[2], &cdd[2]);
-                for (int mu = 0; mu < 3; ++mu) vv[mu] = (double)gi[3 * i + mu] + (double)gU[3 * i + mu];
-                ep_pair<double>(sdd, cdd, s.ell, (double)k2, s.b_ep, s.Zj, dx, dy, dz, L, s.kappa, vv, pv, pg, pl, pe);
-                vC += pv;
-                for (int mu = 0; mu < 3; ++mu) { gC[mu] += pg[mu]; dlC[mu] += pl[mu]; deC[mu] += pe[mu]; }
-            } else {
-                T vv[3], pv, pg[3], pl[3], pe[3];
-                for (int mu = 0; mu < 3; ++mu) vv[mu] = gi[3 * i + mu] + gU[3 * i + mu];
-                const T* ra = s.RT + 3 * a;
-                ep_pair<T>(sd, cd, ell, k2, bep, Zj, xt[3 * i] - ra[0], xt[3 * i + 1] - ra[1], xt[3 * i + 2] - ra[2],
-                           Lt, kap, vv, pv, pg, pl, pe);
-                v += pv;
-                for (int mu = 0; mu < 3; ++mu) { gv[mu] += pg[mu]; dl[mu] += pl[mu]; de[mu] += pe[mu]; }
+                atomicOr(&cmask[a * nwords + (i >> 5)], 1u << (i & 31));
+                continue;
+            }
+            T vv[3], pv, pg[3], pl[3], pe[3];
+            for (int mu = 0; mu < 3; ++mu) vv[mu] = gi[3 * i + mu] + gU[3 * i + mu];
+            ep_pair<T>(sd, cd, ell, k2, bep, Zj, xt[3 * i] - ra[0], xt[3 * i + 1] - ra[1], xt[3 * i + 2] - ra[2],
+                       Lt, kap, vv, pv, pg, pl, pe);
+            v += pv;
+            for (int mu = 0; mu < 3; ++mu) { gv[mu] += pg[mu]; dl[mu] += pl[mu]; de[mu] += pe[mu]; }
+        }
+        v = warp_sum(v);
+#pragma unroll
+        for (int mu = 0; mu < 3; ++mu) { gv[mu] = warp_sum(gv[mu]); dl[mu] = warp_sum(dl[mu]); de[mu] = warp_sum(de[mu]); }
+        if (lane == 0) {
+            vep_p += -Zn * (double)v;
+            for (int mu = 0; mu < 3; ++mu) {
+                f_dv[3 * a + mu] += Zn * (double)gv[mu];
+                f_dl[3 * a + mu] += (double)dl[mu];
+                f_de[3 * a + mu] += (double)de[mu];
             }
         }
-        v = warp_sum(v); vC = warp_sum(vC);
-#pragma unroll
-        for (int mu = 0; mu < 3; ++mu) {
-            gv[mu] = warp_sum(gv[mu]); dl[mu] = warp_sum(dl[mu]); de[mu] = warp_sum(de[mu]);
-            gC[mu] = warp_sum(gC[mu]); dlC[mu] = warp_sum(dlC[mu]); deC[mu] = warp_sum(deC[mu]);
-        }
-        if (lane == 0) {
-            vep_p += -Zn * ((double)v + vC);
-            for (int mu = 0; mu < 3; ++mu) {
-                f_dv[3 * a + mu] += Zn * ((double)gv[mu] + gC[mu]);
-                f_dl[3 * a + mu] += (double)dl[mu] + dlC[mu];
-                f_de[3 * a + mu] += (double)de[mu] + deC[mu];
+    }
+    if (sizeof(T) == 4) {
+        __syncthreads();
+        for (int a = tid; a < N; a += nt) {
+            double vC = 0, gC[3] = {0, 0, 0}, dlC[3] = {0, 0, 0}, deC[3] = {0, 0, 0};
+            bool any = false;
+            for (int wd = 0; wd < nwords; ++wd) {
+                unsigned m = cmask[a * nwords + wd];
+                while (m) {
+                    const int i = wd * 32 + __ffs(m) - 1;
+                    m &= m - 1;
+                    any = true;
+                    const double dx = xs[3 * i] - s.R[3 * a], dy = xs[3 * i + 1] - s.R[3 * a + 1],
+                                 dz = xs[3 * i + 2] - s.R[3 * a + 2];
+                    double sdd[3], cdd[3], vv[3], pv, pg[3], pl[3], pe[3];
+                    sincospi(dx * iL, &sdd[0], &cdd[0]);
+                    sincospi(dy * iL, &sdd[1], &cdd[1]);
+                    sincospi(dz * iL, &sdd[2], &cdd[2]);
+                    for (int mu = 0; mu < 3; ++mu) vv[mu] = (double)gi[3 * i + mu] + (double)gU[3 * i + mu];
+                    ep_pair<double>(sdd, cdd, s.ell, (double)k2, s.b_ep, s.Zj, dx, dy, dz, L, s.kappa, vv, pv, pg, pl,
+                                    pe);
+                    vC += pv;
+                    for (int mu = 0; mu < 3; ++mu) { gC[mu] += pg[mu]; dlC[mu] += pl[mu]; deC[mu] += pe[mu]; }
+                }
+            }
+            if (any) {
+                vep_p += -Zn * vC;
+                for (int mu = 0; mu < 3; ++mu) {
+                    f_dv[3 * a + mu] += Zn * gC[mu];
+                    f_dl[3 * a + mu] += dlC[mu];
+                    f_de[3 * a + mu] += deC[mu];
+                }
             }
         }
     }
@@ -285,7 +315,7 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
     const int nm = 2 * mmax + 1;
     for (int idx = tid; idx < 3 * N; idx += nt) {
         T sn, cs;
-        qsincospi((T)(2.0 * xs[idx] / L), &sn, &cs);
+        qsincospi((T)(2.0 * iL) * xt[idx], &sn, &cs);
         V2<T>* e = etab + (size_t)idx * nm;
         V2<T> cur{T(1), T(0)};
         e[mmax] = cur;
@@ -310,6 +340,7 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
         const double2 rp = s.rho_p[k];
         const double rr = rp.x - (double)re, ri = rp.y - (double)im;   // electrons carry -1
         rho[k] = make_double2(rr, ri);
+        rhot[k] = V2<T>{(T)rr, (T)ri};
         vrec_p += s.kw[k] * (rr * rr + ri * ri);
     }
     __syncthreads();
@@ -318,8 +349,8 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
         T gx = 0, gy = 0, gz = 0;
         for (int k = lane; k < nk; k += 32) {
             const V2<T> e = s.eikRt[(size_t)a * nk + k];
-            const double2 rd = rho[k];
-            const T c = T(2) * (T)Zn * s.kwt[k] * ((T)rd.y * e.x - (T)rd.x * e.y);
+            const V2<T> rd = rhot[k];
+            const T c = T(2) * (T)Zn * s.kwt[k] * (rd.y * e.x - rd.x * e.y);
             const int4 m = s.kvec[k];
             gx += c * twopiL * (T)m.x; gy += c * twopiL * (T)m.y; gz += c * twopiL * (T)m.z;
         }
@@ -364,8 +395,8 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
             T acc4[4][4] = {};
             for (int j = 0; j < np; ++j) {
                 T y4[4], g4[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) { y4[q] = bufA[j * ldt + r0 + q]; g4[q] = bufG[j * ldt + c0 + q]; }
+                load4(bufA + j * ldt + r0, y4);
+                load4(bufG + j * ldt + c0, g4);
 #pragma unroll
                 for (int a_ = 0; a_ < 4; ++a_)
 #pragma unroll
@@ -382,8 +413,8 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
             T acc4[4][4] = {};
             for (int i = 0; i < np; ++i) {
                 T g4[4], m4[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) { g4[q] = bufS[i * ldt + r0 + q]; m4[q] = bufM[i * ldt + c0 + q]; }
+                load4(bufS + i * ldt + r0, g4);
+                load4(bufM + i * ldt + c0, m4);
 #pragma unroll
                 for (int a_ = 0; a_ < 4; ++a_)
 #pragma unroll
@@ -408,12 +439,9 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
             if (act) {
                 for (int j = 0; j < np; ++j) {
                     T c4[4], g4[4], k4[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        c4[q] = bufS[j * 68 + 4 * bg + q];
-                        g4[q] = bufG[j * ldt + 4 * ig + q];
-                        k4[q] = bufA[j * ldt + 4 * ig + q];
-                    }
+                    load4(bufS + j * 68 + 4 * bg, c4);
+                    load4(bufG + j * ldt + 4 * ig, g4);
+                    load4(bufA + j * ldt + 4 * ig, k4);
 #pragma unroll
                     for (int a_ = 0; a_ < 4; ++a_)
 #pragma unroll
@@ -429,7 +457,7 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
                 const int b = b0 + 4 * bg + bb;
                 if (!act || b >= B) continue;
                 const int a = b / G, g = b - a * G;
-                const T z = (T)s.zeta[g];
+                const T z = s.zetat[g];
                 const T* pa = s.ptrig + 6 * a;
 #pragma unroll
                 for (int ii = 0; ii < 4; ++ii) {

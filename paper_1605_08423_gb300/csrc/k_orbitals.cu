@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(512) orbitals_simt(SysView<T> s, const double*
                     t += sd[mu] * sd[mu];
                 }
                 t *= ell * ell;
-                const T z = (T)s.zeta[g];
+                const T z = s.zetat[g];
                 const T e = qexp(-z * t);
                 v[0] = e;
                 if (Q == 5) {
@@ -140,31 +140,43 @@ void launch_orbitals(const SysView<T>& s, const double* pos, int nrows, T* val, 
 }
 
 // ---------------------------------------------------------------------------
-// Proposals of one sweep: Xp = X + sigma xi (Philox normals, purposes 0..2) and
-// the acceptance uniforms (purpose 3), index = sweep * N + electron.  A move of
-// electron i only ever changes r_i, so every proposal of the sweep is known
-// when the sweep starts.
+// Proposals of one sweep: Xp = X + sigma xi (Philox normals, purposes 0..2),
+// their (sin, cos)(pi x'/L) in the working precision, and the acceptance
+// uniforms (purpose 3), index = sweep * N + electron.  A move of electron i
+// only ever changes r_i, so every proposal of the sweep is known when the
+// sweep starts.  X is wrapped into [0, L) first (the mixed sweep stores
+// accepted positions unwrapped).
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void propose_kernel(int W, int N, const double* __restrict__ X, double* __restrict__ Xp,
-                               T* __restrict__ uacc, Key key, uint32_t md, uint32_t sweep, double sigma) {
+__global__ void propose_kernel(int W, int N, double L, double* __restrict__ X, double* __restrict__ Xp,
+                               T* __restrict__ ptp, T* __restrict__ uacc, Key key, uint32_t md, uint32_t sweep,
+                               double sigma) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= W * N) return;
     const int w = t / N, i = t - w * N;
     const uint32_t idx = sweep * (uint32_t)N + (uint32_t)i;
+    const double iL = 1.0 / L;
 #pragma unroll
     for (int mu = 0; mu < 3; ++mu) {
+        double x = X[(size_t)t * 3 + mu];
+        x -= L * floor(x * iL);
+        X[(size_t)t * 3 + mu] = x;
         const T z = Draw<T>::normal(philox((uint32_t)w, md, idx, kPropX + mu, key));
-        Xp[(size_t)t * 3 + mu] = X[(size_t)t * 3 + mu] + sigma * (double)z;
+        const double xp = x + sigma * (double)z;
+        Xp[(size_t)t * 3 + mu] = xp;
+        T sn, cs;
+        qsincospi((T)(xp * iL), &sn, &cs);
+        ptp[(size_t)t * 6 + mu] = sn;
+        ptp[(size_t)t * 6 + 3 + mu] = cs;
     }
     uacc[t] = Draw<T>::uniform(philox((uint32_t)w, md, idx, kAccept, key));
 }
 
 template <typename T>
-void launch_propose(int W, int N, const double* X, double* Xp, T* uacc, Key key, uint32_t md, uint32_t sweep,
-                    double sigma, cudaStream_t st) {
+void launch_propose(int W, int N, double L, double* X, double* Xp, T* ptp, T* uacc, Key key, uint32_t md,
+                    uint32_t sweep, double sigma, cudaStream_t st) {
     const int tot = W * N;
-    propose_kernel<T><<<(tot + 255) / 256, 256, 0, st>>>(W, N, X, Xp, uacc, key, md, sweep, sigma);
+    propose_kernel<T><<<(tot + 255) / 256, 256, 0, st>>>(W, N, L, X, Xp, ptp, uacc, key, md, sweep, sigma);
 }
 
 // Walker start: electron i next to proton i (up electrons on protons 0..N/2-1,
@@ -188,7 +200,9 @@ void launch_init_walkers(int W, int N, double L, const double* R, double* X, Key
 
 template void launch_orbitals<double>(const SysView<double>&, const double*, int, double*, double*, double*, cudaStream_t);
 template void launch_orbitals<float>(const SysView<float>&, const double*, int, float*, float*, float*, cudaStream_t);
-template void launch_propose<double>(int, int, const double*, double*, double*, Key, uint32_t, uint32_t, double, cudaStream_t);
-template void launch_propose<float>(int, int, const double*, double*, float*, Key, uint32_t, uint32_t, double, cudaStream_t);
+template void launch_propose<double>(int, int, double, double*, double*, double*, double*, Key, uint32_t, uint32_t,
+                                     double, cudaStream_t);
+template void launch_propose<float>(int, int, double, double*, double*, float*, float*, Key, uint32_t, uint32_t,
+                                    double, cudaStream_t);
 
 }  // namespace qmc

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 512, 1)
     for (int idx = tid; idx < kRows * 3; idx += nt) {
         const int r = idx / 3, mu = idx % 3, row = row0 + r;
         float sn = 0.f, cs = 1.f;
-        if (row < nrows) sincospif((float)(pos[(size_t)row * 3 + mu] / s.L), &sn, &cs);
+        if (row < nrows) sincospif((float)(pos[(size_t)row * 3 + mu] * (1.0 / s.L)), &sn, &cs);
         rtrig[r][mu] = sn;
         rtrig[r][3 + mu] = cs;
     }
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 512, 1)
                     }
                     t *= ell * ell;
                 }
-                const float z = (float)s.zeta[g];
+                const float z = s.zetat[g];
                 const float e = expf(-z * t);
                 if (Q == 1) {
                     v[0][kk] = e;

@@ -41,7 +41,8 @@ __device__ __forceinline__ T pair_dist(const T* a, const T* b, T ell) {
 
 template <typename T>
 __global__ void __launch_bounds__(256) sweep_kernel(SysView<T> s, double* __restrict__ X, const double* __restrict__ Xp,
-                                                    const T* __restrict__ uacc, const T* __restrict__ Phi,
+                                                    const T* __restrict__ ptp, const T* __restrict__ uacc,
+                                                    const T* __restrict__ Phi,
                                                     T* __restrict__ Gt, unsigned long long* __restrict__ nacc) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = s.N, n = s.n, ld = n + 1;
@@ -66,10 +67,11 @@ __global__ void __launch_bounds__(256) sweep_kernel(SysView<T> s, double* __rest
     const double L = s.L;
     for (int idx = lane; idx < 3 * N; idx += 32) xs[idx] = X[(size_t)w * 3 * N + idx];
     __syncwarp();
+    const double iL = 1.0 / L;
     for (int idx = lane; idx < 3 * N; idx += 32) {
         const int i = idx / 3, mu = idx % 3;
         T sn, cs;
-        qsincospi((T)(xs[idx] / L), &sn, &cs);
+        qsincospi((T)(xs[idx] * iL), &sn, &cs);
         et[6 * i + mu] = sn;
         et[6 * i + 3 + mu] = cs;
     }
@@ -82,13 +84,9 @@ __global__ void __launch_bounds__(256) sweep_kernel(SysView<T> s, double* __rest
         for (int il = 0; il < n; ++il) {
             const int i = sp * n + il;
             const size_t row = (size_t)w * N + i;
-            double xp[3];
             T pt[6];
 #pragma unroll
-            for (int mu = 0; mu < 3; ++mu) {
-                xp[mu] = Xp[row * 3 + mu];
-                qsincospi((T)(xp[mu] / L), &pt[mu], &pt[3 + mu]);
-            }
+            for (int mu = 0; mu < 6; ++mu) pt[mu] = ptp[row * 6 + mu];
             for (int j = lane; j < n; j += 32) phi[j] = Phi[row * n + j];
             __syncwarp();
             T part = 0;
@@ -126,12 +124,23 @@ __global__ void __launch_bounds__(256) sweep_kernel(SysView<T> s, double* __rest
                     for (int j = 0; j < n; ++j) gl[j] -= coef * rowb[j];
                 }
                 if (lane < 3) {
-                    const double x = xp[lane] - L * floor(xp[lane] / L);
-                    xs[3 * i + lane] = x;
-                    T sn, cs;
-                    qsincospi((T)(x / L), &sn, &cs);
-                    et[6 * i + lane] = sn;
-                    et[6 * i + 3 + lane] = cs;
+                    // FP64 form: wrap into [0, L) at once (as the reference chain does).
+                    // Mixed form: keep the proposal as is (every function of the
+                    // positions is periodic; the next proposal pass wraps), so no
+                    // FP64 arithmetic runs per move.
+                    const double xpl = Xp[row * 3 + lane];
+                    if (sizeof(T) == 8) {
+                        const double x = xpl - L * floor(xpl / L);
+                        xs[3 * i + lane] = x;
+                        T sn, cs;
+                        qsincospi((T)(x / L), &sn, &cs);
+                        et[6 * i + lane] = sn;
+                        et[6 * i + 3 + lane] = cs;
+                    } else {
+                        xs[3 * i + lane] = xpl;
+                        et[6 * i + lane] = pt[lane];
+                        et[6 * i + 3 + lane] = pt[3 + lane];
+                    }
                 }
                 ++naccept;
             }
@@ -145,7 +154,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SysView<T> s, double* __rest
 }
 
 template <typename T>
-void launch_sweep(const SysView<T>& s, double* X, const double* Xp, const T* uacc, const T* Phi, T* Gt,
+void launch_sweep(const SysView<T>& s, double* X, const double* Xp, const T* ptp, const T* uacc, const T* Phi, T* Gt,
                   unsigned long long* nacc, cudaStream_t st) {
     const size_t wb = SweepSmem<T>::warp_bytes(s.N, s.n);
     const size_t head = ((size_t)6 * s.N * sizeof(T) + 15) & ~size_t(15);
@@ -159,12 +168,12 @@ void launch_sweep(const SysView<T>& s, double* X, const double* Xp, const T* uac
         cudaFuncSetAttribute(sweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         attr_set[which] = true;
     }
-    sweep_kernel<T><<<(s.W + wpb - 1) / wpb, 32 * wpb, smem, st>>>(s, X, Xp, uacc, Phi, Gt, nacc);
+    sweep_kernel<T><<<(s.W + wpb - 1) / wpb, 32 * wpb, smem, st>>>(s, X, Xp, ptp, uacc, Phi, Gt, nacc);
 }
 
 template void launch_sweep<double>(const SysView<double>&, double*, const double*, const double*, const double*,
-                                   double*, unsigned long long*, cudaStream_t);
+                                   const double*, double*, unsigned long long*, cudaStream_t);
 template void launch_sweep<float>(const SysView<float>&, double*, const double*, const float*, const float*,
-                                  float*, unsigned long long*, cudaStream_t);
+                                  const float*, float*, unsigned long long*, cudaStream_t);
 
 }  // namespace qmc

@@ -8,8 +8,8 @@ namespace qmc {
 template <typename T>
 void launch_orbitals(const SysView<T>& s, const double* pos, int nrows, T* val, T* grad, T* lap, cudaStream_t st);
 template <typename T>
-void launch_propose(int W, int N, const double* X, double* Xp, T* uacc, Key key, uint32_t md, uint32_t sweep,
-                    double sigma, cudaStream_t st);
+void launch_propose(int W, int N, double L, double* X, double* Xp, T* ptp, T* uacc, Key key, uint32_t md,
+                    uint32_t sweep, double sigma, cudaStream_t st);
 void launch_init_walkers(int W, int N, double L, const double* R, double* X, Key key, cudaStream_t st);
 
 // k_orbitals_tc.cu (tensor-core form of the value-only contraction)
@@ -25,7 +25,7 @@ void launch_invert(int W, int N, int n, const T* Phi, T* Gt, double* logdet, int
 
 // k_sweep.cu: one Metropolis sweep per walker (warp per walker).
 template <typename T>
-void launch_sweep(const SysView<T>& s, double* X, const double* Xp, const T* uacc, const T* Phi, T* Gt,
+void launch_sweep(const SysView<T>& s, double* X, const double* Xp, const T* ptp, const T* uacc, const T* Phi, T* Gt,
                   unsigned long long* nacc, cudaStream_t st);
 
 // k_measure.cu: local energy, d ln psi / dR and dE_L / dR per walker.
