@@ -138,6 +138,30 @@ int langevin_step_device(qmc_system* h, double* R_dev, const double* f_dev, cons
                          double T_kelvin, double delta, int s_mode, double alpha);
 
 /*
+ * The same Langevin step for callers that cannot allocate device memory (the
+ * paper has no counterpart: this is a deployment entry point).  cudaMalloc and
+ * cudaFree may synchronise the device, which a host overlapping many
+ * trajectories on streams or running a latency-bound MD loop cannot afford, and
+ * some embedding hosts own all device memory and hand the library only
+ * pre-allocated buffers.  This call allocates nothing and needs no handle:
+ *   R      device [n3], in: R_n, out: R_{n+1} (wrapped into [0, box) if box > 0)
+ *   Rprev  device [n3], R_{n-1} (pass R itself on the first step)
+ *   f      device [n3] force; S, Sprev device [n3][n3] (ignored for QMC_S_IDENTITY;
+ *          pass S as Sprev on the first step)
+ *   alpha  >= 0, used as given (0: Dt = Db = delta); seed/step: Philox key and MD step
+ *   stream cudaStream_t (NULL = default stream); the call returns after the step.
+ * Workspace: a statically allocated device array of QMC_STATIC_MAX_N3^2 doubles
+ * (1.18 MB) that every GPU which loads the library holds until exit.  The first
+ * call on each device looks its address up (make it before any stream capture).
+ * Calls that overlap on the GPU share the array and race.  n3 > QMC_STATIC_MAX_N3
+ * is rejected.  Errors: INVALID, NOT_PD, CUDA.
+ */
+enum { QMC_STATIC_MAX_N3 = 384 };
+int qmc_langevin_step_static(int n3, double* R, const double* Rprev, const double* f, const double* S,
+                             const double* Sprev, double T_kelvin, double delta, int s_mode, double alpha,
+                             uint64_t seed, uint32_t step, double box, void* stream);
+
+/*
  * Per-configuration evaluation (parity checks): for n_conf <= n_walkers
  * configurations X (host [n_conf][N][3]) at nuclei R, returns ln|psi|, E_L
  * and the R-derivatives d ln|psi|/dR, dE_L/dR ([n_conf][N][3]) from the same

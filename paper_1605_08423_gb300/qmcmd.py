@@ -78,6 +78,8 @@ def lib():
         L.qmc_set_profiling.argtypes = [vp, C.c_int]
         L.qmc_set_option.argtypes = [vp, C.c_int, C.c_int]
         L.qmc_kernel_times.argtypes = [vp, C.c_int, _dp, C.POINTER(C.c_longlong)]
+        L.qmc_langevin_step_static.argtypes = [C.c_int, vp, vp, vp, vp, vp, C.c_double, C.c_double, C.c_int,
+                                               C.c_double, C.c_uint64, C.c_uint32, C.c_double, vp]
         L.qmc_launch_count.argtypes = [vp]
         L.qmc_launch_count.restype = C.c_longlong
         L.qmc_kernel_name.argtypes = [C.c_int]
@@ -241,6 +243,17 @@ class QMCSystem:
         ln = (C.c_longlong * NKERNEL)()
         _chk(lib().qmc_kernel_times(self._h, NKERNEL, _p(ms), ln), "qmc_kernel_times")
         return {lib().qmc_kernel_name(k).decode(): (float(ms[k]), int(ln[k])) for k in range(NKERNEL)}
+
+
+def langevin_step_static(R_dev, Rprev_dev, f_dev, S_dev, Sprev_dev, T_kelvin, delta, s_mode, alpha, seed, step,
+                         box, stream_handle=0):
+    """qmc_langevin_step_static on float64 CUDA tensors (R_dev updated in place).
+    For callers that cannot allocate device memory: the call allocates nothing."""
+    n3 = R_dev.numel()
+    ptr = lambda t: C.c_void_p(t.data_ptr() if t is not None else 0)
+    _chk(lib().qmc_langevin_step_static(n3, ptr(R_dev), ptr(Rprev_dev), ptr(f_dev), ptr(S_dev), ptr(Sprev_dev),
+                                        T_kelvin, delta, s_mode, alpha, seed, step, box,
+                                        C.c_void_p(stream_handle or 0)), "qmc_langevin_step_static")
 
 
 def unpack_out(out: np.ndarray, N: int) -> dict:
