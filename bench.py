@@ -45,6 +45,9 @@ def _args():
     ap.add_argument("--fp64-sweeps", type=int, default=4, help="sweeps per step of the FP64-form comparison (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--serve-requests", type=int, default=200, help="served-form requests (0: skip)")
+    ap.add_argument("--serve-trajectories", type=int, default=32)
+    ap.add_argument("--serve-active", type=int, default=8)
     return ap.parse_args()
 
 
@@ -300,6 +303,25 @@ def run_ours(args, ws, rank, local):
                 "mixed_over_fp64": value / (W * N * args.fp64_sweeps / t64)}
         s64.close()
 
+    # served form: many concurrent trajectories, Poisson arrivals, continuous batching
+    serving = None
+    if args.serve_requests > 0:
+        from paper_1605_08423_gb300 import serve
+        system.close()
+        trajs = serve.served_trajectories(n_traj=args.serve_trajectories, seed=7 + rank)
+        free, _ = torch.cuda.mem_get_info()
+        srv = q.Server(int(0.6 * free), args.serve_active)
+        tids = [srv.add_trajectory(t.cfg, t.R, t.T_kelvin, t.delta) for t in trajs]
+        sres, swall = serve.run_poisson(srv, tids, trajs, n_requests=args.serve_requests, mean_ms=2.0,
+                                        seed=13 + rank)
+        serving = serve.summarize(sres, swall)
+        serving.update({"trajectories": len(trajs), "mean_interarrival_ms": 2.0, "max_active": args.serve_active,
+                        "hbm_budget_gb": srv.stats()["budget"] / 1e9, "stats": srv.stats(),
+                        "workload": "N in {32,64,128}, r_s~U(1.2,1.5), T~U(600,3000) K, 1024-8192 walkers, "
+                                    "4 sweeps + 1 continuation per MD step (first step: 4 warm-up sweeps), "
+                                    "mixed form, Langevin step with S = Cov(f)"})
+        srv.close()
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = _cpu_baseline(wl)
@@ -327,10 +349,12 @@ def run_ours(args, ws, rank, local):
                "kernel_ms_per_step": breakdown,
                "fp64_form": fp64,
                "cpu_baseline": cpu,
+               "serving": serving,
                "peaks": peak_kind,
                "result": {"E": res["E"], "E_err": res["E_err"], "accept": res["accept"], "Nc": res["Nc"]}}
         print(json.dumps(out), flush=True)
-    system.close()
+    if args.serve_requests <= 0:
+        system.close()
     if ws > 1:
         dist.destroy_process_group()
 

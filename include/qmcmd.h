@@ -54,7 +54,7 @@ enum { QMC_S_IDENTITY = 0, QMC_S_COV = 1 };    /* acceleration matrix of langevi
  * d the sin-periodised displacement of the SI, U = Pade e-e + e-n terms).
  */
 typedef struct {
-    int32_t n_protons;        /* N, even, 2..256; N electrons, N/2 per spin             */
+    int32_t n_protons;        /* N, even, 2..128; N electrons, N/2 per spin             */
     int32_t n_gauss;          /* Gaussians per proton, 1..8                              */
     int32_t n_walkers;        /* W >= 2                                                  */
     int32_t n_sweeps;         /* measured sweeps per qmc_energy_forces call              */
@@ -198,6 +198,55 @@ const char* qmc_kernel_name(int k);
 
 /* Number of CUDA kernels this handle has launched so far (monotonic). */
 long long qmc_launch_count(qmc_system* h);
+
+/* Checkpoint / resume of a handle's sampler and MD state: walker positions,
+ * the MD step counters and the Langevin history (R_prev, S_prev) -- everything a
+ * later qmc_energy_forces / langevin_step depends on besides the parameters
+ * (every call starts from a full inverse recompute, so inverses are not
+ * stored).  qmc_checkpoint_size gives the byte size; save writes into a
+ * caller-allocated host buffer; load restores into a handle created with the
+ * same parameters (INVALID otherwise).  A handle restored from a checkpoint
+ * continues bit-identically to the one that wrote it. */
+size_t qmc_checkpoint_size(qmc_system* h);
+int qmc_checkpoint_save(qmc_system* h, void* buf);
+int qmc_checkpoint_load(qmc_system* h, const void* buf);
+
+/*
+ * Serving: continuous batching of MD-step requests from many concurrent
+ * Langevin trajectories (each with its own N, density and temperature) on one
+ * GPU.  A trajectory keeps its walkers resident between requests; a request is
+ * one MD step (qmc_energy_forces at the trajectory's current nuclei, then
+ * langevin_step).  Requests of one trajectory run in order; up to max_active
+ * requests of different trajectories run at once on separate streams, so their
+ * kernels overlap.  Admission is by device-memory footprint against
+ * hbm_budget_bytes; idle trajectories are evicted least-recently-used with
+ * their state checkpointed to host memory and restored on re-admission, so a
+ * request's result is the same alone, in the mix and after an eviction.
+ * qmc_server_progress never blocks: the caller's loop calls it to retire
+ * finished requests and start queued ones, and qmc_server_fetch collects a
+ * finished request (1 = done, 0 = still pending).
+ */
+typedef struct qmc_server qmc_server;
+typedef struct {
+    int traj, status;                    /* trajectory id, QMC_OK or the request's error */
+    double E, E_err, n_samples, accept;
+    double* f;                           /* [3N] or NULL (caller-allocated)          */
+    double* cov;                         /* [3N][3N] or NULL                        */
+    double* R_next;                      /* [3N] nuclei after the Langevin step, or NULL */
+    double latency_ms, wait_ms, run_ms;  /* submit->done, submit->start, start->done */
+} qmc_served;
+int qmc_server_create(size_t hbm_budget_bytes, int max_active, qmc_server** out);
+void qmc_server_destroy(qmc_server* s);
+/* Register a trajectory (device memory is taken only when it is admitted). */
+int qmc_server_add_trajectory(qmc_server* s, const qmc_params* p, const double* R0, double T_kelvin, double delta,
+                              int s_mode, int* traj);
+int qmc_server_submit(qmc_server* s, int traj, long long* ticket);
+/* Retire finished requests and start queued ones; returns how many finished. */
+int qmc_server_progress(qmc_server* s);
+int qmc_server_fetch(qmc_server* s, long long ticket, qmc_served* out);
+/* stats[8]: resident bytes, resident trajectories, active, queued, evictions,
+ * completed, admissions, budget. */
+int qmc_server_stats(qmc_server* s, long long* stats);
 
 /* Text of an error code. */
 const char* qmc_strerror(int code);

@@ -543,6 +543,52 @@ int qmc_kernel_times(qmc_system* h, int n, double* ms, long long* launches) {
 
 long long qmc_launch_count(qmc_system* h) { return h ? h->nlaunch : -1; }
 
+// Checkpoint layout: 8 int64 header words [magic, version, N, W, md_step,
+// first_call, langevin_first, langevin_step_no], last_Nc (double), then
+// X [W][N][3], R_prev [3N], S_prev [3N][3N] (doubles).
+namespace {
+constexpr long long kCkptMagic = 0x514D43504B505431LL;  // "QMCPKPT1"
+size_t ckpt_bytes(const qmc_system* h) {
+    const size_t N3 = 3 * (size_t)h->N;
+    return 8 * sizeof(long long) + sizeof(double) + sizeof(double) * ((size_t)h->W * N3 + N3 + N3 * N3);
+}
+}  // namespace
+
+size_t qmc_checkpoint_size(qmc_system* h) { return h ? ckpt_bytes(h) : 0; }
+
+int qmc_checkpoint_save(qmc_system* h, void* buf) {
+    if (!h || !buf) return QMC_ERR_INVALID;
+    const size_t N3 = 3 * (size_t)h->N;
+    long long* hd = (long long*)buf;
+    hd[0] = kCkptMagic; hd[1] = 1; hd[2] = h->N; hd[3] = h->W; hd[4] = h->md_step;
+    hd[5] = h->first_call; hd[6] = h->langevin_first; hd[7] = h->langevin_step_no;
+    double* d = (double*)(hd + 8);
+    d[0] = h->last_Nc;
+    double* X = d + 1;
+    cudaMemcpyAsync(X, h->d_X, sizeof(double) * h->W * N3, cudaMemcpyDeviceToHost, h->stream);
+    cudaMemcpyAsync(X + h->W * N3, h->d_Rprev, sizeof(double) * N3, cudaMemcpyDeviceToHost, h->stream);
+    cudaMemcpyAsync(X + h->W * N3 + N3, h->d_Sprev, sizeof(double) * N3 * N3, cudaMemcpyDeviceToHost, h->stream);
+    return read_err(h);
+}
+
+int qmc_checkpoint_load(qmc_system* h, const void* buf) {
+    if (!h || !buf) return QMC_ERR_INVALID;
+    const long long* hd = (const long long*)buf;
+    if (hd[0] != kCkptMagic || hd[1] != 1 || hd[2] != h->N || hd[3] != h->W) return QMC_ERR_INVALID;
+    const size_t N3 = 3 * (size_t)h->N;
+    h->md_step = (uint32_t)hd[4];
+    h->first_call = hd[5] != 0;
+    h->langevin_first = hd[6] != 0;
+    h->langevin_step_no = (uint32_t)hd[7];
+    const double* d = (const double*)(hd + 8);
+    h->last_Nc = d[0];
+    const double* X = d + 1;
+    cudaMemcpyAsync(h->d_X, X, sizeof(double) * h->W * N3, cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(h->d_Rprev, X + h->W * N3, sizeof(double) * N3, cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(h->d_Sprev, X + h->W * N3 + N3, sizeof(double) * N3 * N3, cudaMemcpyHostToDevice, h->stream);
+    return read_err(h);
+}
+
 const char* qmc_kernel_name(int k) { return (k >= 0 && k < QMC_NKERNEL) ? kKernelNames[k] : "?"; }
 
 const char* qmc_strerror(int code) {

@@ -41,6 +41,13 @@ class Params(C.Structure):
     ]
 
 
+class Served(C.Structure):
+    _fields_ = [("traj", C.c_int), ("status", C.c_int), ("E", C.c_double), ("E_err", C.c_double),
+                ("n_samples", C.c_double), ("accept", C.c_double), ("f", C.POINTER(C.c_double)),
+                ("cov", C.POINTER(C.c_double)), ("R_next", C.POINTER(C.c_double)),
+                ("latency_ms", C.c_double), ("wait_ms", C.c_double), ("run_ms", C.c_double)]
+
+
 class Result(C.Structure):
     _fields_ = [("E", C.c_double), ("E_err", C.c_double), ("f", C.POINTER(C.c_double)),
                 ("cov", C.POINTER(C.c_double)), ("n_samples", C.c_double), ("accept", C.c_double)]
@@ -80,6 +87,19 @@ def lib():
         L.qmc_kernel_times.argtypes = [vp, C.c_int, _dp, C.POINTER(C.c_longlong)]
         L.qmc_langevin_step_static.argtypes = [C.c_int, vp, vp, vp, vp, vp, C.c_double, C.c_double, C.c_int,
                                                C.c_double, C.c_uint64, C.c_uint32, C.c_double, vp]
+        L.qmc_checkpoint_size.argtypes = [vp]
+        L.qmc_checkpoint_size.restype = C.c_size_t
+        L.qmc_checkpoint_save.argtypes = [vp, vp]
+        L.qmc_checkpoint_load.argtypes = [vp, vp]
+        L.qmc_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(vp)]
+        L.qmc_server_destroy.argtypes = [vp]
+        L.qmc_server_destroy.restype = None
+        L.qmc_server_add_trajectory.argtypes = [vp, C.POINTER(Params), _dp, C.c_double, C.c_double, C.c_int,
+                                                C.POINTER(C.c_int)]
+        L.qmc_server_submit.argtypes = [vp, C.c_int, C.POINTER(C.c_longlong)]
+        L.qmc_server_progress.argtypes = [vp]
+        L.qmc_server_fetch.argtypes = [vp, C.c_longlong, C.POINTER(Served)]
+        L.qmc_server_stats.argtypes = [vp, C.POINTER(C.c_longlong)]
         L.qmc_launch_count.argtypes = [vp]
         L.qmc_launch_count.restype = C.c_longlong
         L.qmc_kernel_name.argtypes = [C.c_int]
@@ -235,6 +255,16 @@ class QMCSystem:
     def set_profiling(self, on: bool):
         _chk(lib().qmc_set_profiling(self._h, int(on)), "qmc_set_profiling")
 
+    def checkpoint(self) -> bytes:
+        n = int(lib().qmc_checkpoint_size(self._h))
+        buf = (C.c_ubyte * n)()
+        _chk(lib().qmc_checkpoint_save(self._h, buf), "qmc_checkpoint_save")
+        return bytes(buf)
+
+    def restore(self, blob: bytes):
+        buf = (C.c_ubyte * len(blob)).from_buffer_copy(blob)
+        _chk(lib().qmc_checkpoint_load(self._h, buf), "qmc_checkpoint_load")
+
     def launch_count(self) -> int:
         return int(lib().qmc_launch_count(self._h))
 
@@ -254,6 +284,64 @@ def langevin_step_static(R_dev, Rprev_dev, f_dev, S_dev, Sprev_dev, T_kelvin, de
     _chk(lib().qmc_langevin_step_static(n3, ptr(R_dev), ptr(Rprev_dev), ptr(f_dev), ptr(S_dev), ptr(Sprev_dev),
                                         T_kelvin, delta, s_mode, alpha, seed, step, box,
                                         C.c_void_p(stream_handle or 0)), "qmc_langevin_step_static")
+
+
+class Server:
+    """Continuous-batching request loop (qmc_server_*): one MD step per request."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int):
+        self._s = C.c_void_p()
+        _chk(lib().qmc_server_create(int(hbm_budget_bytes), int(max_active), C.byref(self._s)), "qmc_server_create")
+        self._N = {}
+
+    def close(self):
+        if self._s:
+            lib().qmc_server_destroy(self._s)
+            self._s = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_trajectory(self, cfg: Config, R0, T_kelvin, delta, s_mode=QMC_S_COV) -> int:
+        p = cfg.cparams()
+        tid = C.c_int()
+        _chk(lib().qmc_server_add_trajectory(self._s, C.byref(p), _p(_f64(R0)), T_kelvin, delta, s_mode,
+                                             C.byref(tid)), "qmc_server_add_trajectory")
+        self._N[tid.value] = cfg.N
+        return tid.value
+
+    def submit(self, traj: int) -> int:
+        t = C.c_longlong()
+        _chk(lib().qmc_server_submit(self._s, traj, C.byref(t)), "qmc_server_submit")
+        return t.value
+
+    def progress(self) -> int:
+        rc = lib().qmc_server_progress(self._s)
+        if rc < 0:
+            raise QMCError(rc, "qmc_server_progress")
+        return rc
+
+    def fetch(self, ticket: int, traj: int):
+        """Finished request as a dict, or None while it is pending."""
+        N3 = 3 * self._N[traj]
+        f = np.zeros(N3); S = np.zeros((N3, N3)); Rn = np.zeros(N3)
+        o = Served(0, 0, 0.0, 0.0, 0.0, 0.0, _p(f), _p(S), _p(Rn), 0.0, 0.0, 0.0)
+        rc = lib().qmc_server_fetch(self._s, ticket, C.byref(o))
+        if rc < 0:
+            raise QMCError(rc, "qmc_server_fetch")
+        if rc == 0:
+            return None
+        return dict(traj=o.traj, status=o.status, E=o.E, E_err=o.E_err, Nc=o.n_samples, accept=o.accept, f=f,
+                    S=S, R_next=Rn, latency_ms=o.latency_ms, wait_ms=o.wait_ms, run_ms=o.run_ms)
+
+    def stats(self) -> dict:
+        st = (C.c_longlong * 8)()
+        _chk(lib().qmc_server_stats(self._s, st), "qmc_server_stats")
+        keys = ["resident_bytes", "resident", "active", "queued", "evictions", "completed", "admissions", "budget"]
+        return dict(zip(keys, list(st)))
 
 
 def unpack_out(out: np.ndarray, N: int) -> dict:
