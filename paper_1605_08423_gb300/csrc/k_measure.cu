@@ -451,33 +451,55 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
                         }
                 }
             }
+            // Epilogue.  For chi = exp(-zeta t) with f' = -zeta chi, f'' = zeta^2 chi,
+            // f''' = -zeta^3 chi, the radial chain contracts to
+            //   grad chi = 2 f' p,  H v = 4 f'' p (p.v) + 2 f' q o v,
+            //   grad lap chi = p o (8 f''' |p|^2 + 4 f'' sum q - 2 k^2 f' + 8 f'' q),
+            // so the geometry (p, q, p.gU, q o gU) is computed once per
+            // (nucleus, electron) and shared by that nucleus' Gaussians.
             T fl[4][3] = {}, fe[4][3] = {};
 #pragma unroll
-            for (int bb = 0; bb < 4; ++bb) {
-                const int b = b0 + 4 * bg + bb;
-                if (!act || b >= B) continue;
-                const int a = b / G, g = b - a * G;
-                const T z = s.zetat[g];
-                const T* pa = s.ptrig + 6 * a;
+            for (int ii = 0; ii < 4; ++ii) {
+                const int il = 4 * ig + ii;
+                if (!act || il >= n) continue;
+                const int i = sp * n + il;
+                const T* gu = gU + 3 * i;
+                int a_prev = -1;
+                T t = 0, pv[3] = {0, 0, 0}, qv[3] = {0, 0, 0}, pp = 0, sq = 0, pg = 0, qg[3] = {0, 0, 0};
 #pragma unroll
-                for (int ii = 0; ii < 4; ++ii) {
-                    const int il = 4 * ig + ii;
-                    if (il >= n) continue;
-                    const int i = sp * n + il;
-                    T sd[3], cd[3], t, pv[3], qv[3];
-                    disp_trig(et + 6 * i, pa, ell, sd, cd, t);
+                for (int bb = 0; bb < 4; ++bb) {
+                    const int b = b0 + 4 * bg + bb;
+                    if (b >= B) continue;
+                    const int a = b / G, g = b - a * G;
+                    if (a != a_prev) {
+                        a_prev = a;
+                        T sd[3], cd[3];
+                        disp_trig(et + 6 * i, s.ptrig + 6 * a, ell, sd, cd, t);
+                        pp = 0; sq = 0; pg = 0;
 #pragma unroll
-                    for (int mu = 0; mu < 3; ++mu) { pv[mu] = ell * sd[mu] * cd[mu]; qv[mu] = cd[mu] * cd[mu] - sd[mu] * sd[mu]; }
+                        for (int mu = 0; mu < 3; ++mu) {
+                            pv[mu] = ell * sd[mu] * cd[mu];
+                            qv[mu] = cd[mu] * cd[mu] - sd[mu] * sd[mu];
+                            pp += pv[mu] * pv[mu];
+                            sq += qv[mu];
+                            pg += pv[mu] * gu[mu];
+                            qg[mu] = qv[mu] * gu[mu];
+                        }
+                    }
+                    const T z = s.zetat[g];
                     const T e = qexp(-z * t);
-                    RadialDerivs<T> rd;
-                    radial_chain(pv, qv, -z * e, z * z * e, -z * z * z * e, k2, rd);
-                    T hv[3];
-                    hess_mul(rd.h, gU + 3 * i, hv);
+                    const T f1 = -z * e, f2 = z * z * e, f3 = -z * z * z * e;
+                    const T A = T(8) * f3 * pp + T(4) * f2 * sq - T(2) * k2 * f1;
                     const T zb = z4[bb][ii], pb = p4[bb][ii];
+                    const T g1 = T(2) * f1;
+                    const T cp = pb * g1 + zb * T(4) * f2 * pg;   // p terms of pb grad chi + zb H gU
+                    const T cq = zb * g1;                          // q o gU term of zb H gU
+                    const T hz = T(0.5) * zb;
 #pragma unroll
                     for (int mu = 0; mu < 3; ++mu) {
-                        fl[bb][mu] -= zb * rd.g[mu];
-                        fe[bb][mu] += pb * rd.g[mu] + zb * (hv[mu] + T(0.5) * rd.tl[mu]);
+                        // dl -= zb grad chi;  de += pb grad chi + zb (H gU + 1/2 grad lap chi)
+                        fl[bb][mu] -= zb * g1 * pv[mu];
+                        fe[bb][mu] += cp * pv[mu] + cq * qg[mu] + hz * pv[mu] * (A + T(8) * f2 * qv[mu]);
                     }
                 }
             }

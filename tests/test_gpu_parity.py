@@ -180,3 +180,58 @@ def test_errors_are_reported():
     with pytest.raises(q.QMCError) as e:
         q.QMCSystem(q.Config.from_workload(wl, walkers=1), wl.R)
     assert e.value.code == -1
+
+
+def test_adjoint_forces_vs_finite_differences_of_oracle_energy():
+    """N=64 (2 Gaussians/proton), 8 seeded |psi|^2 configurations: the GPU's
+    adjoint dE_L/dR and d ln psi/dR against central differences (h = 1e-4 bohr)
+    of the oracle's E_L and ln|psi|, on a sample of nuclear coordinates."""
+    wl = synth.workload("h64")
+    X = _sampled(wl, 8, 41, sweeps=6)
+    sysg = q.QMCSystem(q.Config.from_workload(wl, precision=q.QMC_FP64, walkers=8), wl.R)
+    g = sysg.eval_config(X, wl.R)
+    osys = _oracle_sys(wl)
+    h = 1e-4
+    rng = np.random.default_rng(3)
+    coords = [(int(a), int(m)) for a, m in zip(rng.integers(0, wl.N, 6), rng.integers(0, 3, 6))]
+    for a, m in coords:
+        Rp = wl.R.copy(); Rp[a, m] += h
+        Rm = wl.R.copy(); Rm[a, m] -= h
+        lp_p, el_p, _, _ = orc.eval_configs(osys, Rp, X, derivs=False)
+        lp_m, el_m, _, _ = orc.eval_configs(osys, Rm, X, derivs=False)
+        fd_e = (el_p - el_m) / (2 * h)
+        fd_l = (lp_p - lp_m) / (2 * h)
+        scale_e = np.max(np.abs(g["del_"]), axis=(1, 2))
+        scale_l = np.max(np.abs(g["dlnpsi"]), axis=(1, 2))
+        assert np.all(np.abs(g["del_"][:, a, m] - fd_e) <= 1e-5 * scale_e), (a, m, g["del_"][:, a, m], fd_e)
+        assert np.all(np.abs(g["dlnpsi"][:, a, m] - fd_l) <= 1e-5 * scale_l), (a, m)
+
+
+def test_small_system_md_end_to_end_both_forms_and_both_S():
+    """N=16, 256 walkers x 200 sweeps: E, 48 forces and their covariance, then 10
+    Langevin steps at T = 1000 K, Delta = 0.1 with S = I and with S = Cov(f)."""
+    wl = synth.workload("h16")
+    res = {}
+    for prec in (q.QMC_FP64, q.QMC_MIXED):
+        for mode in (q.QMC_S_IDENTITY, q.QMC_S_COV):
+            s = q.QMCSystem(q.Config.from_workload(wl, precision=prec, warmup=20, warmup_cont=5), wl.R)
+            R = wl.R.copy()
+            Es = []
+            for step in range(10):
+                r = s.energy_forces(R)
+                assert np.isfinite(r["E"]) and np.all(np.isfinite(r["f"])) and r["f"].shape == (48,)
+                S = r["S"]
+                assert np.allclose(S, S.T) and np.all(np.linalg.eigvalsh(S) > 0)
+                assert r["Nc"] == 256 * 200 and 0.3 < r["accept"] < 0.95
+                Rn = s.langevin_step(R, r["f"], S if mode == q.QMC_S_COV else None, 1000.0, 0.1, s_mode=mode)
+                disp = Rn.reshape(-1, 3) - R
+                disp -= wl.L * np.round(disp / wl.L)
+                assert np.all(np.abs(disp) < 0.5 * wl.L)
+                R = Rn.reshape(-1, 3)
+                Es.append((r["E"], r["E_err"]))
+            res[(prec, mode)] = Es
+            s.close()
+    # first MD step (same nuclei): FP64 and mixed forms agree within their error bars
+    for mode in (q.QMC_S_IDENTITY, q.QMC_S_COV):
+        (e64, s64), (e32, s32) = res[(q.QMC_FP64, mode)][0], res[(q.QMC_MIXED, mode)][0]
+        assert abs(e64 - e32) < 4 * np.hypot(s64, s32)
