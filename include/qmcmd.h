@@ -180,9 +180,14 @@ int qmc_get_accumulators(qmc_system* h, double* acc);
 
 /* Handle options.  QMC_OPT_TENSOR_CORES (mixed form only, default 1): evaluate
  * the orbital contractions with the tcgen05 tensor-core kernel (3xTF32 split,
- * FP32-level accuracy); 0 selects the SIMT FP32 kernel.  INVALID for an
- * unknown option or when the form has no tensor-core kernel. */
-enum { QMC_OPT_TENSOR_CORES = 1 };
+ * FP32-level accuracy); 0 selects the SIMT FP32 kernel.
+ * QMC_OPT_TC_ADJOINT (mixed form with N <= 128, n_gauss <= 4; default 1):
+ * while tensor cores are on, the B x n contractions of the orbital force terms
+ * (Z = C G, P = C G Y G) and their basis-derivative epilogue run in a separate
+ * tcgen05 kernel (2xTF32 pieces, 3 products); 0 keeps them in the SIMT
+ * measure kernel.  INVALID for an unknown option or when the form has no such
+ * kernel. */
+enum { QMC_OPT_TENSOR_CORES = 1, QMC_OPT_TC_ADJOINT = 2 };
 int qmc_set_option(qmc_system* h, int option, int value);
 
 /* Set the MD step counter used in the Philox counters of the next call. */
@@ -191,7 +196,7 @@ int qmc_set_md_step(qmc_system* h, uint32_t md_step);
 /* Kernel timing: when enabled, CUDA events on h's stream bracket every kernel
  * class; qmc_kernel_times fills ms[k] (total ms) and launches[k] for the
  * n <= QMC_NKERNEL classes named by qmc_kernel_name(k), then resets them. */
-enum { QMC_NKERNEL = 8 };
+enum { QMC_NKERNEL = 9 };
 int qmc_set_profiling(qmc_system* h, int on);
 int qmc_kernel_times(qmc_system* h, int n, double* ms, long long* launches);
 const char* qmc_kernel_name(int k);

@@ -17,9 +17,11 @@ namespace {
 
 constexpr double kBoltzmannHaPerK = 3.166811563e-6;
 
-const char* kKernelNames[QMC_NKERNEL] = {"propose", "orbitals_prop", "sweep", "recompute",
-                                         "orbitals_meas", "measure", "reduce", "langevin"};
-enum { KC_PROPOSE = 0, KC_ORB_PROP, KC_SWEEP, KC_RECOMPUTE, KC_ORB_MEAS, KC_MEASURE, KC_REDUCE, KC_LANGEVIN };
+const char* kKernelNames[QMC_NKERNEL] = {"propose", "orbitals_prop", "sweep",  "recompute", "orbitals_meas",
+                                         "measure", "reduce",        "langevin", "adjoint"};
+enum {
+    KC_PROPOSE = 0, KC_ORB_PROP, KC_SWEEP, KC_RECOMPUTE, KC_ORB_MEAS, KC_MEASURE, KC_REDUCE, KC_LANGEVIN, KC_ADJOINT
+};
 
 struct EventPair { cudaEvent_t a, b; int cls; };
 
@@ -42,6 +44,12 @@ struct qmc_system {
     float2* d_eikR32 = nullptr;
     void* d_chat = nullptr;    // C^T chunks, TF32 hi/lo, swizzled (tensor-core orbital kernel)
     bool use_tc = false;
+    // tensor-core adjoint (mixed form): C rows per Gaussian in TF32 pieces,
+    // K^T per walker-spin, electron data and E_L per walker
+    void* d_ahat = nullptr;
+    float *d_Kt = nullptr, *d_eg = nullptr;
+    double* d_elw = nullptr;
+    bool use_tc_adj = false;
     // walkers
     double *d_X = nullptr, *d_Xp = nullptr;
     void *d_uacc = nullptr, *d_Phi = nullptr, *d_Gt = nullptr, *d_D = nullptr, *d_Lp = nullptr;
@@ -127,6 +135,10 @@ size_t footprint(const qmc_params* p) {
     b += 8 * (4 + 9 * N) + 8 * W * (3 * N + 1) + 8 * (4 + 3 * N + 9 * N * N);   // colsum, dev, out
     b += 8 * (2 * W + 6 * W * N);                    // eval outputs
     b += 8 * (3 * 3 * N + 3 * 9 * N * N);           // Langevin
+    if (t == 4) {                                    // tensor-core operands (mixed form)
+        b += tc_coeff_bytes((int)B, (int)n);
+        b += tc_adjoint_coeff_bytes((int)n, (int)G) + 4 * (2 * W * n * n + 9 * W * N) + 8 * W;
+    }
     return b;
 }
 
@@ -207,10 +219,19 @@ void measure(qmc_system* h, int W, double* el, double* lnpsi, double* dl, double
     prof_begin(h, KC_ORB_MEAS, ep);
     orbitals<T>(h, s, h->d_X, W * h->N, (T*)h->d_Phi, (T*)h->d_D, (T*)h->d_Lp);
     prof_end(h, ep);
+    const bool split = sizeof(T) == 4 && h->use_tc && h->use_tc_adj;
     prof_begin(h, KC_MEASURE, ep);
     launch_measure<T>(s, h->d_X, (const T*)h->d_D, (const T*)h->d_Lp, (const T*)h->d_Gt, h->d_logdet, h->d_acc, el,
-                      lnpsi, dl, de, h->stream);
+                      lnpsi, dl, de, split ? h->d_Kt : nullptr, split ? h->d_eg : nullptr,
+                      split ? h->d_elw : nullptr, h->stream);
     prof_end(h, ep);
+    if (split) {
+        h->nlaunch += 1;
+        prof_begin(h, KC_ADJOINT, ep);
+        launch_adjoint_tc(*(const SysView<float>*)&s, h->d_ahat, (const float*)h->d_Gt, h->d_Kt, h->d_eg, h->d_elw,
+                          h->d_acc, dl, de, h->stream);
+        prof_end(h, ep);
+    }
 }
 
 template <typename T>
@@ -340,6 +361,13 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
     if (h->mixed && tc_orbitals_supported(n, B)) {
         h->d_chat = dalloc<unsigned char>(h, tc_coeff_bytes(B, n), &rc);
         h->use_tc = true;
+        if (tc_adjoint_supported(N, n, h->G)) {
+            h->d_ahat = dalloc<unsigned char>(h, tc_adjoint_coeff_bytes(n, h->G), &rc);
+            h->d_Kt = dalloc<float>(h, (size_t)W * 2 * n * n, &rc);
+            h->d_eg = dalloc<float>(h, (size_t)W * N * 9, &rc);
+            h->d_elw = dalloc<double>(h, W, &rc);
+            h->use_tc_adj = true;
+        }
     }
     if (rc != QMC_OK) { qmc_destroy(h); return rc; }
     std::vector<float> c32(h->coeff_h.begin(), h->coeff_h.end());
@@ -354,6 +382,7 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
     cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
     cudaMemsetAsync(h->d_nacc, 0, sizeof(unsigned long long) * W, st);
     if (h->d_chat) prepare_tc_coeff(h->d_C32, B, n, h->d_chat, st);
+    if (h->d_ahat) prepare_tc_adjoint_coeff(h->d_C32, N, h->G, n, h->d_ahat, st);
     setup_tables(h);
     launch_init_walkers(W, N, p->L, h->d_R, h->d_X, make_key(p->seed), st);
     rc = check_launch();
@@ -512,6 +541,11 @@ int qmc_set_option(qmc_system* h, int option, int value) {
     if (option == QMC_OPT_TENSOR_CORES) {
         if (value && !h->d_chat) return QMC_ERR_INVALID;
         h->use_tc = value != 0;
+        return QMC_OK;
+    }
+    if (option == QMC_OPT_TC_ADJOINT) {
+        if (value && !h->d_ahat) return QMC_ERR_INVALID;
+        h->use_tc_adj = value != 0;
         return QMC_OK;
     }
     return QMC_ERR_INVALID;

@@ -80,13 +80,18 @@ __device__ __forceinline__ void ep_pair(const S sd[3], const S cd[3], S ell, S k
     v = ewald_real<S>(dx, dy, dz, L, kap, g);
 }
 
-template <typename T>
+// kSplit: the B x n orbital contractions and their basis-derivative epilogue
+// are left to the tensor-core adjoint kernel; this kernel then writes what
+// that kernel needs: K^T per spin block (kt_out), the electrons' (sin, cos)
+// and grad U (eg_out, 9 per electron) and E_L of the sample (elw).
+template <typename T, bool kSplit>
 __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, const double* __restrict__ X,
                                                       const T* __restrict__ D, const T* __restrict__ Lp,
                                                       const T* __restrict__ Gt, const double* __restrict__ logdet,
                                                       double* __restrict__ acc, double* __restrict__ out_el,
                                                       double* __restrict__ out_lnpsi, double* __restrict__ out_dl,
-                                                      double* __restrict__ out_de) {
+                                                      double* __restrict__ out_de, float* __restrict__ kt_out,
+                                                      float* __restrict__ eg_out, double* __restrict__ elw) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int N = s.N, n = s.n, G = s.G, nk = s.nk;
     const MLayout<T> lay(N, n, nk, mmax);
@@ -426,6 +431,15 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
                 for (int b_ = 0; b_ < 4; ++b_) bufA[(r0 + a_) * ldt + c0 + b_] = acc4[a_][b_];
         }
         __syncthreads();
+        if constexpr (kSplit) {
+            float* ko = kt_out + ((size_t)w * 2 + sp) * n * n;
+            for (int idx = tid; idx < n * n; idx += nt) {
+                const int i = idx / n, j = idx - i * n;
+                ko[idx] = (float)bufA[j * ldt + i];
+            }
+            __syncthreads();
+            continue;
+        }
         const int B = s.B;
         for (int b0 = 0; b0 < B; b0 += 64) {
             for (int idx = tid; idx < 64 * np; idx += nt) {   // C^T tile
@@ -551,6 +565,13 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
         aw[3 + 2 * N3 + c] += de;
         if (out_dl) { out_dl[(size_t)w * N3 + c] = dl; out_de[(size_t)w * N3 + c] = de; }
     }
+    if constexpr (kSplit) {
+        for (int idx = tid; idx < 9 * N; idx += nt) {
+            const int i = idx / 9, c = idx - 9 * i;
+            eg_out[(size_t)w * 9 * N + idx] = (float)(c < 6 ? et[6 * i + c] : gU[3 * i + c - 6]);
+        }
+        if (tid == 0) elw[w] = EL;
+    }
     if (tid == 0) {
         aw[0] += 1.0; aw[1] += EL; aw[2] += EL * EL;
         if (out_el) { out_el[w] = EL; out_lnpsi[w] = logdet[2 * w] + logdet[2 * w + 1] + Utot; }
@@ -565,23 +586,41 @@ size_t measure_smem_bytes(int N, int n, int nk, int mmax) {
 
 template <typename T>
 void launch_measure(const SysView<T>& s, const double* X, const T* D, const T* Lp, const T* Gt, const double* logdet,
-                    double* acc, double* out_el, double* out_lnpsi, double* out_dl, double* out_de, cudaStream_t st) {
+                    double* acc, double* out_el, double* out_lnpsi, double* out_dl, double* out_de, float* kt_out,
+                    float* eg_out, double* elw, cudaStream_t st) {
     const size_t smem = measure_smem_bytes<T>(s.N, s.n, s.nk, s.mmax);
-    static bool attr_set[2] = {false, false};
-    const int which = sizeof(T) == 8;
-    if (!attr_set[which]) {
-        cudaFuncSetAttribute(measure_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        attr_set[which] = true;
+    static bool attr_set[3] = {false, false, false};
+    const bool split = sizeof(T) == 4 && kt_out != nullptr;
+    const int which = sizeof(T) == 8 ? 1 : (split ? 2 : 0);
+    if constexpr (sizeof(T) == 4) {
+        if (split) {
+            if (!attr_set[which]) {
+                cudaFuncSetAttribute(measure_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     227 * 1024);
+                attr_set[which] = true;
+            }
+            measure_kernel<T, true><<<s.W, 256, smem, st>>>(s, s.mmax, X, D, Lp, Gt, logdet, acc, out_el, out_lnpsi,
+                                                            out_dl, out_de, kt_out, eg_out, elw);
+            return;
+        }
     }
-    measure_kernel<T><<<s.W, 256, smem, st>>>(s, s.mmax, X, D, Lp, Gt, logdet, acc, out_el, out_lnpsi, out_dl, out_de);
+    {
+        if (!attr_set[which]) {
+            cudaFuncSetAttribute(measure_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+            attr_set[which] = true;
+        }
+        measure_kernel<T, false><<<s.W, 256, smem, st>>>(s, s.mmax, X, D, Lp, Gt, logdet, acc, out_el, out_lnpsi,
+                                                         out_dl, out_de, nullptr, nullptr, nullptr);
+    }
 }
 
 template size_t measure_smem_bytes<double>(int, int, int, int);
 template size_t measure_smem_bytes<float>(int, int, int, int);
 template void launch_measure<double>(const SysView<double>&, const double*, const double*, const double*,
                                      const double*, const double*, double*, double*, double*, double*, double*,
-                                     cudaStream_t);
+                                     float*, float*, double*, cudaStream_t);
 template void launch_measure<float>(const SysView<float>&, const double*, const float*, const float*, const float*,
-                                    const double*, double*, double*, double*, double*, double*, cudaStream_t);
+                                    const double*, double*, double*, double*, double*, double*, float*, float*,
+                                    double*, cudaStream_t);
 
 }  // namespace qmc

@@ -19,6 +19,14 @@ void launch_orbitals_tc(const SysView<float>& s, const void* chat, const double*
 void prepare_tc_coeff(const float* C, int B, int n, void* chat, cudaStream_t st);
 size_t tc_coeff_bytes(int B, int n);
 
+// k_adjoint_tc.cu (tensor-core form of the orbital part of the force
+// estimators; the measure kernel then runs with kt_out/eg_out/elw set)
+bool tc_adjoint_supported(int N, int n, int G);
+size_t tc_adjoint_coeff_bytes(int n, int G);
+void prepare_tc_adjoint_coeff(const float* C, int N, int G, int n, void* ahat, cudaStream_t st);
+void launch_adjoint_tc(const SysView<float>& s, const void* ahat, const float* Gt, const float* Kt, const float* eg,
+                       const double* elw, double* acc, double* out_dl, double* out_de, cudaStream_t st);
+
 // k_invert.cu: FP64 Gauss-Jordan inverse of each walker's two Slater blocks.
 template <typename T>
 void launch_invert(int W, int N, int n, const T* Phi, T* Gt, double* logdet, int* err, cudaStream_t st);
@@ -32,7 +40,7 @@ void launch_sweep(const SysView<T>& s, double* X, const double* Xp, const T* ptp
 template <typename T>
 void launch_measure(const SysView<T>& s, const double* X, const T* D, const T* Lp, const T* Gt,
                     const double* logdet, double* acc, double* out_el, double* out_lnpsi, double* out_dl,
-                    double* out_de, cudaStream_t st);
+                    double* out_de, float* kt_out, float* eg_out, double* elw, cudaStream_t st);
 template <typename T>
 size_t measure_smem_bytes(int N, int n, int nk, int mmax);
 

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libqmcmd.so")
 
 QMC_FP64, QMC_MIXED = 0, 1
 QMC_S_IDENTITY, QMC_S_COV = 0, 1
-NKERNEL = 8
+NKERNEL = 9
 
 
 class QMCError(RuntimeError):
@@ -251,6 +251,11 @@ class QMCSystem:
 
     def set_tensor_cores(self, on: bool):
         _chk(lib().qmc_set_option(self._h, 1, int(on)), "qmc_set_option")
+
+    def set_tc_adjoint(self, on: bool):
+        """Orbital force terms in the separate tensor-core kernel (True) or in
+        the SIMT measure kernel (False); effective while tensor cores are on."""
+        _chk(lib().qmc_set_option(self._h, 2, int(on)), "qmc_set_option")
 
     def set_profiling(self, on: bool):
         _chk(lib().qmc_set_profiling(self._h, int(on)), "qmc_set_profiling")

@@ -90,6 +90,35 @@ def test_tensor_core_orbitals_match_simt(name):
     assert np.all(_rel_vec(tc["dlnpsi"], simt["dlnpsi"]) <= 2e-5)
 
 
+@pytest.mark.parametrize("name,nconf", [("h16", 4), ("h64", 4), ("h128", 2)])
+def test_tensor_core_adjoint_matches_simt(name, nconf):
+    """The tcgen05 form of the orbital force terms (Z = C G, P = C G Y G and
+    the basis-derivative epilogue) agrees with the SIMT FP32 form."""
+    wl = synth.workload(name)
+    X = _sampled(wl, nconf, 23, sweeps=4)
+    s = q.QMCSystem(q.Config.from_workload(wl, precision=q.QMC_MIXED, walkers=nconf), wl.R)
+    tc = s.eval_config(X, wl.R)
+    s.set_tc_adjoint(False)
+    simt = s.eval_config(X, wl.R)
+    assert np.array_equal(tc["el"], simt["el"]) and np.array_equal(tc["lnpsi"], simt["lnpsi"])
+    assert np.all(_rel_vec(tc["dlnpsi"], simt["dlnpsi"]) <= 2e-5), _rel_vec(tc["dlnpsi"], simt["dlnpsi"])
+    assert np.all(_rel_vec(tc["del_"], simt["del_"]) <= 2e-5), _rel_vec(tc["del_"], simt["del_"])
+
+
+def test_tensor_core_adjoint_chain_matches_simt():
+    """More walkers than SMs (each persistent CTA takes several walkers), four
+    Gaussians (the A-operand refill path): same chain, forces and S agree."""
+    wl = synth.workload("h128", walkers=320, sweeps=2, warmup=2)
+    cfg = q.Config.from_workload(wl, precision=q.QMC_MIXED)
+    ra = q.QMCSystem(cfg, wl.R).energy_forces(wl.R)
+    b = q.QMCSystem(cfg, wl.R)
+    b.set_tc_adjoint(False)
+    rb = b.energy_forces(wl.R)
+    assert ra["E"] == rb["E"] and ra["accept"] == rb["accept"]
+    assert np.max(np.abs(ra["f"] - rb["f"])) <= 2e-5 * np.max(np.abs(rb["f"]))
+    assert np.max(np.abs(ra["S"] - rb["S"])) <= 1e-4 * np.max(np.abs(rb["S"]))
+
+
 def test_walker_start_matches_oracle():
     wl = synth.workload("h16", walkers=32)
     sysg = q.QMCSystem(q.Config.from_workload(wl), wl.R)
