@@ -28,8 +28,9 @@
 // measure kernel).  Products A0 B0 + A0 B1 + A1 B0 (dropped A1 B1 below
 // 2^-24 relative): FP32-level accuracy.
 //
-// One CTA per SM (persistent), 256 threads: warps w and w + 4 read TMEM lane
-// quarter w % 4 and split the electrons in halves.  Every mbarrier wait is
+// One CTA per SM (persistent), 512 threads: warps w, w + 4, w + 8, w + 12 read
+// TMEM lane quarter w % 4 and split the electrons in four parts.  The next
+// walker-spin's operands are fetched while the current epilogue runs.  Every mbarrier wait is
 // bounded; on a timeout the kernel records kErrTimeout, waits (bounded) for
 // its copies in flight, frees tensor memory and returns.
 #include "common.cuh"
@@ -44,6 +45,10 @@ constexpr int kKc = 32;                     // orbitals per K chunk (128 bytes o
 constexpr int kTileA = kRowsA * kKc * 4;    // 16 KB
 constexpr int kPcs = 2;                     // TF32 pieces per operand
 constexpr long long kWaitIter = 1ll << 26;
+constexpr int kThreads = 512;               // 16 warps: 4 per TMEM lane quarter
+constexpr int kParts = kThreads / 128;      // electron parts per nucleus
+constexpr int kPreItems = 4;                // B items (4 orbitals) per thread: 128 rows x 16 / 512
+constexpr int kPreElec = 2;                 // electron-data floats per thread: 9 x 64 / 512, rounded up
 
 __host__ __device__ inline int adj_n16(int n) { return n <= 16 ? 16 : ((n + 15) / 16) * 16; }
 __host__ __device__ inline int adj_nkc(int n) { return (n + kKc - 1) / kKc; }
@@ -55,7 +60,7 @@ __host__ __device__ inline uint32_t adj_tmem_cols(int n, int G) {
     return c;
 }
 inline size_t adj_smem(int n) {
-    return 1024 + 2 * adj_abytes(n) + adj_bbytes(n) + sizeof(float) * 64 * 9 + sizeof(double) * 2 * 128 * 6;
+    return 1024 + 2 * adj_abytes(n) + adj_bbytes(n) + sizeof(float) * 64 * 12 + sizeof(float) * kParts * 128 * 6;
 }
 }  // namespace
 
@@ -92,6 +97,15 @@ void prepare_tc_adjoint_coeff(const float* C, int N, int G, int n, void* ahat, c
 
 namespace {
 
+// 2^x by the hardware approximation (PTX ex2.approx.ftz.f32, relative error of
+// a few ulp; the exponents here stay above -126, so flushing subnormals to
+// zero changes nothing).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // State of the A-operand pipeline, kept by the issuing thread only.
 struct APipe {
     int held[2];      // Gaussian whose A tiles are (or are being) loaded into buffer b
@@ -102,18 +116,26 @@ struct APipe {
 
 }  // namespace
 
-__global__ void __launch_bounds__(256, 1)
+// Registers of one thread's share of the next walker-spin's operands, loaded
+// from HBM while the current epilogue runs.
+struct BPrefetch {
+    float4 v[kPreItems];   // four consecutive orbitals of one B row
+    float e[kPreElec];     // electron data (sin, cos, grad U)
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
     adjoint_tc_kernel(SysView<float> s, const unsigned char* __restrict__ ahat, const float* __restrict__ Gt,
                       const float* __restrict__ Kt, const float* __restrict__ eg, const double* __restrict__ elw,
                       double* __restrict__ acc, double* __restrict__ out_dl, double* __restrict__ out_de) {
     extern __shared__ unsigned char smraw[];
     unsigned char* base = (unsigned char*)((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
     const int N = s.N, n = s.n, G = s.G, W = s.W;
-    const int n16 = adj_n16(n), NN = 2 * n16, nkc = adj_nkc(n), nK = nkc * kKc;
+    const int n16 = adj_n16(n), NN = 2 * n16, nkc = adj_nkc(n), nK = nkc * kKc, kg = nK / 4;
+    const int kg_shift = nkc == 1 ? 3 : 4;   // kg = 8 nkc is a power of two (nkc <= 2): no integer division
     const size_t abytes = adj_abytes(n), bbytes = adj_bbytes(n);
     unsigned char* sB = base + 2 * abytes;
-    float* se = (float*)(sB + bbytes);                  // [n][9]: sin, cos (pi x / L), grad U of the spin's electrons
-    double* stage = (double*)(se + 64 * 9);             // [2][128][6]
+    float* se = (float*)(sB + bbytes);                  // [n][12]: sin, cos (pi x / L), grad U, pad
+    float* stage = se + 64 * 12;                        // [kParts][128][6]
     __shared__ uint64_t full[2], empty[2], done;
     __shared__ uint32_t tbase;
     __shared__ int abort_flag;
@@ -128,25 +150,96 @@ __global__ void __launch_bounds__(256, 1)
         tc::fence_mbar_init();
         abort_flag = 0;
     }
+    for (int idx = tid; idx < 64 * 12; idx += kThreads) se[idx] = 0.f;
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tbase;
     const uint32_t idesc = tc::idesc_tf32(kRowsA, NN);
 
-    // epilogue role: nucleus a = lane quarter row, electron half h
-    const int quarter = warp & 3, half = warp >> 2;
+    // epilogue role: nucleus a = row of the lane quarter, electron part
+    const int quarter = warp & 3, part = warp >> 2;
     const int a = quarter * 32 + lane;
     const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
     const float ell = (float)s.ell;
     const float twopiL = (float)(2.0 * kPi / s.L), k2 = twopiL * twopiL;
-    float pt[6], zt[4];
+    // per-Gaussian constants of the epilogue (chi = exp(-zeta t) = 2^(-zl t)):
+    //   sum_g zb f'   = -sum zeta (e zb),       4 f'' zb = 4 zeta^2 (e zb),
+    //   pb 2 f' + zb (4 f'' p.gU + A/2) = -2 zeta (e pb) + (e zb) Q_g,
+    //   Q_g = 4 zeta^2 p.gU - 4 zeta^3 |p|^2 + 2 zeta^2 sum q + k^2 zeta
+    float pt[6], zl[4], cz[4], c4z2[4], cq3[4], cq2[4], cq0[4];
 #pragma unroll
     for (int c = 0; c < 6; ++c) pt[c] = a < N ? s.ptrig[6 * a + c] : 0.f;
 #pragma unroll
-    for (int g = 0; g < 4; ++g) zt[g] = g < G ? s.zetat[g] : 0.f;
-    const int hn = n16 / 2;
-    const int i_lo = half * hn, i_hi = (half + 1) * hn < n ? (half + 1) * hn : n;
+    for (int g = 0; g < 4; ++g) {
+        const float z = g < G ? s.zetat[g] : 0.f;
+        zl[g] = z * 1.4426950408889634f;
+        cz[g] = z;
+        c4z2[g] = 4.f * z * z;
+        cq3[g] = -4.f * z * z * z;
+        cq2[g] = 2.f * z * z;
+        cq0[g] = k2 * z;
+    }
+    const int pn = n16 / kParts;
+    const int i_lo = part * pn, i_hi = (part + 1) * pn < n ? (part + 1) * pn : n;
+    const bool vec4 = (n & 3) == 0;
+
+    // walker-spins of this CTA: t = 0, 1, ... -> walker blockIdx.x + (t / 2) * gridDim.x, spin t % 2
+    const int nws = 2 * ((W - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x);
+    auto prefetch = [&](int t, BPrefetch& pf) {
+        const int w = blockIdx.x + (t >> 1) * gridDim.x, sp = t & 1;
+        const float* gsrc = Gt + ((size_t)w * 2 + sp) * n * n;
+        const float* ksrc = Kt + ((size_t)w * 2 + sp) * n * n;
+#pragma unroll
+        for (int k = 0; k < kPreItems; ++k) {
+            const int item = tid + k * kThreads;
+            const int r = item >> kg_shift, k0 = 4 * (item & (kg - 1));
+            const int rr = r < n16 ? r : r - n16;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (item < NN * kg && rr < n && k0 < n) {
+                const float* src = (r < n16 ? gsrc : ksrc) + (size_t)rr * n + k0;
+                if (vec4) {
+                    v = *(const float4*)src;
+                } else {
+                    v.x = src[0];
+                    if (k0 + 1 < n) v.y = src[1];
+                    if (k0 + 2 < n) v.z = src[2];
+                    if (k0 + 3 < n) v.w = src[3];
+                }
+            }
+            pf.v[k] = v;
+        }
+        const float* esrc = eg + ((size_t)w * N + sp * n) * 9;
+#pragma unroll
+        for (int k = 0; k < kPreElec; ++k) {
+            const int idx = tid + k * kThreads;
+            pf.e[k] = idx < 9 * n ? esrc[idx] : 0.f;
+        }
+    };
+    auto store = [&](const BPrefetch& pf) {
+#pragma unroll
+        for (int k = 0; k < kPreItems; ++k) {
+            const int item = tid + k * kThreads;
+            if (item < NN * kg) {
+                const int r = item >> kg_shift, k0 = 4 * (item & (kg - 1));
+                float4 x0, x1;
+                tc::split_tf32(pf.v[k].x, x0.x, x1.x);
+                tc::split_tf32(pf.v[k].y, x0.y, x1.y);
+                tc::split_tf32(pf.v[k].z, x0.z, x1.z);
+                tc::split_tf32(pf.v[k].w, x0.w, x1.w);
+                const int kc = k0 / kKc;
+                const uint32_t off = tc::sw128_off(r, k0 - kc * kKc);
+                *(float4*)(sB + (size_t)(0 * nkc + kc) * NN * 128 + off) = x0;
+                *(float4*)(sB + (size_t)(1 * nkc + kc) * NN * 128 + off) = x1;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kPreElec; ++k) {
+            const int idx = tid + k * kThreads;
+            if (idx < 9 * n) se[(idx / 9) * 12 + idx % 9] = pf.e[k];
+        }
+        tc::fence_proxy_async();
+    };
 
     APipe ap{{-1, -1}, {false, false}, {0u, 0u}, {0u, 0u}};
     uint32_t ph_done = 0;
@@ -157,182 +250,191 @@ __global__ void __launch_bounds__(256, 1)
         ap.held[b] = g;
         ap.pend[b] = true;
     };
-    if (tid == 0) {
+    if (tid == 0 && nws > 0) {
         load_a(0, 0);
         if (G > 1) load_a(1, 1);
     }
+    BPrefetch pf;
+    if (nws > 0) {
+        prefetch(0, pf);
+        store(pf);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
 
-    for (int w = blockIdx.x; w < W; w += gridDim.x) {
-        double dfl[3] = {0.0, 0.0, 0.0}, dfe[3] = {0.0, 0.0, 0.0};
-        for (int sp = 0; sp < 2; ++sp) {
-            // ---- B operand [G^T ; K^T] (two TF32 pieces) and the electron data
-            const float* gsrc = Gt + ((size_t)w * 2 + sp) * n * n;
-            const float* ksrc = Kt + ((size_t)w * 2 + sp) * n * n;
-            const int kg = nK / 4;
-            for (int item = tid; item < NN * kg; item += blockDim.x) {
-                const int r = item / kg, k0 = 4 * (item - r * kg);
-                const int rr = r < n16 ? r : r - n16;
-                const float* src = (r < n16 ? gsrc : ksrc) + (size_t)rr * n;
-                float v[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) v[q] = (rr < n && k0 + q < n) ? src[k0 + q] : 0.f;
-                float4 x0, x1;
-                tc::split_tf32(v[0], x0.x, x1.x);
-                tc::split_tf32(v[1], x0.y, x1.y);
-                tc::split_tf32(v[2], x0.z, x1.z);
-                tc::split_tf32(v[3], x0.w, x1.w);
-                const int kc = k0 / kKc;
-                const uint32_t off = tc::sw128_off(r, k0 - kc * kKc);
-                *(float4*)(sB + (size_t)(0 * nkc + kc) * NN * 128 + off) = x0;
-                *(float4*)(sB + (size_t)(1 * nkc + kc) * NN * 128 + off) = x1;
-            }
-            for (int idx = tid; idx < 9 * n; idx += blockDim.x) se[idx] = eg[((size_t)w * N + sp * n) * 9 + idx];
-            tc::fence_proxy_async();
-            tc::fence_before_sync();
-            __syncthreads();
-            if (abort_flag) break;
-
-            // ---- MMAs (one thread): block g += A_g [G^T ; K^T]^T over the orbitals
-            if (tid == 0) {
-                tc::fence_after_sync();
-                const uint32_t b0 = tc::smem_addr(sB), bstep = (uint32_t)NN * 128;
-                bool epend[2] = {false, false};
-                for (int g = 0; g < G && ok; ++g) {
-                    const int b = g & 1;
-                    if (ap.held[b] != g) load_a(b, g);   // only if no refill was issued for it
-                    if (ap.pend[b]) {
-                        if (!tc::mbar_wait(&full[b], ap.phf[b], kWaitIter)) { ok = false; break; }
-                        ap.phf[b] ^= 1u;
-                        ap.pend[b] = false;
-                    }
-                    const uint32_t a0 = tc::smem_addr(base + (size_t)b * abytes);
-                    const uint32_t d = tmem + (uint32_t)(g * NN);
-                    for (int kc = 0; kc < nkc; ++kc)
-#pragma unroll
-                        for (int ks = 0; ks < kKc / 8; ++ks) {
-                            const uint32_t o = 32u * ks;
-                            const uint32_t aa = a0 + (uint32_t)kc * kTileA + o, bb = b0 + (uint32_t)kc * bstep + o;
-                            const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;
-                            // A1 B0, A0 B1, A0 B0 (smallest first)
-                            tc::mma_tf32(d, tc::desc_sw128(aa + (uint32_t)nkc * kTileA), tc::desc_sw128(bb), idesc,
-                                         first);
-                            tc::mma_tf32(d, tc::desc_sw128(aa), tc::desc_sw128(bb + (uint32_t)nkc * bstep), idesc, 1u);
-                            tc::mma_tf32(d, tc::desc_sw128(aa), tc::desc_sw128(bb), idesc, 1u);
-                        }
-                    // buffer b will take A_{g+2}: signal when these MMAs have read it
-                    if (g + 2 < G) { tc::mma_commit(&empty[b]); epend[b] = true; }
-                    // refill the other buffer with A_{g+1} once the MMAs of g-1 are done,
-                    // while the MMAs of g run
-                    const int b1 = b ^ 1;
-                    if (g + 1 < G && ap.held[b1] != g + 1) {
-                        if (epend[b1]) {
-                            if (!tc::mbar_wait(&empty[b1], ap.phe[b1], kWaitIter)) { ok = false; break; }
-                            ap.phe[b1] ^= 1u;
-                            epend[b1] = false;
-                        }
-                        load_a(b1, g + 1);
-                    }
-                }
-                tc::mma_commit(&done);
-                if (!ok) abort_flag = 1;
-            }
-            if (!tc::mbar_wait(&done, ph_done, kWaitIter)) ok = false;
-            ph_done ^= 1u;
+    float dfl[3] = {0.f, 0.f, 0.f}, dfe[3] = {0.f, 0.f, 0.f};   // this thread's share, both spins
+    for (int t = 0; t < nws; ++t) {
+        const int w = blockIdx.x + (t >> 1) * gridDim.x, sp = t & 1;
+        // ---- MMAs (one thread): block g += A_g [G^T ; K^T]^T over the orbitals
+        if (tid == 0) {
             tc::fence_after_sync();
+            const uint32_t b0 = tc::smem_addr(sB), bstep = (uint32_t)NN * 128;
+            bool epend[2] = {false, false};
+            for (int g = 0; g < G && ok; ++g) {
+                const int b = g & 1;
+                if (ap.held[b] != g) load_a(b, g);   // only if no refill was issued for it
+                if (ap.pend[b]) {
+                    if (!tc::mbar_wait(&full[b], ap.phf[b], kWaitIter)) { ok = false; break; }
+                    ap.phf[b] ^= 1u;
+                    ap.pend[b] = false;
+                }
+                const uint32_t a0 = tc::smem_addr(base + (size_t)b * abytes);
+                const uint32_t d = tmem + (uint32_t)(g * NN);
+                for (int kc = 0; kc < nkc; ++kc)
+#pragma unroll
+                    for (int ks = 0; ks < kKc / 8; ++ks) {
+                        const uint32_t o = 32u * ks;
+                        const uint32_t aa = a0 + (uint32_t)kc * kTileA + o, bb = b0 + (uint32_t)kc * bstep + o;
+                        const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;
+                        // A1 B0, A0 B1, A0 B0 (smallest first)
+                        tc::mma_tf32(d, tc::desc_sw128(aa + (uint32_t)nkc * kTileA), tc::desc_sw128(bb), idesc,
+                                     first);
+                        tc::mma_tf32(d, tc::desc_sw128(aa), tc::desc_sw128(bb + (uint32_t)nkc * bstep), idesc, 1u);
+                        tc::mma_tf32(d, tc::desc_sw128(aa), tc::desc_sw128(bb), idesc, 1u);
+                    }
+                // buffer b will take A_{g+2}: signal when these MMAs have read it
+                if (g + 2 < G) { tc::mma_commit(&empty[b]); epend[b] = true; }
+                // refill the other buffer with A_{g+1} once the MMAs of g-1 are
+                // done, while the MMAs of g run
+                const int b1 = b ^ 1;
+                if (g + 1 < G && ap.held[b1] != g + 1) {
+                    if (epend[b1]) {
+                        if (!tc::mbar_wait(&empty[b1], ap.phe[b1], kWaitIter)) { ok = false; break; }
+                        ap.phe[b1] ^= 1u;
+                        epend[b1] = false;
+                    }
+                    load_a(b1, g + 1);
+                }
+            }
+            tc::mma_commit(&done);
             if (!ok) abort_flag = 1;
-            // prefetch A_0, A_1 for the next walker-spin while the epilogue runs
-            const bool more = sp == 0 || w + (int)gridDim.x < W;
-            if (tid == 0 && ok && more)
-                for (int b = 0; b < 2 && b < G; ++b)
-                    if (ap.held[b] != b) load_a(b, b);
+        }
+        // one thread polls for the MMAs' completion; the others wait at the
+        // CTA barrier (no polling traffic while the tensor core reads its operands)
+        if (tid == 0) {
+            if (!tc::mbar_wait(&done, ph_done, kWaitIter)) { ok = false; abort_flag = 1; }
+            tc::fence_before_sync();
+        }
+        ph_done ^= 1u;
+        __syncthreads();
+        tc::fence_after_sync();
+        const bool more = t + 1 < nws;
+        // the next walker-spin's operands: A_0, A_1 by bulk copy, B and the
+        // electron data into registers, both in flight during the epilogue
+        if (tid == 0 && ok && more)
+            for (int b = 0; b < 2 && b < G; ++b)
+                if (ap.held[b] != b) load_a(b, b);
+        if (more) prefetch(t + 1, pf);
 
-            // ---- epilogue: thread (a, half) over its electrons, 8 at a time
-            float fl[3] = {0.f, 0.f, 0.f}, fe[3] = {0.f, 0.f, 0.f};
-            for (int i0 = i_lo; i0 < i_hi; i0 += 8) {
-                uint32_t zr[4][8], pr[4][8];
+        // ---- epilogue: thread (a, part) over its electrons, 4 at a time
+        if (sp == 0)
+#pragma unroll
+            for (int mu = 0; mu < 3; ++mu) { dfl[mu] = 0.f; dfe[mu] = 0.f; }
+        float* fl = dfl;
+        float* fe = dfe;
+        for (int i0 = i_lo; i0 < i_hi; i0 += 4) {
+            uint32_t zr[4][4], pr[4][4];
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+                if (g < G) {
+                    tc::tmem_ld4(taddr + (uint32_t)(g * NN + i0), zr[g]);
+                    tc::tmem_ld4(taddr + (uint32_t)(g * NN + n16 + i0), pr[g]);
+                }
+            tc::tmem_wait_ld();
+            // electrons i0 .. i0 + 3 < n16: beyond n the accumulator columns
+            // and the electron data are zero, so those terms vanish
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii) {
+                const int i = i0 + ii;
+                const float4 e0 = *(const float4*)(se + 12 * i), e1 = *(const float4*)(se + 12 * i + 4),
+                             e2 = *(const float4*)(se + 12 * i + 8);
+                const float sx[3] = {e0.x, e0.y, e0.z}, cx[3] = {e0.w, e1.x, e1.y}, gu[3] = {e1.z, e1.w, e2.x};
+                float pv[3], qv[3], t2 = 0.f, pp = 0.f, sq = 0.f, pg = 0.f;
+#pragma unroll
+                for (int mu = 0; mu < 3; ++mu) {
+                    const float sd = sx[mu] * pt[3 + mu] - cx[mu] * pt[mu];
+                    const float cd = cx[mu] * pt[3 + mu] + sx[mu] * pt[mu];
+                    t2 += sd * sd;
+                    pv[mu] = ell * sd * cd;
+                    qv[mu] = cd * cd - sd * sd;
+                }
+                t2 *= ell * ell;
+#pragma unroll
+                for (int mu = 0; mu < 3; ++mu) {
+                    pp += pv[mu] * pv[mu];
+                    sq += qv[mu];
+                    pg += pv[mu] * gu[mu];
+                }
+                // chi = exp(-zeta t): f' = -zeta chi, f'' = zeta^2 chi, f''' = -zeta^3 chi;
+                // grad chi = 2 f' p, H v = 4 f'' p (p.v) + 2 f' q o v,
+                // grad lap chi = p o (8 f''' |p|^2 + 4 f'' sum q - 2 k^2 f' + 8 f'' q)
+                float cl = 0.f, cp = 0.f, cpq = 0.f;
 #pragma unroll
                 for (int g = 0; g < 4; ++g)
                     if (g < G) {
-                        tc::tmem_ld8(taddr + (uint32_t)(g * NN + i0), zr[g]);
-                        tc::tmem_ld8(taddr + (uint32_t)(g * NN + n16 + i0), pr[g]);
+                        const float ex = ex2_approx(-zl[g] * t2);
+                        const float ez = ex * __uint_as_float(zr[g][ii]), ep = ex * __uint_as_float(pr[g][ii]);
+                        const float Q = c4z2[g] * pg + cq3[g] * pp + cq2[g] * sq + cq0[g];
+                        cl -= cz[g] * ez;
+                        cpq += c4z2[g] * ez;
+                        cp += ez * Q - 2.f * cz[g] * ep;
                     }
-                tc::tmem_wait_ld();
 #pragma unroll
-                for (int ii = 0; ii < 8; ++ii) {
-                    const int i = i0 + ii;
-                    if (i >= i_hi) break;
-                    const float* e = se + 9 * i;
-                    float sd[3], cd[3], pv[3], qv[3], t = 0.f, pp = 0.f, sq = 0.f, pg = 0.f;
-#pragma unroll
-                    for (int mu = 0; mu < 3; ++mu) {
-                        sd[mu] = e[mu] * pt[3 + mu] - e[3 + mu] * pt[mu];
-                        cd[mu] = e[3 + mu] * pt[3 + mu] + e[mu] * pt[mu];
-                        t += sd[mu] * sd[mu];
-                    }
-                    t *= ell * ell;
-#pragma unroll
-                    for (int mu = 0; mu < 3; ++mu) {
-                        pv[mu] = ell * sd[mu] * cd[mu];
-                        qv[mu] = cd[mu] * cd[mu] - sd[mu] * sd[mu];
-                        pp += pv[mu] * pv[mu];
-                        sq += qv[mu];
-                        pg += pv[mu] * e[6 + mu];
-                    }
-                    // chi = exp(-zeta t): f' = -zeta chi, f'' = zeta^2 chi, f''' = -zeta^3 chi;
-                    // grad chi = 2 f' p, H v = 4 f'' p (p.v) + 2 f' q o v,
-                    // grad lap chi = p o (8 f''' |p|^2 + 4 f'' sum q - 2 k^2 f' + 8 f'' q)
-                    float cl = 0.f, cp = 0.f, cpq = 0.f;
-#pragma unroll
-                    for (int g = 0; g < 4; ++g)
-                        if (g < G) {
-                            const float z = zt[g];
-                            const float ex = expf(-z * t);
-                            const float f1 = -z * ex, f2 = z * z * ex, f3 = -z * z * z * ex;
-                            const float A = 8.f * f3 * pp + 4.f * f2 * sq - 2.f * k2 * f1;
-                            const float zb = __uint_as_float(zr[g][ii]), pb = __uint_as_float(pr[g][ii]);
-                            cl += zb * f1;
-                            cp += pb * 2.f * f1 + zb * (4.f * f2 * pg + 0.5f * A);
-                            cpq += zb * 4.f * f2;
-                        }
-#pragma unroll
-                    for (int mu = 0; mu < 3; ++mu) {
-                        fl[mu] -= 2.f * cl * pv[mu];
-                        fe[mu] += cp * pv[mu] + 2.f * cl * qv[mu] * e[6 + mu] + cpq * pv[mu] * qv[mu];
-                    }
+                for (int mu = 0; mu < 3; ++mu) {
+                    fl[mu] -= 2.f * cl * pv[mu];
+                    fe[mu] += cp * pv[mu] + 2.f * cl * qv[mu] * gu[mu] + cpq * pv[mu] * qv[mu];
                 }
             }
-#pragma unroll
-            for (int mu = 0; mu < 3; ++mu) { dfl[mu] += (double)fl[mu]; dfe[mu] += (double)fe[mu]; }
-            tc::fence_before_sync();
-            __syncthreads();   // TMEM and the B operand are free for the next walker-spin
-            if (abort_flag) break;
         }
+        tc::fence_before_sync();
+        __syncthreads();   // TMEM and the B operand are free for the next walker-spin
         if (abort_flag) break;
-        // ---- per nucleus: the two electron halves, in order, into the walker's sums
-#pragma unroll
-        for (int mu = 0; mu < 3; ++mu) {
-            stage[((size_t)half * 128 + a) * 6 + mu] = dfl[mu];
-            stage[((size_t)half * 128 + a) * 6 + 3 + mu] = dfe[mu];
-        }
-        __syncthreads();
-        if (tid < N) {
-            const int N3 = 3 * N;
-            const double EL = elw[w];
-            double* aw = acc + (size_t)w * (3 + 9 * (size_t)N);
-            bool bad = false;
+        if (sp == 1) {
+            // ---- per nucleus: the electron parts, in order, into the walker's sums
 #pragma unroll
             for (int mu = 0; mu < 3; ++mu) {
-                const int c = 3 * tid + mu;
-                const double dl = stage[(size_t)tid * 6 + mu] + stage[((size_t)128 + tid) * 6 + mu];
-                const double de = stage[(size_t)tid * 6 + 3 + mu] + stage[((size_t)128 + tid) * 6 + 3 + mu];
-                if (!isfinite(dl) || !isfinite(de)) bad = true;
-                aw[3 + c] += dl;
-                aw[3 + N3 + c] += EL * dl;
-                aw[3 + 2 * N3 + c] += de;
-                if (out_dl) { out_dl[(size_t)w * N3 + c] += dl; out_de[(size_t)w * N3 + c] += de; }
+                stage[((size_t)part * 128 + a) * 6 + mu] = dfl[mu];
+                stage[((size_t)part * 128 + a) * 6 + 3 + mu] = dfe[mu];
             }
-            if (bad) raise_err(s.err, kErrNonfinite);
+            __syncthreads();
+            if (tid < N) {
+                const int N3 = 3 * N;
+                const double EL = elw[w];
+                double* aw = acc + (size_t)w * (3 + 9 * (size_t)N) + 3 + 3 * tid;
+                double dl[3], de[3], s0[3], s1[3], s2[3];
+                bool bad = false;
+#pragma unroll
+                for (int mu = 0; mu < 3; ++mu) {   // all loads first, then the updates
+                    s0[mu] = aw[mu];
+                    s1[mu] = aw[N3 + mu];
+                    s2[mu] = aw[2 * N3 + mu];
+                    float l = 0.f, e = 0.f;
+#pragma unroll
+                    for (int q = 0; q < kParts; ++q) {
+                        l += stage[((size_t)q * 128 + tid) * 6 + mu];
+                        e += stage[((size_t)q * 128 + tid) * 6 + 3 + mu];
+                    }
+                    if (!isfinite(l) || !isfinite(e)) bad = true;
+                    dl[mu] = (double)l;
+                    de[mu] = (double)e;
+                }
+#pragma unroll
+                for (int mu = 0; mu < 3; ++mu) {
+                    aw[mu] = s0[mu] + dl[mu];
+                    aw[N3 + mu] = s1[mu] + EL * dl[mu];
+                    aw[2 * N3 + mu] = s2[mu] + de[mu];
+                }
+                if (out_dl)
+#pragma unroll
+                    for (int mu = 0; mu < 3; ++mu) {
+                        out_dl[(size_t)w * N3 + 3 * tid + mu] += dl[mu];
+                        out_de[(size_t)w * N3 + 3 * tid + mu] += de[mu];
+                    }
+                if (bad) raise_err(s.err, kErrNonfinite);
+            }
         }
+        if (more) store(pf);
+        tc::fence_before_sync();
         __syncthreads();
     }
 
@@ -363,7 +465,7 @@ void launch_adjoint_tc(const SysView<float>& s, const void* ahat, const float* G
         cudaFuncSetAttribute(adjoint_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess)
         set_smem = smem;
     const int grid = s.W < sms[dev] ? s.W : sms[dev];
-    adjoint_tc_kernel<<<grid, 256, smem, st>>>(s, (const unsigned char*)ahat, Gt, Kt, eg, elw, acc, out_dl, out_de);
+    adjoint_tc_kernel<<<grid, kThreads, smem, st>>>(s, (const unsigned char*)ahat, Gt, Kt, eg, elw, acc, out_dl, out_de);
 }
 
 }  // namespace qmc

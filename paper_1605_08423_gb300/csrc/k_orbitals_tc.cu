@@ -181,6 +181,9 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 512, 1)
             }
             tc::mma_commit(&mbar);
         }
+        // the other lanes of the issuing warp wait here, not in the mbarrier
+        // poll below, so they do not hold up the single issuing lane
+        __syncwarp();
         if (!tc::mbar_wait(&mbar, (uint32_t)(c & 1), 1ll << 26)) ok = false;
         tc::fence_after_sync();
         __syncthreads();
