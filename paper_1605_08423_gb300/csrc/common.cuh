@@ -65,6 +65,13 @@ __device__ __forceinline__ double qexp(double x) { return exp(x); }
 __device__ __forceinline__ float qexp(float x) { return expf(x); }
 __device__ __forceinline__ double qsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float qsqrt(float x) { return sqrtf(x); }
+// Reciprocal and square root of the pair loops: IEEE in FP64; in FP32 the
+// hardware approximations (a few ulp), well inside the FP32-level tolerance of
+// the mixed form.
+__device__ __forceinline__ double qrcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float qrcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double qsqrt_pair(double x) { return sqrt(x); }
+__device__ __forceinline__ float qsqrt_pair(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
 __device__ __forceinline__ double qerfc(double x) { return erfc(x); }
 __device__ __forceinline__ float qerfc(float x) { return erfcf(x); }
 __device__ __forceinline__ double qrint(double x) { return rint(x); }
@@ -180,19 +187,19 @@ __device__ __forceinline__ void hess_mul(const T h[6], const T v[3], T out[3]) {
 //   e-n: u = -Zj rho / (1 + b rho)      (cusp -Zj)
 template <typename T>
 __device__ __forceinline__ void pade_ee(T b, T r, T& u, T& u1, T& u2) {
-    const T q = T(1) + b * r, iq = T(1) / q;
+    const T q = T(1) + b * r, iq = qrcp(q);
     u = T(0.5) * r * iq; u1 = T(0.5) * iq * iq; u2 = -b * iq * iq * iq;
 }
 template <typename T>
 __device__ __forceinline__ void pade_ep(T b, T Zj, T r, T& u, T& u1, T& u2, T& u3) {
-    const T q = T(1) + b * r, iq = T(1) / q, iq2 = iq * iq;
+    const T q = T(1) + b * r, iq = qrcp(q), iq2 = iq * iq;
     u = -Zj * r * iq; u1 = -Zj * iq2; u2 = T(2) * Zj * b * iq2 * iq; u3 = T(-6) * Zj * b * b * iq2 * iq2;
 }
 
 // From u(rho) derivatives to derivatives in t = rho^2.
 template <typename T>
 __device__ __forceinline__ void rho_to_t(T r, T u1, T u2, T u3, T& f1, T& f2, T& f3) {
-    const T ir = T(1) / r, ir2 = ir * ir, ir3 = ir2 * ir;
+    const T ir = qrcp(r), ir2 = ir * ir, ir3 = ir2 * ir;
     f1 = T(0.5) * u1 * ir;
     f2 = T(0.25) * (u2 * ir2 - u1 * ir3);
     f3 = T(0.125) * (u3 * ir3 - T(3) * u2 * ir2 * ir2 + T(3) * u1 * ir3 * ir2);
@@ -202,7 +209,7 @@ __device__ __forceinline__ void rho_to_t(T r, T u1, T u2, T u3, T& f1, T& f2, T&
 // minimum-image vector r0, phi(r) = erfc(kappa r)/r; optionally the gradient
 // with respect to r0.
 template <typename T>
-__device__ __forceinline__ T ewald_real(T dx, T dy, T dz, T Lt, T kappa, T* grad) {
+__device__ __forceinline__ T ewald_real(T dx, T dy, T dz, T Lt, T kappa, T* grad, bool skip_min = false) {
     const T iL = T(1) / Lt;
     dx -= Lt * qrint(dx * iL); dy -= Lt * qrint(dy * iL); dz -= Lt * qrint(dz * iL);
     const T r0[3] = {dx, dy, dz};
@@ -223,6 +230,7 @@ __device__ __forceinline__ T ewald_real(T dx, T dy, T dz, T Lt, T kappa, T* grad
         const T r2 = a * a + b * b + e * e;
         if (r2 < Lt * Lt && r2 > T(0)) mask |= 1u << c;
     }
+    if (skip_min) mask &= ~1u;   // the minimum image is evaluated elsewhere
     while (mask) {
         const int c = __ffs(mask) - 1;
         mask &= mask - 1;
@@ -237,6 +245,91 @@ __device__ __forceinline__ T ewald_real(T dx, T dy, T dz, T Lt, T kappa, T* grad
             const T dphi = -(ec * ir + c2 * kappa * qexp(-kappa * kappa * r2)) * ir;  // phi'(r)
             const T s = dphi * ir;
             grad[0] += s * a; grad[1] += s * b; grad[2] += s * e;
+        }
+    }
+    return v;
+}
+
+// Position of the n-th (0-based) set bit of m (n < popc(m)), by halving.
+__device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
+    int r = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const int cnt = __popc(m & ((1u << w) - 1u));
+        if (n >= cnt) { n -= cnt; m >>= w; r += w; }
+    }
+    return r;
+}
+
+// Mixed form: real-space Ewald cutoff radius squared.  erfc(kappa r) at
+// r = 0.8 L with kappa = 5 / L is 1.5e-8, below FP32 resolution of the pair
+// sums, so images beyond it are dropped (the FP64 form keeps r < L).
+constexpr float kRealCut2Mixed = 0.64f;
+
+// Warp-cooperative real-space Ewald sum for the mixed form.  Every lane brings
+// one pair displacement (or none: active = false); the candidate images inside
+// the cutoff of all lanes are enumerated through ballots and dealt out to the
+// lanes 32 at a time, so the warp runs ceil(total / 32) image bodies instead of
+// the largest per-lane image count.  Each lane returns its share of the sum of
+// phi(r) over the warp's images and adds its share of the gradient to grad
+// (when kGrad); only warp totals are meaningful.
+template <bool kGrad>
+__device__ __forceinline__ float ewald_real_warp(float dx, float dy, float dz, bool active, bool skip_min, float Lt,
+                                                 float kappa, float* grad) {
+    const float iL = 1.f / Lt;
+    dx -= Lt * rintf(dx * iL); dy -= Lt * rintf(dy * iL); dz -= Lt * rintf(dz * iL);
+    const float rc2 = kRealCut2Mixed * Lt * Lt;
+    // moving component m of the minimum image by L away from zero adds
+    // L (L - 2 |d_m|) >= 0 to r^2
+    const float r0 = dx * dx + dy * dy + dz * dz;
+    const float e0 = Lt * (Lt - 2.f * fabsf(dx)), e1 = Lt * (Lt - 2.f * fabsf(dy)), e2 = Lt * (Lt - 2.f * fabsf(dz));
+    unsigned mask = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float r2 = r0 + ((c & 1) ? e0 : 0.f) + ((c & 2) ? e1 : 0.f) + ((c & 4) ? e2 : 0.f);
+        if (active && r2 < rc2 && r2 > 0.f && !(skip_min && c == 0)) mask |= 1u << c;
+    }
+    // per candidate c: which lanes have it; inclusive prefix of the counts
+    unsigned bal[8];
+    int pre[8];
+    int tot = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        bal[c] = __ballot_sync(0xffffffffu, (mask >> c) & 1u);
+        tot += __popc(bal[c]);
+        pre[c] = tot;
+    }
+    const int lane = threadIdx.x & 31;
+    const float c2k = 1.1283791670955126f * kappa;   // 2 kappa / sqrt(pi)
+    float v = 0.f;
+    for (int base = 0; base < tot; base += 32) {
+        const int k = base + lane;
+        int c = 0;
+#pragma unroll
+        for (int q = 0; q < 7; ++q) c += (k >= pre[q]) ? 1 : 0;
+        unsigned bc = bal[0];
+        int before = 0;
+#pragma unroll
+        for (int q = 1; q < 8; ++q) {
+            bc = (c == q) ? bal[q] : bc;
+            before = (c == q) ? pre[q - 1] : before;
+        }
+        const int src = k < tot ? nth_set_bit(bc, k - before) : lane;
+        const float sx = __shfl_sync(0xffffffffu, dx, src);
+        const float sy = __shfl_sync(0xffffffffu, dy, src);
+        const float sz = __shfl_sync(0xffffffffu, dz, src);
+        if (k < tot) {
+            const float a = sx + ((c & 1) ? (sx >= 0.f ? -Lt : Lt) : 0.f);
+            const float b = sy + ((c & 2) ? (sy >= 0.f ? -Lt : Lt) : 0.f);
+            const float e = sz + ((c & 4) ? (sz >= 0.f ? -Lt : Lt) : 0.f);
+            const float r2 = a * a + b * b + e * e;
+            const float ir = rsqrtf(r2), r = r2 * ir;
+            const float ec = erfcf(kappa * r);
+            v += ec * ir;
+            if (kGrad) {
+                const float s = -(ec * ir + c2k * expf(-kappa * kappa * r2)) * ir * ir;   // phi'(r) / r
+                grad[0] += s * a; grad[1] += s * b; grad[2] += s * e;
+            }
         }
     }
     return v;

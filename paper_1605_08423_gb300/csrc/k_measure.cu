@@ -57,6 +57,29 @@ struct MLayout {
 // e-n Jastrow contributions dl (to d ln psi/dR_a) and de (to dE_L/dR_a, given
 // vv = g_i + grad_i U).  sd, cd: sin, cos(pi (x - R_a)/L) per component.
 template <typename S>
+__device__ __forceinline__ void ep_jastrow(const S sd[3], const S cd[3], S ell, S k2, S bep, S Zj, const S vv[3],
+                                           S dl[3], S de[3]) {
+    S p[3], q[3], t = 0;
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) {
+        p[mu] = ell * sd[mu] * cd[mu];
+        q[mu] = cd[mu] * cd[mu] - sd[mu] * sd[mu];
+        t += sd[mu] * sd[mu];
+    }
+    t *= ell * ell;
+    const S r = qsqrt_pair(t);
+    S u, u1, u2, u3, f1, f2, f3;
+    pade_ep(bep, Zj, r, u, u1, u2, u3);
+    rho_to_t(r, u1, u2, u3, f1, f2, f3);
+    RadialDerivs<S> rd;
+    radial_chain(p, q, f1, f2, f3, k2, rd);
+    S hv[3];
+    hess_mul(rd.h, vv, hv);
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) { dl[mu] = -rd.g[mu]; de[mu] = hv[mu] + S(0.5) * rd.tl[mu]; }
+}
+
+template <typename S>
 __device__ __forceinline__ void ep_pair(const S sd[3], const S cd[3], S ell, S k2, S bep, S Zj, S dx, S dy, S dz, S L,
                                         S kap, const S vv[3], S& v, S g[3], S dl[3], S de[3]) {
     S p[3], q[3], t = 0;
@@ -67,7 +90,7 @@ __device__ __forceinline__ void ep_pair(const S sd[3], const S cd[3], S ell, S k
         t += sd[mu] * sd[mu];
     }
     t *= ell * ell;
-    const S r = qsqrt(t);
+    const S r = qsqrt_pair(t);
     S u, u1, u2, u3, f1, f2, f3;
     pade_ep(bep, Zj, r, u, u1, u2, u3);
     rho_to_t(r, u1, u2, u3, f1, f2, f3);
@@ -149,7 +172,7 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
             if (j == i) continue;
             T sd[3], cd[3], t;
             disp_trig(ei, et + 6 * j, ell, sd, cd, t);
-            const T r = qsqrt(t);
+            const T r = qsqrt_pair(t);
             T u, u1, u2, f1, f2, f3;
             pade_ee(bee, r, u, u1, u2);
             rho_to_t(r, u1, u2, T(0), f1, f2, f3);
@@ -166,7 +189,7 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
         for (int a = j0; a < j1; ++a) {
             T sd[3], cd[3], t;
             disp_trig(ei, s.ptrig + 6 * a, ell, sd, cd, t);
-            const T r = qsqrt(t);
+            const T r = qsqrt_pair(t);
             T u, u1, u2, u3, f1, f2, f3;
             pade_ep(bep, Zj, r, u, u1, u2, u3);
             rho_to_t(r, u1, u2, T(0), f1, f2, f3);
@@ -193,19 +216,21 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
         lU[i] = v[3]; Ui[i] = v[4];
     }
 
-    // ---- P2: g_i = sum_j D_ij G_ji, l_i = sum_j Lp_ij G_ji
-    for (int i = tid; i < N; i += nt) {
+    // ---- P2: g_i = sum_j D_ij G_ji, l_i = sum_j Lp_ij G_ji (warp per electron,
+    // lanes over the orbitals: coalesced rows of D, Lp and G^T)
+    for (int i = warp; i < N; i += nw) {
         const int sp = i / n, il = i - sp * n;
         const T* grow = Gt + (((size_t)w * 2 + sp) * n + il) * n;
         const T* drow = D + ((size_t)w * N + i) * 3 * n;
         const T* lrow = Lp + ((size_t)w * N + i) * n;
         T g0 = 0, g1 = 0, g2 = 0, l = 0;
-        for (int j = 0; j < n; ++j) {
+        for (int j = lane; j < n; j += 32) {
             const T gj = grow[j];
             g0 += drow[j] * gj; g1 += drow[n + j] * gj; g2 += drow[2 * n + j] * gj;
             l += lrow[j] * gj;
         }
-        gi[3 * i] = g0; gi[3 * i + 1] = g1; gi[3 * i + 2] = g2; li[i] = l;
+        g0 = warp_sum(g0); g1 = warp_sum(g1); g2 = warp_sum(g2); l = warp_sum(l);
+        if (lane == 0) { gi[3 * i] = g0; gi[3 * i + 1] = g1; gi[3 * i + 2] = g2; li[i] = l; }
     }
     __syncthreads();
 
@@ -229,13 +254,24 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
     const T Lt = (T)L;
     // balanced cyclic pairing: electron i with i+d (mod N), d = 1..N/2 (d = N/2 only for i < N/2),
     // the distance range split into nparts slices
+    // (mixed form with N a multiple of 32: every warp has one slice, and the
+    // image work of its 32 pairs per step is balanced over the lanes)
+    const bool warp_ewald = sizeof(T) == 4 && (N & 31) == 0;
     for (int tt = tid; tt < nparts * N; tt += nt) {
         const int i = tt % N, pi = tt / N, half = N / 2;
         const int d0 = 1 + (half * pi) / nparts, d1 = 1 + (half * (pi + 1)) / nparts;
         T v = 0;
         for (int d = d0; d < d1; ++d) {
-            if (2 * d == N && i >= half) continue;
+            const bool skip = 2 * d == N && i >= half;
             const int j = (i + d) % N;
+            if constexpr (sizeof(T) == 4) {
+                if (warp_ewald) {
+                    v += ewald_real_warp<false>(xt[3 * i] - xt[3 * j], xt[3 * i + 1] - xt[3 * j + 1],
+                                                xt[3 * i + 2] - xt[3 * j + 2], !skip, false, Lt, kap, nullptr);
+                    continue;
+                }
+            }
+            if (skip) continue;
             v += ewald_real<T>(xt[3 * i] - xt[3 * j], xt[3 * i + 1] - xt[3 * j + 1], xt[3 * i + 2] - xt[3 * j + 2], Lt,
                                kap, nullptr);
         }
@@ -258,8 +294,26 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
         for (int i = lane; i < N; i += 32) {
             T sd[3], cd[3], t;
             disp_trig(et + 6 * i, pa, ell, sd, cd, t);
-            if (sizeof(T) == 4 && t < T(0.09)) {
-                atomicOr(&cmask[a * nwords + (i >> 5)], 1u << (i & 31));
+            const bool close = sizeof(T) == 4 && t < T(0.09);
+            if (close) atomicOr(&cmask[a * nwords + (i >> 5)], 1u << (i & 31));
+            if constexpr (sizeof(T) == 4) {
+                if (warp_ewald) {
+                    // Jastrow terms per lane; the Ewald images balanced over the warp
+                    if (!close) {
+                        T vv[3], pl[3], pe[3];
+                        for (int mu = 0; mu < 3; ++mu) vv[mu] = gi[3 * i + mu] + gU[3 * i + mu];
+                        ep_jastrow<T>(sd, cd, ell, k2, bep, Zj, vv, pl, pe);
+                        for (int mu = 0; mu < 3; ++mu) { dl[mu] += pl[mu]; de[mu] += pe[mu]; }
+                    }
+                    v += ewald_real_warp<true>(xt[3 * i] - ra[0], xt[3 * i + 1] - ra[1], xt[3 * i + 2] - ra[2], true,
+                                               close, Lt, kap, gv);
+                    continue;
+                }
+            }
+            if (close) {   // only the images other than the nearest one here
+                T pg[3] = {0, 0, 0};
+                v += ewald_real<T>(xt[3 * i] - ra[0], xt[3 * i + 1] - ra[1], xt[3 * i + 2] - ra[2], Lt, kap, pg, true);
+                for (int mu = 0; mu < 3; ++mu) gv[mu] += pg[mu];
                 continue;
             }
             T vv[3], pv, pg[3], pl[3], pe[3];
@@ -282,30 +336,80 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
         }
     }
     if (sizeof(T) == 4) {
+        // Close pairs in FP64, one thread per pair: the e-n Jastrow terms and
+        // the nearest-image real-space Coulomb term (the pair's other images
+        // were summed in FP32 above).  Pairs are numbered nucleus by nucleus,
+        // electrons in increasing order; each nucleus sums its pairs' results
+        // in that order, so the sums do not depend on the thread count.
+        int* coff = (int*)uni;                                       // [N + 1] pair offsets
+        double* slot = (double*)(uni + (((size_t)(N + 1) * sizeof(int) + 15) & ~size_t(15)));
+        const size_t uni_bytes = lay.total - lay.uni;
+        const int CH = (int)((uni_bytes - ((size_t)(slot) - (size_t)uni)) / (10 * sizeof(double)));
         __syncthreads();
-        for (int a = tid; a < N; a += nt) {
-            double vC = 0, gC[3] = {0, 0, 0}, dlC[3] = {0, 0, 0}, deC[3] = {0, 0, 0};
-            bool any = false;
-            for (int wd = 0; wd < nwords; ++wd) {
-                unsigned m = cmask[a * nwords + wd];
-                while (m) {
-                    const int i = wd * 32 + __ffs(m) - 1;
-                    m &= m - 1;
-                    any = true;
-                    const double dx = xs[3 * i] - s.R[3 * a], dy = xs[3 * i + 1] - s.R[3 * a + 1],
-                                 dz = xs[3 * i + 2] - s.R[3 * a + 2];
-                    double sdd[3], cdd[3], vv[3], pv, pg[3], pl[3], pe[3];
-                    sincospi(dx * iL, &sdd[0], &cdd[0]);
-                    sincospi(dy * iL, &sdd[1], &cdd[1]);
-                    sincospi(dz * iL, &sdd[2], &cdd[2]);
-                    for (int mu = 0; mu < 3; ++mu) vv[mu] = (double)gi[3 * i + mu] + (double)gU[3 * i + mu];
-                    ep_pair<double>(sdd, cdd, s.ell, (double)k2, s.b_ep, s.Zj, dx, dy, dz, L, s.kappa, vv, pv, pg, pl,
-                                    pe);
-                    vC += pv;
-                    for (int mu = 0; mu < 3; ++mu) { gC[mu] += pg[mu]; dlC[mu] += pl[mu]; deC[mu] += pe[mu]; }
-                }
+        if (warp == 0) {   // exclusive scan of the per-nucleus counts
+            const int per = (N + 31) / 32, a0 = lane * per;
+            int loc = 0;
+            for (int a = a0; a < a0 + per && a < N; ++a)
+                for (int wd = 0; wd < nwords; ++wd) loc += __popc(cmask[a * nwords + wd]);
+            int inc = loc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
             }
-            if (any) {
+            int run = inc - loc;
+            for (int a = a0; a < a0 + per && a < N; ++a) {
+                coff[a] = run;
+                for (int wd = 0; wd < nwords; ++wd) run += __popc(cmask[a * nwords + wd]);
+            }
+            if (lane == 31) coff[N] = inc;
+        }
+        __syncthreads();
+        const int total = coff[N];
+        const double k2d = (2.0 * kPi * iL) * (2.0 * kPi * iL);
+        for (int base = 0; base < total; base += CH) {
+            const int end = base + CH < total ? base + CH : total;
+            for (int t = base + tid; t < end; t += nt) {
+                int lo = 0, hi = N;   // nucleus: coff[a] <= t < coff[a + 1]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (coff[mid] <= t) lo = mid; else hi = mid;
+                }
+                const int a = lo;
+                int k = t - coff[a], i = 0;
+                for (int wd = 0; wd < nwords; ++wd) {
+                    const unsigned m = cmask[a * nwords + wd];
+                    const int c = __popc(m);
+                    if (k < c) { i = wd * 32 + nth_set_bit(m, k); break; }
+                    k -= c;
+                }
+                const double dx = xs[3 * i] - s.R[3 * a], dy = xs[3 * i + 1] - s.R[3 * a + 1],
+                             dz = xs[3 * i + 2] - s.R[3 * a + 2];
+                double sdd[3], cdd[3], vv[3], pl[3], pe[3];
+                sincospi(dx * iL, &sdd[0], &cdd[0]);
+                sincospi(dy * iL, &sdd[1], &cdd[1]);
+                sincospi(dz * iL, &sdd[2], &cdd[2]);
+                for (int mu = 0; mu < 3; ++mu) vv[mu] = (double)gi[3 * i + mu] + (double)gU[3 * i + mu];
+                ep_jastrow<double>(sdd, cdd, s.ell, k2d, s.b_ep, s.Zj, vv, pl, pe);
+                const double mx = dx - L * rint(dx * iL), my = dy - L * rint(dy * iL), mz = dz - L * rint(dz * iL);
+                const double r2 = mx * mx + my * my + mz * mz, r = sqrt(r2), ir = 1.0 / r;
+                const double ec = erfc(s.kappa * r);
+                const double sg = -(ec * ir + 1.1283791670955126 * s.kappa * exp(-s.kappa * s.kappa * r2)) * ir * ir;
+                double* o = slot + (size_t)(t - base) * 10;
+                o[0] = ec * ir;
+                o[1] = sg * mx; o[2] = sg * my; o[3] = sg * mz;
+                for (int mu = 0; mu < 3; ++mu) { o[4 + mu] = pl[mu]; o[7 + mu] = pe[mu]; }
+            }
+            __syncthreads();
+            for (int a = tid; a < N; a += nt) {
+                const int lo = coff[a] > base ? coff[a] : base, hi = coff[a + 1] < end ? coff[a + 1] : end;
+                if (lo >= hi) continue;
+                double vC = 0, gC[3] = {0, 0, 0}, dlC[3] = {0, 0, 0}, deC[3] = {0, 0, 0};
+                for (int t = lo; t < hi; ++t) {
+                    const double* o = slot + (size_t)(t - base) * 10;
+                    vC += o[0];
+                    for (int mu = 0; mu < 3; ++mu) { gC[mu] += o[1 + mu]; dlC[mu] += o[4 + mu]; deC[mu] += o[7 + mu]; }
+                }
                 vep_p += -Zn * vC;
                 for (int mu = 0; mu < 3; ++mu) {
                     f_dv[3 * a + mu] += Zn * gC[mu];
@@ -313,6 +417,7 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
                     f_de[3 * a + mu] += deC[mu];
                 }
             }
+            __syncthreads();
         }
     }
     // ---- P4c: reciprocal space: electron structure factor from per-electron phase tables
@@ -352,6 +457,7 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
     // ---- P4d: reciprocal-space force on the protons (warp per proton)
     for (int a = warp; a < N; a += nw) {
         T gx = 0, gy = 0, gz = 0;
+#pragma unroll 4
         for (int k = lane; k < nk; k += 32) {
             const V2<T> e = s.eikRt[(size_t)a * nk + k];
             const V2<T> rd = rhot[k];

@@ -36,7 +36,7 @@ __device__ __forceinline__ T pair_dist(const T* a, const T* b, T ell) {
         const T sd = a[mu] * b[3 + mu] - a[3 + mu] * b[mu];
         t += sd * sd;
     }
-    return ell * qsqrt(t);
+    return ell * qsqrt_pair(t);
 }
 
 template <typename T>
