@@ -108,14 +108,42 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def _flops_per_launch(cls: str, W, N, n, B, G, acc_ratio, use_tc):
+# Per-unit FLOP model of the measure kernel (FP32 formula operations, a
+# special function -- sqrt, reciprocal, exp, erfc, sin/cos -- counted as one):
+#   Jastrow value/gradient/Laplacian per ordered e-e pair        55
+#   the same per e-n pair                                         55
+#   real-space Ewald per unordered e-e pair: 6 + 10 per image     6 + 10 * 4.19
+#     (4.19 = mean number of images with |r + nL| < L)
+#   e-n pair: Jastrow third-order chain, Hessian product          130
+#     plus Ewald value and gradient: 6 + 19 per image              6 + 19 * 4.19
+#   reciprocal space: structure factor 14 per (electron, k),
+#     force 12 per (nucleus, k)
+#   g_i, l_i: 8 n per electron;  K = G Y G: 8 n^3 per walker
+MEASURE_UNIT = {"ee_jas": 55.0, "ep_jas": 55.0, "ee_ewald": 6.0 + 10.0 * 4.19, "ep": 130.0 + 6.0 + 19.0 * 4.19,
+                "sk": 14.0, "fk": 12.0}
+
+
+def _nk(mmax: int) -> int:
+    """Half-space reciprocal vectors 0 < |m|^2 <= mmax^2 (the Ewald k-sum)."""
+    r = range(-mmax, mmax + 1)
+    return sum(1 for x in range(0, mmax + 1) for y in r for z in r
+               if (x > 0 or (x == 0 and y > 0) or (x == 0 and y == 0 and z > 0)) and x * x + y * y + z * z <= mmax * mmax)
+
+
+def _flops_per_launch(cls: str, W, N, n, B, G, acc_ratio, use_tc, nk=462):
     """Algorithmic FLOPs of one launch of a kernel class (dense multiply-adds x 2)."""
     if cls == "orbitals_prop":
         return 2.0 * W * N * B * n
     if cls == "orbitals_meas":   # grad (3) + Laplacian on the tensor cores; SIMT also forms the values
         return (8.0 if use_tc else 10.0) * W * N * B * n
     if cls == "measure":
-        return 2.0 * W * (4.0 * n ** 3 + 4.0 * N * G * n * n)
+        u = MEASURE_UNIT
+        pairs = (u["ee_jas"] * N * (N - 1) + u["ep_jas"] * N * N + u["ee_ewald"] * N * (N - 1) / 2
+                 + u["ep"] * N * N + (u["sk"] + u["fk"]) * N * nk + 8.0 * n * N + 8.0 * n ** 3)
+        adj = 0.0 if use_tc else 8.0 * N * G * n * n   # Z = C G, P = C K in the SIMT measure kernel
+        return W * (pairs + adj)
+    if cls == "adjoint":         # Z = C G and P = C (G Y G) per spin block on the tensor cores
+        return 8.0 * W * N * G * n * n
     if cls == "sweep":
         return 2.0 * W * N * (n + acc_ratio * 2.0 * n * n)
     return None
@@ -258,16 +286,17 @@ def run_ours(args, ws, rank, local):
     use_tc = prec == q.QMC_MIXED
     roofs = {}
     for cls, (cms, cl) in kt.items():
-        fl = _flops_per_launch(cls, W, N, n, B, G, float(res["accept"]), use_tc)
+        fl = _flops_per_launch(cls, W, N, n, B, G, float(res["accept"]), use_tc, nk=_nk(cfg.mmax))
         if fl is None or cl == 0:
             continue
         avg = cms / cl
         ach = fl / (avg / 1e3) / 1e12
-        if use_tc and cls.startswith("orbitals"):
+        if use_tc and (cls.startswith("orbitals") or cls == "adjoint"):
+            # 2xTF32 pieces: three tensor products per algorithmic product
             roofs[cls] = {"kernel": cls, "bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
                           "frac": ach / tf32_peak, "traffic": None,
                           "peak_source": f"TF32 = {peak_kind} bf16 sustained x 1.1/2.25 (nominal ratio)",
-                          "flops_per_launch": fl, "tensor_pipe_flops_per_launch": 6 * fl, "avg_launch_ms": avg}
+                          "flops_per_launch": fl, "tensor_pipe_flops_per_launch": 3 * fl, "avg_launch_ms": avg}
         else:
             roofs[cls] = {"kernel": cls, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                           "frac": ach / fp32_peak, "traffic": None,

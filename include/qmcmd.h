@@ -179,7 +179,7 @@ int qmc_set_walkers(qmc_system* h, const double* X);
 int qmc_get_accumulators(qmc_system* h, double* acc);
 
 /* Handle options.  QMC_OPT_TENSOR_CORES (mixed form only, default 1): evaluate
- * the orbital contractions with the tcgen05 tensor-core kernel (3xTF32 split,
+ * the orbital contractions with the tcgen05 tensor-core kernel (2xTF32 split,
  * FP32-level accuracy); 0 selects the SIMT FP32 kernel.
  * QMC_OPT_TC_ADJOINT (mixed form with N <= 128, n_gauss <= 4; default 1):
  * while tensor cores are on, the B x n contractions of the orbital force terms

@@ -1,17 +1,18 @@
 // k_orbitals_tc.cu -- tensor-core (tcgen05) form of the walker-batched
 // molecular-orbital contraction for the mixed-precision path.
 //
-//   phi_j(r) = sum_b C[b][j] chi_b(r)   (and grad, Laplacian for Q = 5)
+//   phi_j(r) = sum_b C[b][j] chi_b(r)   (and grad, Laplacian for Q = 4)
 //
 // A CTA owns 128 rows (electron positions).  For each chunk of 32 basis
 // functions the threads evaluate the periodised Gaussians (value, or
 // gradient and Laplacian) of the 128 rows straight into shared memory, in the
-// K-major 128-byte-swizzled layout the tensor core reads, split into three
-// exact TF32 pieces x = x0 + x1 + x2 (representation error ~2^-35).  One thread
-// then issues, per quantity, the six products with i + j <= 2
-//   D += A0 B0 + A0 B1 + A1 B0 + A0 B2 + A1 B1 + A2 B0   (tcgen05.mma kind::tf32)
-// accumulating in tensor memory (FP32).  The dropped products are below 2^-33
-// relative, so the contraction is at least as accurate as FP32 arithmetic.
+// K-major 128-byte-swizzled layout the tensor core reads, split into P exact
+// TF32 pieces.  One thread then issues, per quantity, the piece products with
+// i + j <= P - 1 (tcgen05.mma kind::tf32), accumulating in tensor memory
+// (FP32).  With P = 2 (x = x0 + x1, representation error 2^-24 |x|):
+//   D += A1 B0 + A0 B1 + A0 B0,
+// the dropped A1 B1 is below 2^-22 relative: FP32-level, which is what the
+// results are stored in.  (P = 3, six products, reaches 2^-33.)
 // B = C^T chunk, prepared once per handle in the same swizzled layout.  After
 // the last chunk the accumulators go TMEM -> registers -> shared -> HBM.
 #include "common.cuh"
@@ -26,7 +27,10 @@ constexpr int kKc = 32;        // basis functions per chunk (128 bytes of FP32 p
 constexpr int kTileA = kRows * kKc * 4;   // 16 KB
 }
 
-constexpr int kPieces = 3;   // TF32 pieces per operand
+// pieces used per operand: orbital values (Slater rows) and their derivatives
+constexpr int kPiecesVal = 2;
+constexpr int kPiecesDer = 2;
+constexpr int kPieces = kPiecesVal > kPiecesDer ? kPiecesVal : kPiecesDer;   // prepared coefficient pieces
 
 __host__ __device__ inline int tc_nm(int n) { return n <= 16 ? 16 : ((n + 15) / 16) * 16; }
 
@@ -37,7 +41,8 @@ size_t tc_coeff_bytes(int B, int n) {
 
 bool tc_orbitals_supported(int n, int B) { (void)B; return n >= 1 && n <= 64; }
 
-// C^T chunks, three TF32 pieces, swizzled: chunk c at c * 3 * NM * 128 bytes, piece p at p * NM * 128.
+// C^T chunks, kPieces TF32 pieces, swizzled: chunk c at c * kPieces * NM * 128
+// bytes, piece p at p * NM * 128.
 __global__ void prepare_coeff_kernel(const float* __restrict__ C, int B, int n, int NM, unsigned char* chat) {
     const int nch = (B + kKc - 1) / kKc;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -45,12 +50,11 @@ __global__ void prepare_coeff_kernel(const float* __restrict__ C, int B, int n, 
     const int c = t / (NM * kKc), rem = t - c * NM * kKc, j = rem / kKc, k = rem - j * kKc;
     const int b = c * kKc + k;
     const float x = (b < B && j < n) ? C[(size_t)b * n + j] : 0.f;
-    float x0, x1, x2;
-    tc::split3_tf32(x, x0, x1, x2);
+    float xp[3];
+    if (kPieces == 3) tc::split3_tf32(x, xp[0], xp[1], xp[2]);
+    else tc::split_tf32(x, xp[0], xp[1]);
     unsigned char* base = chat + (size_t)c * kPieces * NM * 128;
-    *(float*)(base + tc::sw128_off(j, k)) = x0;
-    *(float*)(base + (size_t)NM * 128 + tc::sw128_off(j, k)) = x1;
-    *(float*)(base + (size_t)2 * NM * 128 + tc::sw128_off(j, k)) = x2;
+    for (int p = 0; p < kPieces; ++p) *(float*)(base + (size_t)p * NM * 128 + tc::sw128_off(j, k)) = xp[p];
 }
 
 void prepare_tc_coeff(const float* C, int B, int n, void* chat, cudaStream_t st) {
@@ -61,15 +65,15 @@ void prepare_tc_coeff(const float* C, int B, int n, void* chat, cudaStream_t st)
 
 // Q = 1: values (Slater rows / proposals).  Q = 4: d/dx, d/dy, d/dz and the
 // Laplacian (local energy; the values are not needed there).
-template <int Q>
+template <int Q, int P>
 __global__ void __launch_bounds__(Q == 1 ? 256 : 512, 1)
     orbitals_tc_kernel(SysView<float> s, const unsigned char* __restrict__ chat, const double* __restrict__ pos,
                        int nrows, int NM, float* __restrict__ val, float* __restrict__ grad, float* __restrict__ lap) {
     extern __shared__ unsigned char smraw[];
     unsigned char* base = (unsigned char*)((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
     unsigned char* sA = base;                                    // [Q][piece] tiles of 16 KB
-    unsigned char* sB = base + (size_t)Q * kPieces * kTileA;     // [piece] tiles of NM * 128 bytes
-    float* ptr_s = (float*)(sB + (size_t)kPieces * NM * 128);    // [N][6] proton trig
+    unsigned char* sB = base + (size_t)Q * P * kTileA;           // [piece] tiles of NM * 128 bytes
+    float* ptr_s = (float*)(sB + (size_t)P * NM * 128);          // [N][6] proton trig
     __shared__ float rtrig[kRows][6];
     __shared__ uint64_t mbar;
     __shared__ uint32_t tbase;
@@ -100,10 +104,10 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 512, 1)
     bool ok = true;
 
     for (int c = 0; c < nch; ++c) {
-        // B operand: the prepared C^T chunk (16-byte vectors)
+        // B operand: the first P pieces of the prepared C^T chunk (16-byte vectors)
         const uint4* src = (const uint4*)(chat + (size_t)c * chunk_bytes);
         uint4* dst = (uint4*)sB;
-        for (int idx = tid; idx < (int)(chunk_bytes / 16); idx += nt) dst[idx] = src[idx];
+        for (int idx = tid; idx < P * NM * 8; idx += nt) dst[idx] = src[idx];
         // A operand: one item = (row, 4 consecutive basis functions); the
         // displacement to a nucleus is computed once for its Gaussians
         for (int item = tid; item < kRows * (kKc / 4); item += nt) {
@@ -148,15 +152,25 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 512, 1)
             const uint32_t off = tc::sw128_off(r, k0);
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
-                float4 x0, x1, x2;
-                tc::split3_tf32(v[q][0], x0.x, x1.x, x2.x);
-                tc::split3_tf32(v[q][1], x0.y, x1.y, x2.y);
-                tc::split3_tf32(v[q][2], x0.z, x1.z, x2.z);
-                tc::split3_tf32(v[q][3], x0.w, x1.w, x2.w);
-                unsigned char* tq = sA + (size_t)(kPieces * q) * kTileA + off;
-                *(float4*)(tq) = x0;
-                *(float4*)(tq + kTileA) = x1;
-                *(float4*)(tq + 2 * kTileA) = x2;
+                unsigned char* tq = sA + (size_t)(P * q) * kTileA + off;
+                if constexpr (P == 3) {
+                    float4 x0, x1, x2;
+                    tc::split3_tf32(v[q][0], x0.x, x1.x, x2.x);
+                    tc::split3_tf32(v[q][1], x0.y, x1.y, x2.y);
+                    tc::split3_tf32(v[q][2], x0.z, x1.z, x2.z);
+                    tc::split3_tf32(v[q][3], x0.w, x1.w, x2.w);
+                    *(float4*)(tq) = x0;
+                    *(float4*)(tq + kTileA) = x1;
+                    *(float4*)(tq + 2 * kTileA) = x2;
+                } else {
+                    float4 x0, x1;
+                    tc::split_tf32(v[q][0], x0.x, x1.x);
+                    tc::split_tf32(v[q][1], x0.y, x1.y);
+                    tc::split_tf32(v[q][2], x0.z, x1.z);
+                    tc::split_tf32(v[q][3], x0.w, x1.w);
+                    *(float4*)(tq) = x0;
+                    *(float4*)(tq + kTileA) = x1;
+                }
             }
         }
         tc::fence_proxy_async();
@@ -166,17 +180,18 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 512, 1)
             const uint32_t b0 = tc::smem_addr(sB), bstep = (uint32_t)NM * 128;
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
-                const uint32_t a0 = tc::smem_addr(sA + (size_t)(kPieces * q) * kTileA);
+                const uint32_t a0 = tc::smem_addr(sA + (size_t)(P * q) * kTileA);
                 const uint32_t d = tmem + (uint32_t)(q * NM);
 #pragma unroll
                 for (int ks = 0; ks < kKc / 8; ++ks) {
                     const uint32_t o = 32u * ks;
-                    // products A_i B_j with i + j <= 2, smallest first
+                    // products A_i B_j with i + j <= P - 1, smallest first
+                    constexpr int np = P == 3 ? 6 : 3;
                     const int pi[6] = {2, 1, 0, 1, 0, 0}, pj[6] = {0, 1, 2, 0, 1, 0};
 #pragma unroll
-                    for (int m = 0; m < 6; ++m)
+                    for (int m = 6 - np; m < 6; ++m)
                         tc::mma_tf32(d, tc::desc_sw128(a0 + pi[m] * kTileA + o), tc::desc_sw128(b0 + pj[m] * bstep + o),
-                                     idesc, (c > 0 || ks > 0 || m > 0) ? 1u : 0u);
+                                     idesc, (c > 0 || ks > 0 || m > 6 - np) ? 1u : 0u);
                 }
             }
             tc::mma_commit(&mbar);
@@ -229,18 +244,21 @@ void launch_orbitals_tc(const SysView<float>& s, const void* chat, const double*
     // kernel also holds static shared memory, so the opt-in maximum minus that)
     static size_t set4 = 0, set1 = 0;
     if (grad) {
-        const size_t smem = 1024 + (size_t)4 * kPieces * kTileA + (size_t)kPieces * NM * 128 + 24 * (size_t)s.N;
-        if (smem > set4 && cudaFuncSetAttribute(orbitals_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)smem) == cudaSuccess)
+        const size_t smem = 1024 + (size_t)4 * kPiecesDer * kTileA + (size_t)kPiecesDer * NM * 128 + 24 * (size_t)s.N;
+        if (smem > set4 &&
+            cudaFuncSetAttribute(orbitals_tc_kernel<4, kPiecesDer>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) == cudaSuccess)
             set4 = smem;
-        orbitals_tc_kernel<4><<<grid, 512, smem, st>>>(s, (const unsigned char*)chat, pos, nrows, NM, val, grad, lap);
+        orbitals_tc_kernel<4, kPiecesDer>
+            <<<grid, 512, smem, st>>>(s, (const unsigned char*)chat, pos, nrows, NM, val, grad, lap);
     } else {
-        const size_t smem = 1024 + (size_t)kPieces * kTileA + (size_t)kPieces * NM * 128 + 24 * (size_t)s.N;
-        if (smem > set1 && cudaFuncSetAttribute(orbitals_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)smem) == cudaSuccess)
+        const size_t smem = 1024 + (size_t)kPiecesVal * kTileA + (size_t)kPiecesVal * NM * 128 + 24 * (size_t)s.N;
+        if (smem > set1 &&
+            cudaFuncSetAttribute(orbitals_tc_kernel<1, kPiecesVal>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) == cudaSuccess)
             set1 = smem;
-        orbitals_tc_kernel<1><<<grid, 256, smem, st>>>(s, (const unsigned char*)chat, pos, nrows, NM, val, nullptr,
-                                                       nullptr);
+        orbitals_tc_kernel<1, kPiecesVal>
+            <<<grid, 256, smem, st>>>(s, (const unsigned char*)chat, pos, nrows, NM, val, nullptr, nullptr);
     }
 }
 

@@ -77,7 +77,7 @@ def test_eval_config_full_size_sampled(prec):
 
 @pytest.mark.parametrize("name", ["h16", "h64"])
 def test_tensor_core_orbitals_match_simt(name):
-    """The tcgen05 (3xTF32) orbital contraction agrees with the SIMT FP32 one."""
+    """The tcgen05 (2xTF32) orbital contraction agrees with the SIMT FP32 one."""
     wl = synth.workload(name)
     X = _sampled(wl, 6, 21, sweeps=6)
     s = q.QMCSystem(q.Config.from_workload(wl, precision=q.QMC_MIXED, walkers=6), wl.R)
