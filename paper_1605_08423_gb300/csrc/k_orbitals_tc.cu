@@ -21,6 +21,14 @@
 
 namespace qmc {
 
+// 2^x by the hardware approximation (PTX ex2.approx.ftz.f32; a few ulp, the
+// exponents here stay far above the subnormal range)
+__device__ __forceinline__ float tc_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 namespace {
 constexpr int kRows = 128;     // MMA M
 constexpr int kKc = 32;        // basis functions per chunk (128 bytes of FP32 per row)
@@ -75,6 +83,7 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 512, 1)
     unsigned char* sB = base + (size_t)Q * P * kTileA;           // [piece] tiles of NM * 128 bytes
     float* ptr_s = (float*)(sB + (size_t)P * NM * 128);          // [N][6] proton trig
     __shared__ float rtrig[kRows][6];
+    __shared__ float zs[16];   // zeta_g and zeta_g log2(e), g < 8
     __shared__ uint64_t mbar;
     __shared__ uint32_t tbase;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nt = blockDim.x;
@@ -93,6 +102,12 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 512, 1)
         rtrig[r][3 + mu] = cs;
     }
     for (int idx = tid; idx < 6 * N; idx += nt) ptr_s[idx] = s.ptrig[idx];
+    if (tid < 8) {
+        const float z = tid < G ? s.zetat[tid] : 0.f;
+        zs[tid] = z;
+        zs[8 + tid] = z * 1.4426950408889634f;
+    }
+    const int gshift = (G & (G - 1)) == 0 ? __ffs(G) - 1 : -1;
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -110,18 +125,25 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 512, 1)
         for (int idx = tid; idx < P * NM * 8; idx += nt) dst[idx] = src[idx];
         // A operand: one item = (row, 4 consecutive basis functions); the
         // displacement to a nucleus is computed once for its Gaussians
+#pragma unroll 2
         for (int item = tid; item < kRows * (kKc / 4); item += nt) {
             const int r = item / (kKc / 4), k0 = 4 * (item - r * (kKc / 4));
             float v[Q][4];
             int a_prev = -1;
             float t = 0.f, pp = 0.f, sq = 0.f, pv[3] = {0.f, 0.f, 0.f};
+            // nucleus and Gaussian of basis function b = a G + g (shifts when G is a power of two)
+            const int b0 = c * kKc + k0;
+            int a0, g0;
+            if (gshift >= 0) { a0 = b0 >> gshift; g0 = b0 & (G - 1); }
+            else { a0 = b0 / G; g0 = b0 - a0 * G; }
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
-                const int b = c * kKc + k0 + kk;
+                const int b = b0 + kk;
+                int a = a0, g = g0 + kk;
+                while (g >= G) { g -= G; ++a; }
 #pragma unroll
                 for (int q = 0; q < Q; ++q) v[q][kk] = 0.f;
                 if (b >= B || row0 + r >= nrows) continue;
-                const int a = b / G, g = b - a * G;
                 if (a != a_prev) {
                     a_prev = a;
                     const float* pt = ptr_s + 6 * a;
@@ -138,8 +160,8 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 512, 1)
                     }
                     t *= ell * ell;
                 }
-                const float z = s.zetat[g];
-                const float e = expf(-z * t);
+                const float z = zs[g];
+                const float e = tc_ex2(-zs[8 + g] * t);
                 if (Q == 1) {
                     v[0][kk] = e;
                 } else {
