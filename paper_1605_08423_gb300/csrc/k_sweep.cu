@@ -77,6 +77,18 @@ __global__ void __launch_bounds__(256) sweep_kernel(SysView<T> s, double* __rest
     }
     __syncwarp();
     unsigned long long naccept = 0;
+    // the next move's proposal trig, orbital row (n <= 64: two per lane) and
+    // uniform are loaded one move ahead, so their HBM latency overlaps a move
+    T pt_nx[6], ph_nx[2], u_nx;
+    auto fetch = [&](int i) {
+        const size_t row = (size_t)w * N + i;
+#pragma unroll
+        for (int mu = 0; mu < 6; ++mu) pt_nx[mu] = ptp[row * 6 + mu];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) ph_nx[k] = (lane + 32 * k < n) ? Phi[row * n + lane + 32 * k] : T(0);
+        u_nx = uacc[row];
+    };
+    fetch(0);
     for (int sp = 0; sp < 2; ++sp) {
         T* G = Gt + ((size_t)w * 2 + sp) * n * n;
         for (int idx = lane; idx < n * n; idx += 32) Gs[(idx / n) * ld + idx % n] = G[idx];
@@ -86,22 +98,27 @@ __global__ void __launch_bounds__(256) sweep_kernel(SysView<T> s, double* __rest
             const size_t row = (size_t)w * N + i;
             T pt[6];
 #pragma unroll
-            for (int mu = 0; mu < 6; ++mu) pt[mu] = ptp[row * 6 + mu];
-            for (int j = lane; j < n; j += 32) phi[j] = Phi[row * n + j];
+            for (int mu = 0; mu < 6; ++mu) pt[mu] = pt_nx[mu];
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                if (lane + 32 * k < n) phi[lane + 32 * k] = ph_nx[k];
+            const T u = u_nx;
+            if (i + 1 < N) fetch(i + 1);
             __syncwarp();
             T part = 0;
             for (int j = lane; j < n; j += 32) part += phi[j] * Gs[il * ld + j];
             const T ratio = warp_sum(part);
             T du = 0;
             const T* ei = et + 6 * i;
+#pragma unroll 4
             for (int j = lane; j < N; j += 32) {
-                if (j == i) continue;
                 const T* ej = et + 6 * j;
                 T u1, u0, d1, d2;
                 pade_ee(bee, pair_dist(pt, ej, ell), u1, d1, d2);
                 pade_ee(bee, pair_dist(ei, ej, ell), u0, d1, d2);
-                du += u1 - u0;
+                du += (j != i) ? u1 - u0 : T(0);
             }
+#pragma unroll 4
             for (int a = lane; a < N; a += 32) {
                 const T* pa = ptr_s + 6 * a;
                 T u1, u0, d1, d2, d3;
@@ -111,15 +128,20 @@ __global__ void __launch_bounds__(256) sweep_kernel(SysView<T> s, double* __rest
             }
             du = warp_sum(du);
             const T prob = ratio * ratio * qexp(T(2) * du);
-            const T u = uacc[row];
             if (u < prob) {
                 for (int j = lane; j < n; j += 32) rowb[j] = Gs[il * ld + j];
                 __syncwarp();
                 const T ir = T(1) / ratio;
                 for (int l = lane; l < n; l += 32) {
-                    T wl = 0;
                     T* gl = Gs + l * ld;
-                    for (int j = 0; j < n; ++j) wl += phi[j] * gl[j];
+                    T w4[4] = {0, 0, 0, 0};   // four partial sums: short dependency chains
+                    int j = 0;
+                    for (; j + 4 <= n; j += 4) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) w4[q] += phi[j + q] * gl[j + q];
+                    }
+                    for (; j < n; ++j) w4[0] += phi[j] * gl[j];
+                    const T wl = (w4[0] + w4[1]) + (w4[2] + w4[3]);
                     const T coef = (wl - (l == il ? T(1) : T(0))) * ir;
                     for (int j = 0; j < n; ++j) gl[j] -= coef * rowb[j];
                 }
