@@ -23,8 +23,10 @@ namespace qmc {
 
 template <typename T>
 struct MLayout {
-    size_t xs, xt, et, gU, lU, Ui, gi, li, facc, rho, rhot, red, stage, cmask, uni, total;
-    __host__ __device__ MLayout(int N, int n, int nk, int mmax) {
+    size_t xs, xt, et, gU, lU, Ui, gi, li, facc, rhot, red, stage, cmask, uni, total;
+    // split: the B x n orbital contractions run in the adjoint kernel, so the
+    // spin-block work space only holds Y^T / M1 and G (and no epilogue stage)
+    __host__ __device__ MLayout(int N, int n, int nk, int mmax, bool split = false) {
         size_t o = 0;
         auto take = [&](size_t bytes) { size_t r = o; o = (o + bytes + 15) & ~size_t(15); return r; };
         xs = take(sizeof(double) * 3 * N);
@@ -36,15 +38,15 @@ struct MLayout {
         gi = take(sizeof(T) * 3 * N);
         li = take(sizeof(T) * N);
         facc = take(sizeof(double) * 9 * N);
-        rho = take(sizeof(double2) * nk);
         rhot = take(sizeof(V2<T>) * nk);
         red = take(sizeof(double) * 64);
-        stage = take(sizeof(double) * 64 * 6);
+        stage = take(split ? 0 : sizeof(double) * 64 * 6);
         cmask = take(sizeof(unsigned) * (size_t)N * ((N + 31) / 32));
-        const size_t etab = sizeof(V2<T>) * (size_t)N * 3 * (2 * mmax + 1);
+        // phase table e^{i m theta}, m = 0..mmax (negative m by conjugation)
+        const size_t etab = sizeof(V2<T>) * (size_t)N * 3 * (mmax + 1);
         int np = 4;
         while (np < n) np *= 2;
-        const size_t spin = sizeof(T) * (size_t)np * (3 * (np + 4) + 68);
+        const size_t spin = split ? sizeof(T) * 2 * (size_t)np * (np + 4) : sizeof(T) * (size_t)np * (3 * (np + 4) + 68);
         const size_t jpart = sizeof(T) * 5 * 256;   // P1 partials: nparts * N <= 256 rows of 5
         size_t u = etab > spin ? etab : spin;
         uni = take(u > jpart ? u : jpart);
@@ -108,7 +110,7 @@ __device__ __forceinline__ void ep_pair(const S sd[3], const S cd[3], S ell, S k
 // that kernel needs: K^T per spin block (kt_out), the electrons' (sin, cos)
 // and grad U (eg_out, 9 per electron) and E_L of the sample (elw).
 template <typename T, bool kSplit>
-__global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, const double* __restrict__ X,
+__global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T> s, int mmax, const double* __restrict__ X,
                                                       const T* __restrict__ D, const T* __restrict__ Lp,
                                                       const T* __restrict__ Gt, const double* __restrict__ logdet,
                                                       double* __restrict__ acc, double* __restrict__ out_el,
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
                                                       float* __restrict__ eg_out, double* __restrict__ elw) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int N = s.N, n = s.n, G = s.G, nk = s.nk;
-    const MLayout<T> lay(N, n, nk, mmax);
+    const MLayout<T> lay(N, n, nk, mmax, kSplit);
     double* xs = (double*)(sm + lay.xs);
     T* xt = (T*)(sm + lay.xt);
     T* et = (T*)(sm + lay.et);
@@ -129,7 +131,6 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
     double* f_dl = (double*)(sm + lay.facc);
     double* f_de = f_dl + 3 * N;
     double* f_dv = f_de + 3 * N;
-    double2* rho = (double2*)(sm + lay.rho);
     V2<T>* rhot = (V2<T>*)(sm + lay.rhot);
     double* red = (double*)(sm + lay.red);
     double* stage = (double*)(sm + lay.stage);
@@ -422,17 +423,16 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
     }
     // ---- P4c: reciprocal space: electron structure factor from per-electron phase tables
     V2<T>* etab = (V2<T>*)uni;
-    const int nm = 2 * mmax + 1;
+    const int nm = mmax + 1;   // m = 0..mmax; e^{-i m theta} = conj(e^{i m theta})
     for (int idx = tid; idx < 3 * N; idx += nt) {
         T sn, cs;
         qsincospi((T)(2.0 * iL) * xt[idx], &sn, &cs);
         V2<T>* e = etab + (size_t)idx * nm;
         V2<T> cur{T(1), T(0)};
-        e[mmax] = cur;
+        e[0] = cur;
         for (int m = 1; m <= mmax; ++m) {
             cur = V2<T>{cur.x * cs - cur.y * sn, cur.x * sn + cur.y * cs};
-            e[mmax + m] = cur;
-            e[mmax - m] = V2<T>{cur.x, -cur.y};
+            e[m] = cur;
         }
     }
     __syncthreads();
@@ -441,15 +441,16 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
         const int4 m = s.kvec[k];
         T re = 0, im = 0;
         for (int i = 0; i < N; ++i) {
-            const V2<T> a = etab[(3 * i) * nm + m.x + mmax], b = etab[(3 * i + 1) * nm + m.y + mmax],
-                        c = etab[(3 * i + 2) * nm + m.z + mmax];
+            const V2<T> a = etab[(3 * i) * nm + m.x];   // m.x >= 0 in the half space
+            V2<T> b = etab[(3 * i + 1) * nm + (m.y < 0 ? -m.y : m.y)], c = etab[(3 * i + 2) * nm + (m.z < 0 ? -m.z : m.z)];
+            if (m.y < 0) b.y = -b.y;
+            if (m.z < 0) c.y = -c.y;
             const T abx = a.x * b.x - a.y * b.y, aby = a.x * b.y + a.y * b.x;
             re += abx * c.x - aby * c.y;
             im += abx * c.y + aby * c.x;
         }
         const double2 rp = s.rho_p[k];
         const double rr = rp.x - (double)re, ri = rp.y - (double)im;   // electrons carry -1
-        rho[k] = make_double2(rr, ri);
         rhot[k] = V2<T>{(T)rr, (T)ri};
         vrec_p += s.kw[k] * (rr * rr + ri * ri);
     }
@@ -480,6 +481,81 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
     //   M1 = Y G,  K = G M1  (= G Y G),  Z = C G,  P = C K  (per 64-row tile of C)
     // and the basis-derivative contraction is fused onto each Z/P tile.
     const int np = s.np, ldt = np + 4, ng = np / 4;
+    if constexpr (kSplit) {
+        // K = G Y G per spin block for the adjoint kernel, in two buffers: the
+        // 4 x 4 register tiles of M1 = Y G overwrite Y^T once every thread has
+        // read it, and K^T goes out through the G buffer (coalesced stores).
+        T* bufY = (T*)uni;                       // Y^T [j][i], then M1 [i][i']
+        T* bufG2 = bufY + (size_t)np * ldt;      // G [j][i], then K^T [i'][j]
+        const int r0 = 4 * (tid / ng), c0 = 4 * (tid % ng);
+        const bool act = tid < ng * ng;
+        for (int sp = 0; sp < 2; ++sp) {
+            const T* Gsp = Gt + ((size_t)w * 2 + sp) * n * n;
+            for (int idx = tid; idx < np * np; idx += nt) {
+                const int il = idx / np, j = idx - il * np;
+                T g = 0, y = 0;
+                if (il < n && j < n) {
+                    const int i = sp * n + il;
+                    g = Gsp[il * n + j];
+                    const size_t rr = (size_t)w * N + i;
+                    const T* dr = D + rr * 3 * n;
+                    y = T(-0.5) * Lp[rr * n + j] -
+                        (gU[3 * i] * dr[j] + gU[3 * i + 1] * dr[n + j] + gU[3 * i + 2] * dr[2 * n + j]);
+                }
+                bufG2[j * ldt + il] = g;
+                bufY[j * ldt + il] = y;
+            }
+            __syncthreads();
+            T acc4[4][4] = {};
+            if (act) {                           // M1[i][i'] = sum_j Y[i][j] G[j][i']
+                for (int j = 0; j < np; ++j) {
+                    T y4[4], g4[4];
+                    load4(bufY + j * ldt + r0, y4);
+                    load4(bufG2 + j * ldt + c0, g4);
+#pragma unroll
+                    for (int a_ = 0; a_ < 4; ++a_)
+#pragma unroll
+                        for (int b_ = 0; b_ < 4; ++b_) acc4[a_][b_] += y4[a_] * g4[b_];
+                }
+            }
+            __syncthreads();
+            if (act)
+#pragma unroll
+                for (int a_ = 0; a_ < 4; ++a_)
+#pragma unroll
+                    for (int b_ = 0; b_ < 4; ++b_) bufY[(r0 + a_) * ldt + c0 + b_] = acc4[a_][b_];
+            __syncthreads();
+            if (act) {                           // K[j][i'] = sum_i G[j][i] M1[i][i']
+#pragma unroll
+                for (int a_ = 0; a_ < 4; ++a_)
+#pragma unroll
+                    for (int b_ = 0; b_ < 4; ++b_) acc4[a_][b_] = 0;
+                for (int i = 0; i < np; ++i) {
+                    T m4[4];
+                    load4(bufY + i * ldt + c0, m4);
+#pragma unroll
+                    for (int a_ = 0; a_ < 4; ++a_) {
+                        const T gji = bufG2[(r0 + a_) * ldt + i];
+#pragma unroll
+                        for (int b_ = 0; b_ < 4; ++b_) acc4[a_][b_] += gji * m4[b_];
+                    }
+                }
+            }
+            __syncthreads();
+            if (act)
+#pragma unroll
+                for (int a_ = 0; a_ < 4; ++a_)
+#pragma unroll
+                    for (int b_ = 0; b_ < 4; ++b_) bufG2[(c0 + b_) * ldt + r0 + a_] = acc4[a_][b_];
+            __syncthreads();
+            float* ko = kt_out + ((size_t)w * 2 + sp) * n * n;
+            for (int idx = tid; idx < n * n; idx += nt) {
+                const int i = idx / n, j = idx - i * n;
+                ko[idx] = (float)bufG2[i * ldt + j];
+            }
+            __syncthreads();
+        }
+    } else {
     T* bufA = (T*)uni;                       // Y^T [j][i], later K [j][i]
     T* bufG = bufA + (size_t)np * ldt;       // G   [j][i] = G_{j,i}
     T* bufS = bufG + (size_t)np * ldt;       // G^T [i][j], later C^T tile [j][b] (stride 68)
@@ -537,15 +613,6 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
                 for (int b_ = 0; b_ < 4; ++b_) bufA[(r0 + a_) * ldt + c0 + b_] = acc4[a_][b_];
         }
         __syncthreads();
-        if constexpr (kSplit) {
-            float* ko = kt_out + ((size_t)w * 2 + sp) * n * n;
-            for (int idx = tid; idx < n * n; idx += nt) {
-                const int i = idx / n, j = idx - i * n;
-                ko[idx] = (float)bufA[j * ldt + i];
-            }
-            __syncthreads();
-            continue;
-        }
         const int B = s.B;
         for (int b0 = 0; b0 < B; b0 += 64) {
             for (int idx = tid; idx < 64 * np; idx += nt) {   // C^T tile
@@ -656,6 +723,8 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
         }
     }
 
+    }
+
     // ---- P7: accumulate the sample
     const double EL = -0.5 * kin + vee + vep + vrec + s.vconst[0];
     const int N3 = 3 * N;
@@ -686,17 +755,17 @@ __global__ void __launch_bounds__(256) measure_kernel(SysView<T> s, int mmax, co
 }
 
 template <typename T>
-size_t measure_smem_bytes(int N, int n, int nk, int mmax) {
-    return MLayout<T>(N, n, nk, mmax).total;
+size_t measure_smem_bytes(int N, int n, int nk, int mmax, bool split) {
+    return MLayout<T>(N, n, nk, mmax, split).total;
 }
 
 template <typename T>
 void launch_measure(const SysView<T>& s, const double* X, const T* D, const T* Lp, const T* Gt, const double* logdet,
                     double* acc, double* out_el, double* out_lnpsi, double* out_dl, double* out_de, float* kt_out,
                     float* eg_out, double* elw, cudaStream_t st) {
-    const size_t smem = measure_smem_bytes<T>(s.N, s.n, s.nk, s.mmax);
-    static bool attr_set[3] = {false, false, false};
     const bool split = sizeof(T) == 4 && kt_out != nullptr;
+    const size_t smem = measure_smem_bytes<T>(s.N, s.n, s.nk, s.mmax, split);
+    static bool attr_set[3] = {false, false, false};
     const int which = sizeof(T) == 8 ? 1 : (split ? 2 : 0);
     if constexpr (sizeof(T) == 4) {
         if (split) {
@@ -720,8 +789,8 @@ void launch_measure(const SysView<T>& s, const double* X, const T* D, const T* L
     }
 }
 
-template size_t measure_smem_bytes<double>(int, int, int, int);
-template size_t measure_smem_bytes<float>(int, int, int, int);
+template size_t measure_smem_bytes<double>(int, int, int, int, bool);
+template size_t measure_smem_bytes<float>(int, int, int, int, bool);
 template void launch_measure<double>(const SysView<double>&, const double*, const double*, const double*,
                                      const double*, const double*, double*, double*, double*, double*, double*,
                                      float*, float*, double*, cudaStream_t);

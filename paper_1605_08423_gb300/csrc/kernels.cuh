@@ -42,7 +42,7 @@ void launch_measure(const SysView<T>& s, const double* X, const T* D, const T* L
                     const double* logdet, double* acc, double* out_el, double* out_lnpsi, double* out_dl,
                     double* out_de, float* kt_out, float* eg_out, double* elw, cudaStream_t st);
 template <typename T>
-size_t measure_smem_bytes(int N, int n, int nk, int mmax);
+size_t measure_smem_bytes(int N, int n, int nk, int mmax, bool split);
 
 // k_setup.cu: per-R tables (proton trig, structure factors, p-p Ewald terms).
 void launch_setup(int N, double L, double kappa, int nk, const int4* kvec, const double* R, double* kw,
