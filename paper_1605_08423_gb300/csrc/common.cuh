@@ -266,16 +266,38 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
 // sums, so images beyond it are dropped (the FP64 form keeps r < L).
 constexpr float kRealCut2Mixed = 0.64f;
 
-// Warp-cooperative real-space Ewald sum for the mixed form.  Every lane brings
-// one pair displacement (or none: active = false); the candidate images inside
-// the cutoff of all lanes are enumerated through ballots and dealt out to the
-// lanes 32 at a time, so the warp runs ceil(total / 32) image bodies instead of
-// the largest per-lane image count.  Each lane returns its share of the sum of
-// phi(r) over the warp's images and adds its share of the gradient to grad
-// (when kGrad); only warp totals are meaningful.
+// erfc(x) for 0 <= x <= 4.1 in FP32 given e = exp(-x^2):
+//   erfc(x) = e t P(t),  t = 1 / (1 + x / 2),
+// P a degree-8 polynomial fitted (least squares, relative weight) to
+// erfc(x) exp(x^2) / t; relative error 3.1e-7 in FP32 arithmetic (the fit and
+// its check are in fit_erfc.py beside this package).
+__device__ __forceinline__ float erfc_scaled_fit(float x, float e) {
+    const float t = __fdividef(1.0f, 1.0f + 0.5f * x);
+    float p = -4.711474106e-02f;
+    p = p * t + 2.220349312e-01f;
+    p = p * t - 3.470333517e-01f;
+    p = p * t + 1.025151908e-01f;
+    p = p * t + 1.076001227e-01f;
+    p = p * t + 1.385983676e-01f;
+    p = p * t + 2.617502213e-01f;
+    p = p * t + 2.793540657e-01f;
+    p = p * t + 2.822951376e-01f;
+    return e * t * p;
+}
+
+// 2^x by the hardware approximation (PTX ex2.approx.ftz.f32, a few ulp)
+__device__ __forceinline__ float ex2_fast(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Mixed-form real-space Ewald sum of one pair: the images of the minimum-image
+// vector inside the FP32-level cutoff (skip_min: leave out the minimum image),
+// phi(r) = erfc(kappa r) / r and, when grad, its gradient added to grad.
 template <bool kGrad>
-__device__ __forceinline__ float ewald_real_warp(float dx, float dy, float dz, bool active, bool skip_min, float Lt,
-                                                 float kappa, float* grad) {
+__device__ __forceinline__ float ewald_real_cut(float dx, float dy, float dz, bool skip_min, float Lt, float kappa,
+                                                float* grad) {
     const float iL = 1.f / Lt;
     dx -= Lt * rintf(dx * iL); dy -= Lt * rintf(dy * iL); dz -= Lt * rintf(dz * iL);
     const float rc2 = kRealCut2Mixed * Lt * Lt;
@@ -287,49 +309,25 @@ __device__ __forceinline__ float ewald_real_warp(float dx, float dy, float dz, b
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const float r2 = r0 + ((c & 1) ? e0 : 0.f) + ((c & 2) ? e1 : 0.f) + ((c & 4) ? e2 : 0.f);
-        if (active && r2 < rc2 && r2 > 0.f && !(skip_min && c == 0)) mask |= 1u << c;
+        if (r2 < rc2 && r2 > 0.f) mask |= 1u << c;
     }
-    // per candidate c: which lanes have it; inclusive prefix of the counts
-    unsigned bal[8];
-    int pre[8];
-    int tot = 0;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        bal[c] = __ballot_sync(0xffffffffu, (mask >> c) & 1u);
-        tot += __popc(bal[c]);
-        pre[c] = tot;
-    }
-    const int lane = threadIdx.x & 31;
-    const float c2k = 1.1283791670955126f * kappa;   // 2 kappa / sqrt(pi)
+    if (skip_min) mask &= ~1u;
+    const float sx = dx >= 0.f ? -Lt : Lt, sy = dy >= 0.f ? -Lt : Lt, sz = dz >= 0.f ? -Lt : Lt;
+    const float c2k = 1.1283791670955126f * kappa;      // 2 kappa / sqrt(pi)
+    const float nk2 = -1.4426950408889634f * kappa * kappa;   // -kappa^2 log2(e)
     float v = 0.f;
-    for (int base = 0; base < tot; base += 32) {
-        const int k = base + lane;
-        int c = 0;
-#pragma unroll
-        for (int q = 0; q < 7; ++q) c += (k >= pre[q]) ? 1 : 0;
-        unsigned bc = bal[0];
-        int before = 0;
-#pragma unroll
-        for (int q = 1; q < 8; ++q) {
-            bc = (c == q) ? bal[q] : bc;
-            before = (c == q) ? pre[q - 1] : before;
-        }
-        const int src = k < tot ? nth_set_bit(bc, k - before) : lane;
-        const float sx = __shfl_sync(0xffffffffu, dx, src);
-        const float sy = __shfl_sync(0xffffffffu, dy, src);
-        const float sz = __shfl_sync(0xffffffffu, dz, src);
-        if (k < tot) {
-            const float a = sx + ((c & 1) ? (sx >= 0.f ? -Lt : Lt) : 0.f);
-            const float b = sy + ((c & 2) ? (sy >= 0.f ? -Lt : Lt) : 0.f);
-            const float e = sz + ((c & 4) ? (sz >= 0.f ? -Lt : Lt) : 0.f);
-            const float r2 = a * a + b * b + e * e;
-            const float ir = rsqrtf(r2), r = r2 * ir;
-            const float ec = erfcf(kappa * r);
-            v += ec * ir;
-            if (kGrad) {
-                const float s = -(ec * ir + c2k * expf(-kappa * kappa * r2)) * ir * ir;   // phi'(r) / r
-                grad[0] += s * a; grad[1] += s * b; grad[2] += s * e;
-            }
+    while (mask) {
+        const int c = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const float a = dx + ((c & 1) ? sx : 0.f), b = dy + ((c & 2) ? sy : 0.f), e = dz + ((c & 4) ? sz : 0.f);
+        const float r2 = a * a + b * b + e * e;
+        const float ir = rsqrtf(r2), r = r2 * ir;
+        const float ex = ex2_fast(nk2 * r2);              // exp(-kappa^2 r^2)
+        const float ec = erfc_scaled_fit(kappa * r, ex);
+        v += ec * ir;
+        if (kGrad) {
+            const float s = -(ec * ir + c2k * ex) * ir * ir;   // phi'(r) / r
+            grad[0] += s * a; grad[1] += s * b; grad[2] += s * e;
         }
     }
     return v;

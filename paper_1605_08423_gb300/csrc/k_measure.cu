@@ -23,7 +23,7 @@ namespace qmc {
 
 template <typename T>
 struct MLayout {
-    size_t xs, xt, et, gU, lU, Ui, gi, li, facc, rhot, red, stage, cmask, uni, total;
+    size_t xs, xt, et, gU, lU, Ui, gi, li, facc, gacc, rhot, red, stage, cmask, uni, total;
     // split: the B x n orbital contractions run in the adjoint kernel, so the
     // spin-block work space only holds Y^T / M1 and G (and no epilogue stage)
     __host__ __device__ MLayout(int N, int n, int nk, int mmax, bool split = false) {
@@ -38,6 +38,7 @@ struct MLayout {
         gi = take(sizeof(T) * 3 * N);
         li = take(sizeof(T) * N);
         facc = take(sizeof(double) * 9 * N);
+        gacc = take(sizeof(T) * 9 * N);
         rhot = take(sizeof(V2<T>) * nk);
         red = take(sizeof(double) * 64);
         stage = take(split ? 0 : sizeof(double) * 64 * 6);
@@ -131,6 +132,11 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
     double* f_dl = (double*)(sm + lay.facc);
     double* f_de = f_dl + 3 * N;
     double* f_dv = f_de + 3 * N;
+    // FP32-phase partials per nucleus component (one writer each; FP64 sums
+    // above hold the FP64 close-pair terms and the SIMT Pulay epilogue)
+    T* g_dl = (T*)(sm + lay.gacc);
+    T* g_de = g_dl + 3 * N;
+    T* g_dv = g_de + 3 * N;
     V2<T>* rhot = (V2<T>*)(sm + lay.rhot);
     double* red = (double*)(sm + lay.red);
     double* stage = (double*)(sm + lay.stage);
@@ -155,7 +161,7 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
         et[6 * (idx / 3) + idx % 3] = sn;
         et[6 * (idx / 3) + 3 + idx % 3] = cs;
     }
-    for (int idx = tid; idx < 9 * N; idx += nt) f_dl[idx] = 0.0;
+    for (int idx = tid; idx < 9 * N; idx += nt) { f_dl[idx] = 0.0; g_dl[idx] = T(0); }
     for (int idx = tid; idx < N * ((N + 31) / 32); idx += nt) cmask[idx] = 0u;
     __syncthreads();
 
@@ -255,9 +261,6 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
     const T Lt = (T)L;
     // balanced cyclic pairing: electron i with i+d (mod N), d = 1..N/2 (d = N/2 only for i < N/2),
     // the distance range split into nparts slices
-    // (mixed form with N a multiple of 32: every warp has one slice, and the
-    // image work of its 32 pairs per step is balanced over the lanes)
-    const bool warp_ewald = sizeof(T) == 4 && (N & 31) == 0;
     for (int tt = tid; tt < nparts * N; tt += nt) {
         const int i = tt % N, pi = tt / N, half = N / 2;
         const int d0 = 1 + (half * pi) / nparts, d1 = 1 + (half * (pi + 1)) / nparts;
@@ -265,14 +268,12 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
         for (int d = d0; d < d1; ++d) {
             const bool skip = 2 * d == N && i >= half;
             const int j = (i + d) % N;
-            if constexpr (sizeof(T) == 4) {
-                if (warp_ewald) {
-                    v += ewald_real_warp<false>(xt[3 * i] - xt[3 * j], xt[3 * i + 1] - xt[3 * j + 1],
-                                                xt[3 * i + 2] - xt[3 * j + 2], !skip, false, Lt, kap, nullptr);
-                    continue;
-                }
-            }
             if (skip) continue;
+            if constexpr (sizeof(T) == 4) {
+                v += ewald_real_cut<false>(xt[3 * i] - xt[3 * j], xt[3 * i + 1] - xt[3 * j + 1],
+                                           xt[3 * i + 2] - xt[3 * j + 2], false, Lt, kap, nullptr);
+                continue;
+            }
             v += ewald_real<T>(xt[3 * i] - xt[3 * j], xt[3 * i + 1] - xt[3 * j + 1], xt[3 * i + 2] - xt[3 * j + 2], Lt,
                                kap, nullptr);
         }
@@ -287,6 +288,7 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
     // condition), and FP32 rounding of either term would survive the
     // cancellation.  Deferring them keeps FP64 off the common path.
     double vep_p = 0.0;
+    T vep_t = 0;
     const int nwords = (N + 31) / 32;
     for (int a = warp; a < N; a += nw) {
         T v = 0, gv[3] = {0, 0, 0}, dl[3] = {0, 0, 0}, de[3] = {0, 0, 0};
@@ -298,18 +300,17 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
             const bool close = sizeof(T) == 4 && t < T(0.09);
             if (close) atomicOr(&cmask[a * nwords + (i >> 5)], 1u << (i & 31));
             if constexpr (sizeof(T) == 4) {
-                if (warp_ewald) {
-                    // Jastrow terms per lane; the Ewald images balanced over the warp
-                    if (!close) {
-                        T vv[3], pl[3], pe[3];
-                        for (int mu = 0; mu < 3; ++mu) vv[mu] = gi[3 * i + mu] + gU[3 * i + mu];
-                        ep_jastrow<T>(sd, cd, ell, k2, bep, Zj, vv, pl, pe);
-                        for (int mu = 0; mu < 3; ++mu) { dl[mu] += pl[mu]; de[mu] += pe[mu]; }
-                    }
-                    v += ewald_real_warp<true>(xt[3 * i] - ra[0], xt[3 * i + 1] - ra[1], xt[3 * i + 2] - ra[2], true,
-                                               close, Lt, kap, gv);
-                    continue;
+                // FP32: Jastrow terms unless close; the Ewald images inside the
+                // FP32-level cutoff (a close pair's nearest image is done in FP64)
+                if (!close) {
+                    T vv[3], pl[3], pe[3];
+                    for (int mu = 0; mu < 3; ++mu) vv[mu] = gi[3 * i + mu] + gU[3 * i + mu];
+                    ep_jastrow<T>(sd, cd, ell, k2, bep, Zj, vv, pl, pe);
+                    for (int mu = 0; mu < 3; ++mu) { dl[mu] += pl[mu]; de[mu] += pe[mu]; }
                 }
+                v += ewald_real_cut<true>(xt[3 * i] - ra[0], xt[3 * i + 1] - ra[1], xt[3 * i + 2] - ra[2], close, Lt,
+                                          kap, gv);
+                continue;
             }
             if (close) {   // only the images other than the nearest one here
                 T pg[3] = {0, 0, 0};
@@ -327,12 +328,12 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
         v = warp_sum(v);
 #pragma unroll
         for (int mu = 0; mu < 3; ++mu) { gv[mu] = warp_sum(gv[mu]); dl[mu] = warp_sum(dl[mu]); de[mu] = warp_sum(de[mu]); }
-        if (lane == 0) {
-            vep_p += -Zn * (double)v;
+        if (lane == 0) {   // FP32 partials; FP64 only where the sample is accumulated
+            vep_t += -(T)Zn * v;
             for (int mu = 0; mu < 3; ++mu) {
-                f_dv[3 * a + mu] += Zn * (double)gv[mu];
-                f_dl[3 * a + mu] += (double)dl[mu];
-                f_de[3 * a + mu] += (double)de[mu];
+                g_dv[3 * a + mu] = (T)Zn * gv[mu];
+                g_dl[3 * a + mu] = dl[mu];
+                g_de[3 * a + mu] = de[mu];
             }
         }
     }
@@ -437,6 +438,7 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
     }
     __syncthreads();
     double vrec_p = 0.0;
+    T vrec_t = 0;
     for (int k = tid; k < nk; k += nt) {
         const int4 m = s.kvec[k];
         T re = 0, im = 0;
@@ -450,10 +452,11 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
             im += abx * c.y + aby * c.x;
         }
         const double2 rp = s.rho_p[k];
-        const double rr = rp.x - (double)re, ri = rp.y - (double)im;   // electrons carry -1
-        rhot[k] = V2<T>{(T)rr, (T)ri};
-        vrec_p += s.kw[k] * (rr * rr + ri * ri);
+        const T rr = (T)rp.x - re, ri = (T)rp.y - im;   // electrons carry -1
+        rhot[k] = V2<T>{rr, ri};
+        vrec_t += s.kwt[k] * (rr * rr + ri * ri);
     }
+    vrec_p += (double)vrec_t;
     __syncthreads();
     // ---- P4d: reciprocal-space force on the protons (warp per proton)
     for (int a = warp; a < N; a += nw) {
@@ -467,8 +470,9 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
             gx += c * twopiL * (T)m.x; gy += c * twopiL * (T)m.y; gz += c * twopiL * (T)m.z;
         }
         gx = warp_sum(gx); gy = warp_sum(gy); gz = warp_sum(gz);
-        if (lane == 0) { f_dv[3 * a] += (double)gx; f_dv[3 * a + 1] += (double)gy; f_dv[3 * a + 2] += (double)gz; }
+        if (lane == 0) { g_dv[3 * a] += gx; g_dv[3 * a + 1] += gy; g_dv[3 * a + 2] += gz; }
     }
+    vep_p += (double)vep_t;
     const double vee = block_sum(vee_p, red);
     const double vep = block_sum(vep_p, red + 32);
     const double vrec = block_sum(vrec_p, red);
@@ -732,8 +736,8 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
     double* aw = acc + (size_t)w * stride;
     bool bad = !isfinite(EL);
     for (int c = tid; c < N3; c += nt) {
-        const double dl = f_dl[c];
-        const double de = f_de[c] + f_dv[c] + s.dvpp[c];
+        const double dl = f_dl[c] + (double)g_dl[c];
+        const double de = (f_de[c] + (double)g_de[c]) + (f_dv[c] + (double)g_dv[c]) + s.dvpp[c];
         if (!isfinite(dl) || !isfinite(de)) bad = true;
         aw[3 + c] += dl;
         aw[3 + N3 + c] += EL * dl;
