@@ -17,11 +17,11 @@ namespace qmc {
 
 template <typename T>
 struct SweepSmem {
-    // per warp: G^T [n][n+1], old row [n], phi' [n], positions [3N] (double), trig [6N]
+    // per warp: G^T [n][n+1], old row [n], phi' [n], trig [6N]
     __host__ __device__ static size_t warp_bytes(int N, int n) {
         size_t b = (size_t)n * (n + 1) * sizeof(T) + 2 * (size_t)n * sizeof(T);
         b = (b + 7) & ~size_t(7);
-        b += (size_t)3 * N * sizeof(double) + (size_t)6 * N * sizeof(T);
+        b += (size_t)6 * N * sizeof(T);
         return (b + 15) & ~size_t(15);
     }
 };
@@ -40,7 +40,7 @@ __device__ __forceinline__ T pair_dist(const T* a, const T* b, T ell) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) sweep_kernel(SysView<T> s, double* __restrict__ X, const double* __restrict__ Xp,
+__global__ void __launch_bounds__(512) sweep_kernel(SysView<T> s, double* __restrict__ X, const double* __restrict__ Xp,
                                                     const T* __restrict__ ptp, const T* __restrict__ uacc,
                                                     const T* __restrict__ Phi,
                                                     T* __restrict__ Gt, unsigned long long* __restrict__ nacc) {
@@ -55,8 +55,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SysView<T> s, double* __rest
     T* phi = rowb + n;
     size_t o2 = ((size_t)n * ld + 2 * (size_t)n) * sizeof(T);
     o2 = (o2 + 7) & ~size_t(7);
-    double* xs = (double*)(mine + o2);
-    T* et = (T*)(xs + 3 * N);
+    T* et = (T*)(mine + o2);
 
     for (int idx = threadIdx.x; idx < 6 * N; idx += blockDim.x) ptr_s[idx] = s.ptrig[idx];
     __syncthreads();
@@ -65,13 +64,12 @@ __global__ void __launch_bounds__(256) sweep_kernel(SysView<T> s, double* __rest
 
     const T ell = (T)s.ell, bee = (T)s.b_ee, bep = (T)s.b_ep, Zj = (T)s.Zj;
     const double L = s.L;
-    for (int idx = lane; idx < 3 * N; idx += 32) xs[idx] = X[(size_t)w * 3 * N + idx];
-    __syncwarp();
+    double* Xw = X + (size_t)w * 3 * N;   // positions stay in HBM; accepted moves are written through
     const double iL = 1.0 / L;
     for (int idx = lane; idx < 3 * N; idx += 32) {
         const int i = idx / 3, mu = idx % 3;
         T sn, cs;
-        qsincospi((T)(xs[idx] * iL), &sn, &cs);
+        qsincospi((T)(Xw[idx] * iL), &sn, &cs);
         et[6 * i + mu] = sn;
         et[6 * i + 3 + mu] = cs;
     }
@@ -153,13 +151,13 @@ __global__ void __launch_bounds__(256) sweep_kernel(SysView<T> s, double* __rest
                     const double xpl = Xp[row * 3 + lane];
                     if (sizeof(T) == 8) {
                         const double x = xpl - L * floor(xpl / L);
-                        xs[3 * i + lane] = x;
+                        Xw[3 * i + lane] = x;
                         T sn, cs;
                         qsincospi((T)(x / L), &sn, &cs);
                         et[6 * i + lane] = sn;
                         et[6 * i + 3 + lane] = cs;
                     } else {
-                        xs[3 * i + lane] = xpl;
+                        Xw[3 * i + lane] = xpl;
                         et[6 * i + lane] = pt[lane];
                         et[6 * i + 3 + lane] = pt[3 + lane];
                     }
@@ -171,7 +169,6 @@ __global__ void __launch_bounds__(256) sweep_kernel(SysView<T> s, double* __rest
         for (int idx = lane; idx < n * n; idx += 32) G[idx] = Gs[(idx / n) * ld + idx % n];
         __syncwarp();
     }
-    for (int idx = lane; idx < 3 * N; idx += 32) X[(size_t)w * 3 * N + idx] = xs[idx];
     if (lane == 0) nacc[w] += naccept;
 }
 
@@ -180,8 +177,9 @@ void launch_sweep(const SysView<T>& s, double* X, const double* Xp, const T* ptp
                   unsigned long long* nacc, cudaStream_t st) {
     const size_t wb = SweepSmem<T>::warp_bytes(s.N, s.n);
     const size_t head = ((size_t)6 * s.N * sizeof(T) + 15) & ~size_t(15);
-    int wpb = (int)((200 * 1024 - head) / wb);
-    if (wpb > 8) wpb = 8;
+    // as many walkers per CTA as the shared memory of one SM holds (one CTA per SM)
+    int wpb = (int)((226 * 1024 - head) / wb);
+    if (wpb > 16) wpb = 16;
     if (wpb < 1) wpb = 1;
     const size_t smem = head + wpb * wb;
     static bool attr_set[2] = {false, false};
