@@ -74,7 +74,7 @@ void prepare_tc_coeff(const float* C, int B, int n, void* chat, cudaStream_t st)
 // Q = 1: values (Slater rows / proposals).  Q = 4: d/dx, d/dy, d/dz and the
 // Laplacian (local energy; the values are not needed there).
 template <int Q, int P>
-__global__ void __launch_bounds__(Q == 1 ? 256 : 512, 1)
+__global__ void __launch_bounds__(Q == 1 ? 256 : 512, Q == 1 ? 4 : 1)
     orbitals_tc_kernel(SysView<float> s, const unsigned char* __restrict__ chat, const double* __restrict__ pos,
                        int nrows, int NM, float* __restrict__ val, float* __restrict__ grad, float* __restrict__ lap) {
     extern __shared__ unsigned char smraw[];
@@ -118,11 +118,38 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 512, 1)
     const size_t chunk_bytes = (size_t)kPieces * NM * 128;
     bool ok = true;
 
-    for (int c = 0; c < nch; ++c) {
-        // B operand: the first P pieces of the prepared C^T chunk (16-byte vectors)
+    // B operand: the first P pieces of each prepared C^T chunk (16-byte
+    // vectors).  Q = 4 (one CTA per SM): fetched into registers one chunk
+    // ahead and stored once the previous chunk's MMAs are done.  Q = 1 (several
+    // CTAs per SM hide the latency): copied at the start of each chunk.
+    constexpr int kBv = Q == 4 ? 2 : 4;   // P * NM * 8 <= 1024 vectors over 512 (Q = 4) or 256 threads
+    const int nbv = P * NM * 8;
+    uint4 bnext[kBv];
+    auto fetch_b = [&](int c) {
         const uint4* src = (const uint4*)(chat + (size_t)c * chunk_bytes);
+#pragma unroll
+        for (int v = 0; v < kBv; ++v) {
+            const int idx = tid + v * nt;
+            if (idx < nbv) bnext[v] = src[idx];
+        }
+    };
+    auto store_b = [&]() {
         uint4* dst = (uint4*)sB;
-        for (int idx = tid; idx < P * NM * 8; idx += nt) dst[idx] = src[idx];
+#pragma unroll
+        for (int v = 0; v < kBv; ++v) {
+            const int idx = tid + v * nt;
+            if (idx < nbv) dst[idx] = bnext[v];
+        }
+    };
+    fetch_b(0);
+    store_b();
+    for (int c = 0; c < nch; ++c) {
+        if constexpr (Q == 4) {
+            if (c + 1 < nch) fetch_b(c + 1);
+        } else if (c > 0) {
+            fetch_b(c);
+            store_b();
+        }
         // A operand: one item = (row, 4 consecutive basis functions); the
         // displacement to a nucleus is computed once for its Gaussians
 #pragma unroll 2
@@ -185,11 +212,13 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 512, 1)
                     *(float4*)(tq + kTileA) = x1;
                     *(float4*)(tq + 2 * kTileA) = x2;
                 } else {
+                    // hi rounded to TF32; lo = x - hi exactly, whose low bits the
+                    // tensor core drops (sign-symmetric, below 2^-22 |x|)
                     float4 x0, x1;
-                    tc::split_tf32(v[q][0], x0.x, x1.x);
-                    tc::split_tf32(v[q][1], x0.y, x1.y);
-                    tc::split_tf32(v[q][2], x0.z, x1.z);
-                    tc::split_tf32(v[q][3], x0.w, x1.w);
+                    tc::split_tf32_fast(v[q][0], x0.x, x1.x);
+                    tc::split_tf32_fast(v[q][1], x0.y, x1.y);
+                    tc::split_tf32_fast(v[q][2], x0.z, x1.z);
+                    tc::split_tf32_fast(v[q][3], x0.w, x1.w);
                     *(float4*)(tq) = x0;
                     *(float4*)(tq + kTileA) = x1;
                 }
@@ -223,6 +252,7 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 512, 1)
         __syncwarp();
         if (!tc::mbar_wait(&mbar, (uint32_t)(c & 1), 1ll << 26)) ok = false;
         tc::fence_after_sync();
+        if (Q == 4 && c + 1 < nch) store_b();   // the MMAs of chunk c have read sB
         __syncthreads();
     }
     if (!ok && lane == 0) raise_err(s.err, kErrTimeout);

@@ -156,5 +156,13 @@ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
     lo = round_tf32(x - hi);
 }
 
+// x = hi + lo with hi the nearest TF32 value and lo = x - hi (exact in FP32,
+// at most 2^-11 |x|); the tensor core reads lo's TF32 bits, i.e. drops its low
+// bits toward zero, an error below 2^-22 |x| of either sign.
+__device__ __forceinline__ void split_tf32_fast(float x, float& hi, float& lo) {
+    hi = round_tf32(x);
+    lo = x - hi;
+}
+
 }  // namespace tc
 }  // namespace qmc
