@@ -59,6 +59,54 @@ struct MLayout {
 // images and its gradient g with respect to the electron-proton vector; the
 // e-n Jastrow contributions dl (to d ln psi/dR_a) and de (to dE_L/dR_a, given
 // vv = g_i + grad_i U).  sd, cd: sin, cos(pi (x - R_a)/L) per component.
+// FP32 radial factors of the Pade pair functions in t = rho^2, from one
+// reciprocal square root and one reciprocal (the FP64 form goes through
+// pade_* and rho_to_t):  f1 = u'/(2 rho),  f2 = (u''/rho^2 - u'/rho^3)/4,
+// f3 = (u'''/rho^3 - 3 u''/rho^4 + 3 u'/rho^5)/8.
+__device__ __forceinline__ void jas_ee_f32(float t, float b, float& u, float& f1, float& f2) {
+    const float ir = rsqrtf(t), r = t * ir, ir2 = ir * ir;
+    const float iq = __fdividef(1.0f, 1.0f + b * r), iq2 = iq * iq;
+    u = 0.5f * r * iq;
+    const float u1 = 0.5f * iq2, u2 = -b * iq2 * iq;
+    f1 = 0.5f * u1 * ir;
+    f2 = 0.25f * (u2 - u1 * ir) * ir2;
+}
+__device__ __forceinline__ void jas_ep_f32(float t, float b, float Zj, float& u, float& f1, float& f2, float& f3) {
+    const float ir = rsqrtf(t), r = t * ir, ir2 = ir * ir;
+    const float iq = __fdividef(1.0f, 1.0f + b * r), iq2 = iq * iq;
+    u = -Zj * r * iq;
+    const float u1 = -Zj * iq2, u2 = 2.0f * Zj * b * iq2 * iq, u3 = -6.0f * Zj * b * b * iq2 * iq2;
+    f1 = 0.5f * u1 * ir;
+    f2 = 0.25f * (u2 - u1 * ir) * ir2;
+    f3 = 0.125f * (u3 - 3.0f * (u2 - u1 * ir) * ir) * ir2 * ir;
+}
+
+// FP32 e-n pair terms of d ln psi / dR and dE_L / dR (same quantities as
+// ep_jastrow): g = 2 f1 p, H v = 4 f2 p (p.v) + 2 f1 q o v,
+// grad lap u = p o (8 f3 |p|^2 + 8 f2 q + 4 f2 sum q - 2 k^2 f1).
+__device__ __forceinline__ void ep_jastrow_f32(const float sd[3], const float cd[3], float ell, float k2, float bep,
+                                               float Zj, const float vv[3], float dl[3], float de[3]) {
+    float p[3], q[3], s2 = 0.f;
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) {
+        p[mu] = ell * sd[mu] * cd[mu];
+        q[mu] = cd[mu] * cd[mu] - sd[mu] * sd[mu];
+        s2 += sd[mu] * sd[mu];
+    }
+    float u, f1, f2, f3;
+    jas_ep_f32(ell * ell * s2, bep, Zj, u, f1, f2, f3);
+    const float pp = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+    const float sq = q[0] + q[1] + q[2];
+    const float pv = p[0] * vv[0] + p[1] * vv[1] + p[2] * vv[2];
+    const float c2 = 2.f * f1, c4 = 4.f * f2;
+    const float common = 8.f * f3 * pp + c4 * sq - 2.f * k2 * f1;
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) {
+        dl[mu] = -c2 * p[mu];
+        de[mu] = c4 * p[mu] * pv + c2 * q[mu] * vv[mu] + 0.5f * p[mu] * (common + 8.f * f2 * q[mu]);
+    }
+}
+
 template <typename S>
 __device__ __forceinline__ void ep_jastrow(const S sd[3], const S cd[3], S ell, S k2, S bep, S Zj, const S vv[3],
                                            S dl[3], S de[3]) {
@@ -179,10 +227,15 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
             if (j == i) continue;
             T sd[3], cd[3], t;
             disp_trig(ei, et + 6 * j, ell, sd, cd, t);
-            const T r = qsqrt_pair(t);
-            T u, u1, u2, f1, f2, f3;
-            pade_ee(bee, r, u, u1, u2);
-            rho_to_t(r, u1, u2, T(0), f1, f2, f3);
+            T u, f1, f2;
+            if constexpr (sizeof(T) == 4) {
+                jas_ee_f32(t, bee, u, f1, f2);
+            } else {
+                const T r = qsqrt_pair(t);
+                T u1, u2, f3;
+                pade_ee(bee, r, u, u1, u2);
+                rho_to_t(r, u1, u2, T(0), f1, f2, f3);
+            }
             T pp = 0, sq = 0;
 #pragma unroll
             for (int mu = 0; mu < 3; ++mu) {
@@ -196,10 +249,16 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
         for (int a = j0; a < j1; ++a) {
             T sd[3], cd[3], t;
             disp_trig(ei, s.ptrig + 6 * a, ell, sd, cd, t);
-            const T r = qsqrt_pair(t);
-            T u, u1, u2, u3, f1, f2, f3;
-            pade_ep(bep, Zj, r, u, u1, u2, u3);
-            rho_to_t(r, u1, u2, T(0), f1, f2, f3);
+            T u, f1, f2;
+            if constexpr (sizeof(T) == 4) {
+                float f3;
+                jas_ep_f32(t, bep, Zj, u, f1, f2, f3);
+            } else {
+                const T r = qsqrt_pair(t);
+                T u1, u2, u3, f3;
+                pade_ep(bep, Zj, r, u, u1, u2, u3);
+                rho_to_t(r, u1, u2, T(0), f1, f2, f3);
+            }
             T pp = 0, sq = 0;
 #pragma unroll
             for (int mu = 0; mu < 3; ++mu) {
@@ -305,7 +364,7 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
                 if (!close) {
                     T vv[3], pl[3], pe[3];
                     for (int mu = 0; mu < 3; ++mu) vv[mu] = gi[3 * i + mu] + gU[3 * i + mu];
-                    ep_jastrow<T>(sd, cd, ell, k2, bep, Zj, vv, pl, pe);
+                    ep_jastrow_f32(sd, cd, ell, k2, bep, Zj, vv, pl, pe);
                     for (int mu = 0; mu < 3; ++mu) { dl[mu] += pl[mu]; de[mu] += pe[mu]; }
                 }
                 v += ewald_real_cut<true>(xt[3 * i] - ra[0], xt[3 * i + 1] - ra[1], xt[3 * i + 2] - ra[2], close, Lt,
