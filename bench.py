@@ -119,6 +119,12 @@ class ClockSampler:
 #   reciprocal space: structure factor 14 per (electron, k),
 #     force 12 per (nucleus, k)
 #   g_i, l_i: 8 n per electron;  K = G Y G: 8 n^3 per walker
+# DRAM bytes per walker sample of the measure kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture at 2048 walkers, scaled by walkers:
+# traffic grows with the walker count); profiles/measure_kernel_h128_w2048_mixed.md.
+# None once the kernel has changed since that capture.
+MEASURE_DRAM_BYTES_PER_WALKER = (573.377792e6 + 78.720256e6) / 2048
+
 MEASURE_UNIT = {"ee_jas": 55.0, "ep_jas": 55.0, "ee_ewald": 6.0 + 10.0 * 4.19, "ep": 130.0 + 6.0 + 19.0 * 4.19,
                 "sk": 14.0, "fk": 12.0}
 
@@ -303,6 +309,9 @@ def run_ours(args, ws, rank, local):
                           "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock",
                           "flops_per_launch": fl, "avg_launch_ms": avg}
     dom = max(kt, key=lambda k: kt[k][0])
+    if "measure" in roofs and use_tc and N == 128 and G == 4 and MEASURE_DRAM_BYTES_PER_WALKER:
+        roofs["measure"]["traffic"] = MEASURE_DRAM_BYTES_PER_WALKER * W
+        roofs["measure"]["traffic_source"] = "ncu dram bytes, 2048-walker capture scaled to the launch"
     roof = roofs.get(dom, {"kernel": dom, "bound": "alu", "achieved": None, "peak": fp32_peak,
                            "unit": "TFLOP/s", "frac": None, "traffic": None})
     breakdown = {k: {"ms": v[0] / args.steps, "launches": v[1] // max(args.steps, 1)} for k, v in kt.items()}
