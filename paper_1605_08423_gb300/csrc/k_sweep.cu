@@ -17,14 +17,38 @@ namespace qmc {
 
 template <typename T>
 struct SweepSmem {
-    // per warp: G^T [n][n+1], old row [n], phi' [n], trig [6N]
+    // Rows of the staged inverse are 16-byte vectors: nv = n rounded up to a
+    // whole vector (zero padded), row stride ld = nv + one vector, so that the
+    // 16-byte accesses of 8 consecutive lanes (one per row) hit distinct banks.
+    static constexpr int VE = 16 / sizeof(T);   // elements per 16-byte vector
+    __host__ __device__ static int nv(int n) { return (n + VE - 1) / VE * VE; }
+    __host__ __device__ static int ld(int n) { return nv(n) + VE; }
+    // per warp: G^T [n][ld], old row [nv], phi' [nv], trig [6N]
     __host__ __device__ static size_t warp_bytes(int N, int n) {
-        size_t b = (size_t)n * (n + 1) * sizeof(T) + 2 * (size_t)n * sizeof(T);
-        b = (b + 7) & ~size_t(7);
+        size_t b = ((size_t)n * ld(n) + 2 * (size_t)nv(n)) * sizeof(T);
         b += (size_t)6 * N * sizeof(T);
         return (b + 15) & ~size_t(15);
     }
 };
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+
+__device__ __forceinline__ float vdot(float4 a, float4 b, float acc[4]) {
+    acc[0] += a.x * b.x; acc[1] += a.y * b.y; acc[2] += a.z * b.z; acc[3] += a.w * b.w;
+    return 0.f;
+}
+__device__ __forceinline__ double vdot(double2 a, double2 b, double acc[4]) {
+    acc[0] += a.x * b.x; acc[1] += a.y * b.y;
+    return 0.0;
+}
+__device__ __forceinline__ float4 vaxpy(float4 g, float c, float4 r) {
+    return make_float4(g.x - c * r.x, g.y - c * r.y, g.z - c * r.z, g.w - c * r.w);
+}
+__device__ __forceinline__ double2 vaxpy(double2 g, double c, double2 r) {
+    return make_double2(g.x - c * r.x, g.y - c * r.y);
+}
 
 template <typename T>
 __device__ __forceinline__ T pair_dist(const T* a, const T* b, T ell) {
@@ -45,17 +69,17 @@ __global__ void __launch_bounds__(512) sweep_kernel(SysView<T> s, double* __rest
                                                     const T* __restrict__ Phi,
                                                     T* __restrict__ Gt, unsigned long long* __restrict__ nacc) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int N = s.N, n = s.n, ld = n + 1;
+    using V = typename Vec16<T>::type;
+    constexpr int VE = SweepSmem<T>::VE;
+    const int N = s.N, n = s.n, nv = SweepSmem<T>::nv(n), ld = SweepSmem<T>::ld(n), nvv = nv / VE;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     T* ptr_s = (T*)smraw;                                    // [N][6] proton trig
     size_t off = ((size_t)6 * N * sizeof(T) + 15) & ~size_t(15);
     unsigned char* mine = smraw + off + (size_t)warp * SweepSmem<T>::warp_bytes(N, n);
     T* Gs = (T*)mine;
     T* rowb = Gs + (size_t)n * ld;
-    T* phi = rowb + n;
-    size_t o2 = ((size_t)n * ld + 2 * (size_t)n) * sizeof(T);
-    o2 = (o2 + 7) & ~size_t(7);
-    T* et = (T*)(mine + o2);
+    T* phi = rowb + nv;
+    T* et = phi + nv;
 
     for (int idx = threadIdx.x; idx < 6 * N; idx += blockDim.x) ptr_s[idx] = s.ptrig[idx];
     __syncthreads();
@@ -74,6 +98,7 @@ __global__ void __launch_bounds__(512) sweep_kernel(SysView<T> s, double* __rest
         et[6 * i + 3 + mu] = cs;
     }
     __syncwarp();
+    for (int j = n + lane; j < nv; j += 32) phi[j] = T(0);   // padding stays zero
     unsigned long long naccept = 0;
     // the next move's proposal trig, orbital row (n <= 64: two per lane) and
     // uniform are loaded one move ahead, so their HBM latency overlaps a move
@@ -89,7 +114,10 @@ __global__ void __launch_bounds__(512) sweep_kernel(SysView<T> s, double* __rest
     fetch(0);
     for (int sp = 0; sp < 2; ++sp) {
         T* G = Gt + ((size_t)w * 2 + sp) * n * n;
-        for (int idx = lane; idx < n * n; idx += 32) Gs[(idx / n) * ld + idx % n] = G[idx];
+        for (int idx = lane; idx < n * nv; idx += 32) {
+            const int r = idx / nv, c = idx - r * nv;
+            Gs[r * ld + c] = c < n ? G[r * n + c] : T(0);
+        }
         __syncwarp();
         for (int il = 0; il < n; ++il) {
             const int i = sp * n + il;
@@ -127,21 +155,18 @@ __global__ void __launch_bounds__(512) sweep_kernel(SysView<T> s, double* __rest
             du = warp_sum(du);
             const T prob = ratio * ratio * qexp(T(2) * du);
             if (u < prob) {
-                for (int j = lane; j < n; j += 32) rowb[j] = Gs[il * ld + j];
+                for (int j = lane; j < nv; j += 32) rowb[j] = Gs[il * ld + j];
                 __syncwarp();
                 const T ir = T(1) / ratio;
+                const V* phv = (const V*)phi;
+                const V* rbv = (const V*)rowb;
                 for (int l = lane; l < n; l += 32) {
-                    T* gl = Gs + l * ld;
-                    T w4[4] = {0, 0, 0, 0};   // four partial sums: short dependency chains
-                    int j = 0;
-                    for (; j + 4 <= n; j += 4) {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) w4[q] += phi[j + q] * gl[j + q];
-                    }
-                    for (; j < n; ++j) w4[0] += phi[j] * gl[j];
+                    V* gl = (V*)(Gs + l * ld);
+                    T w4[4] = {0, 0, 0, 0};   // partial sums per vector component: short chains
+                    for (int jv = 0; jv < nvv; ++jv) vdot(phv[jv], gl[jv], w4);
                     const T wl = (w4[0] + w4[1]) + (w4[2] + w4[3]);
                     const T coef = (wl - (l == il ? T(1) : T(0))) * ir;
-                    for (int j = 0; j < n; ++j) gl[j] -= coef * rowb[j];
+                    for (int jv = 0; jv < nvv; ++jv) gl[jv] = vaxpy(gl[jv], coef, rbv[jv]);
                 }
                 if (lane < 3) {
                     // FP64 form: wrap into [0, L) at once (as the reference chain does).
@@ -167,6 +192,7 @@ __global__ void __launch_bounds__(512) sweep_kernel(SysView<T> s, double* __rest
             __syncwarp();
         }
         for (int idx = lane; idx < n * n; idx += 32) G[idx] = Gs[(idx / n) * ld + idx % n];
+        (void)VE;
         __syncwarp();
     }
     if (lane == 0) nacc[w] += naccept;
