@@ -151,11 +151,46 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 512, Q == 1 ? 4 : 1)
             store_b();
         }
         // A operand: one item = (row, 4 consecutive basis functions); the
-        // displacement to a nucleus is computed once for its Gaussians
-#pragma unroll 2
-        for (int item = tid; item < kRows * (kKc / 4); item += nt) {
+        // displacement to a nucleus is computed once for its Gaussians.  In the
+        // value kernel all items of a thread are evaluated before any is
+        // stored, so their arithmetic overlaps (the stores could alias the
+        // tables it reads); the derivative kernel stores item by item.
+        constexpr int IT = kRows * (kKc / 4) / (Q == 1 ? 256 : 512);   // items per thread
+        float vv[IT][Q][4];
+        auto store_item = [&](int u) {
+            const int item = tid + u * nt;
             const int r = item / (kKc / 4), k0 = 4 * (item - r * (kKc / 4));
-            float v[Q][4];
+            const uint32_t off = tc::sw128_off(r, k0);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                unsigned char* tq = sA + (size_t)(P * q) * kTileA + off;
+                const float* v = vv[u][q];
+                if constexpr (P == 3) {
+                    float4 x0, x1, x2;
+                    tc::split3_tf32(v[0], x0.x, x1.x, x2.x);
+                    tc::split3_tf32(v[1], x0.y, x1.y, x2.y);
+                    tc::split3_tf32(v[2], x0.z, x1.z, x2.z);
+                    tc::split3_tf32(v[3], x0.w, x1.w, x2.w);
+                    *(float4*)(tq) = x0;
+                    *(float4*)(tq + kTileA) = x1;
+                    *(float4*)(tq + 2 * kTileA) = x2;
+                } else {
+                    // hi rounded to TF32; lo = x - hi exactly, whose low bits the
+                    // tensor core drops (sign-symmetric, below 2^-22 |x|)
+                    float4 x0, x1;
+                    tc::split_tf32_fast(v[0], x0.x, x1.x);
+                    tc::split_tf32_fast(v[1], x0.y, x1.y);
+                    tc::split_tf32_fast(v[2], x0.z, x1.z);
+                    tc::split_tf32_fast(v[3], x0.w, x1.w);
+                    *(float4*)(tq) = x0;
+                    *(float4*)(tq + kTileA) = x1;
+                }
+            }
+        };
+#pragma unroll
+        for (int u = 0; u < IT; ++u) {
+            const int item = tid + u * nt;
+            const int r = item / (kKc / 4), k0 = 4 * (item - r * (kKc / 4));
             int a_prev = -1;
             float t = 0.f, pp = 0.f, sq = 0.f, pv[3] = {0.f, 0.f, 0.f};
             // nucleus and Gaussian of basis function b = a G + g (shifts when G is a power of two)
@@ -169,7 +204,7 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 512, Q == 1 ? 4 : 1)
                 int a = a0, g = g0 + kk;
                 while (g >= G) { g -= G; ++a; }
 #pragma unroll
-                for (int q = 0; q < Q; ++q) v[q][kk] = 0.f;
+                for (int q = 0; q < Q; ++q) vv[u][q][kk] = 0.f;
                 if (b >= B || row0 + r >= nrows) continue;
                 if (a != a_prev) {
                     a_prev = a;
@@ -190,39 +225,19 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 512, Q == 1 ? 4 : 1)
                 const float z = zs[g];
                 const float e = tc_ex2(-zs[8 + g] * t);
                 if (Q == 1) {
-                    v[0][kk] = e;
+                    vv[u][0][kk] = e;
                 } else {
                     const float f1 = -z * e, f2 = z * z * e;
 #pragma unroll
-                    for (int mu = 0; mu < 3; ++mu) v[mu][kk] = 2.f * f1 * pv[mu];
-                    v[Q - 1][kk] = 4.f * f2 * pp + 2.f * f1 * sq;
+                    for (int mu = 0; mu < 3; ++mu) vv[u][mu][kk] = 2.f * f1 * pv[mu];
+                    vv[u][Q - 1][kk] = 4.f * f2 * pp + 2.f * f1 * sq;
                 }
             }
-            const uint32_t off = tc::sw128_off(r, k0);
+            if constexpr (Q != 1) store_item(u);   // register budget: one item at a time
+        }
+        if constexpr (Q == 1) {
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                unsigned char* tq = sA + (size_t)(P * q) * kTileA + off;
-                if constexpr (P == 3) {
-                    float4 x0, x1, x2;
-                    tc::split3_tf32(v[q][0], x0.x, x1.x, x2.x);
-                    tc::split3_tf32(v[q][1], x0.y, x1.y, x2.y);
-                    tc::split3_tf32(v[q][2], x0.z, x1.z, x2.z);
-                    tc::split3_tf32(v[q][3], x0.w, x1.w, x2.w);
-                    *(float4*)(tq) = x0;
-                    *(float4*)(tq + kTileA) = x1;
-                    *(float4*)(tq + 2 * kTileA) = x2;
-                } else {
-                    // hi rounded to TF32; lo = x - hi exactly, whose low bits the
-                    // tensor core drops (sign-symmetric, below 2^-22 |x|)
-                    float4 x0, x1;
-                    tc::split_tf32_fast(v[q][0], x0.x, x1.x);
-                    tc::split_tf32_fast(v[q][1], x0.y, x1.y);
-                    tc::split_tf32_fast(v[q][2], x0.z, x1.z);
-                    tc::split_tf32_fast(v[q][3], x0.w, x1.w);
-                    *(float4*)(tq) = x0;
-                    *(float4*)(tq + kTileA) = x1;
-                }
-            }
+            for (int u = 0; u < IT; ++u) store_item(u);
         }
         tc::fence_proxy_async();
         __syncthreads();
