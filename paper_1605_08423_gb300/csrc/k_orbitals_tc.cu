@@ -74,17 +74,18 @@ void prepare_tc_coeff(const float* C, int B, int n, void* chat, cudaStream_t st)
 // Q = 1: values (Slater rows / proposals).  Q = 4: d/dx, d/dy, d/dz and the
 // Laplacian (local energy; the values are not needed there).
 template <int Q, int P>
-__global__ void __launch_bounds__(Q == 1 ? 256 : 512, Q == 1 ? 4 : 1)
+__global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
     orbitals_tc_kernel(SysView<float> s, const unsigned char* __restrict__ chat, const double* __restrict__ pos,
                        int nrows, int NM, float* __restrict__ val, float* __restrict__ grad, float* __restrict__ lap) {
     extern __shared__ unsigned char smraw[];
     unsigned char* base = (unsigned char*)((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
     unsigned char* sA = base;                                    // [Q][piece] tiles of 16 KB
-    unsigned char* sB = base + (size_t)Q * P * kTileA;           // [piece] tiles of NM * 128 bytes
-    float* ptr_s = (float*)(sB + (size_t)P * NM * 128);          // [N][6] proton trig
+    unsigned char* sB = base + (size_t)Q * P * kTileA;           // [buffer][piece] tiles of NM * 128 bytes
+    constexpr int kBbuf = Q == 4 ? 2 : 1;                        // B buffers
+    float* ptr_s = (float*)(sB + (size_t)kBbuf * P * NM * 128);  // [N][6] proton trig
     __shared__ float rtrig[kRows][6];
     __shared__ float zs[16];   // zeta_g and zeta_g log2(e), g < 8
-    __shared__ uint64_t mbar;
+    __shared__ uint64_t mbarh[2], fullh[2];
     __shared__ uint32_t tbase;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nt = blockDim.x;
     const int row0 = blockIdx.x * kRows;
@@ -93,7 +94,11 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 512, Q == 1 ? 4 : 1)
     constexpr uint32_t kCols = (Q == 1) ? 64u : 256u;      // TMEM columns (power of two >= Q * NM)
 
     if (warp == 0) { tc::tmem_alloc(&tbase, kCols); tc::tmem_relinquish(); }
-    if (tid == 0) tc::mbar_init(&mbar, 1);
+    if (tid == 0) {
+        tc::mbar_init(&mbarh[0], 1); tc::mbar_init(&mbarh[1], 1);
+        tc::mbar_init(&fullh[0], 16); tc::mbar_init(&fullh[1], 16);   // one arrival per producer warp
+        tc::fence_mbar_init();
+    }
     for (int idx = tid; idx < kRows * 3; idx += nt) {
         const int r = idx / 3, mu = idx % 3, row = row0 + r;
         float sn = 0.f, cs = 1.f;
@@ -118,6 +123,145 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 512, Q == 1 ? 4 : 1)
     const size_t chunk_bytes = (size_t)kPieces * NM * 128;
     bool ok = true;
 
+    if constexpr (Q == 4 && P == 2) {
+    // Derivative kernel (Q = 4): a chunk of 32 basis functions is produced in
+    // two halves (basis 0-15 and 16-31 = k-steps 0-1 and 2-3, disjoint 64-byte
+    // column ranges of every A row).  Warps 0-15 produce and arrive on
+    // fullh[h]; warp 16 waits on it and issues the half's MMAs, which commit to
+    // mbarh[h] (one completion per chunk), so the tensor core works on one half
+    // while the producers fill the other.  Half h of chunk c is overwritten
+    // only after the MMAs of (c - 1, h) are done.  B is double-buffered: chunk
+    // c + 1 is fetched into registers a chunk ahead and stored once the MMAs of
+    // chunk c - 1, the buffer's last reader, are done.
+    constexpr int kProd = 512;                 // producer threads
+    constexpr int kBv4 = 2;                    // P * NM * 8 <= 1024 vectors over 512 producers
+    const int nbv4 = P * NM * 8;
+    const size_t bbytes = (size_t)P * NM * 128;
+    uint4 bnx[kBv4];
+    auto fetch_b4 = [&](int c) {
+        const uint4* src = (const uint4*)(chat + (size_t)c * chunk_bytes);
+#pragma unroll
+        for (int v = 0; v < kBv4; ++v) {
+            const int idx = tid + v * kProd;
+            if (idx < nbv4) bnx[v] = src[idx];
+        }
+    };
+    auto store_b4 = [&](int buf) {
+        uint4* dst = (uint4*)(sB + (size_t)buf * bbytes);
+#pragma unroll
+        for (int v = 0; v < kBv4; ++v) {
+            const int idx = tid + v * kProd;
+            if (idx < nbv4) dst[idx] = bnx[v];
+        }
+    };
+    if (tid < kProd) {
+        fetch_b4(0);
+        store_b4(0);
+        if (nch > 1) fetch_b4(1);
+    }
+    const bool issuer = warp == kProd / 32;
+    for (int c = 0; c < nch; ++c) {
+        for (int h = 0; h < 2; ++h) {
+            if (issuer) {
+                if (lane == 0) {
+                    if (!tc::mbar_wait(&fullh[h], (uint32_t)(c & 1), 1ll << 26)) ok = false;
+                    tc::fence_after_sync();
+                    const uint32_t b0 = tc::smem_addr(sB + (size_t)(c & 1) * bbytes), bstep = (uint32_t)NM * 128;
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) {
+                        const uint32_t a0 = tc::smem_addr(sA + (size_t)(P * q) * kTileA);
+                        const uint32_t d = tmem + (uint32_t)(q * NM);
+#pragma unroll
+                        for (int kh = 0; kh < 2; ++kh) {
+                            const int ks = 2 * h + kh;
+                            const uint32_t o = 32u * ks;
+                            // products A_i B_j with i + j <= P - 1, smallest first
+                            constexpr int np = P == 3 ? 6 : 3;
+                            const int pi[6] = {2, 1, 0, 1, 0, 0}, pj[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+                            for (int m = 6 - np; m < 6; ++m)
+                                tc::mma_tf32(d, tc::desc_sw128(a0 + pi[m] * kTileA + o),
+                                             tc::desc_sw128(b0 + pj[m] * bstep + o), idesc,
+                                             (c > 0 || ks > 0 || m > 6 - np) ? 1u : 0u);
+                        }
+                    }
+                    tc::mma_commit(&mbarh[h]);
+                }
+                __syncwarp();
+                continue;
+            }
+            if (c > 0) {
+                if (!tc::mbar_wait(&mbarh[h], (uint32_t)((c - 1) & 1), 1ll << 26)) ok = false;
+                tc::fence_after_sync();
+            }
+            if (h == 1 && c + 1 < nch) {
+                store_b4((c + 1) & 1);
+                if (c + 2 < nch) fetch_b4(c + 2);
+            }
+            // one item = (row, 4 consecutive basis functions of the half); the
+            // displacement to a nucleus is computed once for its Gaussians
+            const int r = tid >> 2, k0 = 16 * h + 4 * (tid & 3);
+            float v[Q][4];
+            int a_prev = -1;
+            float t = 0.f, pp = 0.f, sq = 0.f, pv[3] = {0.f, 0.f, 0.f};
+            const int b0 = c * kKc + k0;
+            int a0, g0;
+            if (gshift >= 0) { a0 = b0 >> gshift; g0 = b0 & (G - 1); }
+            else { a0 = b0 / G; g0 = b0 - a0 * G; }
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const int b = b0 + kk;
+                int a = a0, g = g0 + kk;
+                while (g >= G) { g -= G; ++a; }
+#pragma unroll
+                for (int q = 0; q < Q; ++q) v[q][kk] = 0.f;
+                if (b >= B || row0 + r >= nrows) continue;
+                if (a != a_prev) {
+                    a_prev = a;
+                    const float* pt = ptr_s + 6 * a;
+                    t = 0.f; pp = 0.f; sq = 0.f;
+#pragma unroll
+                    for (int mu = 0; mu < 3; ++mu) {
+                        const float sx = rtrig[r][mu], cx = rtrig[r][3 + mu];
+                        const float sd = sx * pt[3 + mu] - cx * pt[mu];
+                        const float cd = cx * pt[3 + mu] + sx * pt[mu];
+                        t += sd * sd;
+                        pv[mu] = ell * sd * cd;
+                        pp += pv[mu] * pv[mu];
+                        sq += cd * cd - sd * sd;
+                    }
+                    t *= ell * ell;
+                }
+                const float z = zs[g];
+                const float e = tc_ex2(-zs[8 + g] * t);
+                const float f1 = -z * e, f2 = z * z * e;
+#pragma unroll
+                for (int mu = 0; mu < 3; ++mu) v[mu][kk] = 2.f * f1 * pv[mu];
+                v[Q - 1][kk] = 4.f * f2 * pp + 2.f * f1 * sq;
+            }
+            const uint32_t off = tc::sw128_off(r, k0);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                unsigned char* tq = sA + (size_t)(P * q) * kTileA + off;
+                float4 x0, x1;
+                tc::split_tf32_fast(v[q][0], x0.x, x1.x);
+                tc::split_tf32_fast(v[q][1], x0.y, x1.y);
+                tc::split_tf32_fast(v[q][2], x0.z, x1.z);
+                tc::split_tf32_fast(v[q][3], x0.w, x1.w);
+                *(float4*)(tq) = x0;
+                *(float4*)(tq + kTileA) = x1;
+            }
+            // this warp's share of half h is in shared memory
+            tc::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&fullh[h]);
+        }
+    }
+    // all MMAs done (they complete in order) before TMEM and sA are read
+    if (!tc::mbar_wait(&mbarh[1], (uint32_t)((nch - 1) & 1), 1ll << 26)) ok = false;
+    tc::fence_after_sync();
+    __syncthreads();
+    } else {
     // B operand: the first P pieces of each prepared C^T chunk (16-byte
     // vectors).  Q = 4 (one CTA per SM): fetched into registers one chunk
     // ahead and stored once the previous chunk's MMAs are done.  Q = 1 (several
@@ -260,15 +404,16 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 512, Q == 1 ? 4 : 1)
                                      idesc, (c > 0 || ks > 0 || m > 6 - np) ? 1u : 0u);
                 }
             }
-            tc::mma_commit(&mbar);
+            tc::mma_commit(&mbarh[0]);
         }
         // the other lanes of the issuing warp wait here, not in the mbarrier
         // poll below, so they do not hold up the single issuing lane
         __syncwarp();
-        if (!tc::mbar_wait(&mbar, (uint32_t)(c & 1), 1ll << 26)) ok = false;
+        if (!tc::mbar_wait(&mbarh[0], (uint32_t)(c & 1), 1ll << 26)) ok = false;
         tc::fence_after_sync();
         if (Q == 4 && c + 1 < nch) store_b();   // the MMAs of chunk c have read sB
         __syncthreads();
+    }
     }
     if (!ok && lane == 0) raise_err(s.err, kErrTimeout);
 
@@ -311,13 +456,13 @@ void launch_orbitals_tc(const SysView<float>& s, const void* chat, const double*
     // kernel also holds static shared memory, so the opt-in maximum minus that)
     static size_t set4 = 0, set1 = 0;
     if (grad) {
-        const size_t smem = 1024 + (size_t)4 * kPiecesDer * kTileA + (size_t)kPiecesDer * NM * 128 + 24 * (size_t)s.N;
+        const size_t smem = 1024 + (size_t)4 * kPiecesDer * kTileA + (size_t)2 * kPiecesDer * NM * 128 + 24 * (size_t)s.N;
         if (smem > set4 &&
             cudaFuncSetAttribute(orbitals_tc_kernel<4, kPiecesDer>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) == cudaSuccess)
             set4 = smem;
         orbitals_tc_kernel<4, kPiecesDer>
-            <<<grid, 512, smem, st>>>(s, (const unsigned char*)chat, pos, nrows, NM, val, grad, lap);
+            <<<grid, 544, smem, st>>>(s, (const unsigned char*)chat, pos, nrows, NM, val, grad, lap);
     } else {
         const size_t smem = 1024 + (size_t)kPiecesVal * kTileA + (size_t)kPiecesVal * NM * 128 + 24 * (size_t)s.N;
         if (smem > set1 &&

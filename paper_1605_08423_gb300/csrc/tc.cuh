@@ -110,6 +110,11 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 // Make mbarrier initialisation visible to the async proxy (bulk copies).
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
 
+// Arrive once on `mbar` (plain arrival, no transaction bytes).
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_addr(mbar)) : "memory");
+}
+
 // Arrive once on `mbar` and add `bytes` to the transaction count its current
 // phase waits for.
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
