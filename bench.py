@@ -123,7 +123,7 @@ class ClockSampler:
 # dram__bytes_write.sum of one ncu capture at 2048 walkers, scaled by walkers:
 # traffic grows with the walker count); profiles/measure_kernel_h128_w2048_mixed.md.
 # None once the kernel has changed since that capture.
-MEASURE_DRAM_BYTES_PER_WALKER = (573.377792e6 + 78.720256e6) / 2048
+MEASURE_DRAM_BYTES_PER_WALKER = None   # kernel changed since the last capture
 
 MEASURE_UNIT = {"ee_jas": 55.0, "ep_jas": 55.0, "ee_ewald": 6.0 + 10.0 * 4.19, "ep": 130.0 + 6.0 + 19.0 * 4.19,
                 "sk": 14.0, "fk": 12.0}
@@ -144,8 +144,10 @@ def _flops_per_launch(cls: str, W, N, n, B, G, acc_ratio, use_tc, nk=462):
         return (8.0 if use_tc else 10.0) * W * N * B * n
     if cls == "measure":
         u = MEASURE_UNIT
+        # (the mixed form computes the reciprocal-space force, fk, as a GEMM
+        # over walkers timed with the adjoint class)
         pairs = (u["ee_jas"] * N * (N - 1) + u["ep_jas"] * N * N + u["ee_ewald"] * N * (N - 1) / 2
-                 + u["ep"] * N * N + (u["sk"] + u["fk"]) * N * nk + 8.0 * n * N + 8.0 * n ** 3)
+                 + u["ep"] * N * N + (u["sk"] + (0.0 if use_tc else u["fk"])) * N * nk + 8.0 * n * N + 8.0 * n ** 3)
         adj = 0.0 if use_tc else 8.0 * N * G * n * n   # Z = C G, P = C K in the SIMT measure kernel
         return W * (pairs + adj)
     if cls == "adjoint":         # Z = C G and P = C (G Y G) per spin block on the tensor cores

@@ -7,6 +7,8 @@
 #include <new>
 #include <vector>
 
+#include <cublas_v2.h>
+
 #include "../../include/qmcmd.h"
 #include "common.cuh"
 #include "kernels.cuh"
@@ -50,6 +52,10 @@ struct qmc_system {
     float *d_Kt = nullptr, *d_eg = nullptr;
     double* d_elw = nullptr;
     bool use_tc_adj = false;
+    // reciprocal-space force as one GEMM over walkers (split path):
+    // F[W][3N] = rho[W][2 nk] . T^T, T = [3N][2 nk] built per R
+    float *d_Trec = nullptr, *d_rk = nullptr, *d_frec = nullptr;
+    cublasHandle_t blas = nullptr;
     // walkers
     double *d_X = nullptr, *d_Xp = nullptr;
     void *d_uacc = nullptr, *d_Phi = nullptr, *d_Gt = nullptr, *d_D = nullptr, *d_Lp = nullptr;
@@ -138,6 +144,7 @@ size_t footprint(const qmc_params* p) {
     if (t == 4) {                                    // tensor-core operands (mixed form)
         b += tc_coeff_bytes((int)B, (int)n);
         b += tc_adjoint_coeff_bytes((int)n, (int)G) + 4 * (2 * W * n * n + 9 * W * N) + 8 * W;
+        b += 4 * (3 * N * 2 * nk + W * 2 * nk + W * 3 * N);   // reciprocal-force GEMM operands
     }
     return b;
 }
@@ -187,6 +194,10 @@ void setup_tables(qmc_system* h) {
     h->nlaunch += 5;
     launch_setup(h->N, h->p.L, h->p.ewald_kappa, h->nk, h->d_kvec, h->d_R, h->d_kw, h->d_ptrig64, h->d_ptrig32,
                  h->d_eikR, h->d_rhop, h->d_vconst, h->d_dvpp, h->d_R32, h->d_eikR32, h->d_kw32, h->stream);
+    if (h->d_Trec) {
+        h->nlaunch += 1;
+        launch_recforce_table(h->N, h->nk, h->p.L, h->d_kvec, h->d_kw, h->d_eikR, h->d_Trec, h->stream);
+    }
 }
 
 // Orbital rows at `pos`: tensor-core kernel in the mixed form, SIMT otherwise.
@@ -223,13 +234,20 @@ void measure(qmc_system* h, int W, double* el, double* lnpsi, double* dl, double
     prof_begin(h, KC_MEASURE, ep);
     launch_measure<T>(s, h->d_X, (const T*)h->d_D, (const T*)h->d_Lp, (const T*)h->d_Gt, h->d_logdet, h->d_acc, el,
                       lnpsi, dl, de, split ? h->d_Kt : nullptr, split ? h->d_eg : nullptr,
-                      split ? h->d_elw : nullptr, h->stream);
+                      split ? h->d_elw : nullptr, split ? h->d_rk : nullptr, h->stream);
     prof_end(h, ep);
     if (split) {
         h->nlaunch += 1;
         prof_begin(h, KC_ADJOINT, ep);
+        // reciprocal-space forces of all walkers: F = T . rho (column-major
+        // [3N x 2nk] . [2nk x W]); plain FP32 SGEMM (cuBLAS)
+        const int m3 = 3 * h->N, k2 = 2 * h->nk;
+        const float one = 1.f, zero = 0.f;
+        cublasSetStream(h->blas, h->stream);
+        cublasSgemm(h->blas, CUBLAS_OP_N, CUBLAS_OP_N, m3, W, k2, &one, h->d_Trec, m3, h->d_rk, k2, &zero, h->d_frec,
+                    m3);
         launch_adjoint_tc(*(const SysView<float>*)&s, h->d_ahat, (const float*)h->d_Gt, h->d_Kt, h->d_eg, h->d_elw,
-                          h->d_acc, dl, de, h->stream);
+                          h->d_frec, h->d_acc, dl, de, h->stream);
         prof_end(h, ep);
     }
 }
@@ -366,6 +384,11 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
             h->d_Kt = dalloc<float>(h, (size_t)W * 2 * n * n, &rc);
             h->d_eg = dalloc<float>(h, (size_t)W * N * 9, &rc);
             h->d_elw = dalloc<double>(h, W, &rc);
+            h->d_Trec = dalloc<float>(h, (size_t)3 * N * 2 * nk, &rc);
+            h->d_rk = dalloc<float>(h, (size_t)W * 2 * nk, &rc);
+            h->d_frec = dalloc<float>(h, (size_t)W * 3 * N, &rc);
+            if (rc == QMC_OK && cublasCreate(&h->blas) != CUBLAS_STATUS_SUCCESS) { h->blas = nullptr; rc = QMC_ERR_CUDA; }
+            if (h->blas) cublasSetMathMode(h->blas, CUBLAS_PEDANTIC_MATH);   // plain FP32 products
             h->use_tc_adj = true;
         }
     }
@@ -395,6 +418,7 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
 void qmc_destroy(qmc_system* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->blas) cublasDestroy(h->blas);
     for (void* a : h->allocs) cudaFree(a);
     for (auto& e : h->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (auto& e : h->free_events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }

@@ -125,7 +125,8 @@ struct BPrefetch {
 __global__ void __launch_bounds__(kThreads + 32, 1)
     adjoint_tc_kernel(SysView<float> s, const unsigned char* __restrict__ ahat, const float* __restrict__ Gt,
                       const float* __restrict__ Kt, const float* __restrict__ eg, const double* __restrict__ elw,
-                      double* __restrict__ acc, double* __restrict__ out_dl, double* __restrict__ out_de) {
+                      const float* __restrict__ frec, double* __restrict__ acc, double* __restrict__ out_dl,
+                      double* __restrict__ out_de) {
     extern __shared__ unsigned char smraw[];
     unsigned char* base = (unsigned char*)((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
     const int N = s.N, n = s.n, G = s.G, W = s.W;
@@ -443,6 +444,8 @@ __global__ void __launch_bounds__(kThreads + 32, 1)
                             l += stage[((size_t)q * 128 + tid) * 6 + mu];
                             e += stage[((size_t)q * 128 + tid) * 6 + 3 + mu];
                         }
+                        // plus the reciprocal-space force of this sample (GEMM over walkers)
+                        if (frec) e += frec[(size_t)w * N3 + 3 * tid + mu];
                         if (!isfinite(l) || !isfinite(e)) bad = true;
                         dl[mu] = (double)l;
                         de[mu] = (double)e;
@@ -473,7 +476,8 @@ __global__ void __launch_bounds__(kThreads + 32, 1)
 }
 
 void launch_adjoint_tc(const SysView<float>& s, const void* ahat, const float* Gt, const float* Kt, const float* eg,
-                       const double* elw, double* acc, double* out_dl, double* out_de, cudaStream_t st) {
+                       const double* elw, const float* frec, double* acc, double* out_dl, double* out_de,
+                       cudaStream_t st) {
     static int sms[64] = {0};
     static size_t set_smem = 0;
     int dev = 0;
@@ -485,7 +489,8 @@ void launch_adjoint_tc(const SysView<float>& s, const void* ahat, const float* G
         cudaFuncSetAttribute(adjoint_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess)
         set_smem = smem;
     const int grid = s.W < sms[dev] ? s.W : sms[dev];
-    adjoint_tc_kernel<<<grid, kThreads + 32, smem, st>>>(s, (const unsigned char*)ahat, Gt, Kt, eg, elw, acc, out_dl, out_de);
+    adjoint_tc_kernel<<<grid, kThreads + 32, smem, st>>>(s, (const unsigned char*)ahat, Gt, Kt, eg, elw, frec, acc, out_dl,
+                                                         out_de);
 }
 
 }  // namespace qmc

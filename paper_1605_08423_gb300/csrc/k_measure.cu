@@ -157,7 +157,9 @@ __device__ __forceinline__ void ep_pair(const S sd[3], const S cd[3], S ell, S k
 // kSplit: the B x n orbital contractions and their basis-derivative epilogue
 // are left to the tensor-core adjoint kernel; this kernel then writes what
 // that kernel needs: K^T per spin block (kt_out), the electrons' (sin, cos)
-// and grad U (eg_out, 9 per electron) and E_L of the sample (elw).
+// and grad U (eg_out, 9 per electron) and E_L of the sample (elw); the
+// reciprocal-space force, a fixed [3N][2 nk] matrix times rho(k), is left to a
+// GEMM over all walkers, so the structure factor goes out too (rk_out).
 template <typename T, bool kSplit>
 __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T> s, int mmax, const double* __restrict__ X,
                                                       const T* __restrict__ D, const T* __restrict__ Lp,
@@ -165,7 +167,8 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
                                                       double* __restrict__ acc, double* __restrict__ out_el,
                                                       double* __restrict__ out_lnpsi, double* __restrict__ out_dl,
                                                       double* __restrict__ out_de, float* __restrict__ kt_out,
-                                                      float* __restrict__ eg_out, double* __restrict__ elw) {
+                                                      float* __restrict__ eg_out, double* __restrict__ elw,
+                                                      float* __restrict__ rk_out) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int N = s.N, n = s.n, G = s.G, nk = s.nk;
     const MLayout<T> lay(N, n, nk, mmax, kSplit);
@@ -513,12 +516,17 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
         const double2 rp = s.rho_p[k];
         const T rr = (T)rp.x - re, ri = (T)rp.y - im;   // electrons carry -1
         rhot[k] = V2<T>{rr, ri};
+        if constexpr (kSplit) {
+            rk_out[(size_t)w * 2 * nk + 2 * k] = (float)rr;
+            rk_out[(size_t)w * 2 * nk + 2 * k + 1] = (float)ri;
+        }
         vrec_t += s.kwt[k] * (rr * rr + ri * ri);
     }
     vrec_p += (double)vrec_t;
     __syncthreads();
-    // ---- P4d: reciprocal-space force on the protons (warp per proton)
-    for (int a = warp; a < N; a += nw) {
+    // ---- P4d: reciprocal-space force on the protons (warp per proton; the
+    // split path leaves it to the GEMM)
+    for (int a = warp; a < (kSplit ? 0 : N); a += nw) {
         T gx = 0, gy = 0, gz = 0;
 #pragma unroll 4
         for (int k = lane; k < nk; k += 32) {
@@ -825,7 +833,7 @@ size_t measure_smem_bytes(int N, int n, int nk, int mmax, bool split) {
 template <typename T>
 void launch_measure(const SysView<T>& s, const double* X, const T* D, const T* Lp, const T* Gt, const double* logdet,
                     double* acc, double* out_el, double* out_lnpsi, double* out_dl, double* out_de, float* kt_out,
-                    float* eg_out, double* elw, cudaStream_t st) {
+                    float* eg_out, double* elw, float* rk_out, cudaStream_t st) {
     const bool split = sizeof(T) == 4 && kt_out != nullptr;
     const size_t smem = measure_smem_bytes<T>(s.N, s.n, s.nk, s.mmax, split);
     static bool attr_set[3] = {false, false, false};
@@ -838,7 +846,7 @@ void launch_measure(const SysView<T>& s, const double* X, const T* D, const T* L
                 attr_set[which] = true;
             }
             measure_kernel<T, true><<<s.W, 256, smem, st>>>(s, s.mmax, X, D, Lp, Gt, logdet, acc, out_el, out_lnpsi,
-                                                            out_dl, out_de, kt_out, eg_out, elw);
+                                                            out_dl, out_de, kt_out, eg_out, elw, rk_out);
             return;
         }
     }
@@ -848,7 +856,7 @@ void launch_measure(const SysView<T>& s, const double* X, const T* D, const T* L
             attr_set[which] = true;
         }
         measure_kernel<T, false><<<s.W, 256, smem, st>>>(s, s.mmax, X, D, Lp, Gt, logdet, acc, out_el, out_lnpsi,
-                                                         out_dl, out_de, nullptr, nullptr, nullptr);
+                                                         out_dl, out_de, nullptr, nullptr, nullptr, nullptr);
     }
 }
 
@@ -856,9 +864,9 @@ template size_t measure_smem_bytes<double>(int, int, int, int, bool);
 template size_t measure_smem_bytes<float>(int, int, int, int, bool);
 template void launch_measure<double>(const SysView<double>&, const double*, const double*, const double*,
                                      const double*, const double*, double*, double*, double*, double*, double*,
-                                     float*, float*, double*, cudaStream_t);
+                                     float*, float*, double*, float*, cudaStream_t);
 template void launch_measure<float>(const SysView<float>&, const double*, const float*, const float*, const float*,
                                     const double*, double*, double*, double*, double*, double*, float*, float*,
-                                    double*, cudaStream_t);
+                                    double*, float*, cudaStream_t);
 
 }  // namespace qmc

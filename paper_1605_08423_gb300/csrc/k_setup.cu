@@ -74,6 +74,28 @@ __global__ void kw_kernel(int nk, double L, double kappa, const int4* __restrict
     kw32[k] = (float)kw[k];
 }
 
+// Reciprocal-space force on the nuclei as a matrix acting on the electron
+// structure factor of a sample: with rho(k) = rho_p(k) - rho_e(k) = (rr, ri),
+//   F_{a,mu} = sum_k 2 Z w_k (2 pi m_mu / L) [ri cos(k.R_a) - rr sin(k.R_a)],
+// T is [3N][2 nk] column-major (column 2k multiplies rr(k), 2k + 1 ri(k)).
+__global__ void recforce_table_kernel(int N, int nk, double L, const int4* __restrict__ kvec,
+                                      const double* __restrict__ kw, const double2* __restrict__ eikR, float* T) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * N * nk) return;
+    const int k = t / (3 * N), c = t - k * 3 * N, a = c / 3, mu = c - 3 * a;
+    const int4 m = kvec[k];
+    const double mm = mu == 0 ? m.x : (mu == 1 ? m.y : m.z);
+    const double f = 2.0 * kw[k] * (2.0 * kPi / L) * mm;   // proton charge 1
+    const double2 e = eikR[(size_t)a * nk + k];
+    T[(size_t)(2 * k) * 3 * N + c] = (float)(-f * e.y);
+    T[(size_t)(2 * k + 1) * 3 * N + c] = (float)(f * e.x);
+}
+
+void launch_recforce_table(int N, int nk, double L, const int4* kvec, const double* kw, const double2* eikR, float* T,
+                           cudaStream_t st) {
+    recforce_table_kernel<<<(3 * N * nk + 255) / 256, 256, 0, st>>>(N, nk, L, kvec, kw, eikR, T);
+}
+
 void launch_setup(int N, double L, double kappa, int nk, const int4* kvec, const double* R, double* kw,
                   double* ptrig64, float* ptrig32, double2* eikR, double2* rho_p, double* vconst, double* dvpp,
                   float* R32, float2* eikR32, float* kw32, cudaStream_t st) {

@@ -25,7 +25,8 @@ bool tc_adjoint_supported(int N, int n, int G);
 size_t tc_adjoint_coeff_bytes(int n, int G);
 void prepare_tc_adjoint_coeff(const float* C, int N, int G, int n, void* ahat, cudaStream_t st);
 void launch_adjoint_tc(const SysView<float>& s, const void* ahat, const float* Gt, const float* Kt, const float* eg,
-                       const double* elw, double* acc, double* out_dl, double* out_de, cudaStream_t st);
+                       const double* elw, const float* frec, double* acc, double* out_dl, double* out_de,
+                       cudaStream_t st);
 
 // k_invert.cu: FP64 Gauss-Jordan inverse of each walker's two Slater blocks.
 template <typename T>
@@ -40,7 +41,7 @@ void launch_sweep(const SysView<T>& s, double* X, const double* Xp, const T* ptp
 template <typename T>
 void launch_measure(const SysView<T>& s, const double* X, const T* D, const T* Lp, const T* Gt,
                     const double* logdet, double* acc, double* out_el, double* out_lnpsi, double* out_dl,
-                    double* out_de, float* kt_out, float* eg_out, double* elw, cudaStream_t st);
+                    double* out_de, float* kt_out, float* eg_out, double* elw, float* rk_out, cudaStream_t st);
 template <typename T>
 size_t measure_smem_bytes(int N, int n, int nk, int mmax, bool split);
 
@@ -48,6 +49,10 @@ size_t measure_smem_bytes(int N, int n, int nk, int mmax, bool split);
 void launch_setup(int N, double L, double kappa, int nk, const int4* kvec, const double* R, double* kw,
                   double* ptrig64, float* ptrig32, double2* eikR, double2* rho_p, double* vconst, double* dvpp,
                   float* R32, float2* eikR32, float* kw32, cudaStream_t st);
+
+// k_setup.cu: the reciprocal-space force as a [3N][2 nk] matrix on rho(k) (split measure path).
+void launch_recforce_table(int N, int nk, double L, const int4* kvec, const double* kw, const double2* eikR, float* T,
+                           cudaStream_t st);
 
 // k_reduce.cu: walker reductions and the covariance matrix.
 void launch_reduce(int W, int N, double moves, const double* acc, const unsigned long long* nacc,
