@@ -198,9 +198,174 @@ __global__ void __launch_bounds__(512) sweep_kernel(SysView<T> s, double* __rest
     if (lane == 0) nacc[w] += naccept;
 }
 
+
+// Mixed form, n <= 64: two warps per walker and the inverse in registers.
+// Thread tw (0..63) of a walker owns row tw of the staged inverse (G^T row,
+// zero-padded to 64 columns), so a move touches no shared-memory copy of G:
+//   w_l = sum_j phi'_j G^T[l][j] for every row (the ratio is w_il),
+//   on acceptance the owner of row il puts it in shared memory and every
+//   thread applies G^T[l] -= (w_l - delta_{l,il}) / R * G^T[il].
+// The Jastrow difference is split over the 64 threads (two e-e and two e-n
+// partners each).  The two warps of a walker meet at a named barrier (one
+// per walker of the CTA).  Same proposals, uniforms and acceptance rule as
+// sweep_kernel; the mixed form keeps accepted proposals unwrapped.
+constexpr int kSwWalkers = 4;   // walkers per CTA (8 warps)
+constexpr int kSwRow = 64;      // register row length (n <= 64)
+
+__global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<float> s, double* __restrict__ X,
+                                                                  const double* __restrict__ Xp,
+                                                                  const float* __restrict__ ptp,
+                                                                  const float* __restrict__ uacc,
+                                                                  const float* __restrict__ Phi,
+                                                                  float* __restrict__ Gt,
+                                                                  unsigned long long* __restrict__ nacc) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = s.N, n = s.n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int p = warp >> 1, h = warp & 1, tw = tid & 63;
+    float* ptr_s = (float*)smraw;                                       // [N][6] proton trig
+    float* mine = ptr_s + ((6 * N + 3) & ~3) + (size_t)p * (2 * kSwRow + 6 * N + 8);
+    float* phi = mine;                  // [64] orbital row at the proposal (zero beyond n)
+    float* rowb = phi + kSwRow;         // [64] row il of G^T on acceptance
+    float* red = rowb + kSwRow;         // [8] du halves, ratio
+    float* et = red + 8;                // [N][6] (sin, cos)(pi x / L) of the current positions
+    for (int idx = tid; idx < 6 * N; idx += blockDim.x) ptr_s[idx] = s.ptrig[idx];
+    __syncthreads();
+    const int w = blockIdx.x * kSwWalkers + p;
+    if (w >= s.W) return;              // whole walkers only: both of its warps leave
+    auto bar = [&]() { asm volatile("bar.sync %0, 64;\n" ::"r"(1 + p) : "memory"); };
+
+    const float ell = (float)s.ell, bee = (float)s.b_ee, bep = (float)s.b_ep, Zj = (float)s.Zj;
+    const double iL = 1.0 / s.L;
+    double* Xw = X + (size_t)w * 3 * N;
+    for (int idx = tw; idx < 3 * N; idx += 64) {
+        const int i = idx / 3, mu = idx % 3;
+        float sn, cs;
+        sincospif((float)(Xw[idx] * iL), &sn, &cs);
+        et[6 * i + mu] = sn;
+        et[6 * i + 3 + mu] = cs;
+    }
+    float pt_nx[6], ph_nx, u_nx;
+    auto fetch = [&](int i) {
+        const size_t row = (size_t)w * N + i;
+#pragma unroll
+        for (int mu = 0; mu < 6; ++mu) pt_nx[mu] = ptp[row * 6 + mu];
+        ph_nx = tw < n ? Phi[row * n + tw] : 0.f;
+        u_nx = uacc[row];
+    };
+    fetch(0);
+    unsigned long long naccept = 0;
+    const bool vec4 = (n & 3) == 0;
+    for (int sp = 0; sp < 2; ++sp) {
+        float* G = Gt + ((size_t)w * 2 + sp) * n * n;
+        float g[kSwRow];
+#pragma unroll
+        for (int jv = 0; jv < kSwRow / 4; ++jv) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int j = 4 * jv;
+            if (tw < n && j < n) {
+                if (vec4) {
+                    v = *(const float4*)(G + (size_t)tw * n + j);
+                } else {
+                    v.x = G[(size_t)tw * n + j];
+                    if (j + 1 < n) v.y = G[(size_t)tw * n + j + 1];
+                    if (j + 2 < n) v.z = G[(size_t)tw * n + j + 2];
+                    if (j + 3 < n) v.w = G[(size_t)tw * n + j + 3];
+                }
+            }
+            g[j] = v.x; g[j + 1] = v.y; g[j + 2] = v.z; g[j + 3] = v.w;
+        }
+        for (int il = 0; il < n; ++il) {
+            const int i = sp * n + il;
+            const size_t row = (size_t)w * N + i;
+            float pt[6];
+#pragma unroll
+            for (int mu = 0; mu < 6; ++mu) pt[mu] = pt_nx[mu];
+            phi[tw] = ph_nx;
+            const float u = u_nx;
+            if (i + 1 < N) fetch(i + 1);
+            bar();   // phi and the previous move's position updates are visible
+            // w_l for this thread's row: four partial sums
+            const float4* phv = (const float4*)phi;
+            float a4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int jv = 0; jv < kSwRow / 4; ++jv) {
+                const float4 ph = phv[jv];
+                a4[0] += ph.x * g[4 * jv]; a4[1] += ph.y * g[4 * jv + 1];
+                a4[2] += ph.z * g[4 * jv + 2]; a4[3] += ph.w * g[4 * jv + 3];
+            }
+            const float wl = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+            // Jastrow difference: partners tw and tw + 64
+            float du = 0.f;
+            const float* ei = et + 6 * i;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int j = tw + 64 * k;
+                if (j < N) {
+                    const float* ej = et + 6 * j;
+                    float u1, u0, d1, d2;
+                    pade_ee(bee, pair_dist(pt, ej, ell), u1, d1, d2);
+                    pade_ee(bee, pair_dist(ei, ej, ell), u0, d1, d2);
+                    du += (j != i) ? u1 - u0 : 0.f;
+                    const float* pa = ptr_s + 6 * j;
+                    float d3;
+                    pade_ep(bep, Zj, pair_dist(pt, pa, ell), u1, d1, d2, d3);
+                    pade_ep(bep, Zj, pair_dist(ei, pa, ell), u0, d1, d2, d3);
+                    du += u1 - u0;
+                }
+            }
+            du = warp_sum(du);
+            if (lane == 0) red[h] = du;
+            if (tw == il) red[2] = wl;
+            bar();
+            const float ratio = red[2];
+            const float dut = red[0] + red[1];
+            const float prob = ratio * ratio * expf(2.f * dut);
+            if (u < prob) {
+                if (tw == il) {
+#pragma unroll
+                    for (int jv = 0; jv < kSwRow / 4; ++jv)
+                        ((float4*)rowb)[jv] = make_float4(g[4 * jv], g[4 * jv + 1], g[4 * jv + 2], g[4 * jv + 3]);
+                }
+                bar();
+                const float coef = (wl - (tw == il ? 1.f : 0.f)) * __fdividef(1.f, ratio);
+                const float4* rbv = (const float4*)rowb;
+#pragma unroll
+                for (int jv = 0; jv < kSwRow / 4; ++jv) {
+                    const float4 rb = rbv[jv];
+                    g[4 * jv] -= coef * rb.x; g[4 * jv + 1] -= coef * rb.y;
+                    g[4 * jv + 2] -= coef * rb.z; g[4 * jv + 3] -= coef * rb.w;
+                }
+                if (tw < 3) {   // keep the proposal as is (periodic functions; the next proposal pass wraps)
+                    Xw[3 * i + tw] = Xp[row * 3 + tw];
+                    et[6 * i + tw] = tw == 0 ? pt[0] : (tw == 1 ? pt[1] : pt[2]);
+                    et[6 * i + 3 + tw] = tw == 0 ? pt[3] : (tw == 1 ? pt[4] : pt[5]);
+                }
+                ++naccept;
+            }
+        }
+        if (tw < n) {
+#pragma unroll
+            for (int j = 0; j < kSwRow; ++j)
+                if (j < n) G[(size_t)tw * n + j] = g[j];
+        }
+        bar();
+    }
+    if (tw == 0) nacc[w] += naccept;
+}
+
 template <typename T>
 void launch_sweep(const SysView<T>& s, double* X, const double* Xp, const T* ptp, const T* uacc, const T* Phi, T* Gt,
                   unsigned long long* nacc, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (s.n <= kSwRow) {   // mixed form: inverse rows in registers
+            const size_t smem = sizeof(float) * (((6 * s.N + 3) & ~3) + kSwWalkers * (2 * kSwRow + 6 * s.N + 8));
+            sweep_reg_kernel<<<(s.W + kSwWalkers - 1) / kSwWalkers, 64 * kSwWalkers, smem, st>>>(
+                *(const SysView<float>*)&s, X, Xp, (const float*)ptp, (const float*)uacc, (const float*)Phi,
+                (float*)Gt, nacc);
+            return;
+        }
+    }
     const size_t wb = SweepSmem<T>::warp_bytes(s.N, s.n);
     const size_t head = ((size_t)6 * s.N * sizeof(T) + 15) & ~size_t(15);
     // as many walkers per CTA as the shared memory of one SM holds (one CTA per SM)
