@@ -222,6 +222,24 @@ void recompute(qmc_system* h, int W) {
     prof_end(h, ep);
 }
 
+// Periodic recompute inside a call.  Mixed form: Slater blocks at the current
+// positions and one FP32 Newton-Schulz step on the carried inverse (FP64
+// Gauss-Jordan for blocks too far off); FP64 form: the full FP64 recompute.
+template <typename T>
+void recompute_in_call(qmc_system* h, int W) {
+    if constexpr (sizeof(T) == 4) {
+        EventPair ep;
+        prof_begin(h, KC_RECOMPUTE, ep);
+        SysView<T> s = view<T>(h, W);
+        h->nlaunch += 2;
+        orbitals<T>(h, s, h->d_X, W * h->N, (T*)h->d_Phi, nullptr, nullptr);
+        launch_refine(W, h->N, h->n, (const float*)h->d_Phi, (float*)h->d_Gt, h->d_logdet, h->d_err, h->stream);
+        prof_end(h, ep);
+    } else {
+        recompute<T>(h, W);
+    }
+}
+
 template <typename T>
 void measure(qmc_system* h, int W, double* el, double* lnpsi, double* dl, double* de) {
     SysView<T> s = view<T>(h, W);
@@ -277,7 +295,7 @@ void run_call(qmc_system* h) {
         launch_sweep<T>(s, h->d_X, h->d_Xp, (const T*)h->d_ptp, (const T*)h->d_uacc, (const T*)h->d_Phi,
                         (T*)h->d_Gt, h->d_nacc, h->stream);
         prof_end(h, ep);
-        if ((sw + 1) % h->p.recompute_every == 0) recompute<T>(h, W);
+        if ((sw + 1) % h->p.recompute_every == 0) recompute_in_call<T>(h, W);
         if (sw >= nw && ((sw - nw + 1) % h->p.measure_every) == 0) measure<T>(h, W, nullptr, nullptr, nullptr, nullptr);
     }
     EventPair ep;

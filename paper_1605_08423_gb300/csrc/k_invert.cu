@@ -11,10 +11,11 @@
 
 namespace qmc {
 
+// Gauss-Jordan inverse of walker w's spin block sp by the whole CTA, in the
+// FP64 work space sm (n (n + 1) + n doubles and n ints).
 template <typename T>
-__global__ void __launch_bounds__(256) invert_kernel(int N, int n, const T* __restrict__ Phi, T* __restrict__ Gt,
-                                                     double* __restrict__ logdet, int* err) {
-    extern __shared__ double sm[];
+__device__ void gj_invert(int N, int n, const T* __restrict__ Phi, T* __restrict__ Gt, double* __restrict__ logdet,
+                          int* err, int w, int sp, double* sm) {
     const int ld = n + 1;
     double* M = sm;                      // [n][n+1]
     double* col = M + (size_t)n * ld;    // [n]
@@ -23,7 +24,6 @@ __global__ void __launch_bounds__(256) invert_kernel(int N, int n, const T* __re
     __shared__ int singular;
     __shared__ double ipv_s;
     __shared__ int sgn;
-    const int w = blockIdx.x >> 1, sp = blockIdx.x & 1;
     const int tid = threadIdx.x, nt = blockDim.x;
     const T* A = Phi + ((size_t)w * N + (size_t)sp * n) * n;
     for (int idx = tid; idx < n * n; idx += nt) M[(idx / n) * ld + idx % n] = (double)A[idx];
@@ -122,6 +122,120 @@ __global__ void __launch_bounds__(256) invert_kernel(int N, int n, const T* __re
         out[idx] = (T)M[j * ld + i];
     }
     if (tid == 0) logdet[2 * w + sp] = log(mant) + expo * 0.69314718055994530942;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) invert_kernel(int N, int n, const T* __restrict__ Phi, T* __restrict__ Gt,
+                                                     double* __restrict__ logdet, int* err) {
+    extern __shared__ double sm[];
+    gj_invert<T>(N, n, Phi, Gt, logdet, err, blockIdx.x >> 1, blockIdx.x & 1, sm);
+}
+
+// Mixed form, periodic recompute inside a call: one Newton-Schulz step
+//   R = I - A G,  G <- G + G R   (FP32, error O(|R|^2))
+// on the inverse the Sherman-Morrison updates have carried since the last
+// recompute; A = the Slater block just evaluated at the current positions.
+// The rank-1 updates leave |R| near FP32 rounding, so one step restores the
+// inverse to FP32 accuracy at the cost of two n^3 FP32 products (the FP64
+// Gauss-Jordan runs at 1/64 of that rate on this part).  If max |R_ij| >= 0.01
+// (or is not finite) the block is inverted from scratch by Gauss-Jordan in
+// FP64 instead.  ln|det| is not updated here (nothing in a call reads it
+// after the first recompute, which is always Gauss-Jordan).
+__global__ void __launch_bounds__(256) refine_kernel(int N, int n, int np, const float* __restrict__ Phi,
+                                                     float* __restrict__ Gt, double* __restrict__ logdet, int* err) {
+    extern __shared__ double sm[];
+    const int ld = np + 4, ng = np / 4;
+    float* AT = (float*)sm;                  // A^T [j][i]; later G'^T
+    float* Gm = AT + (size_t)np * ld;        // G [j][k] = Gt[k][j]
+    float* R = Gm + (size_t)np * ld;         // R [i][k]
+    __shared__ float rmax_s[8];
+    const int w = blockIdx.x >> 1, sp = blockIdx.x & 1;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const float* A = Phi + ((size_t)w * N + (size_t)sp * n) * n;
+    float* Go = Gt + ((size_t)w * 2 + sp) * n * n;
+    for (int idx = tid; idx < np * np; idx += nt) {
+        const int i = idx / np, j = idx - i * np;
+        const bool in = i < n && j < n;
+        AT[j * ld + i] = in ? A[i * n + j] : 0.f;
+        Gm[j * ld + i] = in ? Go[i * n + j] : 0.f;
+    }
+    __syncthreads();
+    const int r0 = 4 * (tid / ng), c0 = 4 * (tid % ng);
+    const bool act = tid < ng * ng;
+    float acc[4][4] = {};
+    float rm = 0.f;
+    if (act) {                               // (A G)[i][k] = sum_j A[i][j] G[j][k]
+        for (int j = 0; j < np; ++j) {
+            const float4 a4 = *(const float4*)(AT + j * ld + r0), g4 = *(const float4*)(Gm + j * ld + c0);
+            const float av[4] = {a4.x, a4.y, a4.z, a4.w}, gv[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * gv[b];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int i = r0 + a, k = c0 + b;
+                const float r = (i < n && k < n) ? (i == k ? 1.f : 0.f) - acc[a][b] : 0.f;
+                R[i * ld + k] = r;
+                rm = fmaxf(rm, isfinite(r) ? fabsf(r) : 1e30f);
+            }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rm = fmaxf(rm, __shfl_xor_sync(0xffffffffu, rm, o));
+    if (lane == 0) rmax_s[warp] = rm;
+    __syncthreads();
+    float rmax = 0.f;
+    for (int q = 0; q < nt / 32; ++q) rmax = fmaxf(rmax, rmax_s[q]);
+    if (!(rmax < 0.01f)) {                   // too far off: FP64 Gauss-Jordan from scratch
+        __syncthreads();
+        gj_invert<float>(N, n, Phi, Gt, logdet, err, w, sp, sm);
+        return;
+    }
+    if (act) {                               // G'[j][k] = G[j][k] + sum_i G[j][i] R[i][k]
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = Gm[(r0 + a) * ld + c0 + b];
+        for (int i = 0; i < np; ++i) {
+            const float4 r4 = *(const float4*)(R + i * ld + c0);
+            const float rv[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float gji = Gm[(r0 + a) * ld + i];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] += gji * rv[b];
+            }
+        }
+    }
+    __syncthreads();                         // every read of A^T done: it takes G'^T
+    if (act)
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) AT[(c0 + b) * ld + r0 + a] = acc[a][b];
+    __syncthreads();
+    for (int idx = tid; idx < n * n; idx += nt) {
+        const int k = idx / n, j = idx - k * n;     // Gt[k][j] = G'[j][k]
+        Go[idx] = AT[k * ld + j];
+    }
+}
+
+void launch_refine(int W, int N, int n, const float* Phi, float* Gt, double* logdet, int* err, cudaStream_t st) {
+    int np = 4;
+    while (np < n) np *= 2;
+    const size_t gj = (size_t)n * (n + 1) * sizeof(double) + n * sizeof(double) + n * sizeof(int);
+    const size_t ns = (size_t)3 * np * (np + 4) * sizeof(float);
+    const size_t smem = gj > ns ? gj : ns;
+    // raise the dynamic shared-memory limit to what this launch needs (the
+    // kernel also holds static shared memory, so not to the opt-in maximum)
+    static size_t attr = 0;
+    if (smem > attr &&
+        cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess)
+        attr = smem;
+    refine_kernel<<<2 * W, 256, smem, st>>>(N, n, np, Phi, Gt, logdet, err);
 }
 
 template <typename T>

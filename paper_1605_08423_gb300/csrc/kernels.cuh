@@ -32,6 +32,10 @@ void launch_adjoint_tc(const SysView<float>& s, const void* ahat, const float* G
 template <typename T>
 void launch_invert(int W, int N, int n, const T* Phi, T* Gt, double* logdet, int* err, cudaStream_t st);
 
+// k_invert.cu: mixed-form periodic recompute (one Newton-Schulz step, FP64
+// Gauss-Jordan where the carried inverse is too far off).
+void launch_refine(int W, int N, int n, const float* Phi, float* Gt, double* logdet, int* err, cudaStream_t st);
+
 // k_sweep.cu: one Metropolis sweep per walker (warp per walker).
 template <typename T>
 void launch_sweep(const SysView<T>& s, double* X, const double* Xp, const T* ptp, const T* uacc, const T* Phi, T* Gt,
