@@ -53,6 +53,15 @@ class ChainArgs(C.Structure):
     ]
 
 
+class ToyArgs(C.Structure):
+    _fields_ = [
+        ("k", C.c_double), ("a", C.c_double), ("T", C.c_double), ("delta", C.c_double),
+        ("lam", C.c_double), ("mu", C.c_double), ("alpha", C.c_double),
+        ("scheme", C.c_int32), ("s_mode", C.c_int32), ("n_steps", C.c_int32), ("n_burn", C.c_int32),
+        ("seed", C.c_uint64),
+    ]
+
+
 _dp = C.POINTER(C.c_double)
 
 
@@ -78,9 +87,14 @@ def lib():
         L.orc_reduce.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
         L.orc_langevin.restype = C.c_int
         L.orc_langevin.argtypes = [C.c_int, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
-                                   C.c_double, _dp, C.c_int, C.c_double, _dp]
+                                   C.c_double, _dp, C.c_int, C.c_double, C.c_int, _dp]
         L.orc_langevin_noise.argtypes = [C.c_uint64, C.c_uint32, C.c_int, _dp]
         L.orc_num_threads.restype = C.c_int
+        L.orc_toy_eval.argtypes = [C.POINTER(ToyArgs), C.c_double, C.c_double, _dp]
+        L.orc_toy_step.restype = C.c_int
+        L.orc_toy_step.argtypes = [C.POINTER(ToyArgs), _dp, _dp, _dp, _dp]
+        L.orc_toy_run.argtypes = [C.POINTER(ToyArgs), C.c_int, _dp, _dp]
+        L.orc_toy_noise.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, _dp]
         _lib = L
     return _lib
 
@@ -203,13 +217,16 @@ def reduce(acc, N):
     return dict(E=E.value, E_err=Ee.value, f=f, S=S, Nc=Nc.value)
 
 
-def langevin(R, Rprev, f, S, Sprev, T, delta, alpha, xi, noise_correction=False, box=0.0):
+LV_ADOPTED, LV_FAST, LV_NOROGNA = 0, 1, 2
+
+
+def langevin(R, Rprev, f, S, Sprev, T, delta, alpha, xi, noise_correction=False, box=0.0, scheme=LV_ADOPTED):
     R = np.ascontiguousarray(R, dtype=np.float64).ravel()
     n = R.size
     arr = [np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (Rprev, f, S, Sprev, xi)]
     out = np.zeros(n)
     rc = lib().orc_langevin(n, _ptr(R), _ptr(arr[0]), _ptr(arr[1]), _ptr(arr[2]), _ptr(arr[3]), T, delta,
-                            alpha, _ptr(arr[4]), int(noise_correction), box, _ptr(out))
+                            alpha, _ptr(arr[4]), int(noise_correction), box, int(scheme), _ptr(out))
     if rc != 0:
         raise ValueError("S is not positive definite")
     return out
@@ -223,3 +240,47 @@ def langevin_noise(seed, md_step, n):
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+# ---- rotating-spring toy model (SI, "A simple toy model") ----
+TOY_PLAIN, TOY_STANDARD, TOY_FIRST, TOY_FAST, TOY_ADOPTED, TOY_NOROGNA = range(6)
+TOY_S_G, TOY_S_HG = 0, 1
+TOY_SCHEMES = {"plain": TOY_PLAIN, "standard": TOY_STANDARD, "first": TOY_FIRST, "fast": TOY_FAST,
+               "adopted": TOY_ADOPTED, "norogna": TOY_NOROGNA}
+
+
+def toy_args(scheme=TOY_ADOPTED, s_mode=TOY_S_G, *, k=2.0, a=1.4, T=0.01, delta=0.05, lam=0.1, mu=0.5,
+             alpha=0.2, n_steps=1000, n_burn=0, seed=1) -> ToyArgs:
+    """Toy-model parameters; defaults are the SI's figure (k = 2, a = 1.4, T = 0.01,
+    mu = 1/2, alpha = 0.2) with the printed G_lambda at lambda = 1/10."""
+    return ToyArgs(k, a, T, delta, lam, mu, alpha, scheme, s_mode, n_steps, n_burn, seed)
+
+
+def toy_eval(args: ToyArgs, x: float, y: float) -> dict:
+    o = np.zeros(17)
+    lib().orc_toy_eval(C.byref(args), x, y, _ptr(o))
+    return dict(U=o[0], f=o[1:3].copy(), S=o[3:7].reshape(2, 2).copy(), Sinv=o[7:11].reshape(2, 2).copy(),
+                H=o[11:15].reshape(2, 2).copy(), Gamma=o[15:17].copy())
+
+
+def toy_step(args: ToyArgs, R, Rp, xi) -> np.ndarray:
+    R, Rp, xi = (np.ascontiguousarray(v, dtype=np.float64) for v in (R, Rp, xi))
+    out = np.zeros(2)
+    if lib().orc_toy_step(C.byref(args), _ptr(R), _ptr(Rp), _ptr(xi), _ptr(out)) != 0:
+        raise ValueError("S is not positive definite")
+    return out
+
+
+def toy_run(args: ToyArgs, xy0) -> np.ndarray:
+    """Trajectories from xy0 [n][2]; returns [n][7] = x, y, sum U, sum U^2, sum |R|,
+    angle travelled, status (sums over the positions after steps n_burn..n_steps-1)."""
+    xy0 = np.ascontiguousarray(xy0, dtype=np.float64).reshape(-1, 2)
+    out = np.zeros((xy0.shape[0], 7))
+    lib().orc_toy_run(C.byref(args), xy0.shape[0], _ptr(xy0), _ptr(out))
+    return out
+
+
+def toy_noise(seed, traj, step) -> np.ndarray:
+    xi = np.zeros(2)
+    lib().orc_toy_noise(seed, traj, step, _ptr(xi))
+    return xi

@@ -24,7 +24,12 @@
 //   vmc chain ............ importance-sampled brute-force integral on a tiny system
 //   reduce ............... i.i.d. synthetic samples with known covariance
 //   langevin_step ........ harmonic closed forms (steepest descent, Newton step,
-//                          stationary covariance, autocorrelation)
+//                          stationary covariance, autocorrelation); fast and
+//                          simple-rule variants against their closed forms
+//   toy model ............ finite differences of U, H, S^{-1}; the S-difference
+//                          corrections against the cumbersome term (Gauss-Hermite
+//                          averages); stationary <U> against quadratures of the
+//                          canonical density and of the simple rule's density
 //   "parity unpinned": the statistical quality of the random-coefficient
 //   wavefunction itself (nothing in the paper fixes it).
 
@@ -662,12 +667,20 @@ static void reduce(int W, int N3, const double* acc, double* E, double* Eerr, do
 //   <z z^T> = S^{-1},  Dt = (1-e^{-a D})/a,  Db = (1-e^{-2 a D})/(2a)  (Dt = Db = D at a = 0).
 // z = L^{-T} xi with S = L L^T (Cholesky) and xi ~ N(0, I).  Optional noise
 // correction (SI "Noise correction"): T -> T - D/2.  box > 0 wraps R' into [0, box).
+// scheme selects the variant of the SI:
+//   LV_ADOPTED  the equation above;
+//   LV_FAST     the faster iteration scheme (Eq. finaldyn):
+//               R' = R + D S^{-1} f + sqrt(2 T D) z - (1/2) S^{-1} (S_prev - S)(R_prev - R);
+//   LV_NOROGNA  the same without the S_prev term (Eq. norogna), which the SI
+//               shows samples a wrong distribution when S depends on R.
 // ---------------------------------------------------------------------------
+enum LangevinScheme { LV_ADOPTED = 0, LV_FAST = 1, LV_NOROGNA = 2 };
+
 static int langevin(int n, const double* R, const double* Rprev, const double* f, const double* S,
                     const double* Sprev, double T, double delta, double alpha, const double* xi,
-                    int noise_correction, double box, double* Rout) {
+                    int noise_correction, double box, int scheme, double* Rout) {
     double Dt = delta, Db = delta;
-    if (alpha > 0) {
+    if (scheme == LV_ADOPTED && alpha > 0) {
         Dt = (1.0 - std::exp(-alpha * delta)) / alpha;
         Db = (1.0 - std::exp(-2.0 * alpha * delta)) / (2.0 * alpha);
     }
@@ -687,7 +700,8 @@ static int langevin(int n, const double* R, const double* Rprev, const double* f
     std::vector<double> g(n), y(n), x(n), z(n);
     for (int i = 0; i < n; ++i) {
         double s = 0;
-        for (int j = 0; j < n; ++j) s += (Sprev[(size_t)i * n + j] - S[(size_t)i * n + j]) * (Rprev[j] - R[j]);
+        if (scheme != LV_NOROGNA)
+            for (int j = 0; j < n; ++j) s += (Sprev[(size_t)i * n + j] - S[(size_t)i * n + j]) * (Rprev[j] - R[j]);
         g[i] = f[i] - s / (2.0 * Db);
     }
     for (int i = 0; i < n; ++i) {                       // L y = g
@@ -711,6 +725,259 @@ static int langevin(int n, const double* R, const double* Rprev, const double* f
         Rout[i] = box > 0 ? wrap(r, box) : r;
     }
     return 0;
+}
+
+
+// ---------------------------------------------------------------------------
+// Rotating-spring toy model (SI, "A simple toy model") and the integrator
+// variants compared on it.  The end point R = (x, y) of a spring of rest
+// length a and stiffness k, free to rotate about the origin:
+//   U(x, y) = k/2 (sqrt(x^2 + y^2) - a)^2,   f = -grad U.
+// Acceleration matrices (gamma = 0, Euclidean canonical measure):
+//   TOY_S_G   S = G_lambda, the matrix printed in the SI (identity at lambda = 1)
+//   TOY_S_HG  S = H + mu G_lambda, H = grad grad U (the SI's regularised Hessian)
+// Schemes, one step from R (and R_prev for the two-point ones), <z z^T> = S^{-1}(R):
+//   TOY_PLAIN     S = I: R' = R + D f + sqrt(2 T D) xi
+//   TOY_STANDARD  Eq. standard: R' = R + D S^{-1} f + T D Gamma + sqrt(2 T D) z,
+//                 Gamma_j = sum_i d_i (S^{-1})_{ji}  (the "cumbersome term")
+//   TOY_FIRST     Eq. smartMarkov: y = R + sqrt(2 T D) z,
+//                 R' = y + D S^{-1}(R) f(R) - 1/2 S^{-1}(R) [S(y) - S(R)] (y - R)
+//   TOY_FAST      Eq. finaldyn: R' = R + D S^{-1} f + sqrt(2 T D) z
+//                                 - 1/2 S^{-1} [S(R_prev) - S(R)] (R_prev - R)
+//   TOY_ADOPTED   Eq. finaldyn_new: R' = R + Dt S^{-1} [f - (S(R_prev) - S(R))(R_prev - R)/(2 Db)]
+//                                 + sqrt(2 T Db) z,  Dt, Db as in the hydrogen step
+//   TOY_NOROGNA   Eq. norogna: R' = R + D S^{-1} f + sqrt(2 T D) z
+// On the first step R_prev = R.  Derivatives (f, H, Gamma) come from nested
+// forward-mode dual numbers, never from hand-derived formulas.
+// ---------------------------------------------------------------------------
+enum ToyScheme { TOY_PLAIN = 0, TOY_STANDARD = 1, TOY_FIRST = 2, TOY_FAST = 3, TOY_ADOPTED = 4, TOY_NOROGNA = 5 };
+enum ToySMode { TOY_S_G = 0, TOY_S_HG = 1 };
+constexpr uint32_t P_TOY = 8;   // Philox purpose word of the toy-model noise
+
+// Dual number with the two tangents d/dx, d/dy over a value type V that may
+// itself be a dual number (nesting gives second and third derivatives).
+template <class V> struct Du {
+    V v, dx, dy;
+    Du() : v(0.0), dx(0.0), dy(0.0) {}
+    Du(double c) : v(c), dx(0.0), dy(0.0) {}
+    Du(V a, V b, V c) : v(a), dx(b), dy(c) {}
+};
+template <class V> Du<V> operator+(const Du<V>& a, const Du<V>& b) { return Du<V>(a.v + b.v, a.dx + b.dx, a.dy + b.dy); }
+template <class V> Du<V> operator-(const Du<V>& a, const Du<V>& b) { return Du<V>(a.v - b.v, a.dx - b.dx, a.dy - b.dy); }
+template <class V> Du<V> operator-(const Du<V>& a) { return Du<V>(-a.v, -a.dx, -a.dy); }
+template <class V> Du<V> operator*(const Du<V>& a, const Du<V>& b) {
+    return Du<V>(a.v * b.v, a.dx * b.v + a.v * b.dx, a.dy * b.v + a.v * b.dy);
+}
+template <class V> Du<V> operator/(const Du<V>& a, const Du<V>& b) {
+    const V q = a.v / b.v;
+    return Du<V>(q, (a.dx - q * b.dx) / b.v, (a.dy - q * b.dy) / b.v);
+}
+template <class V> Du<V> operator+(const Du<V>& a, double c) { return a + Du<V>(c); }
+template <class V> Du<V> operator+(double c, const Du<V>& a) { return Du<V>(c) + a; }
+template <class V> Du<V> operator-(const Du<V>& a, double c) { return a - Du<V>(c); }
+template <class V> Du<V> operator-(double c, const Du<V>& a) { return Du<V>(c) - a; }
+template <class V> Du<V> operator*(const Du<V>& a, double c) { return a * Du<V>(c); }
+template <class V> Du<V> operator*(double c, const Du<V>& a) { return Du<V>(c) * a; }
+template <class V> Du<V> operator/(const Du<V>& a, double c) { return a / Du<V>(c); }
+template <class V> Du<V> operator/(double c, const Du<V>& a) { return Du<V>(c) / a; }
+template <class V> Du<V> sqrt(const Du<V>& a) {
+    using std::sqrt;
+    const V s = sqrt(a.v);
+    return Du<V>(s, a.dx / (s + s), a.dy / (s + s));
+}
+template <class V> Du<V> lift(const V& c) { return Du<V>(c, V(0.0), V(0.0)); }
+template <class V> Du<V> seed_x(const V& x) { return Du<V>(x, V(1.0), V(0.0)); }
+template <class V> Du<V> seed_y(const V& y) { return Du<V>(y, V(0.0), V(1.0)); }
+
+struct ToyModel {
+    double k, a;        // spring stiffness and rest length
+    double lambda;      // G_lambda parameter, as printed
+    double mu;          // weight of G_lambda in S = H + mu G_lambda
+    int s_mode;         // TOY_S_G or TOY_S_HG
+};
+
+template <class V> V toy_U(const ToyModel& m, const V& x, const V& y) {
+    using std::sqrt;
+    const V d = sqrt(x * x + y * y) - m.a;
+    return 0.5 * m.k * d * d;
+}
+// grad U by one level of dual numbers.
+template <class V> void toy_grad(const ToyModel& m, const V& x, const V& y, V g[2]) {
+    const Du<V> ux = toy_U(m, seed_x(x), lift(y));
+    const Du<V> uy = toy_U(m, lift(x), seed_y(y));
+    g[0] = ux.dx; g[1] = uy.dy;
+}
+// H = grad grad U: one more level of dual numbers on toy_grad.
+template <class V> void toy_hess(const ToyModel& m, const V& x, const V& y, V H[2][2]) {
+    Du<V> gx[2], gy[2];
+    toy_grad(m, seed_x(x), lift(y), gx);
+    toy_grad(m, lift(x), seed_y(y), gy);
+    for (int i = 0; i < 2; ++i) { H[i][0] = gx[i].dx; H[i][1] = gy[i].dy; }
+}
+// G_lambda as printed in the SI.
+template <class V> void toy_G(const ToyModel& m, const V& x, const V& y, V G[2][2]) {
+    const double l = m.lambda;
+    const V r2 = x * x + y * y;
+    G[0][0] = (x * x + y * y * l) / (r2 * l);
+    G[0][1] = (x * y * (1.0 - l)) / (r2 * l);
+    G[1][0] = G[0][1];
+    G[1][1] = (x * x * l + y * y) / (r2 * l);
+}
+template <class V> void toy_S(const ToyModel& m, const V& x, const V& y, V S[2][2]) {
+    toy_G(m, x, y, S);
+    if (m.s_mode == TOY_S_HG) {
+        V H[2][2];
+        toy_hess(m, x, y, H);
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) S[i][j] = H[i][j] + m.mu * S[i][j];
+    }
+}
+// S^{-1} by the 2x2 adjugate formula.
+template <class V> void toy_Sinv(const ToyModel& m, const V& x, const V& y, V Si[2][2]) {
+    V S[2][2];
+    toy_S(m, x, y, S);
+    const V det = S[0][0] * S[1][1] - S[0][1] * S[1][0];
+    Si[0][0] = S[1][1] / det; Si[0][1] = -S[0][1] / det;
+    Si[1][0] = -S[1][0] / det; Si[1][1] = S[0][0] / det;
+}
+// Gamma_j = sum_i d_i (S^{-1})_{ji} (SI, Eq. for the cumbersome term).
+static void toy_gamma(const ToyModel& m, double x, double y, double Gam[2]) {
+    Du<double> Sx[2][2], Sy[2][2];
+    toy_Sinv(m, seed_x(x), lift(y), Sx);
+    toy_Sinv(m, lift(x), seed_y(y), Sy);
+    for (int j = 0; j < 2; ++j) Gam[j] = Sx[j][0].dx + Sy[j][1].dy;
+}
+
+// 2x2 Cholesky S = L L^T; false if S is not positive definite.
+static bool chol2(const double S[2][2], double L[2][2]) {
+    if (!(S[0][0] > 0)) return false;
+    L[0][0] = std::sqrt(S[0][0]); L[0][1] = 0.0;
+    L[1][0] = S[1][0] / L[0][0];
+    const double d = S[1][1] - L[1][0] * L[1][0];
+    if (!(d > 0)) return false;
+    L[1][1] = std::sqrt(d);
+    return true;
+}
+static void chol2_solve(const double L[2][2], const double b[2], double x[2]) {     // S x = b
+    const double y0 = b[0] / L[0][0], y1 = (b[1] - L[1][0] * y0) / L[1][1];
+    x[1] = y1 / L[1][1];
+    x[0] = (y0 - L[1][0] * x[1]) / L[0][0];
+}
+static void chol2_noise(const double L[2][2], const double xi[2], double z[2]) {   // z = L^{-T} xi
+    z[1] = xi[1] / L[1][1];
+    z[0] = (xi[0] - L[1][0] * z[1]) / L[0][0];
+}
+
+struct ToyStep {
+    ToyModel m;
+    double T, delta, alpha;
+    int scheme;
+};
+
+// One step of the selected scheme from R (R_prev used by TOY_FAST / TOY_ADOPTED).
+// Returns false when S(R) is not positive definite.
+static bool toy_step(const ToyStep& c, const double R[2], const double Rp[2], const double xi[2], double Rn[2]) {
+    const ToyModel& m = c.m;
+    double g[2];
+    toy_grad(m, R[0], R[1], g);
+    const double f[2] = {-g[0], -g[1]};
+    const double D = c.delta, T = c.T > 0 ? c.T : 0.0;
+    if (c.scheme == TOY_PLAIN) {
+        const double amp = std::sqrt(2.0 * T * D);
+        for (int j = 0; j < 2; ++j) Rn[j] = R[j] + D * f[j] + amp * xi[j];
+        return true;
+    }
+    double S[2][2], L[2][2], z[2], sf[2];
+    toy_S(m, R[0], R[1], S);
+    if (!chol2(S, L)) return false;
+    chol2_noise(L, xi, z);
+    chol2_solve(L, f, sf);
+    const double amp = std::sqrt(2.0 * T * D);
+    switch (c.scheme) {
+    case TOY_STANDARD: {
+        double Gam[2];
+        toy_gamma(m, R[0], R[1], Gam);
+        for (int j = 0; j < 2; ++j) Rn[j] = R[j] + D * sf[j] + T * D * Gam[j] + amp * z[j];
+        return true;
+    }
+    case TOY_FIRST: {
+        double y[2], Sy[2][2], v[2], w[2];
+        for (int j = 0; j < 2; ++j) y[j] = R[j] + amp * z[j];
+        toy_S(m, y[0], y[1], Sy);
+        for (int i = 0; i < 2; ++i) {
+            v[i] = 0.0;
+            for (int j = 0; j < 2; ++j) v[i] += (Sy[i][j] - S[i][j]) * (y[j] - R[j]);
+        }
+        chol2_solve(L, v, w);
+        for (int j = 0; j < 2; ++j) Rn[j] = y[j] + D * sf[j] - 0.5 * w[j];
+        return true;
+    }
+    case TOY_FAST: {
+        double Sp[2][2], v[2], w[2];
+        toy_S(m, Rp[0], Rp[1], Sp);
+        for (int i = 0; i < 2; ++i) {
+            v[i] = 0.0;
+            for (int j = 0; j < 2; ++j) v[i] += (Sp[i][j] - S[i][j]) * (Rp[j] - R[j]);
+        }
+        chol2_solve(L, v, w);
+        for (int j = 0; j < 2; ++j) Rn[j] = R[j] + D * sf[j] + amp * z[j] - 0.5 * w[j];
+        return true;
+    }
+    case TOY_ADOPTED: {
+        double Dt = D, Db = D;
+        if (c.alpha > 0) {
+            Dt = (1.0 - std::exp(-c.alpha * D)) / c.alpha;
+            Db = (1.0 - std::exp(-2.0 * c.alpha * D)) / (2.0 * c.alpha);
+        }
+        double Sp[2][2], h[2], x[2];
+        toy_S(m, Rp[0], Rp[1], Sp);
+        for (int i = 0; i < 2; ++i) {
+            double v = 0.0;
+            for (int j = 0; j < 2; ++j) v += (Sp[i][j] - S[i][j]) * (Rp[j] - R[j]);
+            h[i] = f[i] - v / (2.0 * Db);
+        }
+        chol2_solve(L, h, x);
+        const double ampb = std::sqrt(2.0 * T * Db);
+        for (int j = 0; j < 2; ++j) Rn[j] = R[j] + Dt * x[j] + ampb * z[j];
+        return true;
+    }
+    default:   // TOY_NOROGNA
+        for (int j = 0; j < 2; ++j) Rn[j] = R[j] + D * sf[j] + amp * z[j];
+        return true;
+    }
+}
+
+// Two standard normals from one Philox block (Box-Muller, both branches),
+// counter = (trajectory, step, 0, P_TOY).
+static void toy_noise(const Rng& rng, uint32_t traj, uint32_t step, double xi[2]) {
+    uint32_t w[4];
+    rng.block(traj, step, 0u, P_TOY, w);
+    const double u1 = uniform53(w[0], w[1]), u2 = uniform53(w[2], w[3]);
+    const double rho = std::sqrt(-2.0 * std::log(u1));
+    xi[0] = rho * std::cos(2.0 * M_PI * u2);
+    xi[1] = rho * std::sin(2.0 * M_PI * u2);
+}
+
+// One trajectory of n_steps steps from xy0.  out = [x, y, sum U, sum U^2,
+// sum |R|, unwrapped polar angle travelled, status]; the sums run over the
+// positions after steps n_burn..n_steps-1; status = 0, or s+1 when S was not
+// positive definite at step s (the trajectory stops there).
+static void toy_run(const ToyStep& c, const Rng& rng, uint32_t traj, int n_steps, int n_burn, const double xy0[2],
+                    double out[7]) {
+    double R[2] = {xy0[0], xy0[1]}, Rp[2] = {xy0[0], xy0[1]}, Rn[2], xi[2];
+    double su = 0.0, su2 = 0.0, sr = 0.0, theta = 0.0, status = 0.0;
+    for (int s = 0; s < n_steps; ++s) {
+        toy_noise(rng, traj, (uint32_t)s, xi);
+        if (!toy_step(c, R, Rp, xi, Rn)) { status = s + 1; break; }
+        theta += std::atan2(R[0] * Rn[1] - R[1] * Rn[0], R[0] * Rn[0] + R[1] * Rn[1]);
+        Rp[0] = R[0]; Rp[1] = R[1];
+        R[0] = Rn[0]; R[1] = Rn[1];
+        if (s >= n_burn) {
+            const double u = toy_U(c.m, R[0], R[1]);
+            su += u; su2 += u * u; sr += std::sqrt(R[0] * R[0] + R[1] * R[1]);
+        }
+    }
+    out[0] = R[0]; out[1] = R[1]; out[2] = su; out[3] = su2; out[4] = sr; out[5] = theta; out[6] = status;
 }
 
 }  // namespace orc
@@ -796,14 +1063,56 @@ void orc_reduce(int W, int N3, const double* acc, double* E, double* Eerr, doubl
 
 int orc_langevin(int n, const double* R, const double* Rprev, const double* f, const double* S,
                  const double* Sprev, double T, double delta, double alpha, const double* xi,
-                 int noise_correction, double box, double* Rout) {
-    return orc::langevin(n, R, Rprev, f, S, Sprev, T, delta, alpha, xi, noise_correction, box, Rout);
+                 int noise_correction, double box, int scheme, double* Rout) {
+    return orc::langevin(n, R, Rprev, f, S, Sprev, T, delta, alpha, xi, noise_correction, box, scheme, Rout);
 }
 
 // Langevin noise xi_c for component c of MD step m (Philox, purpose P_LANGEVIN).
 void orc_langevin_noise(uint64_t seed, uint32_t md_step, int n, double* xi) {
     orc::Rng rng(seed);
     for (int c = 0; c < n; ++c) xi[c] = rng.normal((uint32_t)c, md_step, 0u, orc::P_LANGEVIN);
+}
+
+// ---- toy model ----
+struct ToyArgs {
+    double k, a, T, delta, lambda, mu, alpha;
+    int32_t scheme, s_mode, n_steps, n_burn;
+    uint64_t seed;
+};
+static orc::ToyStep toy_cfg(const ToyArgs* a) {
+    orc::ToyStep c;
+    c.m.k = a->k; c.m.a = a->a; c.m.lambda = a->lambda; c.m.mu = a->mu; c.m.s_mode = a->s_mode;
+    c.T = a->T; c.delta = a->delta; c.alpha = a->alpha; c.scheme = a->scheme;
+    return c;
+}
+// Model quantities at (x, y): out = [U, f_x, f_y, S (4), S^{-1} (4), H (4), Gamma (2)].
+void orc_toy_eval(const ToyArgs* a, double x, double y, double* out) {
+    const orc::ToyStep c = toy_cfg(a);
+    double g[2], S[2][2], Si[2][2], H[2][2], Gam[2];
+    orc::toy_grad(c.m, x, y, g);
+    orc::toy_S(c.m, x, y, S);
+    orc::toy_Sinv(c.m, x, y, Si);
+    orc::toy_hess(c.m, x, y, H);
+    orc::toy_gamma(c.m, x, y, Gam);
+    out[0] = orc::toy_U(c.m, x, y); out[1] = -g[0]; out[2] = -g[1];
+    for (int i = 0; i < 4; ++i) { out[3 + i] = S[i / 2][i % 2]; out[7 + i] = Si[i / 2][i % 2]; out[11 + i] = H[i / 2][i % 2]; }
+    out[15] = Gam[0]; out[16] = Gam[1];
+}
+// One step of the scheme in a->scheme from R (R_prev = Rp) with the given xi; 0 or -1 (S not PD).
+int orc_toy_step(const ToyArgs* a, const double* R, const double* Rp, const double* xi, double* Rn) {
+    return orc::toy_step(toy_cfg(a), R, Rp, xi, Rn) ? 0 : -1;
+}
+// n_traj independent trajectories (OpenMP over trajectories); xy0 [n_traj][2], out [n_traj][7].
+void orc_toy_run(const ToyArgs* a, int n_traj, const double* xy0, double* out) {
+    const orc::ToyStep c = toy_cfg(a);
+    const orc::Rng rng(a->seed);
+#pragma omp parallel for schedule(dynamic)
+    for (int t = 0; t < n_traj; ++t)
+        orc::toy_run(c, rng, (uint32_t)t, a->n_steps, a->n_burn, xy0 + 2 * (size_t)t, out + 7 * (size_t)t);
+}
+// The two toy-model normals of (trajectory, step).
+void orc_toy_noise(uint64_t seed, uint32_t traj, uint32_t step, double* xi) {
+    orc::toy_noise(orc::Rng(seed), traj, step, xi);
 }
 
 int orc_num_threads() {

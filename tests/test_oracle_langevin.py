@@ -138,3 +138,45 @@ def test_non_positive_definite_S_is_rejected():
     with pytest.raises(ValueError):
         orc.langevin(np.zeros(2), np.zeros(2), np.zeros(2), np.diag([1.0, -1.0]), np.eye(2), 0.1, 0.1, 0.0,
                      np.zeros(2))
+
+
+def test_fast_scheme_is_adopted_at_zero_alpha_and_ignores_alpha():
+    """Eq. finaldyn is Eq. finaldyn_new at alpha = 0 (Dt = Db = Delta)."""
+    rng = np.random.default_rng(11)
+    n = 6
+    S, Sp = _spd(n, 12), _spd(n, 13)
+    R, Rp, f, xi = (rng.standard_normal(n) for _ in range(4))
+    a = orc.langevin(R, Rp, f, S, Sp, 0.3, 0.4, 0.0, xi)
+    b = orc.langevin(R, Rp, f, S, Sp, 0.3, 0.4, 2.5, xi, scheme=orc.LV_FAST)
+    assert np.allclose(a, b, rtol=0, atol=1e-13)
+    # and its S_prev term is -1/2 S^{-1} (S_prev - S)(R_prev - R) written out
+    c = orc.langevin(R, Rp, f, S, S, 0.3, 0.4, 0.0, xi, scheme=orc.LV_FAST)
+    assert np.allclose(b - c, -0.5 * np.linalg.solve(S, (Sp - S) @ (Rp - R)), atol=1e-12)
+
+
+def test_norogna_scheme_drops_the_two_time_term():
+    rng = np.random.default_rng(14)
+    n = 5
+    S, Sp = _spd(n, 15), _spd(n, 16)
+    R, Rp, f, xi = (rng.standard_normal(n) for _ in range(4))
+    a = orc.langevin(R, Rp, f, S, Sp, 0.2, 0.3, 1.0, xi, scheme=orc.LV_NOROGNA)
+    b = orc.langevin(R, R, f, S, S, 0.2, 0.3, 0.0, xi)
+    assert np.allclose(a, b, rtol=0, atol=1e-13)
+
+
+def test_fast_scheme_stationary_covariance_closed_form():
+    """Constant S = K/alpha0: the fast scheme is R' = (1 - alpha0 D) R + sqrt(2 T D) z,
+    whose stationary covariance is 2 T K^{-1} / (2 - alpha0 D) (discrete Lyapunov)."""
+    K = _spd(3, 17, cond=20.0)
+    a0, T, d = 0.9, 0.4, 0.8
+    S = K / a0
+    rng = np.random.default_rng(18)
+    R = np.zeros(3)
+    traj = np.empty((40000, 3))
+    for t in range(len(traj)):
+        R = orc.langevin(R, R, -K @ R, S, S, T, d, 7.0, rng.standard_normal(3), scheme=orc.LV_FAST)
+        traj[t] = R
+    cov = np.cov(traj[200:].T)
+    target = 2 * T * np.linalg.inv(K) / (2 - a0 * d)
+    rel = np.abs(cov - target) / np.sqrt(np.outer(np.diag(target), np.diag(target)))
+    assert rel.max() < 0.06, (cov, target)
