@@ -48,6 +48,9 @@ def _args():
     ap.add_argument("--serve-requests", type=int, default=200, help="served-form requests (0: skip)")
     ap.add_argument("--serve-trajectories", type=int, default=32)
     ap.add_argument("--serve-active", type=int, default=8)
+    ap.add_argument("--no-toy", action="store_true", help="skip the toy-model integrator leg")
+    ap.add_argument("--toy-only", action="store_true", help="run only the toy-model leg (one JSON line)")
+    ap.add_argument("--toy-steps", type=int, default=None, help="steps per trajectory of the timed toy launch")
     return ap.parse_args()
 
 
@@ -174,6 +177,104 @@ def _cpu_baseline(wl, walkers_per_core=1):
                       f"{dt:.1f} s", "force_evals_per_s": W / dt, "seconds": dt, "moves": moves}
 
 
+# Rotating-spring toy model (SI, "A simple toy model"): the integrator comparison
+# on the GPU.  Timed configuration: the adopted scheme with S = G_lambda, one
+# trajectory per thread, 152 SMs x 3 resident CTAs x 256 threads.
+TOY_BENCH = {"n_traj": N_SM * 3 * 256, "n_steps": 20000, "n_burn": 2000, "delta": 0.2, "seed": 11}
+# FP64 operations per step of that scheme, from its formulas (a special function
+# -- log, sqrt, sincos, atan2, reciprocal -- counted as one): noise 11, force 6,
+# S 10, Cholesky 7, z 4, S^{-1} f 8, S-difference term and its solve 20,
+# update 12, polar angle 8, radius 4, sums 7.
+TOY_FLOPS_PER_STEP = 97
+FP64_NOMINAL_TFLOPS = 1.25     # GB300 dense FP64, nominal (no measured FP64 peak on this machine)
+
+
+def _toy_bench(stream, steps, rank, n_steps=None, table=True):
+    """Time the toy-model launch; also <U> against the time step for every scheme."""
+    import numpy as np
+    import torch
+    from paper_1605_08423_gb300 import qmcmd as q
+    from paper_1605_08423_gb300 import synth
+    cfg = dict(TOY_BENCH)
+    if n_steps:
+        cfg["n_steps"], cfg["n_burn"] = n_steps, n_steps // 10
+    n = cfg["n_traj"]
+    xy = torch.tensor(synth.toy_starts(n, cfg["seed"] + rank), device="cuda")
+    out = torch.empty((n, q.QMC_TOY_NOUT), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")      # 256 MB > L2
+    p = q.toy_params(q.QMC_TOY_ADOPTED, q.QMC_TOY_S_G, delta=cfg["delta"], n_steps=cfg["n_steps"],
+                     n_burn=cfg["n_burn"], seed=cfg["seed"] + rank)
+    pw = q.toy_params(q.QMC_TOY_ADOPTED, q.QMC_TOY_S_G, delta=cfg["delta"], n_steps=200, n_burn=0,
+                      seed=cfg["seed"] + rank)
+    for _ in range(3):
+        q.toy_langevin_device(pw, xy, out, stream.cuda_stream)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(max(steps, 1)):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        q.toy_langevin_device(p, xy, out, stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    o = out.cpu().numpy()
+    avg = sum(ms) / len(ms)
+    nsteps = n * cfg["n_steps"]
+    value = nsteps / (avg / 1e3)
+    ach = value * TOY_FLOPS_PER_STEP / 1e12
+    mean_u = float(o[:, 2].sum() / (n * (cfg["n_steps"] - cfg["n_burn"])))
+    # <U> versus the time step (the SI's figure): 16384 trajectories, 2000 time units each
+    rows = {}
+    xs = xy[:16384].contiguous()
+    os_ = out[:16384]
+    modes = ((q.QMC_TOY_S_G, synth.TOY_MU, "G_lambda"), (q.QMC_TOY_S_HG, 2.0, "H+2G_lambda")) if table else ()
+    for s_mode, mu, tag in modes:
+        for name, sc in q.TOY_SCHEMES.items():
+            row = {}
+            for d in (0.4, 0.2, 0.1, 0.05):
+                pp = q.toy_params(sc, s_mode, mu=mu, delta=d, n_steps=int(round(2000 / d)),
+                                  n_burn=int(round(200 / d)), seed=cfg["seed"] + 1)
+                q.toy_langevin_device(pp, xs, os_, stream.cuda_stream)
+                torch.cuda.synchronize()
+                oo = os_.cpu().numpy()
+                ok = oo[:, 6] == 0
+                m = oo[ok, 2] / (pp.n_steps - pp.n_burn)
+                row[str(d)] = {"mean_U": float(m.mean()) if ok.any() else None,
+                               "err": float(m.std() / max(ok.sum(), 1) ** 0.5) if ok.any() else None,
+                               "stopped": int((~ok).sum())}
+            rows[f"{tag}/{name}"] = row
+    return {"metric": "toy-model trajectory steps/s (adopted scheme, S = G_lambda, FP64)", "value": value,
+            "unit": "trajectory steps/s", "ms_per_launch": avg, "launches_timed": len(ms),
+            "config": {"workload": f"rotating spring k={synth.TOY_K}, a={synth.TOY_A}, T={synth.TOY_T}, "
+                                   f"lambda={synth.TOY_LAMBDA}, alpha={synth.TOY_ALPHA}, delta={cfg['delta']}, "
+                                   f"{n} trajectories x {cfg['n_steps']} steps",
+                       "l2": "L2 flushed (256 MB write) before every timed launch"},
+            "roofline": {"kernel": "toy_kernel", "bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS,
+                         "unit": "TFLOP/s", "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None,
+                         "peak_source": "nominal GB300 dense FP64", "flops_per_step": TOY_FLOPS_PER_STEP},
+            "mean_U": mean_u, "canonical_mean_U": synth.TOY_T / 2,
+            "stopped_trajectories": int((o[:, 6] != 0).sum()),
+            "mean_U_vs_delta": rows or None}
+
+
+def _toy_cpu_baseline():
+    """The oracle's toy model on the host cores: 4096 trajectories x 20000 steps."""
+    import numpy as np
+    from oracle import oracle as orc
+    from paper_1605_08423_gb300 import synth
+    cfg = TOY_BENCH
+    a = orc.toy_args(orc.TOY_ADOPTED, orc.TOY_S_G, delta=cfg["delta"], n_steps=cfg["n_steps"],
+                     n_burn=cfg["n_burn"], seed=cfg["seed"])
+    xy0 = synth.toy_starts(4096, cfg["seed"])
+    orc.lib()                      # build / load outside the timed region
+    t0 = time.perf_counter()
+    orc.toy_run(a, xy0)
+    dt = time.perf_counter() - t0
+    return {"value": 4096 * cfg["n_steps"] / dt, "unit": "trajectory steps/s", "cores": orc.num_threads(),
+            "kind": "oracle", "sample": f"4096 trajectories x {cfg['n_steps']} steps, {dt:.2f} s"}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -199,6 +300,20 @@ def run_reference(args, ws, rank):
                             "sample": last["sample"]},
            "e2e": {"value": value, "unit": "electron moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def run_toy_only(args, rank, local):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    toy = _toy_bench(stream, args.steps, rank, n_steps=args.toy_steps, table=False)
+    if rank == 0:
+        print(json.dumps({**toy, "n_gpus": 1, "steps": args.steps, "warmup": 3, "higher_is_better": True,
+                          "dtype": "f64", "data": "synthetic"}), flush=True)
 
 
 def run_ours(args, ws, rank, local):
@@ -362,6 +477,11 @@ def run_ours(args, ws, rank, local):
                                     "mixed form, Langevin step with S = Cov(f)"})
         srv.close()
 
+    toy = None
+    if not args.no_toy:
+        toy = _toy_bench(stream, args.steps, rank)
+        toy["cpu_baseline"] = _toy_cpu_baseline() if rank == 0 and ws == 1 and not args.no_cpu_baseline else None
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = _cpu_baseline(wl)
@@ -390,6 +510,7 @@ def run_ours(args, ws, rank, local):
                "fp64_form": fp64,
                "cpu_baseline": cpu,
                "serving": serving,
+               "toy_langevin": toy,
                "peaks": peak_kind,
                "result": {"E": res["E"], "E_err": res["E_err"], "accept": res["accept"], "Nc": res["Nc"]}}
         print(json.dumps(out), flush=True)
@@ -404,6 +525,9 @@ def main():
     ws, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.toy_only:
+        run_toy_only(args, rank, local)
         return
     run_ours(args, ws, rank, local)
 

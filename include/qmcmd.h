@@ -188,7 +188,74 @@ int qmc_get_accumulators(qmc_system* h, double* acc);
  * measure kernel.  INVALID for an unknown option or when the form has no such
  * kernel. */
 enum { QMC_OPT_TENSOR_CORES = 1, QMC_OPT_TC_ADJOINT = 2 };
+/* QMC_OPT_INTEGRATOR selects the scheme of later langevin_step /
+ * langevin_step_device calls with s_mode QMC_S_COV (SI, integration schemes):
+ *   QMC_LV_ADOPTED (default)  the adopted step written at langevin_step;
+ *   QMC_LV_FAST               Eq. finaldyn, the same with Dt = Db = Delta whatever
+ *                             alpha: R' = R + Delta S^{-1} f + sqrt(2 T Delta) z
+ *                                         - 1/2 S^{-1} (S_prev - S)(R_prev - R);
+ *   QMC_LV_NOROGNA            Eq. norogna, without the S_prev term (samples a wrong
+ *                             distribution when S depends on R; kept for comparison).
+ * QMC_OPT_NOISE_CORRECTION (default 0): 1 lowers the temperature of the step to
+ * T - Delta/2 (SI "Noise correction", 2 T Delta = 2 T_target Delta - Delta^2, T
+ * in hartree); a step with Delta >= 2 T is then INVALID. */
+enum { QMC_OPT_INTEGRATOR = 3, QMC_OPT_NOISE_CORRECTION = 4 };
+enum { QMC_LV_ADOPTED = 0, QMC_LV_FAST = 1, QMC_LV_NOROGNA = 2 };
 int qmc_set_option(qmc_system* h, int option, int value);
+
+/*
+ * Rotating-spring toy model (SI, "A simple toy model"): the planar spring end
+ * point R = (x, y) with U = k/2 (|R| - a)^2, free to rotate, integrated by the
+ * SI's schemes for many independent trajectories at once (one GPU thread
+ * each, FP64).  The acceleration matrix is
+ *   QMC_TOY_S_G   S = G_lambda, the matrix printed in the SI
+ *                 (G_lambda = P_r/lambda + P_t, P_r = R R^T/|R|^2, P_t = I - P_r);
+ *   QMC_TOY_S_HG  S = H + mu G_lambda, H = grad grad U (positive definite only for
+ *                 |R| > k a / (k + mu)).
+ * Schemes (z = L^{-T} xi with S(R) = L L^T, xi ~ N(0, I); R_prev = R on the first step):
+ *   QMC_TOY_PLAIN     S = I: R' = R + D f + sqrt(2 T D) xi
+ *   QMC_TOY_STANDARD  Eq. standard with the cumbersome term Gamma_j = sum_i d_i S^{-1}_{ji}:
+ *                     R' = R + D S^{-1} f + T D Gamma + sqrt(2 T D) z
+ *   QMC_TOY_FIRST     Eq. smartMarkov: y = R + sqrt(2 T D) z,
+ *                     R' = y + D S^{-1} f - 1/2 S^{-1} [S(y) - S(R)] (y - R)
+ *   QMC_TOY_FAST      Eq. finaldyn: R' = R + D S^{-1} f + sqrt(2 T D) z
+ *                                       - 1/2 S^{-1} [S(R_prev) - S(R)] (R_prev - R)
+ *   QMC_TOY_ADOPTED   Eq. finaldyn_new with Dt, Db of alpha (as langevin_step)
+ *   QMC_TOY_NOROGNA   Eq. norogna: R' = R + D S^{-1} f + sqrt(2 T D) z
+ * Noise: Philox4x32-10, key = seed, counter = (trajectory, step, 0, 8); the two
+ * normals are the cosine and sine branches of Box-Muller on the block's two
+ * 53-bit uniforms.
+ * xy0 is [n_traj][2]; out is [n_traj][QMC_TOY_NOUT] =
+ *   [x, y, sum U, sum U^2, sum |R|, polar angle travelled (unwrapped), status]
+ * with the sums over the positions after steps n_burn .. n_steps-1 and status
+ * s + 1 if S(R) was not positive definite at step s (that trajectory stops
+ * there; others continue), else 0.
+ * qmc_toy_langevin takes host arrays, returns after the run and gives
+ * QMC_ERR_NOT_PD (with out filled) when any trajectory stopped;
+ * qmc_toy_langevin_device takes device arrays and is asynchronous on `stream`
+ * (a cudaStream_t, NULL = default stream); read the status column.
+ * Errors: INVALID (unknown scheme or s_mode, delta <= 0, lambda <= 0, T < 0,
+ * alpha < 0, n_burn outside [0, n_steps], null arrays), OOM, CUDA, NOT_PD.
+ */
+enum { QMC_TOY_PLAIN = 0, QMC_TOY_STANDARD = 1, QMC_TOY_FIRST = 2, QMC_TOY_FAST = 3, QMC_TOY_ADOPTED = 4,
+       QMC_TOY_NOROGNA = 5 };
+enum { QMC_TOY_S_G = 0, QMC_TOY_S_HG = 1 };
+enum { QMC_TOY_NOUT = 7 };
+typedef struct {
+    double k, a;        /* spring stiffness and rest length                    */
+    double T;           /* temperature, energy units of U                      */
+    double delta;       /* time step D                                         */
+    double lambda;      /* G_lambda parameter as printed (> 0; 1 gives S = I)  */
+    double mu;          /* weight of G_lambda in QMC_TOY_S_HG                  */
+    double alpha;       /* QMC_TOY_ADOPTED (0: Dt = Db = D)                    */
+    int32_t scheme;     /* QMC_TOY_*                                           */
+    int32_t s_mode;     /* QMC_TOY_S_G or QMC_TOY_S_HG                         */
+    int32_t n_steps, n_burn;
+    uint64_t seed;
+} qmc_toy_params;
+int qmc_toy_langevin(const qmc_toy_params* p, int n_traj, const double* xy0, double* out);
+int qmc_toy_langevin_device(const qmc_toy_params* p, int n_traj, const double* xy0_dev, double* out_dev,
+                            void* stream);
 
 /* Set the MD step counter used in the Philox counters of the next call. */
 int qmc_set_md_step(qmc_system* h, uint32_t md_step);

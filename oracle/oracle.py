@@ -95,6 +95,7 @@ def lib():
         L.orc_toy_step.argtypes = [C.POINTER(ToyArgs), _dp, _dp, _dp, _dp]
         L.orc_toy_run.argtypes = [C.POINTER(ToyArgs), C.c_int, _dp, _dp]
         L.orc_toy_noise.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, _dp]
+        L.orc_toy_run_ids.argtypes = [C.POINTER(ToyArgs), C.c_int, C.POINTER(C.c_int), _dp, _dp]
         _lib = L
     return _lib
 
@@ -277,6 +278,15 @@ def toy_run(args: ToyArgs, xy0) -> np.ndarray:
     xy0 = np.ascontiguousarray(xy0, dtype=np.float64).reshape(-1, 2)
     out = np.zeros((xy0.shape[0], 7))
     lib().orc_toy_run(C.byref(args), xy0.shape[0], _ptr(xy0), _ptr(out))
+    return out
+
+
+def toy_run_ids(args: ToyArgs, ids, xy0) -> np.ndarray:
+    """toy_run for selected trajectories of a larger run (ids = their indices there)."""
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    xy0 = np.ascontiguousarray(xy0, dtype=np.float64).reshape(-1, 2)
+    out = np.zeros((len(ids), 7))
+    lib().orc_toy_run_ids(C.byref(args), len(ids), ids.ctypes.data_as(C.POINTER(C.c_int)), _ptr(xy0), _ptr(out))
     return out
 
 

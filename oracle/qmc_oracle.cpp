@@ -1110,6 +1110,15 @@ void orc_toy_run(const ToyArgs* a, int n_traj, const double* xy0, double* out) {
     for (int t = 0; t < n_traj; ++t)
         orc::toy_run(c, rng, (uint32_t)t, a->n_steps, a->n_burn, xy0 + 2 * (size_t)t, out + 7 * (size_t)t);
 }
+// The same for selected trajectories of a larger run: ids [n] are their indices
+// there (the Philox stream), xy0 [n][2] their start points, out [n][7].
+void orc_toy_run_ids(const ToyArgs* a, int n, const int* ids, const double* xy0, double* out) {
+    const orc::ToyStep c = toy_cfg(a);
+    const orc::Rng rng(a->seed);
+#pragma omp parallel for schedule(dynamic)
+    for (int t = 0; t < n; ++t)
+        orc::toy_run(c, rng, (uint32_t)ids[t], a->n_steps, a->n_burn, xy0 + 2 * (size_t)t, out + 7 * (size_t)t);
+}
 // The two toy-model normals of (trajectory, step).
 void orc_toy_noise(uint64_t seed, uint32_t traj, uint32_t step, double* xi) {
     orc::toy_noise(orc::Rng(seed), traj, step, xi);

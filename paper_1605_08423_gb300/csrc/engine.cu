@@ -71,6 +71,8 @@ struct qmc_system {
     std::vector<void*> allocs;
     uint32_t md_step = 0;
     bool first_call = true;
+    int lv_scheme = kLvAdopted;          // QMC_OPT_INTEGRATOR
+    bool lv_noise_correction = false;    // QMC_OPT_NOISE_CORRECTION
     bool langevin_first = true;
     uint32_t langevin_step_no = 0;
     double last_Nc = 0.0;
@@ -497,6 +499,11 @@ int langevin_step_device(qmc_system* h, double* R_dev, const double* f_dev, cons
     if (!h || !R_dev || !f_dev || (!S_dev && s_mode == QMC_S_COV)) return QMC_ERR_INVALID;
     if (s_mode != QMC_S_IDENTITY && s_mode != QMC_S_COV) return QMC_ERR_INVALID;
     if (!(delta > 0) || T_kelvin < 0) return QMC_ERR_INVALID;
+    double T_ha = T_kelvin * kBoltzmannHaPerK;
+    if (h->lv_noise_correction) {       // SI "Noise correction": 2 T D = 2 T_target D - D^2
+        T_ha -= 0.5 * delta;
+        if (!(T_ha > 0)) return QMC_ERR_INVALID;
+    }
     const int n3 = 3 * h->N;
     cudaStream_t st = h->stream;
     const int identity = s_mode == QMC_S_IDENTITY;
@@ -513,8 +520,8 @@ int langevin_step_device(qmc_system* h, double* R_dev, const double* f_dev, cons
     EventPair ep;
     prof_begin(h, KC_LANGEVIN, ep);
     h->nlaunch += 1;
-    launch_langevin(n3, R_dev, h->d_Rprev, f_dev, h->d_S, h->d_Sprev, h->d_Lwork, T_kelvin * kBoltzmannHaPerK, delta,
-                    a, make_key(h->p.seed), h->langevin_step_no, h->p.L, identity, h->d_err, st);
+    launch_langevin(n3, R_dev, h->d_Rprev, f_dev, h->d_S, h->d_Sprev, h->d_Lwork, T_ha, delta, a,
+                    make_key(h->p.seed), h->langevin_step_no, h->p.L, identity, h->lv_scheme, h->d_err, st);
     prof_end(h, ep);
     h->langevin_step_no++;
     return check_launch();
@@ -588,6 +595,15 @@ int qmc_set_option(qmc_system* h, int option, int value) {
     if (option == QMC_OPT_TC_ADJOINT) {
         if (value && !h->d_ahat) return QMC_ERR_INVALID;
         h->use_tc_adj = value != 0;
+        return QMC_OK;
+    }
+    if (option == QMC_OPT_INTEGRATOR) {
+        if (value != QMC_LV_ADOPTED && value != QMC_LV_FAST && value != QMC_LV_NOROGNA) return QMC_ERR_INVALID;
+        h->lv_scheme = value == QMC_LV_FAST ? kLvFast : value == QMC_LV_NOROGNA ? kLvNorogna : kLvAdopted;
+        return QMC_OK;
+    }
+    if (option == QMC_OPT_NOISE_CORRECTION) {
+        h->lv_noise_correction = value != 0;
         return QMC_OK;
     }
     return QMC_ERR_INVALID;

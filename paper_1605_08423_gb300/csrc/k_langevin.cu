@@ -4,6 +4,11 @@
 // with S = L L^T (Cholesky), x = S^{-1} g by two triangular solves and z = L^{-T} xi,
 // xi ~ N(0, I) from Philox (counter = (component, md step, 0, 7)).  One CTA, FP64.
 // identity != 0 runs the conventional dynamics (S = I, alpha = 0).
+// scheme selects the SI's variant: kLvAdopted (above), kLvFast (Eq. finaldyn:
+// Dt = Db = D whatever alpha, i.e. R' = R + D S^{-1} f + sqrt(2 T D) z
+// - 1/2 S^{-1}(S_prev - S)(R_prev - R)) or kLvNorogna (Eq. norogna: no S_prev
+// term, Dt = Db = D).  T arrives already lowered by the noise correction when
+// the caller asked for it.
 // On exit (R_prev, S_prev) hold the pair of this step for the next call.
 #include "common.cuh"
 #include "kernels.cuh"
@@ -13,7 +18,7 @@ namespace qmc {
 __global__ void __launch_bounds__(1024) langevin_kernel(int n, double* R, double* Rprev, const double* __restrict__ f,
                                                         const double* __restrict__ S, double* Sprev, double* Lc,
                                                         double T, double delta, double alpha, Key key, uint32_t md,
-                                                        double box, int identity, int* err) {
+                                                        double box, int identity, int scheme, int* err) {
     extern __shared__ double v[];
     double* g = v;          // [n]
     double* x = g + n;      // [n]
@@ -23,7 +28,7 @@ __global__ void __launch_bounds__(1024) langevin_kernel(int n, double* R, double
     __shared__ int notpd;
     const int tid = threadIdx.x, nt = blockDim.x;
     double Dt = delta, Db = delta;
-    if (!identity && alpha > 0.0) {
+    if (!identity && scheme == kLvAdopted && alpha > 0.0) {
         Dt = (1.0 - exp(-alpha * delta)) / alpha;
         Db = (1.0 - exp(-2.0 * alpha * delta)) / (2.0 * alpha);
     }
@@ -57,7 +62,7 @@ __global__ void __launch_bounds__(1024) langevin_kernel(int n, double* R, double
     // g = f - (S_prev - S)(R_prev - R) / (2 Db);  xi;  keep R
     for (int i = tid; i < n; i += nt) {
         double t = f[i];
-        if (!identity) {
+        if (!identity && scheme != kLvNorogna) {
             double s = 0.0;
             for (int j = 0; j < n; ++j) s += (Sprev[(size_t)i * n + j] - S[(size_t)i * n + j]) * (Rprev[j] - R[j]);
             t -= s / (2.0 * Db);
@@ -105,10 +110,10 @@ __global__ void __launch_bounds__(1024) langevin_kernel(int n, double* R, double
 
 void launch_langevin(int n3, double* R, double* Rprev, const double* f, const double* S, double* Sprev,
                      double* Lwork, double T_ha, double delta, double alpha, Key key, uint32_t md, double box,
-                     int identity, int* err, cudaStream_t st) {
+                     int identity, int scheme, int* err, cudaStream_t st) {
     const size_t smem = 4 * (size_t)n3 * sizeof(double);
     langevin_kernel<<<1, 1024, smem, st>>>(n3, R, Rprev, f, S, Sprev, Lwork, T_ha, delta, alpha, key, md, box,
-                                           identity, err);
+                                           identity, scheme, err);
 }
 
 }  // namespace qmc

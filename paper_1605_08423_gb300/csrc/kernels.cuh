@@ -62,9 +62,24 @@ void launch_recforce_table(int N, int nk, double L, const int4* kvec, const doub
 void launch_reduce(int W, int N, double moves, const double* acc, const unsigned long long* nacc,
                    double* colsum, double* dev, double* out, int* err, cudaStream_t st);
 
-// k_langevin.cu
+// k_langevin.cu (scheme: kLvAdopted, kLvFast or kLvNorogna)
+enum : int { kLvAdopted = 0, kLvFast = 1, kLvNorogna = 2 };
 void launch_langevin(int n3, double* R, double* Rprev, const double* f, const double* S, double* Sprev,
                      double* Lwork, double T_ha, double delta, double alpha, Key key, uint32_t md, double box,
-                     int identity, int* err, cudaStream_t st);
+                     int identity, int scheme, int* err, cudaStream_t st);
+
+// k_toy.cu: rotating-spring toy model, one thread per trajectory (FP64).
+struct ToyDev {
+    double k, a;          // U = k/2 (|R| - a)^2
+    double sr_const;      // radial eigenvalue of S: 1/lambda (G_lambda) or k + mu/lambda (H + mu G_lambda)
+    double mu;            // tangential eigenvalue of S is 1 (G_lambda) or k (1 - a/r) + mu
+    double T, delta;
+    double dt, db;        // adopted scheme: (1 - e^{-alpha D})/alpha, (1 - e^{-2 alpha D})/(2 alpha)
+    double half_idb;      // 1 / (2 db)
+    double amp, ampb;     // sqrt(2 T D), sqrt(2 T Db)
+    int scheme, s_mode, n_steps, n_burn;
+    Key key;
+};
+void launch_toy(const ToyDev& p, int n_traj, const double* xy0, double* out, cudaStream_t st);
 
 }  // namespace qmc

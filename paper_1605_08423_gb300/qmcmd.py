@@ -22,6 +22,13 @@ LIB_PATH = os.path.join(_HERE, "lib", "libqmcmd.so")
 QMC_FP64, QMC_MIXED = 0, 1
 QMC_S_IDENTITY, QMC_S_COV = 0, 1
 NKERNEL = 9
+QMC_OPT_TENSOR_CORES, QMC_OPT_TC_ADJOINT, QMC_OPT_INTEGRATOR, QMC_OPT_NOISE_CORRECTION = 1, 2, 3, 4
+QMC_LV_ADOPTED, QMC_LV_FAST, QMC_LV_NOROGNA = 0, 1, 2
+QMC_TOY_PLAIN, QMC_TOY_STANDARD, QMC_TOY_FIRST, QMC_TOY_FAST, QMC_TOY_ADOPTED, QMC_TOY_NOROGNA = range(6)
+QMC_TOY_S_G, QMC_TOY_S_HG = 0, 1
+QMC_TOY_NOUT = 7
+TOY_SCHEMES = {"plain": QMC_TOY_PLAIN, "standard": QMC_TOY_STANDARD, "first": QMC_TOY_FIRST,
+               "fast": QMC_TOY_FAST, "adopted": QMC_TOY_ADOPTED, "norogna": QMC_TOY_NOROGNA}
 
 
 class QMCError(RuntimeError):
@@ -51,6 +58,13 @@ class Served(C.Structure):
 class Result(C.Structure):
     _fields_ = [("E", C.c_double), ("E_err", C.c_double), ("f", C.POINTER(C.c_double)),
                 ("cov", C.POINTER(C.c_double)), ("n_samples", C.c_double), ("accept", C.c_double)]
+
+
+class ToyParams(C.Structure):
+    _fields_ = [("k", C.c_double), ("a", C.c_double), ("T", C.c_double), ("delta", C.c_double),
+                ("lam", C.c_double), ("mu", C.c_double), ("alpha", C.c_double),
+                ("scheme", C.c_int32), ("s_mode", C.c_int32), ("n_steps", C.c_int32), ("n_burn", C.c_int32),
+                ("seed", C.c_uint64)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -104,6 +118,8 @@ def lib():
         L.qmc_launch_count.restype = C.c_longlong
         L.qmc_kernel_name.argtypes = [C.c_int]
         L.qmc_kernel_name.restype = C.c_char_p
+        L.qmc_toy_langevin.argtypes = [C.POINTER(ToyParams), C.c_int, _dp, _dp]
+        L.qmc_toy_langevin_device.argtypes = [C.POINTER(ToyParams), C.c_int, vp, vp, vp]
         L.qmc_strerror.argtypes = [C.c_int]
         L.qmc_strerror.restype = C.c_char_p
         _lib = L
@@ -250,12 +266,19 @@ class QMCSystem:
         _chk(lib().qmc_sync(self._h), "qmc_sync")
 
     def set_tensor_cores(self, on: bool):
-        _chk(lib().qmc_set_option(self._h, 1, int(on)), "qmc_set_option")
+        _chk(lib().qmc_set_option(self._h, QMC_OPT_TENSOR_CORES, int(on)), "qmc_set_option")
+
+    def set_integrator(self, scheme: int):
+        """QMC_LV_ADOPTED (default), QMC_LV_FAST or QMC_LV_NOROGNA for later Langevin steps."""
+        _chk(lib().qmc_set_option(self._h, QMC_OPT_INTEGRATOR, int(scheme)), "qmc_set_option")
+
+    def set_noise_correction(self, on: bool):
+        _chk(lib().qmc_set_option(self._h, QMC_OPT_NOISE_CORRECTION, int(on)), "qmc_set_option")
 
     def set_tc_adjoint(self, on: bool):
         """Orbital force terms in the separate tensor-core kernel (True) or in
         the SIMT measure kernel (False); effective while tensor cores are on."""
-        _chk(lib().qmc_set_option(self._h, 2, int(on)), "qmc_set_option")
+        _chk(lib().qmc_set_option(self._h, QMC_OPT_TC_ADJOINT, int(on)), "qmc_set_option")
 
     def set_profiling(self, on: bool):
         _chk(lib().qmc_set_profiling(self._h, int(on)), "qmc_set_profiling")
@@ -289,6 +312,35 @@ def langevin_step_static(R_dev, Rprev_dev, f_dev, S_dev, Sprev_dev, T_kelvin, de
     _chk(lib().qmc_langevin_step_static(n3, ptr(R_dev), ptr(Rprev_dev), ptr(f_dev), ptr(S_dev), ptr(Sprev_dev),
                                         T_kelvin, delta, s_mode, alpha, seed, step, box,
                                         C.c_void_p(stream_handle or 0)), "qmc_langevin_step_static")
+
+
+def toy_params(scheme=QMC_TOY_ADOPTED, s_mode=QMC_TOY_S_G, *, k=2.0, a=1.4, T=0.01, delta=0.05, lam=0.1, mu=0.5,
+               alpha=0.2, n_steps=1000, n_burn=0, seed=1) -> ToyParams:
+    """Parameters of the rotating-spring toy model (defaults: the SI's figure, k = 2,
+    a = 1.4, T = 0.01, mu = 1/2, alpha = 0.2, printed G_lambda at lambda = 1/10)."""
+    return ToyParams(k, a, T, delta, lam, mu, alpha, scheme, s_mode, n_steps, n_burn, seed)
+
+
+def toy_langevin(p: ToyParams, xy0) -> np.ndarray:
+    """qmc_toy_langevin on host arrays: xy0 [n][2] -> out [n][QMC_TOY_NOUT].
+    Trajectories stopped by an indefinite S keep their status column; the call
+    then raises QMCError(QMC_ERR_NOT_PD) with the array attached as .out."""
+    xy0 = _f64(np.asarray(xy0).reshape(-1, 2))
+    out = np.zeros((xy0.shape[0], QMC_TOY_NOUT))
+    rc = lib().qmc_toy_langevin(C.byref(p), xy0.shape[0], _p(xy0), _p(out))
+    if rc != 0:
+        err = QMCError(rc, "qmc_toy_langevin")
+        err.out = out
+        raise err
+    return out
+
+
+def toy_langevin_device(p: ToyParams, xy0_dev, out_dev, stream_handle=0):
+    """qmc_toy_langevin_device on float64 CUDA tensors ([n][2] in, [n][QMC_TOY_NOUT] out)."""
+    n = xy0_dev.shape[0]
+    _chk(lib().qmc_toy_langevin_device(C.byref(p), n, C.c_void_p(xy0_dev.data_ptr()),
+                                       C.c_void_p(out_dev.data_ptr()), C.c_void_p(stream_handle or 0)),
+         "qmc_toy_langevin_device")
 
 
 class Server:

@@ -133,3 +133,19 @@ def near_protons(n_conf: int, R: np.ndarray, n_up: int, spread: float, L: float,
     sites = np.concatenate([np.arange(n_up), n_up + np.arange(n_dn)]) % N
     X = R[sites][None, :, :] + spread * rng.standard_normal((n_conf, N, 3))
     return np.mod(X, L)
+
+
+# Rotating-spring toy model (SI, "A simple toy model"): the figure's parameters.
+# lambda is the parameter of the printed G_lambda; the caption's "lambda = 10"
+# is read as its reciprocal (radial step reduced tenfold), which is also what
+# makes alpha = 0.2 equal to k lambda, i.e. H = alpha S along the radius.
+TOY_K, TOY_A, TOY_T, TOY_LAMBDA, TOY_MU, TOY_ALPHA = 2.0, 1.4, 0.01, 0.1, 0.5, 0.2
+
+
+def toy_starts(n_traj: int, seed: int, a: float = TOY_A, spread: float = 0.05) -> np.ndarray:
+    """Start points [n_traj, 2] of toy-model trajectories: uniform polar angle,
+    radius a + N(0, spread^2) (inside the thermal ring for the figure's T)."""
+    rng = np.random.default_rng(seed + 7919)
+    th = rng.uniform(0.0, 2.0 * math.pi, n_traj)
+    r = a + spread * rng.standard_normal(n_traj)
+    return np.stack([r * np.cos(th), r * np.sin(th)], 1)

@@ -187,6 +187,39 @@ def test_langevin_step_matches_oracle(mode):
         Rprev, Sprev, R = R, S, Ro
 
 
+@pytest.mark.parametrize("scheme,noise_corr", [(q.QMC_LV_FAST, False), (q.QMC_LV_NOROGNA, False),
+                                               (q.QMC_LV_ADOPTED, True), (q.QMC_LV_FAST, True)])
+def test_langevin_integrator_variants_match_oracle(scheme, noise_corr):
+    wl = synth.workload("h16", walkers=2)
+    sysg = q.QMCSystem(q.Config.from_workload(wl), wl.R)
+    sysg.set_integrator(scheme)
+    sysg.set_noise_correction(noise_corr)
+    n = 3 * wl.N
+    rng = np.random.default_rng(5)
+    T_K, delta, alpha = 1500.0, 0.004, 41.0
+    T = T_K * synth.K_B_HARTREE_PER_KELVIN
+    R = wl.R.ravel().copy()
+    Rprev, Sprev = R.copy(), None
+    oscheme = {q.QMC_LV_ADOPTED: orc.LV_ADOPTED, q.QMC_LV_FAST: orc.LV_FAST, q.QMC_LV_NOROGNA: orc.LV_NOROGNA}
+    for step in range(3):
+        f = rng.standard_normal(n)
+        S = _spd(n, 20 + step) * 1e-3
+        if Sprev is None:
+            Sprev = S
+        xi = orc.langevin_noise(wl.seed, step, n)
+        Ro = orc.langevin(R, Rprev, f, S, Sprev, T, delta, alpha, xi, noise_correction=noise_corr, box=wl.L,
+                          scheme=oscheme[scheme])
+        Rg = sysg.langevin_step(R, f, S, T_K, delta, s_mode=q.QMC_S_COV, alpha=alpha)
+        assert np.max(np.abs(Rg - Ro)) < 1e-10, (step, np.max(np.abs(Rg - Ro)))
+        Rprev, Sprev, R = R, S, Ro
+    if noise_corr:      # Delta >= 2 T leaves no temperature to correct with
+        with pytest.raises(q.QMCError) as e:
+            sysg.langevin_step(R, np.zeros(n), np.eye(n), T_K, 2.5 * T, s_mode=q.QMC_S_COV, alpha=alpha)
+        assert e.value.code == -1
+    with pytest.raises(q.QMCError):
+        sysg.set_integrator(7)
+
+
 def test_autograd_function_backward_is_minus_force():
     import torch
     wl = synth.workload("h16", walkers=64, sweeps=10, warmup=5)
