@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
         T v = 0;
         for (int d = d0; d < d1; ++d) {
             const bool skip = 2 * d == N && i >= half;
-            const int j = (i + d) % N;
+            const int j = i + d < N ? i + d : i + d - N;      // (i + d) mod N, d < N
             if (skip) continue;
             if constexpr (sizeof(T) == 4) {
                 v += ewald_real_cut<false>(xt[3 * i] - xt[3 * j], xt[3 * i + 1] - xt[3 * j + 1],

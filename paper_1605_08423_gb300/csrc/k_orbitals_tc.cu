@@ -425,6 +425,10 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
     const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
     const int r = quarter * 32 + lane;
     const int rows_here = (nrows - row0) < kRows ? (nrows - row0) : kRows;
+    // rows of n floats go out as 16-byte vectors when n / 4 is a power of two
+    // (index arithmetic by shifts; every output row then starts 16-byte aligned)
+    const int nv = n >> 2;
+    const int vshift = ((n & 3) == 0 && (nv & (nv - 1)) == 0) ? __ffs(nv) - 1 : -1;
     for (int q = 0; q < Q; ++q) {
         for (int c0 = cgroup * 16; c0 < NM; c0 += 16 * ngroups) {
             float v[16];
@@ -434,12 +438,18 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
                 *(float4*)(stage + (size_t)r * lds + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
         }
         __syncthreads();
-        for (int idx = tid; idx < rows_here * n; idx += nt) {
-            const int rr = idx / n, j = idx - rr * n, row = row0 + rr;
-            const float x = stage[(size_t)rr * lds + j];
-            if (Q == 1) val[(size_t)row * n + j] = x;
-            else if (q == Q - 1) lap[(size_t)row * n + j] = x;
-            else grad[((size_t)row * 3 + q) * n + j] = x;
+        float* dst = Q == 1 ? val : (q == Q - 1 ? lap : grad + (size_t)q * n);
+        const size_t pitch = (Q == 1 || q == Q - 1) ? (size_t)n : (size_t)3 * n;   // floats between rows
+        if (vshift >= 0) {
+            for (int idx = tid; idx < (rows_here << vshift); idx += nt) {
+                const int rr = idx >> vshift, j = (idx & (nv - 1)) << 2;
+                *(float4*)(dst + (size_t)(row0 + rr) * pitch + j) = *(const float4*)(stage + (size_t)rr * lds + j);
+            }
+        } else {
+            for (int idx = tid; idx < rows_here * n; idx += nt) {
+                const int rr = idx / n, j = idx - rr * n;
+                dst[(size_t)(row0 + rr) * pitch + j] = stage[(size_t)rr * lds + j];
+            }
         }
         __syncthreads();
     }
