@@ -125,6 +125,7 @@ struct SysView {
     int N, n, G, B, W;
     int np;                 // n padded to a power of two >= 4 (tiled products)
     double L, ell;          // box side, L/pi
+    double iL;              // 1/L
     double b_ee, b_ep, Zj;  // Jastrow parameters (Zj = e-n cusp amplitude)
     double kappa;           // Ewald splitting
     const double* zeta;     // [G]
@@ -295,23 +296,19 @@ __device__ __forceinline__ float ex2_fast(float x) {
 // Mixed-form real-space Ewald sum of one pair: the images of the minimum-image
 // vector inside the FP32-level cutoff (skip_min: leave out the minimum image),
 // phi(r) = erfc(kappa r) / r and, when grad, its gradient added to grad.
+// iL = 1/Lt and rc2 = kRealCut2Mixed Lt^2 come from the caller (loop invariants).
 template <bool kGrad>
-__device__ __forceinline__ float ewald_real_cut(float dx, float dy, float dz, bool skip_min, float Lt, float kappa,
-                                                float* grad) {
-    const float iL = 1.f / Lt;
+__device__ __forceinline__ float ewald_real_cut(float dx, float dy, float dz, bool skip_min, float Lt, float iL,
+                                                float rc2, float kappa, float* grad) {
     dx -= Lt * rintf(dx * iL); dy -= Lt * rintf(dy * iL); dz -= Lt * rintf(dz * iL);
-    const float rc2 = kRealCut2Mixed * Lt * Lt;
     // moving component m of the minimum image by L away from zero adds
-    // L (L - 2 |d_m|) >= 0 to r^2
+    // L (L - 2 |d_m|) > 0 to r^2 (so only the minimum image can sit at r = 0)
     const float r0 = dx * dx + dy * dy + dz * dz;
     const float e0 = Lt * (Lt - 2.f * fabsf(dx)), e1 = Lt * (Lt - 2.f * fabsf(dy)), e2 = Lt * (Lt - 2.f * fabsf(dz));
-    unsigned mask = 0;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const float r2 = r0 + ((c & 1) ? e0 : 0.f) + ((c & 2) ? e1 : 0.f) + ((c & 4) ? e2 : 0.f);
-        if (r2 < rc2 && r2 > 0.f) mask |= 1u << c;
-    }
-    if (skip_min) mask &= ~1u;
+    const float r1 = r0 + e0, r2_ = r0 + e1, r3 = r1 + e1, r4 = r0 + e2;
+    unsigned mask = (r0 < rc2 && r0 > 0.f && !skip_min) ? 1u : 0u;
+    mask |= (r1 < rc2 ? 2u : 0u) | (r2_ < rc2 ? 4u : 0u) | (r3 < rc2 ? 8u : 0u) | (r4 < rc2 ? 16u : 0u) |
+            (r1 + e2 < rc2 ? 32u : 0u) | (r2_ + e2 < rc2 ? 64u : 0u) | (r3 + e2 < rc2 ? 128u : 0u);
     const float sx = dx >= 0.f ? -Lt : Lt, sy = dy >= 0.f ? -Lt : Lt, sz = dz >= 0.f ? -Lt : Lt;
     const float c2k = 1.1283791670955126f * kappa;      // 2 kappa / sqrt(pi)
     const float nk2 = -1.4426950408889634f * kappa * kappa;   // -kappa^2 log2(e)

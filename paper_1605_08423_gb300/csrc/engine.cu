@@ -176,7 +176,7 @@ SysView<T> view(qmc_system* h, int W) {
     s.N = h->N; s.n = h->n; s.G = h->G; s.B = h->B; s.W = W;
     s.np = 4;
     while (s.np < s.n) s.np *= 2;
-    s.L = h->p.L; s.ell = h->p.L / kPi;
+    s.L = h->p.L; s.ell = h->p.L / kPi; s.iL = 1.0 / h->p.L;
     s.b_ee = h->p.b_ee; s.b_ep = h->p.b_ep; s.Zj = 1.0; s.kappa = h->p.ewald_kappa;
     s.zeta = h->d_zeta;
     s.zetat = (const T*)(sizeof(T) == 8 ? (const void*)h->d_zeta : (const void*)h->d_zeta32);

@@ -23,7 +23,7 @@ namespace qmc {
 
 template <typename T>
 struct MLayout {
-    size_t xs, xt, et, gU, lU, Ui, gi, li, facc, gacc, rhot, red, stage, cmask, uni, total;
+    size_t xs, xt, et, gU, lU, Ui, gi, vv, li, facc, gacc, rhot, red, stage, cmask, uni, total;
     // split: the B x n orbital contractions run in the adjoint kernel, so the
     // spin-block work space only holds Y^T / M1 and G (and no epilogue stage)
     __host__ __device__ MLayout(int N, int n, int nk, int mmax, bool split = false) {
@@ -36,6 +36,7 @@ struct MLayout {
         lU = take(sizeof(T) * N);
         Ui = take(sizeof(T) * N);
         gi = take(sizeof(T) * 3 * N);
+        vv = take(sizeof(T) * 3 * N);
         li = take(sizeof(T) * N);
         facc = take(sizeof(double) * 9 * N);
         gacc = take(sizeof(T) * 9 * N);
@@ -179,6 +180,7 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
     T* lU = (T*)(sm + lay.lU);
     T* Ui = (T*)(sm + lay.Ui);
     T* gi = (T*)(sm + lay.gi);
+    T* vvs = (T*)(sm + lay.vv);
     T* li = (T*)(sm + lay.li);
     double* f_dl = (double*)(sm + lay.facc);
     double* f_de = f_dl + 3 * N;
@@ -198,10 +200,10 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const double L = s.L;
     const T ell = (T)s.ell, bee = (T)s.b_ee, bep = (T)s.b_ep, Zj = (T)s.Zj, kap = (T)s.kappa;
-    const T twopiL = T(2.0 * kPi / L), k2 = twopiL * twopiL;
+    const double iL = s.iL;
+    const T twopiL = T(2.0 * kPi * iL), k2 = twopiL * twopiL;
     const double Zn = 1.0;  // proton charge
 
-    const double iL = 1.0 / L;
     // ---- P0: positions and their (sin, cos)(pi x / L)
     for (int idx = tid; idx < 3 * N; idx += nt) {
         const double x = X[(size_t)w * 3 * N + idx];
@@ -311,6 +313,7 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
         for (int mu = 0; mu < 3; ++mu) {
             const T g = gi[3 * i + mu], t = g + gU[3 * i + mu];
             g2 += g * g; t2 += t * t;
+            vvs[3 * i + mu] = t;     // grad_i ln psi, for the e-n pair terms
         }
         kin_p += (double)(li[i] - g2 + lU[i] + t2);
         u_p += (double)Ui[i];
@@ -321,6 +324,7 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
     // ---- P4a: electron-electron real-space Ewald
     double vee_p = 0.0;
     const T Lt = (T)L;
+    const float iLt = 1.f / (float)Lt, rc2 = kRealCut2Mixed * (float)Lt * (float)Lt;
     // balanced cyclic pairing: electron i with i+d (mod N), d = 1..N/2 (d = N/2 only for i < N/2),
     // the distance range split into nparts slices
     for (int tt = tid; tt < nparts * N; tt += nt) {
@@ -333,7 +337,7 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
             if (skip) continue;
             if constexpr (sizeof(T) == 4) {
                 v += ewald_real_cut<false>(xt[3 * i] - xt[3 * j], xt[3 * i + 1] - xt[3 * j + 1],
-                                           xt[3 * i + 2] - xt[3 * j + 2], false, Lt, kap, nullptr);
+                                           xt[3 * i + 2] - xt[3 * j + 2], false, Lt, iLt, rc2, kap, nullptr);
                 continue;
             }
             v += ewald_real<T>(xt[3 * i] - xt[3 * j], xt[3 * i + 1] - xt[3 * j + 1], xt[3 * i + 2] - xt[3 * j + 2], Lt,
@@ -354,8 +358,12 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
     const int nwords = (N + 31) / 32;
     for (int a = warp; a < N; a += nw) {
         T v = 0, gv[3] = {0, 0, 0}, dl[3] = {0, 0, 0}, de[3] = {0, 0, 0};
-        const T* pa = s.ptrig + 6 * a;
-        const T* ra = s.RT + 3 * a;
+        // the nucleus' trig values and position stay in registers over its electrons
+        T pa[6], ra[3];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) pa[c] = s.ptrig[6 * a + c];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ra[c] = s.RT[3 * a + c];
         for (int i = lane; i < N; i += 32) {
             T sd[3], cd[3], t;
             disp_trig(et + 6 * i, pa, ell, sd, cd, t);
@@ -366,12 +374,12 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
                 // FP32-level cutoff (a close pair's nearest image is done in FP64)
                 if (!close) {
                     T vv[3], pl[3], pe[3];
-                    for (int mu = 0; mu < 3; ++mu) vv[mu] = gi[3 * i + mu] + gU[3 * i + mu];
+                    for (int mu = 0; mu < 3; ++mu) vv[mu] = vvs[3 * i + mu];
                     ep_jastrow_f32(sd, cd, ell, k2, bep, Zj, vv, pl, pe);
                     for (int mu = 0; mu < 3; ++mu) { dl[mu] += pl[mu]; de[mu] += pe[mu]; }
                 }
                 v += ewald_real_cut<true>(xt[3 * i] - ra[0], xt[3 * i + 1] - ra[1], xt[3 * i + 2] - ra[2], close, Lt,
-                                          kap, gv);
+                                          iLt, rc2, kap, gv);
                 continue;
             }
             if (close) {   // only the images other than the nearest one here
