@@ -126,7 +126,7 @@ class ClockSampler:
 # dram__bytes_write.sum of one ncu capture at 2048 walkers, scaled by walkers:
 # traffic grows with the walker count); profiles/measure_kernel_h128_w2048_mixed.md.
 # None once the kernel has changed since that capture.
-MEASURE_DRAM_BYTES_PER_WALKER = (594.8032e6 + 85.243136e6) / 2048
+MEASURE_DRAM_BYTES_PER_WALKER = (593.609216e6 + 85.250816e6) / 2048
 
 MEASURE_UNIT = {"ee_jas": 55.0, "ep_jas": 55.0, "ee_ewald": 6.0 + 10.0 * 4.19, "ep": 130.0 + 6.0 + 19.0 * 4.19,
                 "sk": 14.0, "fk": 12.0}
