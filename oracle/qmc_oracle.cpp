@@ -12,8 +12,7 @@
 // to the nuclear positions R are taken by forward-mode dual numbers (type D3),
 // never by hand, so that this file contains no adjoint code.
 //
-// Readings of passages that the paper leaves open are listed at each function
-// and collected in the design doc of the repository.
+// Readings of passages that the paper leaves open are stated at each function.
 //
 // Parity status (each function is pinned by a test under tests/ against a
 // closed form, a textbook constant, a finite difference or brute force):
