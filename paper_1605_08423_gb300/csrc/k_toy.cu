@@ -31,6 +31,8 @@
 
 #include "qmcmd.h"
 
+#include <cmath>
+
 namespace qmc {
 
 namespace {
