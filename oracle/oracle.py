@@ -89,6 +89,10 @@ def lib():
         L.orc_langevin.argtypes = [C.c_int, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
                                    C.c_double, _dp, C.c_int, C.c_double, C.c_int, _dp]
         L.orc_langevin_noise.argtypes = [C.c_uint64, C.c_uint32, C.c_int, _dp]
+        L.orc_langevin_first_predict.restype = C.c_int
+        L.orc_langevin_first_predict.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_double, _dp, _dp]
+        L.orc_langevin_first_correct.restype = C.c_int
+        L.orc_langevin_first_correct.argtypes = [C.c_int, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double, _dp]
         L.orc_num_threads.restype = C.c_int
         L.orc_toy_eval.argtypes = [C.POINTER(ToyArgs), C.c_double, C.c_double, _dp]
         L.orc_toy_step.restype = C.c_int
@@ -229,6 +233,27 @@ def langevin(R, Rprev, f, S, Sprev, T, delta, alpha, xi, noise_correction=False,
     rc = lib().orc_langevin(n, _ptr(R), _ptr(arr[0]), _ptr(arr[1]), _ptr(arr[2]), _ptr(arr[3]), T, delta,
                             alpha, _ptr(arr[4]), int(noise_correction), box, int(scheme), _ptr(out))
     if rc != 0:
+        raise ValueError("S is not positive definite")
+    return out
+
+
+def langevin_first_predict(R, S, T, delta, xi):
+    """First simplified scheme, predict half: y = R + sqrt(2 T D) z, <z z^T> = S^{-1}."""
+    R = np.ascontiguousarray(R, dtype=np.float64).ravel()
+    S, xi = (np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (S, xi))
+    y = np.zeros(R.size)
+    if lib().orc_langevin_first_predict(R.size, _ptr(R), _ptr(S), T, delta, _ptr(xi), _ptr(y)) != 0:
+        raise ValueError("S is not positive definite")
+    return y
+
+
+def langevin_first_correct(R, f, S, Sy, y, delta, box=0.0):
+    """First simplified scheme, correct half: R' = y + D S^{-1} f - 1/2 S^{-1} (S(y) - S)(y - R)."""
+    R = np.ascontiguousarray(R, dtype=np.float64).ravel()
+    f, S, Sy, y = (np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (f, S, Sy, y))
+    out = np.zeros(R.size)
+    if lib().orc_langevin_first_correct(R.size, _ptr(R), _ptr(f), _ptr(S), _ptr(Sy), _ptr(y), delta, box,
+                                        _ptr(out)) != 0:
         raise ValueError("S is not positive definite")
     return out
 

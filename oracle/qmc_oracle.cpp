@@ -728,6 +728,72 @@ static int langevin(int n, const double* R, const double* Rprev, const double* f
 
 
 // ---------------------------------------------------------------------------
+// First simplified scheme (SI, Eq. smartMarkov) for a given S(R) and S(y), in
+// its two halves: predict  y = R + sqrt(2 T D) z,  <z z^T> = S^{-1}(R)
+// (z = L^{-T} xi, S(R) = L L^T), and correct
+//   R' = y + D S^{-1}(R) f(R) - 1/2 S^{-1}(R) [S(y) - S(R)] (y - R).
+// box > 0 wraps R' (not y) into [0, box).  Both return -1 when S(R) is not
+// positive definite.
+// ---------------------------------------------------------------------------
+static bool cholesky(int n, const double* S, std::vector<double>& Lc) {
+    Lc.assign((size_t)n * n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        double s = S[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) s -= Lc[(size_t)j * n + k] * Lc[(size_t)j * n + k];
+        if (!(s > 0)) return false;
+        Lc[(size_t)j * n + j] = std::sqrt(s);
+        for (int i = j + 1; i < n; ++i) {
+            double t = S[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) t -= Lc[(size_t)i * n + k] * Lc[(size_t)j * n + k];
+            Lc[(size_t)i * n + j] = t / Lc[(size_t)j * n + j];
+        }
+    }
+    return true;
+}
+
+static int first_predict(int n, const double* R, const double* S, double T, double delta, const double* xi,
+                         double* y) {
+    std::vector<double> Lc;
+    if (!cholesky(n, S, Lc)) return -1;
+    std::vector<double> z(n);
+    for (int i = n - 1; i >= 0; --i) {                  // L^T z = xi
+        double s = xi[i];
+        for (int k = i + 1; k < n; ++k) s -= Lc[(size_t)k * n + i] * z[k];
+        z[i] = s / Lc[(size_t)i * n + i];
+    }
+    const double amp = T > 0 ? std::sqrt(2.0 * T * delta) : 0.0;
+    for (int i = 0; i < n; ++i) y[i] = R[i] + amp * z[i];
+    return 0;
+}
+
+static int first_correct(int n, const double* R, const double* f, const double* S, const double* Sy,
+                         const double* y, double delta, double box, double* Rout) {
+    std::vector<double> Lc;
+    if (!cholesky(n, S, Lc)) return -1;
+    std::vector<double> g(n), w(n), x(n);
+    for (int i = 0; i < n; ++i) {
+        double v = 0;
+        for (int j = 0; j < n; ++j) v += (Sy[(size_t)i * n + j] - S[(size_t)i * n + j]) * (y[j] - R[j]);
+        g[i] = delta * f[i] - 0.5 * v;
+    }
+    for (int i = 0; i < n; ++i) {                       // L w = g
+        double s = g[i];
+        for (int k = 0; k < i; ++k) s -= Lc[(size_t)i * n + k] * w[k];
+        w[i] = s / Lc[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {                  // L^T x = w
+        double s = w[i];
+        for (int k = i + 1; k < n; ++k) s -= Lc[(size_t)k * n + i] * x[k];
+        x[i] = s / Lc[(size_t)i * n + i];
+    }
+    for (int i = 0; i < n; ++i) {
+        const double r = y[i] + x[i];
+        Rout[i] = box > 0 ? wrap(r, box) : r;
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
 // Rotating-spring toy model (SI, "A simple toy model") and the integrator
 // variants compared on it.  The end point R = (x, y) of a spring of rest
 // length a and stiffness k, free to rotate about the origin:
@@ -1064,6 +1130,15 @@ int orc_langevin(int n, const double* R, const double* Rprev, const double* f, c
                  const double* Sprev, double T, double delta, double alpha, const double* xi,
                  int noise_correction, double box, int scheme, double* Rout) {
     return orc::langevin(n, R, Rprev, f, S, Sprev, T, delta, alpha, xi, noise_correction, box, scheme, Rout);
+}
+
+int orc_langevin_first_predict(int n, const double* R, const double* S, double T, double delta, const double* xi,
+                               double* y) {
+    return orc::first_predict(n, R, S, T, delta, xi, y);
+}
+int orc_langevin_first_correct(int n, const double* R, const double* f, const double* S, const double* Sy,
+                               const double* y, double delta, double box, double* Rout) {
+    return orc::first_correct(n, R, f, S, Sy, y, delta, box, Rout);
 }
 
 // Langevin noise xi_c for component c of MD step m (Philox, purpose P_LANGEVIN).

@@ -180,3 +180,39 @@ def test_fast_scheme_stationary_covariance_closed_form():
     target = 2 * T * np.linalg.inv(K) / (2 - a0 * d)
     rel = np.abs(cov - target) / np.sqrt(np.outer(np.diag(target), np.diag(target)))
     assert rel.max() < 0.06, (cov, target)
+
+
+def test_first_simplified_scheme_closed_forms():
+    """Eq. smartMarkov: at T = 0 it is the drift step R + D S^{-1} f; with S(y) = S
+    its correction vanishes; the S-difference term is written out."""
+    rng = np.random.default_rng(21)
+    n = 5
+    S, Sy = _spd(n, 22), _spd(n, 23)
+    R, f, xi = (rng.standard_normal(n) for _ in range(3))
+    y0 = orc.langevin_first_predict(R, S, 0.0, 0.3, xi)
+    assert np.array_equal(y0, R)
+    assert np.allclose(orc.langevin_first_correct(R, f, S, Sy, y0, 0.3), R + 0.3 * np.linalg.solve(S, f), atol=1e-13)
+    T, d = 0.4, 0.3
+    y = orc.langevin_first_predict(R, S, T, d, xi)
+    Lc = np.linalg.cholesky(S)
+    assert np.allclose(y, R + math.sqrt(2 * T * d) * np.linalg.solve(Lc.T, xi), atol=1e-13)
+    a = orc.langevin_first_correct(R, f, S, S, y, d)
+    assert np.allclose(a, y + d * np.linalg.solve(S, f), atol=1e-12)
+    b = orc.langevin_first_correct(R, f, S, Sy, y, d)
+    assert np.allclose(b - a, -0.5 * np.linalg.solve(S, (Sy - S) @ (y - R)), atol=1e-12)
+
+
+def test_first_simplified_scheme_samples_canonical_with_position_dependent_S():
+    """V = x^2/2, S(x) = 1 + x^2, T = 1: with S evaluated at the predicted point the
+    chain samples e^{-V/T} (<x^2> = 1), as the two-time scheme does."""
+    n, steps, d, T = 48, 6000, 0.02, 1.0
+    rng = np.random.default_rng(24)
+    R = rng.standard_normal(n) * 0.5
+    acc = []
+    for t in range(steps):
+        S = np.diag(1 + R ** 2)
+        y = orc.langevin_first_predict(R, S, T, d, rng.standard_normal(n))
+        R = orc.langevin_first_correct(R, -R, S, np.diag(1 + y ** 2), y, d)
+        if t > 1000:
+            acc.append(R ** 2)
+    assert abs(float(np.mean(acc)) - 1.0) < 0.15
