@@ -138,6 +138,26 @@ int langevin_step_device(qmc_system* h, double* R_dev, const double* f_dev, cons
                          double T_kelvin, double delta, int s_mode, double alpha);
 
 /*
+ * First simplified scheme of the SI (Eq. smartMarkov), which needs S at the
+ * predicted point and therefore a second energy/force evaluation per MD step,
+ * in two calls around it:
+ *   langevin_first_predict  R (host [3N], in) -> y = R + sqrt(2 T Delta) z,
+ *                           <z z^T> = S^{-1}(R) (R overwritten with y, not
+ *                           wrapped); keeps R, f(R), S(R) and the Cholesky
+ *                           factor of S(R) in h.  Noise as in langevin_step.
+ *   (the caller evaluates S(y), e.g. qmc_energy_forces at y)
+ *   langevin_first_correct  y (host [3N], in) -> R' = y + Delta S^{-1}(R) f(R)
+ *                           - 1/2 S^{-1}(R) [S(y) - S(R)] (y - R), wrapped into
+ *                           [0, L); advances the MD step counter.
+ * QMC_OPT_NOISE_CORRECTION applies to the predict half.  A correct call
+ * without a pending predict is INVALID; a checkpoint does not carry a pending
+ * predict.  Errors: INVALID, NOT_PD (S(R)), CUDA.
+ */
+int langevin_first_predict(qmc_system* h, double* R, const double* f, const double* S, double T_kelvin,
+                           double delta);
+int langevin_first_correct(qmc_system* h, double* y, const double* S_y);
+
+/*
  * The same Langevin step for callers that cannot allocate device memory (the
  * paper has no counterpart: this is a deployment entry point).  cudaMalloc and
  * cudaFree may synchronise the device, which a host overlapping many

@@ -67,6 +67,10 @@ struct qmc_system {
     double *d_eval = nullptr;  // eval_config outputs
     // Langevin
     double *d_Rl = nullptr, *d_Rprev = nullptr, *d_f = nullptr, *d_S = nullptr, *d_Sprev = nullptr, *d_Lwork = nullptr;
+    // first simplified scheme between its two halves: R, f(R), S(R) and the factor of S(R)
+    double *d_fsR = nullptr, *d_fsf = nullptr, *d_fsS = nullptr, *d_fsL = nullptr;
+    bool fs_pending = false;
+    double fs_delta = 0.0;
     int* d_err = nullptr;
     std::vector<void*> allocs;
     uint32_t md_step = 0;
@@ -143,6 +147,7 @@ size_t footprint(const qmc_params* p) {
     b += 8 * (4 + 9 * N) + 8 * W * (3 * N + 1) + 8 * (4 + 3 * N + 9 * N * N);   // colsum, dev, out
     b += 8 * (2 * W + 6 * W * N);                    // eval outputs
     b += 8 * (3 * 3 * N + 3 * 9 * N * N);           // Langevin
+    b += 8 * (2 * 3 * N + 2 * 9 * N * N);           // first simplified scheme between its halves
     if (t == 4) {                                    // tensor-core operands (mixed form)
         b += tc_coeff_bytes((int)B, (int)n);
         b += tc_adjoint_coeff_bytes((int)n, (int)G) + 4 * (2 * W * n * n + 9 * W * N) + 8 * W;
@@ -395,6 +400,10 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
     h->d_S = dalloc<double>(h, 9 * (size_t)N * N, &rc);
     h->d_Sprev = dalloc<double>(h, 9 * (size_t)N * N, &rc);
     h->d_Lwork = dalloc<double>(h, 9 * (size_t)N * N, &rc);
+    h->d_fsR = dalloc<double>(h, 3 * N, &rc);
+    h->d_fsf = dalloc<double>(h, 3 * N, &rc);
+    h->d_fsS = dalloc<double>(h, 9 * (size_t)N * N, &rc);
+    h->d_fsL = dalloc<double>(h, 9 * (size_t)N * N, &rc);
     h->d_err = dalloc<int>(h, 1, &rc);
     if (h->mixed && tc_orbitals_supported(n, B)) {
         h->d_chat = dalloc<unsigned char>(h, tc_coeff_bytes(B, n), &rc);
@@ -539,6 +548,52 @@ int langevin_step(qmc_system* h, double* R, const double* f, const double* S, do
                                   alpha);
     if (rc != QMC_OK) return rc;
     cudaMemcpyAsync(R, h->d_Rl, sizeof(double) * n3, cudaMemcpyDeviceToHost, st);
+    return read_err(h);
+}
+
+int langevin_first_predict(qmc_system* h, double* R, const double* f, const double* S, double T_kelvin, double delta) {
+    if (!h || !R || !f || !S || !(delta > 0) || T_kelvin < 0) return QMC_ERR_INVALID;
+    double T_ha = T_kelvin * kBoltzmannHaPerK;
+    if (h->lv_noise_correction) {
+        T_ha -= 0.5 * delta;
+        if (!(T_ha > 0)) return QMC_ERR_INVALID;
+    }
+    const int n3 = 3 * h->N;
+    cudaStream_t st = h->stream;
+    cudaMemcpyAsync(h->d_fsR, R, sizeof(double) * n3, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(h->d_fsf, f, sizeof(double) * n3, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(h->d_fsS, S, sizeof(double) * n3 * n3, cudaMemcpyHostToDevice, st);
+    EventPair ep;
+    prof_begin(h, KC_LANGEVIN, ep);
+    h->nlaunch += 1;
+    launch_first_predict(n3, h->d_fsR, h->d_fsS, h->d_fsL, T_ha, delta, make_key(h->p.seed), h->langevin_step_no,
+                         h->d_Rl, h->d_err, st);
+    prof_end(h, ep);
+    int rc = check_launch();
+    if (rc != QMC_OK) return rc;
+    cudaMemcpyAsync(R, h->d_Rl, sizeof(double) * n3, cudaMemcpyDeviceToHost, st);
+    rc = read_err(h);
+    h->fs_pending = rc == QMC_OK;
+    h->fs_delta = delta;
+    return rc;
+}
+
+int langevin_first_correct(qmc_system* h, double* y, const double* S_y) {
+    if (!h || !y || !S_y || !h->fs_pending) return QMC_ERR_INVALID;
+    const int n3 = 3 * h->N;
+    cudaStream_t st = h->stream;
+    cudaMemcpyAsync(h->d_Rl, y, sizeof(double) * n3, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(h->d_S, S_y, sizeof(double) * n3 * n3, cudaMemcpyHostToDevice, st);
+    EventPair ep;
+    prof_begin(h, KC_LANGEVIN, ep);
+    h->nlaunch += 1;
+    launch_first_correct(n3, h->d_Rl, h->d_fsR, h->d_fsf, h->d_fsS, h->d_S, h->d_fsL, h->fs_delta, h->p.L, st);
+    prof_end(h, ep);
+    int rc = check_launch();
+    if (rc != QMC_OK) return rc;
+    cudaMemcpyAsync(y, h->d_Rl, sizeof(double) * n3, cudaMemcpyDeviceToHost, st);
+    h->fs_pending = false;
+    h->langevin_step_no++;
     return read_err(h);
 }
 

@@ -68,6 +68,12 @@ void launch_langevin(int n3, double* R, double* Rprev, const double* f, const do
                      double* Lwork, double T_ha, double delta, double alpha, Key key, uint32_t md, double box,
                      int identity, int scheme, int* err, cudaStream_t st);
 
+// k_langevin.cu: first simplified scheme, predict (y) and correct (R') halves
+void launch_first_predict(int n3, const double* R, const double* S, double* Lwork, double T_ha, double delta, Key key,
+                          uint32_t md, double* y, int* err, cudaStream_t st);
+void launch_first_correct(int n3, double* y, const double* R, const double* f, const double* S, const double* Sy,
+                          const double* Lwork, double delta, double box, cudaStream_t st);
+
 // k_toy.cu: rotating-spring toy model, one thread per trajectory (FP64).
 struct ToyDev {
     double k, a;          // U = k/2 (|R| - a)^2

@@ -91,6 +91,8 @@ def lib():
         L.qmc_energy_forces_device.argtypes = [vp, vp, vp]
         L.langevin_step.argtypes = [vp, _dp, _dp, _dp, C.c_double, C.c_double, C.c_int, C.c_double]
         L.langevin_step_device.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, C.c_int, C.c_double]
+        L.langevin_first_predict.argtypes = [vp, _dp, _dp, _dp, C.c_double, C.c_double]
+        L.langevin_first_correct.argtypes = [vp, _dp, _dp]
         L.qmc_eval_config.argtypes = [vp, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
         L.qmc_get_walkers.argtypes = [vp, _dp]
         L.qmc_set_walkers.argtypes = [vp, _dp]
@@ -256,6 +258,19 @@ class QMCSystem:
         """R_dev: float64 cuda tensor [N,3]; out_dev: float64 cuda tensor [4+3N+9N^2] (asynchronous)."""
         _chk(lib().qmc_energy_forces_device(self._h, C.c_void_p(R_dev.data_ptr()), C.c_void_p(out_dev.data_ptr())),
              "qmc_energy_forces_device")
+
+    def langevin_first_predict(self, R, f, S, T_kelvin, delta) -> np.ndarray:
+        """First simplified scheme, predict half: returns y (S(R), f(R) kept in the handle)."""
+        y = _f64(R).copy().ravel()
+        _chk(lib().langevin_first_predict(self._h, _p(y), _p(_f64(f)), _p(_f64(S)), T_kelvin, delta),
+             "langevin_first_predict")
+        return y
+
+    def langevin_first_correct(self, y, S_y) -> np.ndarray:
+        """First simplified scheme, correct half: returns R' given S at the predicted point."""
+        Rn = _f64(y).copy().ravel()
+        _chk(lib().langevin_first_correct(self._h, _p(Rn), _p(_f64(S_y))), "langevin_first_correct")
+        return Rn
 
     def langevin_step_device(self, R_dev, f_dev, S_dev, T_kelvin, delta, s_mode=QMC_S_COV, alpha=0.0):
         _chk(lib().langevin_step_device(self._h, C.c_void_p(R_dev.data_ptr()), C.c_void_p(f_dev.data_ptr()),

@@ -220,6 +220,34 @@ def test_langevin_integrator_variants_match_oracle(scheme, noise_corr):
         sysg.set_integrator(7)
 
 
+def test_langevin_first_simplified_scheme_matches_oracle():
+    """Eq. smartMarkov in its two halves (predict y, the caller's S(y), correct)."""
+    wl = synth.workload("h16", walkers=2)
+    sysg = q.QMCSystem(q.Config.from_workload(wl), wl.R)
+    n = 3 * wl.N
+    rng = np.random.default_rng(6)
+    T_K, delta = 1500.0, 0.004
+    T = T_K * synth.K_B_HARTREE_PER_KELVIN
+    R = wl.R.ravel().copy()
+    for step in range(3):
+        f = rng.standard_normal(n)
+        S, Sy = _spd(n, 30 + step) * 1e-3, _spd(n, 40 + step) * 1e-3
+        xi = orc.langevin_noise(wl.seed, step, n)
+        yo = orc.langevin_first_predict(R, S, T, delta, xi)
+        yg = sysg.langevin_first_predict(R, f, S, T_K, delta)
+        assert np.max(np.abs(yg - yo)) < 1e-10, (step, np.max(np.abs(yg - yo)))
+        Ro = orc.langevin_first_correct(R, f, S, Sy, yo, delta, box=wl.L)
+        Rg = sysg.langevin_first_correct(yg, Sy)
+        assert np.max(np.abs(Rg - Ro)) < 1e-10, (step, np.max(np.abs(Rg - Ro)))
+        R = Ro
+    with pytest.raises(q.QMCError) as e:          # no pending predict
+        sysg.langevin_first_correct(R, np.eye(n))
+    assert e.value.code == -1
+    with pytest.raises(q.QMCError) as e:
+        sysg.langevin_first_predict(R, np.zeros(n), -np.eye(n), T_K, delta)
+    assert e.value.code == -4
+
+
 def test_autograd_function_backward_is_minus_force():
     import torch
     wl = synth.workload("h16", walkers=64, sweeps=10, warmup=5)
