@@ -42,6 +42,7 @@ class Params(C.Structure):
         ("L", C.c_double), ("b_ee", C.c_double), ("b_ep", C.c_double), ("Z", C.c_double),
         ("Zj", C.c_double), ("kappa", C.c_double),
         ("zeta", C.POINTER(C.c_double)), ("coeff", C.POINTER(C.c_double)),
+        ("zeta_j", C.c_double), ("fj", C.POINTER(C.c_double)),
     ]
 
 
@@ -82,6 +83,8 @@ def lib():
         L.orc_eval_configs.restype = C.c_int
         L.orc_eval_configs.argtypes = [C.POINTER(Params), _dp, C.c_int, _dp, C.c_int, _dp, _dp, _dp, _dp]
         L.orc_init_walkers.argtypes = [C.POINTER(Params), _dp, C.c_int, C.c_uint64, _dp]
+        L.orc_jastrow_delta.restype = C.c_double
+        L.orc_jastrow_delta.argtypes = [C.POINTER(Params), _dp, _dp, C.c_int, _dp]
         L.orc_vmc.argtypes = [C.POINTER(Params), _dp, C.POINTER(ChainArgs), _dp, _dp,
                               C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
         L.orc_reduce.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
@@ -125,17 +128,21 @@ class System:
     kappa: float | None = None
     mmax: int = 6
     periodic: bool = True
+    zeta_j: float = 0.7933844        # exponent of the U_{3+4} Jastrow orbitals (SI's Z_1 = Z_2)
+    fj: np.ndarray | None = None     # [N][N] symmetric U_{3+4} coefficients; None: term off
 
     def cparams(self) -> Params:
         self._zeta = np.ascontiguousarray(self.zeta, dtype=np.float64)
         self._coeff = np.ascontiguousarray(self.coeff, dtype=np.float64)
+        self._fj = None if self.fj is None else np.ascontiguousarray(self.fj, dtype=np.float64).reshape(self.N, self.N)
         n_up = self.N // 2 if self.n_up is None else self.n_up
         n_dn = self.N - n_up if self.n_dn is None else self.n_dn
         kappa = 5.0 / self.L if self.kappa is None else self.kappa
         return Params(self.N, n_up, n_dn, self._coeff.shape[1], len(self._zeta), int(self.periodic),
                       self.mmax, 0, self.L, self.b_ee, self.b_ep, self.Z,
                       self.Z if self.Zj is None else self.Zj, kappa,
-                      _ptr(self._zeta), _ptr(self._coeff))
+                      _ptr(self._zeta), _ptr(self._coeff), self.zeta_j,
+                      _ptr(self._fj) if self._fj is not None else C.cast(None, _dp))
 
     @property
     def n_elec(self) -> int:
@@ -188,6 +195,13 @@ def eval_configs(sys: System, R, X, derivs=True):
     if rc != 0:
         raise ValueError("singular Slater block")
     return lp, el, dl, de
+
+
+def jastrow_delta(sys: System, R, X, i, xn) -> float:
+    """U(X with electron i at xn) - U(X), as the oracle's Metropolis step computes it."""
+    p = sys.cparams()
+    R, X, xn = (np.ascontiguousarray(a, dtype=np.float64) for a in (R, X, xn))
+    return lib().orc_jastrow_delta(C.byref(p), _ptr(R), _ptr(X), int(i), _ptr(xn))
 
 
 def init_walkers(sys: System, R, W, seed):

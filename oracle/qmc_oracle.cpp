@@ -22,6 +22,9 @@
 //                          translation / permutation / coefficient invariances, cusps
 //   vmc chain ............ importance-sampled brute-force integral on a tiny system
 //   reduce ............... i.i.d. synthetic samples with known covariance
+//   U_{3+4} Jastrow ...... closed form on one nucleus, finite differences in r
+//                          and R, permutation invariance, linearity in f, the
+//                          Metropolis delta against full evaluations
 //   langevin_step ........ harmonic closed forms (steepest descent, Newton step,
 //                          stationary covariance, autocorrelation); fast and
 //                          simple-rule variants against their closed forms
@@ -150,6 +153,10 @@ struct Params {
     double  kappa;        // Ewald splitting parameter
     const double* zeta;   // [n_gauss]
     const double* coeff;  // [N*n_gauss][n_orb], row b = a*n_gauss + g
+    // 3- and 4-body e-e-n-n Jastrow U_{3+4} (SI, Jastrow section), one
+    // periodised Gaussian exp(-zeta_j |d|^2) per nucleus; fj = null: term off
+    double zeta_j;
+    const double* fj;     // [N][N] symmetric coefficients f^{ab}
 };
 
 // ---------------------------------------------------------------------------
@@ -440,6 +447,31 @@ static WfOut<S> wavefunction(const Params& p, const S* R, const double* X) {
             lU[i] += lp;
         }
     }
+    // U_{3+4} = sum_{i<j} sum_{a,b} f^{ab} chi_a(r_i) chi_b(r_j) (SI, e-e-n-n term with
+    // one Jastrow orbital per nucleus); its gradient and Laplacian in r_i are
+    // the pair terms containing i differentiated in r_i.  Written as the
+    // plain pair sum: O(Ne^2 N^2).
+    if (p.fj) {
+        const int N = p.N;
+        std::vector<S> chi((size_t)Ne * N), gchi((size_t)Ne * N * 3), lchi((size_t)Ne * N);
+        for (int i = 0; i < Ne; ++i)
+            for (int a = 0; a < N; ++a) {
+                S gr[3];
+                gaussian(p, X + 3 * i, R + 3 * a, p.zeta_j, chi[(size_t)i * N + a], gr, lchi[(size_t)i * N + a]);
+                for (int mu = 0; mu < 3; ++mu) gchi[((size_t)i * N + a) * 3 + mu] = gr[mu];
+            }
+        for (int i = 0; i < Ne; ++i)
+            for (int j = 0; j < Ne; ++j) {
+                if (j == i) continue;
+                for (int a = 0; a < N; ++a) {
+                    S fx(0.0);   // sum_b f^{ab} chi_b(r_j)
+                    for (int b = 0; b < N; ++b) fx += p.fj[(size_t)a * N + b] * chi[(size_t)j * N + b];
+                    if (j > i) U += chi[(size_t)i * N + a] * fx;
+                    for (int mu = 0; mu < 3; ++mu) gU[i * 3 + mu] += gchi[((size_t)i * N + a) * 3 + mu] * fx;
+                    lU[i] += lchi[(size_t)i * N + a] * fx;
+                }
+            }
+    }
     out.lnpsi += U;
     // kinetic energy: lap_i ln psi = (l_i - |g_i|^2) + lap_i U ; grad_i ln psi = g_i + grad_i U
     S kin(0.0);
@@ -533,6 +565,12 @@ static double pair_u(const Params& p, const double* x, const double* c, bool ee)
     return u;
 }
 
+static double jastrow_orbital(const Params& p, const double* x, const double* Ra) {
+    double c, gr[3], lp;
+    gaussian<double>(p, x, Ra, p.zeta_j, c, gr, lp);
+    return c;
+}
+
 static double jastrow_delta(const Params& p, const double* R, const double* X, int i, const double* xn) {
     const int Ne = p.n_up + p.n_dn;
     double du = 0;
@@ -541,6 +579,17 @@ static double jastrow_delta(const Params& p, const double* R, const double* X, i
         du += pair_u(p, xn, X + 3 * j, true) - pair_u(p, X + 3 * i, X + 3 * j, true);
     }
     for (int a = 0; a < p.N; ++a) du += pair_u(p, xn, R + 3 * a, false) - pair_u(p, X + 3 * i, R + 3 * a, false);
+    if (p.fj) {   // U_{3+4}: the pairs (i, j) with chi(r_i) replaced
+        const int N = p.N;
+        for (int a = 0; a < N; ++a) {
+            const double dchi = jastrow_orbital(p, xn, R + 3 * a) - jastrow_orbital(p, X + 3 * i, R + 3 * a);
+            for (int j = 0; j < Ne; ++j) {
+                if (j == i) continue;
+                for (int b = 0; b < N; ++b)
+                    du += dchi * p.fj[(size_t)a * N + b] * jastrow_orbital(p, X + 3 * j, R + 3 * b);
+            }
+        }
+    }
     return du;
 }
 
@@ -1097,6 +1146,11 @@ int orc_eval_configs(const orc::Params* p, const double* R, int nconf, const dou
             for (int k = 0; k < N3; ++k) { dlnpsi[(size_t)c * N3 + k] = r.dlnpsi[k]; del[(size_t)c * N3 + k] = r.del[k]; }
     }
     return bad ? -1 : 0;
+}
+
+// Change of U when electron i of X moves to xn (the Metropolis Jastrow ratio's exponent).
+double orc_jastrow_delta(const orc::Params* p, const double* R, const double* X, int i, const double* xn) {
+    return orc::jastrow_delta(*p, R, X, i, xn);
 }
 
 // Walker start positions, X [W][Ne][3].
