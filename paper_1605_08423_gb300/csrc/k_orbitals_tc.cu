@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
     float* ptr_s = (float*)(sB + (size_t)kBbuf * P * NM * 128);  // [N][6] proton trig
     __shared__ float rtrig[kRows][6];
     __shared__ float zs[16];   // zeta_g and zeta_g log2(e), g < 8
-    __shared__ uint64_t mbarh[2], fullh[2];
+    __shared__ uint64_t mbarh[2], fullh[2], bbar;
     __shared__ uint32_t tbase;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nt = blockDim.x;
     const int row0 = blockIdx.x * kRows;
@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
     if (tid == 0) {
         tc::mbar_init(&mbarh[0], 1); tc::mbar_init(&mbarh[1], 1);
         tc::mbar_init(&fullh[0], 16); tc::mbar_init(&fullh[1], 16);   // one arrival per producer warp
+        tc::mbar_init(&bbar, 1);                                         // B chunk bulk copies (value kernel)
         tc::fence_mbar_init();
     }
     for (int idx = tid; idx < kRows * 3; idx += nt) {
@@ -285,14 +286,23 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
             if (idx < nbv) dst[idx] = bnext[v];
         }
     };
-    fetch_b(0);
-    store_b();
+    // Q = 1: B comes by one bulk copy per chunk (a single thread, no
+    // registers), issued as soon as the previous chunk's MMAs are done, so it
+    // lands while the threads evaluate the chunk's basis functions; the
+    // issuing thread waits for it before the MMAs.
+    const uint32_t bcopy = (uint32_t)(P * NM * 128);   // a whole chunk: the prepared pieces are the P used
+    if constexpr (Q == 1) {
+        if (tid == 0) {
+            tc::mbar_arrive_expect_tx(&bbar, bcopy);
+            tc::bulk_g2s(sB, chat, bcopy, &bbar);
+        }
+    } else {
+        fetch_b(0);
+        store_b();
+    }
     for (int c = 0; c < nch; ++c) {
         if constexpr (Q == 4) {
             if (c + 1 < nch) fetch_b(c + 1);
-        } else if (c > 0) {
-            fetch_b(c);
-            store_b();
         }
         // A operand: one item = (row, 4 consecutive basis functions); the
         // displacement to a nucleus is computed once for its Gaussians.  In the
@@ -386,6 +396,7 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
         tc::fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
+            if (Q == 1 && !tc::mbar_wait(&bbar, (uint32_t)(c & 1), 1ll << 26)) ok = false;   // B of chunk c
             tc::fence_after_sync();
             const uint32_t b0 = tc::smem_addr(sB), bstep = (uint32_t)NM * 128;
 #pragma unroll
@@ -412,8 +423,14 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
         if (!tc::mbar_wait(&mbarh[0], (uint32_t)(c & 1), 1ll << 26)) ok = false;
         tc::fence_after_sync();
         if (Q == 4 && c + 1 < nch) store_b();   // the MMAs of chunk c have read sB
+        if (Q == 1 && tid == 0 && c + 1 < nch) {
+            tc::mbar_arrive_expect_tx(&bbar, bcopy);
+            tc::bulk_g2s(sB, chat + (size_t)(c + 1) * chunk_bytes, bcopy, &bbar);
+        }
         __syncthreads();
     }
+    // a copy still in flight after a wait that gave up lands before the CTA leaves
+    if (Q == 1 && tid == 0 && !ok) tc::mbar_wait(&bbar, (uint32_t)((nch - 1) & 1), 1ll << 26);
     }
     if (!ok && lane == 0) raise_err(s.err, kErrTimeout);
 
