@@ -59,3 +59,20 @@ def test_footprint_scales_with_walkers(lib):
     a = q.footprint_bytes(q.Config.from_workload(wl, walkers=1000))
     b = q.footprint_bytes(q.Config.from_workload(wl, walkers=2000))
     assert 1.8 < b / a < 2.1
+
+
+def test_toy_parameters_validated_without_gpu(lib):
+    # qmc_toy_params: 7 doubles, 4 int32, uint64
+    assert C.sizeof(q.ToyParams) == 7 * 8 + 4 * 4 + 8
+    xy0 = (C.c_double * 4)()
+    out = (C.c_double * 14)()
+    bad = [dict(delta=0.0), dict(lam=0.0), dict(T=-1.0), dict(alpha=-0.1), dict(n_steps=-1),
+           dict(n_steps=3, n_burn=4), dict(scheme=6), dict(scheme=-1), dict(s_mode=2)]
+    for kw in bad:
+        p = q.toy_params(**kw)
+        assert lib.qmc_toy_langevin(C.byref(p), 2, xy0, out) == -1, kw
+        assert lib.qmc_toy_langevin_device(C.byref(p), 2, None, None, None) == -1, kw
+    p = q.toy_params()
+    assert lib.qmc_toy_langevin(C.byref(p), -1, xy0, out) == -1
+    assert lib.qmc_toy_langevin(C.byref(p), 2, None, out) == -1
+    assert lib.qmc_toy_langevin(C.byref(p), 0, None, None) == 0      # nothing to do
