@@ -71,6 +71,12 @@ typedef struct {
     uint64_t seed;            /* Philox4x32-10 key                                       */
     const double* zeta;       /* [n_gauss] exponents, bohr^-2 (copied)                   */
     const double* coeff;      /* [N*n_gauss][N/2] orbital coefficients (copied)          */
+    /* 3- and 4-body e-e-n-n Jastrow term of the SI, one periodised Gaussian
+     * chi_a(r) = exp(-zeta_j |d(r - R_a)|^2) per proton:
+     *   U += sum_{i<j} sum_{a,b} fj[a][b] chi_a(r_i) chi_b(r_j).
+     * fj = NULL switches it off.  FP64 form with N <= 64 only (INVALID otherwise). */
+    double zeta_j;            /* Jastrow-orbital exponent, bohr^-2 (the SI uses 0.7933844) */
+    const double* fj;         /* [N][N] symmetric coefficients (copied), or NULL         */
 } qmc_params;
 
 /* Result of one energy/force evaluation.  f and cov are caller-allocated host

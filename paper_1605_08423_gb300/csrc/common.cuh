@@ -145,6 +145,8 @@ struct SysView {
     const double* vconst;   // [1] proton-proton real-space + self energy
     const double* dvpp;     // [3N] d(proton-proton real-space energy)/dR
     int* err;
+    const double* fj;       // [N][N] e-e-n-n Jastrow coefficients (FP64 form), or null
+    double zeta_j;          // their Gaussians' exponent
 };
 
 // Radial-function chain for f(t), t = |d|^2 with d the sin-periodised

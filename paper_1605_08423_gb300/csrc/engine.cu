@@ -31,7 +31,8 @@ struct EventPair { cudaEvent_t a, b; int cls; };
 
 struct qmc_system {
     qmc_params p;
-    std::vector<double> zeta_h, coeff_h;
+    std::vector<double> zeta_h, coeff_h, fj_h;
+    double* d_fj = nullptr;    // e-e-n-n Jastrow coefficients [N][N] (FP64 form)
     int N, n, G, B, W, nk, mmax;
     bool mixed;
     cudaStream_t stream = nullptr, own_stream = nullptr;
@@ -124,6 +125,7 @@ int validate(const qmc_params* p) {
     if (p->precision != QMC_FP64 && p->precision != QMC_MIXED) return QMC_ERR_INVALID;
     if (p->ewald_mmax < 1 || p->ewald_mmax > 12) return QMC_ERR_INVALID;
     if (!(p->L > 0) || !(p->ewald_kappa > 0) || !(p->sigma > 0) || p->b_ee < 0 || p->b_ep < 0) return QMC_ERR_INVALID;
+    if (p->fj && (p->precision != QMC_FP64 || p->n_protons > 64 || !(p->zeta_j > 0))) return QMC_ERR_INVALID;
     if (p->n_sweeps / p->measure_every < 1) return QMC_ERR_INVALID;
     return QMC_OK;
 }
@@ -148,6 +150,7 @@ size_t footprint(const qmc_params* p) {
     b += 8 * (2 * W + 6 * W * N);                    // eval outputs
     b += 8 * (3 * 3 * N + 3 * 9 * N * N);           // Langevin
     b += 8 * (2 * 3 * N + 2 * 9 * N * N);           // first simplified scheme between its halves
+    if (p->fj) b += 8 * N * N;                       // e-e-n-n Jastrow coefficients
     if (t == 4) {                                    // tensor-core operands (mixed form)
         b += tc_coeff_bytes((int)B, (int)n);
         b += tc_adjoint_coeff_bytes((int)n, (int)G) + 4 * (2 * W * n * n + 9 * W * N) + 8 * W;
@@ -194,6 +197,7 @@ SysView<T> view(qmc_system* h, int W) {
     s.nk = h->nk; s.mmax = h->mmax;
     s.kvec = h->d_kvec; s.kw = h->d_kw; s.eikR = h->d_eikR; s.rho_p = h->d_rhop;
     s.vconst = h->d_vconst; s.dvpp = h->d_dvpp; s.err = h->d_err;
+    s.fj = h->d_fj; s.zeta_j = h->p.zeta_j;
     return s;
 }
 
@@ -353,6 +357,10 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
     h->coeff_h.assign(p->coeff, p->coeff + (size_t)h->B * h->n);
     h->p.zeta = h->zeta_h.data();
     h->p.coeff = h->coeff_h.data();
+    if (p->fj) {
+        h->fj_h.assign(p->fj, p->fj + (size_t)h->N * h->N);
+        h->p.fj = h->fj_h.data();
+    }
     std::vector<int4> kv;
     enumerate_kvec(h->mmax, kv);
     h->nk = (int)kv.size();
@@ -405,6 +413,7 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
     h->d_fsS = dalloc<double>(h, 9 * (size_t)N * N, &rc);
     h->d_fsL = dalloc<double>(h, 9 * (size_t)N * N, &rc);
     h->d_err = dalloc<int>(h, 1, &rc);
+    if (!h->fj_h.empty()) h->d_fj = dalloc<double>(h, (size_t)N * N, &rc);
     if (h->mixed && tc_orbitals_supported(n, B)) {
         h->d_chat = dalloc<unsigned char>(h, tc_coeff_bytes(B, n), &rc);
         h->use_tc = true;
@@ -428,6 +437,7 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
     cudaMemcpyAsync(h->d_R, R, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(h->d_zeta, h->zeta_h.data(), sizeof(double) * h->G, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(h->d_C64, h->coeff_h.data(), sizeof(double) * B * n, cudaMemcpyHostToDevice, st);
+    if (h->d_fj) cudaMemcpyAsync(h->d_fj, h->fj_h.data(), sizeof(double) * N * N, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(h->d_C32, c32.data(), sizeof(float) * B * n, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(h->d_zeta32, z32.data(), sizeof(float) * h->G, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(h->d_kvec, kv.data(), sizeof(int4) * nk, cudaMemcpyHostToDevice, st);

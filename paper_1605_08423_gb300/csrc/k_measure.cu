@@ -50,7 +50,10 @@ struct MLayout {
         while (np < n) np *= 2;
         const size_t spin = split ? sizeof(T) * 2 * (size_t)np * (np + 4) : sizeof(T) * (size_t)np * (3 * (np + 4) + 68);
         const size_t jpart = sizeof(T) * 5 * 256;   // P1 partials: nparts * N <= 256 rows of 5
+        // e-e-n-n Jastrow work space of the FP64 form: c [N], S [N][3], 8 warps x 5N
+        const size_t j34 = sizeof(T) == 8 ? sizeof(T) * 44 * (size_t)N : 0;
         size_t u = etab > spin ? etab : spin;
+        u = u > j34 ? u : j34;
         uni = take(u > jpart ? u : jpart);
         total = o;
     }
@@ -153,6 +156,24 @@ __device__ __forceinline__ void ep_pair(const S sd[3], const S cd[3], S ell, S k
 #pragma unroll
     for (int mu = 0; mu < 3; ++mu) { dl[mu] = -rd.g[mu]; de[mu] = hv[mu] + S(0.5) * rd.tl[mu]; }
     v = ewald_real<S>(dx, dy, dz, L, kap, g);
+}
+
+// e-e-n-n Jastrow orbital chi_a(r_i) = exp(-zeta |d|^2) of electron trig ei and
+// nucleus trig pa with its gradient, Hessian, Laplacian and gradient of the
+// Laplacian in the electron coordinate (radial chain of f(t) = exp(-zeta t)).
+template <typename T>
+__device__ __forceinline__ T jas34_orbital(const T* ei, const T* pa, T ell, T zeta, T k2, RadialDerivs<T>& rd) {
+    T sd[3], cd[3], t;
+    disp_trig(ei, pa, ell, sd, cd, t);
+    T p[3], q[3];
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) {
+        p[mu] = ell * sd[mu] * cd[mu];
+        q[mu] = cd[mu] * cd[mu] - sd[mu] * sd[mu];
+    }
+    const T e = qexp(-zeta * t);
+    radial_chain(p, q, -zeta * e, zeta * zeta * e, -zeta * zeta * zeta * e, k2, rd);
+    return e;
 }
 
 // kSplit: the B x n orbital contractions and their basis-derivative epilogue
@@ -305,6 +326,60 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
     }
     __syncthreads();
 
+    // ---- P2b (FP64 form with the e-e-n-n Jastrow term):
+    //   U34 = sum_{i<j} chi_i^T F chi_j = 1/2 sum_i chi_i . w_i,  w_i = F (c - chi_i),  c = sum_j chi_j,
+    //   grad_i U34 = sum_a grad chi_a(r_i) w_ia,  lap_i U34 = sum_a lap chi_a(r_i) w_ia,
+    // added to grad U, lap U and the per-electron U sums.  c and S_a = sum_j grad chi_a(r_j)
+    // stay in the work space for the force terms after P3.
+    T* j34c = (T*)uni;               // [N]
+    T* j34S = j34c + N;              // [N][3]
+    T* j34w = j34S + 3 * N;          // per warp: chi_i [N], grad chi_i [N][3], lap chi_i [N]
+    if constexpr (sizeof(T) == 8) {
+        if (s.fj) {
+            const T zj = (T)s.zeta_j;
+            for (int a = tid; a < N; a += nt) {
+                T c = 0, g[3] = {0, 0, 0};
+                for (int j = 0; j < N; ++j) {
+                    RadialDerivs<T> rd;
+                    c += jas34_orbital(et + 6 * j, s.ptrig + 6 * a, ell, zj, k2, rd);
+                    for (int mu = 0; mu < 3; ++mu) g[mu] += rd.g[mu];
+                }
+                j34c[a] = c;
+                for (int mu = 0; mu < 3; ++mu) j34S[3 * a + mu] = g[mu];
+            }
+            __syncthreads();
+            T* stc = j34w + (size_t)warp * 5 * N;
+            for (int i = warp; i < N; i += nw) {
+                for (int a = lane; a < N; a += 32) {
+                    RadialDerivs<T> rd;
+                    stc[a] = jas34_orbital(et + 6 * i, s.ptrig + 6 * a, ell, zj, k2, rd);
+                }
+                __syncwarp();
+                T g[3] = {0, 0, 0}, l = 0, u = 0;
+                for (int a = lane; a < N; a += 32) {
+                    RadialDerivs<T> rd;
+                    const T chi = jas34_orbital(et + 6 * i, s.ptrig + 6 * a, ell, zj, k2, rd);
+                    const double* fa = s.fj + (size_t)a * N;
+                    T w = 0;
+                    for (int b = 0; b < N; ++b) w += (T)fa[b] * (j34c[b] - stc[b]);
+                    for (int mu = 0; mu < 3; ++mu) g[mu] += rd.g[mu] * w;
+                    l += rd.lap * w;
+                    u += chi * w;
+                }
+                for (int mu = 0; mu < 3; ++mu) g[mu] = warp_sum(g[mu]);
+                l = warp_sum(l);
+                u = warp_sum(u);
+                if (lane == 0) {
+                    for (int mu = 0; mu < 3; ++mu) gU[3 * i + mu] += g[mu];
+                    lU[i] += l;
+                    Ui[i] += T(0.5) * u;
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+        }
+    }
+
     // ---- P3: kinetic energy and U
     double kin_p = 0.0, u_p = 0.0;
     for (int i = tid; i < N; i += nt) {
@@ -320,6 +395,54 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
     }
     const double kin = block_sum(kin_p, red);
     const double Utot = block_sum(u_p, red + 32);
+
+    // ---- P3b (FP64 form with the e-e-n-n Jastrow term): its terms of d ln psi / dR_a
+    // and dE_L / dR_a.  With s_a^(i) = S_a - grad chi_a(r_i), v_ia = sum_b grad chi_b(r_i) f_ba,
+    // lam_ia = sum_b lap chi_b(r_i) f_ba and vv_i = g_i + grad_i U:
+    //   dlnpsi/dR_a += -sum_i grad chi_a(r_i) w_ia
+    //   dE_L/dR_a   += sum_i [ 1/2 (grad lap chi_a(r_i) w_ia + lam_ia s_a^(i))
+    //                          + (Hess chi_a(r_i) vv_i) w_ia + (vv_i . v_ia) s_a^(i) ]
+    // (the R_a-derivative of -1/2 sum_i [lap_i U34 + 2 vv_i . grad_i U34]).
+    if constexpr (sizeof(T) == 8) {
+        if (s.fj) {
+            const T zj = (T)s.zeta_j;
+            T* st = j34w + (size_t)warp * 5 * N;   // chi_i [N], grad chi_i [N][3], lap chi_i [N]
+            for (int i = warp; i < N; i += nw) {
+                for (int a = lane; a < N; a += 32) {
+                    RadialDerivs<T> rd;
+                    st[a] = jas34_orbital(et + 6 * i, s.ptrig + 6 * a, ell, zj, k2, rd);
+                    for (int mu = 0; mu < 3; ++mu) st[N + 3 * a + mu] = rd.g[mu];
+                    st[4 * N + a] = rd.lap;
+                }
+                __syncwarp();
+                T vv[3];
+                for (int mu = 0; mu < 3; ++mu) vv[mu] = gi[3 * i + mu] + gU[3 * i + mu];
+                for (int a = lane; a < N; a += 32) {
+                    RadialDerivs<T> rd;
+                    jas34_orbital(et + 6 * i, s.ptrig + 6 * a, ell, zj, k2, rd);
+                    const double* fa = s.fj + (size_t)a * N;   // row a = column a (f symmetric)
+                    T w = 0, v[3] = {0, 0, 0}, lam = 0;
+                    for (int b = 0; b < N; ++b) {
+                        const T f = (T)fa[b];
+                        w += f * (j34c[b] - st[b]);
+                        for (int mu = 0; mu < 3; ++mu) v[mu] += st[N + 3 * b + mu] * f;
+                        lam += st[4 * N + b] * f;
+                    }
+                    T hv[3];
+                    hess_mul(rd.h, vv, hv);
+                    const T vvv = vv[0] * v[0] + vv[1] * v[1] + vv[2] * v[2];
+                    for (int mu = 0; mu < 3; ++mu) {
+                        const T sa = j34S[3 * a + mu] - rd.g[mu];
+                        atomicAdd(&f_dl[3 * a + mu], (double)(-rd.g[mu] * w));
+                        atomicAdd(&f_de[3 * a + mu],
+                                  (double)(T(0.5) * (rd.tl[mu] * w + lam * sa) + hv[mu] * w + vvv * sa));
+                    }
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+        }
+    }
 
     // ---- P4a: electron-electron real-space Ewald
     double vee_p = 0.0;

@@ -23,10 +23,12 @@ struct SweepSmem {
     static constexpr int VE = 16 / sizeof(T);   // elements per 16-byte vector
     __host__ __device__ static int nv(int n) { return (n + VE - 1) / VE * VE; }
     __host__ __device__ static int ld(int n) { return nv(n) + VE; }
-    // per warp: G^T [n][ld], old row [nv], phi' [nv], trig [6N]
+    // per warp: G^T [n][ld], old row [nv], phi' [nv], trig [6N], and for the
+    // e-e-n-n Jastrow term three [N] vectors (sum over electrons of chi_a,
+    // chi_a at the moving electron and at its proposal)
     __host__ __device__ static size_t warp_bytes(int N, int n) {
         size_t b = ((size_t)n * ld(n) + 2 * (size_t)nv(n)) * sizeof(T);
-        b += (size_t)6 * N * sizeof(T);
+        b += (size_t)9 * N * sizeof(T);
         return (b + 15) & ~size_t(15);
     }
 };
@@ -48,6 +50,19 @@ __device__ __forceinline__ float4 vaxpy(float4 g, float c, float4 r) {
 }
 __device__ __forceinline__ double2 vaxpy(double2 g, double c, double2 r) {
     return make_double2(g.x - c * r.x, g.y - c * r.y);
+}
+
+// exp(-zeta |d|^2) for the periodised displacement between two points given
+// by their (sin, cos)(pi x / L) triples (e-e-n-n Jastrow orbital)
+template <typename T>
+__device__ __forceinline__ T jas_orbital(const T* a, const T* b, T ell, T zeta) {
+    T t = 0;
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) {
+        const T sd = a[mu] * b[3 + mu] - a[3 + mu] * b[mu];
+        t += sd * sd;
+    }
+    return qexp(-zeta * ell * ell * t);
 }
 
 template <typename T>
@@ -80,6 +95,9 @@ __global__ void __launch_bounds__(512) sweep_kernel(SysView<T> s, double* __rest
     T* rowb = Gs + (size_t)n * ld;
     T* phi = rowb + nv;
     T* et = phi + nv;
+    T* c34 = et + 6 * N;     // [N] sum over electrons of chi_a (e-e-n-n Jastrow term, FP64 form)
+    T* cho = c34 + N;        // [N] chi_a at the moving electron
+    T* chn = cho + N;        // [N] chi_a at its proposal
 
     for (int idx = threadIdx.x; idx < 6 * N; idx += blockDim.x) ptr_s[idx] = s.ptrig[idx];
     __syncthreads();
@@ -98,6 +116,16 @@ __global__ void __launch_bounds__(512) sweep_kernel(SysView<T> s, double* __rest
         et[6 * i + 3 + mu] = cs;
     }
     __syncwarp();
+    const bool j34 = sizeof(T) == 8 && s.fj != nullptr;
+    const T zj = (T)s.zeta_j;
+    if (j34) {
+        for (int a = lane; a < N; a += 32) {
+            T c = 0;
+            for (int j = 0; j < N; ++j) c += jas_orbital(et + 6 * j, ptr_s + 6 * a, ell, zj);
+            c34[a] = c;
+        }
+        __syncwarp();
+    }
     for (int j = n + lane; j < nv; j += 32) phi[j] = T(0);   // padding stays zero
     unsigned long long naccept = 0;
     // the next move's proposal trig, orbital row (n <= 64: two per lane) and
@@ -152,6 +180,21 @@ __global__ void __launch_bounds__(512) sweep_kernel(SysView<T> s, double* __rest
                 pade_ep(bep, Zj, pair_dist(ei, pa, ell), u0, d1, d2, d3);
                 du += u1 - u0;
             }
+            if (j34) {
+                // e-e-n-n term: the pairs (i, j != i) change by
+                // sum_a (chi_a(r'_i) - chi_a(r_i)) sum_b f_ab (c_b - chi_b(r_i))
+                for (int a = lane; a < N; a += 32) {
+                    chn[a] = jas_orbital(pt, ptr_s + 6 * a, ell, zj);
+                    cho[a] = jas_orbital(ei, ptr_s + 6 * a, ell, zj);
+                }
+                __syncwarp();
+                for (int a = lane; a < N; a += 32) {
+                    const double* fa = s.fj + (size_t)a * N;
+                    T wa = 0;
+                    for (int b = 0; b < N; ++b) wa += (T)fa[b] * (c34[b] - cho[b]);
+                    du += (chn[a] - cho[a]) * wa;
+                }
+            }
             du = warp_sum(du);
             const T prob = ratio * ratio * qexp(T(2) * du);
             if (u < prob) {
@@ -187,6 +230,8 @@ __global__ void __launch_bounds__(512) sweep_kernel(SysView<T> s, double* __rest
                         et[6 * i + 3 + lane] = pt[3 + lane];
                     }
                 }
+                if (j34)
+                    for (int a = lane; a < N; a += 32) c34[a] += chn[a] - cho[a];
                 ++naccept;
             }
             __syncwarp();

@@ -5,6 +5,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_1605_08423_gb300 import build as gbuild
@@ -35,8 +36,8 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_struct_layouts_match_header(lib):
-    # qmc_params: 10 int32, 5 double, uint64, 2 pointers
-    assert C.sizeof(q.Params) == 10 * 4 + 5 * 8 + 8 + 2 * 8
+    # qmc_params: 10 int32, 5 double, uint64, 2 pointers, then the e-e-n-n Jastrow double and pointer
+    assert C.sizeof(q.Params) == 10 * 4 + 5 * 8 + 8 + 2 * 8 + 8 + 8
     assert C.sizeof(q.Result) == 6 * 8
 
 
@@ -52,6 +53,11 @@ def test_invalid_parameters_rejected_without_gpu(lib):
     rc = lib.qmc_init(C.byref(odd.cparams()), (C.c_double * 48)(), C.byref(h))
     assert rc == -1
     assert q.strerror(-7) == "singular Slater matrix"
+    # the e-e-n-n Jastrow term: FP64 form, N <= 64, positive exponent
+    fj = np.eye(wl.N) * 0.1
+    assert q.footprint_bytes(q.Config.from_workload(wl, fj=fj)) > 0
+    assert q.footprint_bytes(q.Config.from_workload(wl, fj=fj, precision=q.QMC_MIXED)) == 0
+    assert q.footprint_bytes(q.Config.from_workload(wl, fj=fj, zeta_j=0.0)) == 0
 
 
 def test_footprint_scales_with_walkers(lib):
