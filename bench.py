@@ -51,6 +51,8 @@ def _args():
     ap.add_argument("--no-toy", action="store_true", help="skip the toy-model integrator leg")
     ap.add_argument("--toy-only", action="store_true", help="run only the toy-model leg (one JSON line)")
     ap.add_argument("--toy-steps", type=int, default=None, help="steps per trajectory of the timed toy launch")
+    ap.add_argument("--no-jastrow34", action="store_true", help="skip the e-e-n-n Jastrow (FP64 form) leg")
+    ap.add_argument("--jastrow34-only", action="store_true", help="run only that leg (one JSON line)")
     return ap.parse_args()
 
 
@@ -256,6 +258,44 @@ def _toy_bench(stream, steps, rank, n_steps=None, table=True):
             "mean_U": mean_u, "canonical_mean_U": synth.TOY_T / 2,
             "stopped_trajectories": int((o[:, 6] != 0).sum()),
             "mean_U_vs_delta": rows or None}
+
+
+def _jastrow34_bench(stream):
+    """The FP64 form with and without the e-e-n-n Jastrow term (N = 64, 1024 walkers,
+    4 measured sweeps + 1 continuation per call, a sample every sweep)."""
+    import numpy as np
+    import torch
+    from paper_1605_08423_gb300 import qmcmd as q
+    from paper_1605_08423_gb300 import synth
+    wl = synth.workload("h64", walkers=1024, sweeps=4, warmup=2)
+    A = np.random.default_rng(5).uniform(-0.3, 0.3, (wl.N, wl.N))
+    fj = 0.5 * (A + A.T)
+    R_dev = torch.tensor(wl.R, dtype=torch.float64, device="cuda")
+    out = {"metric": "FP64-form electron moves/s and force-evals/s with and without U_{3+4}",
+           "config": {"workload": f"h64: N={wl.N} H, r_s={wl.rs}, {wl.n_gauss} s-Gaussians/proton, FP64 form, "
+                                  f"{wl.walkers} walkers x {wl.sweeps} sweeps (+1 continuation), sample every "
+                                  "sweep, U_{3+4} coefficients symmetric U(-0.3, 0.3), exponent 0.7933844"}}
+    for tag, f in (("without", None), ("with", fj)):
+        cfg = q.Config.from_workload(wl, precision=q.QMC_FP64, warmup=2, warmup_cont=1, measure_every=1,
+                                     recompute_every=4, fj=f)
+        sysq = q.QMCSystem(cfg, wl.R)
+        sysq.set_stream(stream.cuda_stream)
+        o = torch.zeros(4 + 3 * wl.N + 9 * wl.N * wl.N, dtype=torch.float64, device="cuda")
+        sysq.energy_forces_device(R_dev, o)
+        sysq.sync()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sysq.energy_forces_device(R_dev, o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sysq.sync()
+        t = e0.elapsed_time(e1) / 1e3
+        out[tag] = {"electron_moves_per_s": wl.walkers * wl.N * (cfg.sweeps + cfg.warmup_cont) / t,
+                    "force_evals_per_s": wl.walkers * cfg.sweeps / t, "ms_per_call": 1e3 * t,
+                    "E": float(o[0].item())}
+        sysq.close()
+    return out
 
 
 def _toy_cpu_baseline():
@@ -482,6 +522,13 @@ def run_ours(args, ws, rank, local):
         toy = _toy_bench(stream, args.steps, rank)
         toy["cpu_baseline"] = _toy_cpu_baseline() if rank == 0 and ws == 1 and not args.no_cpu_baseline else None
 
+    j34 = None
+    if not args.no_jastrow34 and rank == 0:
+        try:
+            j34 = _jastrow34_bench(stream)
+        except Exception as exc:   # a secondary leg: report, do not lose the headline line
+            j34 = {"error": f"{type(exc).__name__}: {exc}"}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = _cpu_baseline(wl)
@@ -511,6 +558,7 @@ def run_ours(args, ws, rank, local):
                "cpu_baseline": cpu,
                "serving": serving,
                "toy_langevin": toy,
+               "jastrow34_fp64": j34,
                "peaks": peak_kind,
                "result": {"E": res["E"], "E_err": res["E_err"], "accept": res["accept"], "Nc": res["Nc"]}}
         print(json.dumps(out), flush=True)
@@ -528,6 +576,16 @@ def main():
         return
     if args.toy_only:
         run_toy_only(args, rank, local)
+        return
+    if args.jastrow34_only:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        torch.cuda.set_device(local)
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        if rank == 0:
+            print(json.dumps(_jastrow34_bench(stream)), flush=True)
         return
     run_ours(args, ws, rank, local)
 
