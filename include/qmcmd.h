@@ -335,7 +335,8 @@ typedef struct {
 } qmc_served;
 int qmc_server_create(size_t hbm_budget_bytes, int max_active, qmc_server** out);
 void qmc_server_destroy(qmc_server* s);
-/* Register a trajectory (device memory is taken only when it is admitted). */
+/* Register a trajectory (device memory is taken only when it is admitted).
+ * Parameters with the e-e-n-n Jastrow term (p->fj != NULL) are INVALID here. */
 int qmc_server_add_trajectory(qmc_server* s, const qmc_params* p, const double* R0, double T_kelvin, double delta,
                               int s_mode, int* traj);
 int qmc_server_submit(qmc_server* s, int traj, long long* ticket);
