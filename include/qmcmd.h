@@ -61,7 +61,8 @@ typedef struct {
     int32_t n_warmup;         /* sweeps before the first measurement of the first call   */
     int32_t n_warmup_cont;    /* same, for later calls (walkers carried over)            */
     int32_t measure_every;    /* sweeps between samples, >= 1                           */
-    int32_t recompute_every;  /* sweeps between full FP64 inverse recomputes, >= 1       */
+    int32_t recompute_every;  /* sweeps between periodic inverse recomputes, >= 1 (FP64  */
+                              /* Gauss-Jordan unless QMC_OPT_RECOMPUTE says otherwise)   */
     int32_t precision;        /* QMC_FP64 or QMC_MIXED                                   */
     int32_t ewald_mmax;       /* reciprocal cutoff |m| <= mmax (k = 2 pi m / L)          */
     double L;                 /* box side, bohr                                          */
@@ -74,7 +75,8 @@ typedef struct {
     /* 3- and 4-body e-e-n-n Jastrow term of the SI, one periodised Gaussian
      * chi_a(r) = exp(-zeta_j |d(r - R_a)|^2) per proton:
      *   U += sum_{i<j} sum_{a,b} fj[a][b] chi_a(r_i) chi_b(r_j).
-     * fj = NULL switches it off.  FP64 form with N <= 64 only (INVALID otherwise). */
+     * fj = NULL switches it off.  FP64 form with N <= 64 only, and fj must be
+     * exactly symmetric (fj[a][b] == fj[b][a]); INVALID otherwise. */
     double zeta_j;            /* Jastrow-orbital exponent, bohr^-2 (the SI uses 0.7933844) */
     const double* fj;         /* [N][N] symmetric coefficients (copied), or NULL         */
 } qmc_params;
@@ -123,6 +125,37 @@ int qmc_energy_forces(qmc_system* h, const double* R, qmc_result* out);
 /* Same, device pointers, asynchronous: R_dev [N][3]; out_dev receives
  * [E, E_err, n_samples, accept, f(3N), S(3N*3N)] as FP64. */
 int qmc_energy_forces_device(qmc_system* h, const double* R_dev, double* out_dev);
+
+/*
+ * Walker sharding.  Walkers are independent Markov chains, so one energy/force
+ * evaluation can be split over P processes (one GPU each), each holding a
+ * slice of the walkers (QMC_OPT_WALKER_OFFSET = index of its first walker).
+ * The reduction of qmc_energy_forces then takes three calls around two sums
+ * over the processes (e.g. an all-reduce); every pointer is a device pointer
+ * and every call is asynchronous on the handle's stream:
+ *   qmc_shard_sample_device   sampling at nuclei R_dev ([N][3]) as in
+ *                             qmc_energy_forces_device, then this handle's
+ *                             sums_dev [3 + 9N + 3] = [column sums of the
+ *                             per-walker accumulators (layout of
+ *                             qmc_get_accumulators), accepted moves, walkers,
+ *                             moves]                      -> sum over processes
+ *   qmc_shard_reduce_device   from the summed sums_dev: E, N_c, acceptance and
+ *                             f into out_dev (layout of qmc_energy_forces_device),
+ *                             and this handle's gram_dev [1 + 9N^2] =
+ *                             [sum_w (E_w - E)^2, sum_w (f_w - f)(f_w - f)^T] with
+ *                             the global E and f         -> sum over processes
+ *   qmc_shard_finish_device   E_err and S into out_dev from the summed gram_dev;
+ *                             walkers_total (the walkers of all processes) sets
+ *                             N_c for the alpha of a later langevin_step.
+ * The result equals that of one handle holding all walkers, up to the order
+ * of the FP64 sums.  Every process then applies the same Langevin step (same
+ * seed, same MD step, same inputs: the same R').  Errors: INVALID, CUDA; device
+ * errors via qmc_sync.
+ */
+int qmc_shard_sample_device(qmc_system* h, const double* R_dev, double* sums_dev);
+int qmc_shard_reduce_device(qmc_system* h, const double* sums_dev, double* out_dev, double* gram_dev);
+int qmc_shard_finish_device(qmc_system* h, const double* sums_dev, const double* gram_dev, double* out_dev,
+                            long long walkers_total);
 
 /*
  * Accelerated first-order Langevin step (SI, adopted integrator):
@@ -227,6 +260,27 @@ enum { QMC_OPT_TENSOR_CORES = 1, QMC_OPT_TC_ADJOINT = 2 };
  * in hartree); a step with Delta >= 2 T is then INVALID. */
 enum { QMC_OPT_INTEGRATOR = 3, QMC_OPT_NOISE_CORRECTION = 4 };
 enum { QMC_LV_ADOPTED = 0, QMC_LV_FAST = 1, QMC_LV_NOROGNA = 2 };
+/* QMC_OPT_RECOMPUTE selects the periodic inverse recompute inside a call
+ * (every recompute_every sweeps; the recompute at the start of every call is
+ * always the FP64 one):
+ *   QMC_RECOMPUTE_FP64 (default)  Slater blocks at the current positions, then
+ *                                 FP64 Gauss-Jordan inverse and ln|det| (resets the
+ *                                 drift of the Sherman-Morrison updates);
+ *   QMC_RECOMPUTE_NEWTON          mixed form only: one FP32 Newton-Schulz step
+ *                                 G <- G + G (I - A G) on the carried inverse, FP64
+ *                                 Gauss-Jordan for blocks with max|I - A G| >= 0.01
+ *                                 (faster on parts with a slow FP64 pipe; FP32-level).
+ * INVALID for other values, and for QMC_RECOMPUTE_NEWTON in the FP64 form. */
+enum { QMC_OPT_RECOMPUTE = 5 };
+/* QMC_OPT_WALKER_OFFSET (value >= 0, default 0): the handle's walker w draws
+ * its random numbers from Philox stream value + w, so that handles holding
+ * consecutive slices of one walker population (walker sharding, below)
+ * reproduce the chains of a single handle holding all of them.  Setting it
+ * places the walkers again (as qmc_init does, with the new streams) and makes
+ * the next call a first call (n_warmup sweeps, MD step counter 0); set it
+ * right after qmc_init. */
+enum { QMC_OPT_WALKER_OFFSET = 6 };
+enum { QMC_RECOMPUTE_FP64 = 0, QMC_RECOMPUTE_NEWTON = 1 };
 int qmc_set_option(qmc_system* h, int option, int value);
 
 /*

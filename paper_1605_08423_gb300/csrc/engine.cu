@@ -7,8 +7,6 @@
 #include <new>
 #include <vector>
 
-#include <cublas_v2.h>
-
 #include "../../include/qmcmd.h"
 #include "common.cuh"
 #include "kernels.cuh"
@@ -56,7 +54,6 @@ struct qmc_system {
     // reciprocal-space force as one GEMM over walkers (split path):
     // F[W][3N] = rho[W][2 nk] . T^T, T = [3N][2 nk] built per R
     float *d_Trec = nullptr, *d_rk = nullptr, *d_frec = nullptr;
-    cublasHandle_t blas = nullptr;
     // walkers
     double *d_X = nullptr, *d_Xp = nullptr;
     void *d_uacc = nullptr, *d_Phi = nullptr, *d_Gt = nullptr, *d_D = nullptr, *d_Lp = nullptr;
@@ -75,9 +72,11 @@ struct qmc_system {
     int* d_err = nullptr;
     std::vector<void*> allocs;
     uint32_t md_step = 0;
+    uint32_t w0 = 0;                     // QMC_OPT_WALKER_OFFSET: Philox stream of walker 0
     bool first_call = true;
     int lv_scheme = kLvAdopted;          // QMC_OPT_INTEGRATOR
     bool lv_noise_correction = false;    // QMC_OPT_NOISE_CORRECTION
+    bool ns_recompute = false;           // QMC_OPT_RECOMPUTE == QMC_RECOMPUTE_NEWTON (mixed form)
     bool langevin_first = true;
     uint32_t langevin_step_no = 0;
     double last_Nc = 0.0;
@@ -127,6 +126,12 @@ int validate(const qmc_params* p) {
     if (!(p->L > 0) || !(p->ewald_kappa > 0) || !(p->sigma > 0) || p->b_ee < 0 || p->b_ep < 0) return QMC_ERR_INVALID;
     if (p->fj && (p->precision != QMC_FP64 || p->n_protons > 64 || !(p->zeta_j > 0))) return QMC_ERR_INVALID;
     if (p->n_sweeps / p->measure_every < 1) return QMC_ERR_INVALID;
+    if (p->fj) {   // the kernels use row a of f as its column a: f must be exactly symmetric
+        const int N = p->n_protons;
+        for (int a = 0; a < N; ++a)
+            for (int b = a + 1; b < N; ++b)
+                if (!(p->fj[(size_t)a * N + b] == p->fj[(size_t)b * N + a])) return QMC_ERR_INVALID;
+    }
     return QMC_OK;
 }
 
@@ -233,22 +238,26 @@ void recompute(qmc_system* h, int W) {
     prof_end(h, ep);
 }
 
-// Periodic recompute inside a call.  Mixed form: Slater blocks at the current
-// positions and one FP32 Newton-Schulz step on the carried inverse (FP64
-// Gauss-Jordan for blocks too far off); FP64 form: the full FP64 recompute.
+// Periodic recompute inside a call: the full FP64 recompute (Slater blocks at
+// the current positions, FP64 Gauss-Jordan inverse and ln|det|), which resets
+// the drift of the rank-1 updates.  With QMC_RECOMPUTE_NEWTON the mixed form
+// instead corrects the carried inverse by one FP32 Newton-Schulz step (FP64
+// Gauss-Jordan only for blocks too far off).
 template <typename T>
 void recompute_in_call(qmc_system* h, int W) {
     if constexpr (sizeof(T) == 4) {
-        EventPair ep;
-        prof_begin(h, KC_RECOMPUTE, ep);
-        SysView<T> s = view<T>(h, W);
-        h->nlaunch += 2;
-        orbitals<T>(h, s, h->d_X, W * h->N, (T*)h->d_Phi, nullptr, nullptr);
-        launch_refine(W, h->N, h->n, (const float*)h->d_Phi, (float*)h->d_Gt, h->d_logdet, h->d_err, h->stream);
-        prof_end(h, ep);
-    } else {
-        recompute<T>(h, W);
+        if (h->ns_recompute) {
+            EventPair ep;
+            prof_begin(h, KC_RECOMPUTE, ep);
+            SysView<T> s = view<T>(h, W);
+            h->nlaunch += 2;
+            orbitals<T>(h, s, h->d_X, W * h->N, (T*)h->d_Phi, nullptr, nullptr);
+            launch_refine(W, h->N, h->n, (const float*)h->d_Phi, (float*)h->d_Gt, h->d_logdet, h->d_err, h->stream);
+            prof_end(h, ep);
+            return;
+        }
     }
+    recompute<T>(h, W);
 }
 
 template <typename T>
@@ -268,21 +277,20 @@ void measure(qmc_system* h, int W, double* el, double* lnpsi, double* dl, double
     if (split) {
         h->nlaunch += 1;
         prof_begin(h, KC_ADJOINT, ep);
-        // reciprocal-space forces of all walkers: F = T . rho (column-major
-        // [3N x 2nk] . [2nk x W]); plain FP32 SGEMM (cuBLAS)
-        const int m3 = 3 * h->N, k2 = 2 * h->nk;
-        const float one = 1.f, zero = 0.f;
-        cublasSetStream(h->blas, h->stream);
-        cublasSgemm(h->blas, CUBLAS_OP_N, CUBLAS_OP_N, m3, W, k2, &one, h->d_Trec, m3, h->d_rk, k2, &zero, h->d_frec,
-                    m3);
+        // reciprocal-space forces of all walkers: F[W][3N] = rho[W][2nk] . T[2nk][3N]
+        h->nlaunch += 1;
+        launch_recforce_gemm(W, 3 * h->N, 2 * h->nk, h->d_rk, h->d_Trec, h->d_frec, h->stream);
         launch_adjoint_tc(*(const SysView<float>*)&s, h->d_ahat, (const float*)h->d_Gt, h->d_Kt, h->d_eg, h->d_elw,
                           h->d_frec, h->d_acc, dl, de, h->stream);
         prof_end(h, ep);
     }
 }
 
+// Sampling part of one energy/force call (recompute, warm-up and measured
+// sweeps with their samples in the per-walker accumulators); returns the
+// number of electron moves.
 template <typename T>
-void run_call(qmc_system* h) {
+double run_sampling(qmc_system* h) {
     const int W = h->W, N = h->N;
     SysView<T> s = view<T>(h, W);
     const Key key = make_key(h->p.seed);
@@ -297,7 +305,7 @@ void run_call(qmc_system* h) {
         h->nlaunch += 3;
         prof_begin(h, KC_PROPOSE, ep);
         launch_propose<T>(W, N, h->p.L, h->d_X, h->d_Xp, (T*)h->d_ptp, (T*)h->d_uacc, key, md, (uint32_t)sw,
-                          h->p.sigma, h->stream);
+                          h->p.sigma, h->w0, h->stream);
         prof_end(h, ep);
         prof_begin(h, KC_ORB_PROP, ep);
         orbitals<T>(h, s, h->d_Xp, W * N, (T*)h->d_Phi, nullptr, nullptr);
@@ -309,15 +317,20 @@ void run_call(qmc_system* h) {
         if ((sw + 1) % h->p.recompute_every == 0) recompute_in_call<T>(h, W);
         if (sw >= nw && ((sw - nw + 1) % h->p.measure_every) == 0) measure<T>(h, W, nullptr, nullptr, nullptr, nullptr);
     }
-    EventPair ep;
-    prof_begin(h, KC_REDUCE, ep);
-    const double moves = (double)W * total * N;
-    h->nlaunch += 5;
-    launch_reduce(W, N, moves, h->d_acc, h->d_nacc, h->d_colsum, h->d_dev, h->d_out, h->d_err, h->stream);
-    prof_end(h, ep);
-    h->last_Nc = (double)W * (h->p.n_sweeps / h->p.measure_every);
     h->md_step++;
     h->first_call = false;
+    return (double)W * total * N;
+}
+
+template <typename T>
+void run_call(qmc_system* h) {
+    const double moves = run_sampling<T>(h);
+    EventPair ep;
+    prof_begin(h, KC_REDUCE, ep);
+    h->nlaunch += 5;
+    launch_reduce(h->W, h->N, moves, h->d_acc, h->d_nacc, h->d_colsum, h->d_dev, h->d_out, h->d_err, h->stream);
+    prof_end(h, ep);
+    h->last_Nc = (double)h->W * (h->p.n_sweeps / h->p.measure_every);
 }
 
 int read_err(qmc_system* h) {
@@ -425,8 +438,6 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
             h->d_Trec = dalloc<float>(h, (size_t)3 * N * 2 * nk, &rc);
             h->d_rk = dalloc<float>(h, (size_t)W * 2 * nk, &rc);
             h->d_frec = dalloc<float>(h, (size_t)W * 3 * N, &rc);
-            if (rc == QMC_OK && cublasCreate(&h->blas) != CUBLAS_STATUS_SUCCESS) { h->blas = nullptr; rc = QMC_ERR_CUDA; }
-            if (h->blas) cublasSetMathMode(h->blas, CUBLAS_PEDANTIC_MATH);   // plain FP32 products
             h->use_tc_adj = true;
         }
     }
@@ -446,7 +457,7 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
     if (h->d_chat) prepare_tc_coeff(h->d_C32, B, n, h->d_chat, st);
     if (h->d_ahat) prepare_tc_adjoint_coeff(h->d_C32, N, h->G, n, h->d_ahat, st);
     setup_tables(h);
-    launch_init_walkers(W, N, p->L, h->d_R, h->d_X, make_key(p->seed), st);
+    launch_init_walkers(W, N, p->L, h->d_R, h->d_X, make_key(p->seed), 0u, st);
     rc = check_launch();
     if (rc == QMC_OK) rc = cuda_rc(cudaStreamSynchronize(st));
     if (rc != QMC_OK) { qmc_destroy(h); return rc; }
@@ -457,7 +468,6 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
 void qmc_destroy(qmc_system* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    if (h->blas) cublasDestroy(h->blas);
     for (void* a : h->allocs) cudaFree(a);
     for (auto& e : h->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (auto& e : h->free_events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -511,6 +521,42 @@ int qmc_energy_forces(qmc_system* h, const double* R, qmc_result* out) {
     std::memcpy(out->f, o.data() + 4, sizeof(double) * 3 * N);
     std::memcpy(out->cov, o.data() + 4 + 3 * N, sizeof(double) * 9 * (size_t)N * N);
     return QMC_OK;
+}
+
+int qmc_shard_sample_device(qmc_system* h, const double* R_dev, double* sums_dev) {
+    if (!h || !R_dev || !sums_dev) return QMC_ERR_INVALID;
+    const int N = h->N;
+    cudaMemcpyAsync(h->d_R, R_dev, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, h->stream);
+    setup_tables(h);
+    const double moves = h->mixed ? run_sampling<float>(h) : run_sampling<double>(h);
+    EventPair ep;
+    prof_begin(h, KC_REDUCE, ep);
+    h->nlaunch += 2;
+    launch_shard_sums(h->W, N, moves, h->d_acc, h->d_nacc, sums_dev, h->stream);
+    prof_end(h, ep);
+    return check_launch();
+}
+
+int qmc_shard_reduce_device(qmc_system* h, const double* sums_dev, double* out_dev, double* gram_dev) {
+    if (!h || !sums_dev || !out_dev || !gram_dev) return QMC_ERR_INVALID;
+    EventPair ep;
+    prof_begin(h, KC_REDUCE, ep);
+    h->nlaunch += 4;
+    launch_shard_reduce(h->W, h->N, h->d_acc, sums_dev, h->d_dev, out_dev, gram_dev, h->d_err, h->stream);
+    prof_end(h, ep);
+    return check_launch();
+}
+
+int qmc_shard_finish_device(qmc_system* h, const double* sums_dev, const double* gram_dev, double* out_dev,
+                            long long walkers_total) {
+    if (!h || !sums_dev || !gram_dev || !out_dev || walkers_total < 2) return QMC_ERR_INVALID;
+    EventPair ep;
+    prof_begin(h, KC_REDUCE, ep);
+    h->nlaunch += 1;
+    launch_shard_finish(h->N, sums_dev, gram_dev, out_dev, h->stream);
+    prof_end(h, ep);
+    h->last_Nc = (double)walkers_total * (h->p.n_sweeps / h->p.measure_every);
+    return check_launch();
 }
 
 int langevin_step_device(qmc_system* h, double* R_dev, const double* f_dev, const double* S_dev, double T_kelvin,
@@ -669,6 +715,21 @@ int qmc_set_option(qmc_system* h, int option, int value) {
     }
     if (option == QMC_OPT_NOISE_CORRECTION) {
         h->lv_noise_correction = value != 0;
+        return QMC_OK;
+    }
+    if (option == QMC_OPT_WALKER_OFFSET) {
+        if (value < 0) return QMC_ERR_INVALID;
+        h->w0 = (uint32_t)value;
+        h->first_call = true;
+        h->md_step = 0;
+        h->nlaunch += 1;
+        launch_init_walkers(h->W, h->N, h->p.L, h->d_R, h->d_X, make_key(h->p.seed), h->w0, h->stream);
+        return check_launch();
+    }
+    if (option == QMC_OPT_RECOMPUTE) {
+        if (value != QMC_RECOMPUTE_FP64 && value != QMC_RECOMPUTE_NEWTON) return QMC_ERR_INVALID;
+        if (value == QMC_RECOMPUTE_NEWTON && !h->mixed) return QMC_ERR_INVALID;
+        h->ns_recompute = value == QMC_RECOMPUTE_NEWTON;
         return QMC_OK;
     }
     return QMC_ERR_INVALID;

@@ -14,126 +14,27 @@
 // (Eq. smartMarkov) in two halves, around the caller's evaluation of S(y).
 #include "common.cuh"
 #include "kernels.cuh"
+#include "langevin_core.cuh"
 
 namespace qmc {
-
-namespace {
-
-// Cholesky S = L L^T of an n x n SPD matrix (row-major) by one CTA,
-// left-looking, column by column, into the lower triangle of Lc.  Returns
-// false on every thread if S is not positive definite (the pivot test uses a
-// block-wide sum, so all threads see the same value).
-__device__ bool cta_cholesky(int n, const double* __restrict__ S, double* Lc, double* red) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int j = 0; j < n; ++j) {
-        double p = 0.0;
-        for (int k = tid; k < j; k += nt) p += Lc[(size_t)j * n + k] * Lc[(size_t)j * n + k];
-        p = block_sum(p, red);
-        const double d = S[(size_t)j * n + j] - p;
-        if (!(d > 0.0)) return false;
-        const double ljj = sqrt(d);
-        if (tid == 0) Lc[(size_t)j * n + j] = ljj;
-        for (int i = j + 1 + tid; i < n; i += nt) {
-            double t = S[(size_t)i * n + j];
-            for (int k = 0; k < j; ++k) t -= Lc[(size_t)i * n + k] * Lc[(size_t)j * n + k];
-            Lc[(size_t)i * n + j] = t / ljj;
-        }
-        __syncthreads();
-    }
-    return true;
-}
-
-// In-place forward solve L w = g (g in shared memory), column oriented.
-__device__ void cta_forward(int n, const double* Lc, double* g) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int k = 0; k < n; ++k) {
-        const double wk = g[k] / Lc[(size_t)k * n + k];
-        __syncthreads();
-        if (tid == 0) g[k] = wk;
-        for (int i = k + 1 + tid; i < n; i += nt) g[i] -= Lc[(size_t)i * n + k] * wk;
-        __syncthreads();
-    }
-}
-
-// Back solve L^T x = w (w in shared memory, consumed), column oriented.
-__device__ void cta_backward(int n, const double* Lc, double* w, double* x) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int k = n - 1; k >= 0; --k) {
-        const double xk = w[k] / Lc[(size_t)k * n + k];
-        __syncthreads();
-        if (tid == 0) x[k] = xk;
-        for (int i = tid; i < k; i += nt) w[i] -= Lc[(size_t)k * n + i] * xk;
-        __syncthreads();
-    }
-}
-
-}  // namespace
 
 __global__ void __launch_bounds__(1024) langevin_kernel(int n, double* R, double* Rprev, const double* __restrict__ f,
                                                         const double* __restrict__ S, double* Sprev, double* Lc,
                                                         double T, double delta, double alpha, Key key, uint32_t md,
                                                         double box, int identity, int scheme, int* err) {
     extern __shared__ double v[];
-    double* g = v;          // [n]
-    double* x = g + n;      // [n]
-    double* z = x + n;      // [n]
-    double* r0 = z + n;     // [n]
     __shared__ double red[32];
     const int tid = threadIdx.x, nt = blockDim.x;
-    double Dt = delta, Db = delta;
-    if (!identity && scheme == kLvAdopted && alpha > 0.0) {
-        Dt = (1.0 - exp(-alpha * delta)) / alpha;
-        Db = (1.0 - exp(-2.0 * alpha * delta)) / (2.0 * alpha);
-    }
-    if (!identity && !cta_cholesky(n, S, Lc, red)) {
+    double* r1 = nullptr;
+    if (!cta_langevin_step(n, R, Rprev, f, S, Sprev, Lc, T, delta, alpha, key, md, box, identity, scheme, v, red,
+                           &r1)) {
         if (tid == 0) raise_err(err, kErrNotPD);
         return;
     }
-    // g = f - (S_prev - S)(R_prev - R) / (2 Db);  xi;  keep R
+    const double* r0 = r1 - n;   // R, kept by the step before any write
     for (int i = tid; i < n; i += nt) {
-        double t = f[i];
-        if (!identity && scheme != kLvNorogna) {
-            double s = 0.0;
-            for (int j = 0; j < n; ++j) s += (Sprev[(size_t)i * n + j] - S[(size_t)i * n + j]) * (Rprev[j] - R[j]);
-            t -= s / (2.0 * Db);
-        }
-        g[i] = t;
-        const uint4 w = philox((uint32_t)i, md, 0u, kLangevin, key);
-        z[i] = Draw<double>::normal(w);
-        r0[i] = R[i];
-    }
-    __syncthreads();
-    if (!identity) {
-        // forward solve L y = g (column oriented), y stored in g
-        for (int k = 0; k < n; ++k) {
-            const double yk = g[k] / Lc[(size_t)k * n + k];
-            __syncthreads();
-            if (tid == 0) g[k] = yk;
-            for (int i = k + 1 + tid; i < n; i += nt) g[i] -= Lc[(size_t)i * n + k] * yk;
-            __syncthreads();
-        }
-        // back solves L^T x = y and L^T z = xi
-        for (int k = n - 1; k >= 0; --k) {
-            const double xk = g[k] / Lc[(size_t)k * n + k];
-            const double zk = z[k] / Lc[(size_t)k * n + k];
-            __syncthreads();
-            if (tid == 0) { x[k] = xk; z[k] = zk; }
-            for (int i = tid; i < k; i += nt) {
-                g[i] -= Lc[(size_t)k * n + i] * xk;
-                z[i] -= Lc[(size_t)k * n + i] * zk;
-            }
-            __syncthreads();
-        }
-    } else {
-        for (int i = tid; i < n; i += nt) x[i] = g[i];
-        __syncthreads();
-    }
-    const double amp = T > 0.0 ? sqrt(2.0 * T * Db) : 0.0;
-    for (int i = tid; i < n; i += nt) {
-        double r = r0[i] + Dt * x[i] + amp * z[i];
-        if (box > 0.0) r -= box * floor(r / box);
         Rprev[i] = r0[i];
-        R[i] = r;
+        R[i] = r1[i];
     }
     for (size_t idx = tid; idx < (size_t)n * n; idx += nt) Sprev[idx] = identity ? (idx % (n + 1) == 0 ? 1.0 : 0.0) : S[idx];
 }
@@ -201,7 +102,7 @@ void launch_first_correct(int n3, double* y, const double* R, const double* f, c
 void launch_langevin(int n3, double* R, double* Rprev, const double* f, const double* S, double* Sprev,
                      double* Lwork, double T_ha, double delta, double alpha, Key key, uint32_t md, double box,
                      int identity, int scheme, int* err, cudaStream_t st) {
-    const size_t smem = 4 * (size_t)n3 * sizeof(double);
+    const size_t smem = 5 * (size_t)n3 * sizeof(double);
     langevin_kernel<<<1, 1024, smem, st>>>(n3, R, Rprev, f, S, Sprev, Lwork, T_ha, delta, alpha, key, md, box,
                                            identity, scheme, err);
 }

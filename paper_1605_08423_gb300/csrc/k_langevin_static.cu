@@ -21,102 +21,34 @@
 
 #include "../../include/qmcmd.h"
 #include "common.cuh"
+#include "langevin_core.cuh"
 
 namespace qmc {
 
 static __device__ __align__(256) double g_langevin_scratch[QMC_STATIC_MAX_N3 * QMC_STATIC_MAX_N3];
 static __device__ __align__(256) int g_langevin_err;
 
-// Same arithmetic as langevin_kernel, with the previous pair (R_prev, S_prev)
-// given by the caller (nothing is stored) and the result written to Rout.
-__global__ void __launch_bounds__(1024) langevin_static_kernel(int n, const double* __restrict__ R,
-                                                               const double* __restrict__ Rprev,
+// The step of langevin_kernel (same device code, cta_langevin_step), with the
+// previous pair (R_prev, S_prev) given by the caller (nothing is stored) and
+// the result written to Rout.  Rout may be R itself (the entry point passes
+// the same buffer): R, Rprev and Rout are therefore not __restrict__, and every
+// read of R and Rprev is done before the barrier that precedes the store.
+__global__ void __launch_bounds__(1024) langevin_static_kernel(int n, const double* R, const double* Rprev,
                                                                const double* __restrict__ f,
                                                                const double* __restrict__ S,
                                                                const double* __restrict__ Sprev, double* Lc,
-                                                               double* __restrict__ Rout, double T, double delta,
-                                                               double alpha, Key key, uint32_t md, double box,
-                                                               int identity, int* err) {
+                                                               double* Rout, double T, double delta, double alpha,
+                                                               Key key, uint32_t md, double box, int identity,
+                                                               int* err) {
     extern __shared__ double v[];
-    double* g = v;
-    double* x = g + n;
-    double* z = x + n;
-    double* r0 = z + n;
     __shared__ double red[32];
-    __shared__ int notpd;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    double Dt = delta, Db = delta;
-    if (!identity && alpha > 0.0) {
-        Dt = (1.0 - exp(-alpha * delta)) / alpha;
-        Db = (1.0 - exp(-2.0 * alpha * delta)) / (2.0 * alpha);
+    double* r1 = nullptr;
+    if (!cta_langevin_step(n, R, Rprev, f, S, Sprev, Lc, T, delta, alpha, key, md, box, identity, kLvAdopted, v, red,
+                           &r1)) {
+        if (threadIdx.x == 0) atomicOr(err, kErrNotPD);
+        return;
     }
-    if (tid == 0) notpd = 0;
-    if (!identity) {
-        for (int j = 0; j < n; ++j) {
-            double p = 0.0;
-            for (int k = tid; k < j; k += nt) p += Lc[(size_t)j * n + k] * Lc[(size_t)j * n + k];
-            p = block_sum(p, red);
-            const double d = S[(size_t)j * n + j] - p;
-            if (!(d > 0.0)) {
-                if (tid == 0) notpd = 1;
-                break;
-            }
-            const double ljj = sqrt(d);
-            if (tid == 0) Lc[(size_t)j * n + j] = ljj;
-            for (int i = j + 1 + tid; i < n; i += nt) {
-                double t = S[(size_t)i * n + j];
-                for (int k = 0; k < j; ++k) t -= Lc[(size_t)i * n + k] * Lc[(size_t)j * n + k];
-                Lc[(size_t)i * n + j] = t / ljj;
-            }
-            __syncthreads();
-        }
-        __syncthreads();
-        if (notpd) {
-            if (tid == 0) atomicOr(err, kErrNotPD);
-            return;
-        }
-    }
-    for (int i = tid; i < n; i += nt) {
-        double t = f[i];
-        if (!identity) {
-            double s = 0.0;
-            for (int j = 0; j < n; ++j) s += (Sprev[(size_t)i * n + j] - S[(size_t)i * n + j]) * (Rprev[j] - R[j]);
-            t -= s / (2.0 * Db);
-        }
-        g[i] = t;
-        z[i] = Draw<double>::normal(philox((uint32_t)i, md, 0u, kLangevin, key));
-        r0[i] = R[i];
-    }
-    __syncthreads();
-    if (!identity) {
-        for (int k = 0; k < n; ++k) {
-            const double yk = g[k] / Lc[(size_t)k * n + k];
-            __syncthreads();
-            if (tid == 0) g[k] = yk;
-            for (int i = k + 1 + tid; i < n; i += nt) g[i] -= Lc[(size_t)i * n + k] * yk;
-            __syncthreads();
-        }
-        for (int k = n - 1; k >= 0; --k) {
-            const double xk = g[k] / Lc[(size_t)k * n + k];
-            const double zk = z[k] / Lc[(size_t)k * n + k];
-            __syncthreads();
-            if (tid == 0) { x[k] = xk; z[k] = zk; }
-            for (int i = tid; i < k; i += nt) {
-                g[i] -= Lc[(size_t)k * n + i] * xk;
-                z[i] -= Lc[(size_t)k * n + i] * zk;
-            }
-            __syncthreads();
-        }
-    } else {
-        for (int i = tid; i < n; i += nt) x[i] = g[i];
-        __syncthreads();
-    }
-    const double amp = T > 0.0 ? sqrt(2.0 * T * Db) : 0.0;
-    for (int i = tid; i < n; i += nt) {
-        double r = r0[i] + Dt * x[i] + amp * z[i];
-        if (box > 0.0) r -= box * floor(r / box);
-        Rout[i] = r;
-    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Rout[i] = r1[i];
 }
 
 namespace {
@@ -169,7 +101,7 @@ extern "C" int qmc_langevin_step_static(int n3, double* R, const double* Rprev, 
     cudaStream_t st = (cudaStream_t)stream;
     const int identity = s_mode == QMC_S_IDENTITY;
     if (cudaMemsetAsync(a.err, 0, sizeof(int), st) != cudaSuccess) return QMC_ERR_CUDA;
-    const size_t smem = 4 * (size_t)n3 * sizeof(double);
+    const size_t smem = 5 * (size_t)n3 * sizeof(double);
     langevin_static_kernel<<<1, 1024, smem, st>>>(n3, R, Rprev, f, S, Sprev, a.scratch, R,
                                                    T_kelvin * 3.166811563e-6, delta, identity ? 0.0 : alpha,
                                                    make_key(seed), step, box, identity, a.err);

@@ -359,9 +359,9 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
                 for (int a = lane; a < N; a += 32) {
                     RadialDerivs<T> rd;
                     const T chi = jas34_orbital(et + 6 * i, s.ptrig + 6 * a, ell, zj, k2, rd);
-                    const double* fa = s.fj + (size_t)a * N;
+                    const double* fa = s.fj + a;   // column a = row a (f symmetric): coalesced over lanes
                     T w = 0;
-                    for (int b = 0; b < N; ++b) w += (T)fa[b] * (j34c[b] - stc[b]);
+                    for (int b = 0; b < N; ++b) w += (T)fa[(size_t)b * N] * (j34c[b] - stc[b]);
                     for (int mu = 0; mu < 3; ++mu) g[mu] += rd.g[mu] * w;
                     l += rd.lap * w;
                     u += chi * w;
@@ -420,10 +420,10 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
                 for (int a = lane; a < N; a += 32) {
                     RadialDerivs<T> rd;
                     jas34_orbital(et + 6 * i, s.ptrig + 6 * a, ell, zj, k2, rd);
-                    const double* fa = s.fj + (size_t)a * N;   // row a = column a (f symmetric)
+                    const double* fa = s.fj + a;   // column a = row a (f symmetric): coalesced over lanes
                     T w = 0, v[3] = {0, 0, 0}, lam = 0;
                     for (int b = 0; b < N; ++b) {
-                        const T f = (T)fa[b];
+                        const T f = (T)fa[(size_t)b * N];
                         w += f * (j34c[b] - st[b]);
                         for (int mu = 0; mu < 3; ++mu) v[mu] += st[N + 3 * b + mu] * f;
                         lam += st[4 * N + b] * f;

@@ -145,12 +145,13 @@ void launch_orbitals(const SysView<T>& s, const double* pos, int nrows, T* val, 
 // uniforms (purpose 3), index = sweep * N + electron.  A move of electron i
 // only ever changes r_i, so every proposal of the sweep is known when the
 // sweep starts.  X is wrapped into [0, L) first (the mixed sweep stores
-// accepted positions unwrapped).
+// accepted positions unwrapped).  The Philox stream of walker w is w0 + w
+// (w0: the handle's first walker in a walker-sharded run).
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void propose_kernel(int W, int N, double L, double* __restrict__ X, double* __restrict__ Xp,
                                T* __restrict__ ptp, T* __restrict__ uacc, Key key, uint32_t md, uint32_t sweep,
-                               double sigma) {
+                               double sigma, uint32_t w0) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= W * N) return;
     const int w = t / N, i = t - w * N;
@@ -161,7 +162,7 @@ __global__ void propose_kernel(int W, int N, double L, double* __restrict__ X, d
         double x = X[(size_t)t * 3 + mu];
         x -= L * floor(x * iL);
         X[(size_t)t * 3 + mu] = x;
-        const T z = Draw<T>::normal(philox((uint32_t)w, md, idx, kPropX + mu, key));
+        const T z = Draw<T>::normal(philox(w0 + (uint32_t)w, md, idx, kPropX + mu, key));
         const double xp = x + sigma * (double)z;
         Xp[(size_t)t * 3 + mu] = xp;
         T sn, cs;
@@ -169,40 +170,41 @@ __global__ void propose_kernel(int W, int N, double L, double* __restrict__ X, d
         ptp[(size_t)t * 6 + mu] = sn;
         ptp[(size_t)t * 6 + 3 + mu] = cs;
     }
-    uacc[t] = Draw<T>::uniform(philox((uint32_t)w, md, idx, kAccept, key));
+    uacc[t] = Draw<T>::uniform(philox(w0 + (uint32_t)w, md, idx, kAccept, key));
 }
 
 template <typename T>
 void launch_propose(int W, int N, double L, double* X, double* Xp, T* ptp, T* uacc, Key key, uint32_t md,
-                    uint32_t sweep, double sigma, cudaStream_t st) {
+                    uint32_t sweep, double sigma, uint32_t w0, cudaStream_t st) {
     const int tot = W * N;
-    propose_kernel<T><<<(tot + 255) / 256, 256, 0, st>>>(W, N, L, X, Xp, ptp, uacc, key, md, sweep, sigma);
+    propose_kernel<T><<<(tot + 255) / 256, 256, 0, st>>>(W, N, L, X, Xp, ptp, uacc, key, md, sweep, sigma, w0);
 }
 
 // Walker start: electron i next to proton i (up electrons on protons 0..N/2-1,
-// down electrons on N/2..N-1) plus 0.5 bohr Gaussian noise, wrapped.
+// down electrons on N/2..N-1) plus 0.5 bohr Gaussian noise, wrapped; the
+// Philox stream of walker w is w0 + w.
 __global__ void init_walkers_kernel(int W, int N, double L, const double* __restrict__ R, double* __restrict__ X,
-                                    Key key) {
+                                    Key key, uint32_t w0) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= W * N) return;
     const int w = t / N, i = t - w * N;
 #pragma unroll
     for (int mu = 0; mu < 3; ++mu) {
-        const double z = Draw<double>::normal(philox((uint32_t)w, 0u, (uint32_t)i, kInitX + mu, key));
+        const double z = Draw<double>::normal(philox(w0 + (uint32_t)w, 0u, (uint32_t)i, kInitX + mu, key));
         const double x = R[3 * i + mu] + 0.5 * z;
         X[(size_t)t * 3 + mu] = x - L * floor(x / L);
     }
 }
 
-void launch_init_walkers(int W, int N, double L, const double* R, double* X, Key key, cudaStream_t st) {
-    init_walkers_kernel<<<(W * N + 255) / 256, 256, 0, st>>>(W, N, L, R, X, key);
+void launch_init_walkers(int W, int N, double L, const double* R, double* X, Key key, uint32_t w0, cudaStream_t st) {
+    init_walkers_kernel<<<(W * N + 255) / 256, 256, 0, st>>>(W, N, L, R, X, key, w0);
 }
 
 template void launch_orbitals<double>(const SysView<double>&, const double*, int, double*, double*, double*, cudaStream_t);
 template void launch_orbitals<float>(const SysView<float>&, const double*, int, float*, float*, float*, cudaStream_t);
 template void launch_propose<double>(int, int, double, double*, double*, double*, double*, Key, uint32_t, uint32_t,
-                                     double, cudaStream_t);
+                                     double, uint32_t, cudaStream_t);
 template void launch_propose<float>(int, int, double, double*, double*, float*, float*, Key, uint32_t, uint32_t,
-                                    double, cudaStream_t);
+                                    double, uint32_t, cudaStream_t);
 
 }  // namespace qmc

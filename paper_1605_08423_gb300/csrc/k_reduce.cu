@@ -6,6 +6,15 @@
 //   E_err^2 = sum_w (E_w - E)^2 / (W (W-1)),  N_c = number of samples.
 // FP64, fixed-order trees (bitwise reproducible; no atomics).
 // Output layout: [E, E_err, N_c, accept, f(3N), S(3N x 3N)].
+//
+// Walker-sharded form (walkers split over processes, one GPU each): the same
+// reduction in three steps around two sums over the processes --
+//   local column sums (plus walkers and moves)          -> summed over processes
+//   E, f from the global sums; local sums of (E_w - E)^2 and of
+//   (f_w - f)(f_w - f)^T with the global E, f          -> summed over processes
+//   E_err and S from the global sums and walker count.
+// The result equals the single-process reduction over all walkers up to the
+// order of the FP64 sums.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -25,7 +34,9 @@ __global__ void colsum_kernel(int W, int ncol, const double* __restrict__ acc, c
     if (threadIdx.x == 0) colsum[c] = s;
 }
 
-__global__ void finalize_kernel(int W, int N, double moves, const double* __restrict__ colsum, double* out, int* err) {
+// E, f, N_c and the acceptance ratio from column sums (moves < 0: read the
+// number of moves from colsum[ncol + 2], as the sharded form stores it).
+__global__ void finalize_kernel(int N, double moves, const double* __restrict__ colsum, double* out, int* err) {
     const int N3 = 3 * N, ncol = 3 + 9 * N;
     const double cnt = colsum[0];
     const double E = colsum[1] / cnt;
@@ -37,7 +48,7 @@ __global__ void finalize_kernel(int W, int N, double moves, const double* __rest
     if (threadIdx.x == 0) {
         out[0] = E;
         out[2] = cnt;
-        out[3] = colsum[ncol] / moves;
+        out[3] = colsum[ncol] / (moves < 0.0 ? colsum[ncol + 2] : moves);
         if (!isfinite(E)) raise_err(err, kErrNonfinite);
     }
 }
@@ -59,7 +70,8 @@ __global__ void deviation_kernel(int W, int N, const double* __restrict__ acc, c
     }
 }
 
-__global__ void eerr_kernel(int W, int N, const double* __restrict__ dev, double* out) {
+// sum_w (E_w - E)^2: written as sqrt(sum / (W (W - 1))) when finish != 0, else as the plain sum.
+__global__ void eerr_kernel(int W, int N, const double* __restrict__ dev, double* dst, int finish) {
     __shared__ double red[32];
     const int N3 = 3 * N;
     double s = 0.0;
@@ -68,11 +80,13 @@ __global__ void eerr_kernel(int W, int N, const double* __restrict__ dev, double
         s += d * d;
     }
     s = block_sum(s, red);
-    if (threadIdx.x == 0) out[1] = W > 1 ? sqrt(s / ((double)W * (W - 1))) : 0.0;
+    if (threadIdx.x == 0) dst[0] = finish ? (W > 1 ? sqrt(s / ((double)W * (W - 1))) : 0.0) : s;
 }
 
-// S tile (32 x 32) per block; 256 threads, 4 outputs each.
-__global__ void __launch_bounds__(256) gram_kernel(int W, int N, const double* __restrict__ dev, double* out) {
+// dst[i][j] = scale * sum_w dev[w][i] dev[w][j]: a 32 x 32 tile per block,
+// 256 threads, 4 outputs each.
+__global__ void __launch_bounds__(256) gram_kernel(int W, int N, const double* __restrict__ dev, double* dst,
+                                                   double scale) {
     __shared__ double A[32][33], Bm[32][33];
     const int N3 = 3 * N, ld = N3 + 1;
     const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
@@ -93,11 +107,10 @@ __global__ void __launch_bounds__(256) gram_kernel(int W, int N, const double* _
         }
         __syncthreads();
     }
-    const double scale = W > 1 ? 1.0 / ((double)W * (W - 1)) : 0.0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int i = i0 + ty + 8 * q, j = j0 + tx;
-        if (i < N3 && j < N3) out[4 + N3 + (size_t)i * N3 + j] = acc[q] * scale;
+        if (i < N3 && j < N3) dst[(size_t)i * N3 + j] = acc[q] * scale;
     }
 }
 
@@ -105,12 +118,56 @@ void launch_reduce(int W, int N, double moves, const double* acc, const unsigned
                         double* dev, double* out, int* err, cudaStream_t st) {
     const int ncol = 3 + 9 * N, N3 = 3 * N;
     colsum_kernel<<<ncol + 1, 256, 0, st>>>(W, ncol, acc, nacc, colsum);
-    finalize_kernel<<<1, 256, 0, st>>>(W, N, moves, colsum, out, err);
+    finalize_kernel<<<1, 256, 0, st>>>(N, moves, colsum, out, err);
     const size_t tot = (size_t)W * (N3 + 1);
     deviation_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(W, N, acc, out, dev);
-    eerr_kernel<<<1, 256, 0, st>>>(W, N, dev, out);
+    eerr_kernel<<<1, 256, 0, st>>>(W, N, dev, out + 1, 1);
     dim3 g((N3 + 31) / 32, (N3 + 31) / 32);
-    gram_kernel<<<g, 256, 0, st>>>(W, N, dev, out);
+    gram_kernel<<<g, 256, 0, st>>>(W, N, dev, out + 4 + N3, W > 1 ? 1.0 / ((double)W * (W - 1)) : 0.0);
+}
+
+// ---------------------------------------------------------------------------
+// Walker-sharded form.
+// ---------------------------------------------------------------------------
+__global__ void shard_counts_kernel(int N, double walkers, double moves, double* sums) {
+    const int ncol = 3 + 9 * N;
+    sums[ncol + 1] = walkers;
+    sums[ncol + 2] = moves;
+}
+
+// E_err and S from the summed partial sums: scale by 1 / (W (W - 1)), W the
+// summed walker count.
+__global__ void shard_finish_kernel(int N, const double* __restrict__ sums, const double* __restrict__ gram,
+                                    double* out) {
+    const int N3 = 3 * N, ncol = 3 + 9 * N;
+    const double W = sums[ncol + 1];
+    const double scale = W > 1.0 ? 1.0 / (W * (W - 1.0)) : 0.0;
+    const size_t tot = (size_t)N3 * N3;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x)
+        out[4 + N3 + i] = gram[1 + i] * scale;
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[1] = sqrt(gram[0] * scale);
+}
+
+void launch_shard_sums(int W, int N, double moves, const double* acc, const unsigned long long* nacc, double* sums,
+                       cudaStream_t st) {
+    const int ncol = 3 + 9 * N;
+    colsum_kernel<<<ncol + 1, 256, 0, st>>>(W, ncol, acc, nacc, sums);
+    shard_counts_kernel<<<1, 1, 0, st>>>(N, (double)W, moves, sums);
+}
+
+void launch_shard_reduce(int W, int N, const double* acc, const double* sums, double* dev, double* out, double* gram,
+                         int* err, cudaStream_t st) {
+    const int N3 = 3 * N;
+    finalize_kernel<<<1, 256, 0, st>>>(N, -1.0, sums, out, err);
+    const size_t tot = (size_t)W * (N3 + 1);
+    deviation_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(W, N, acc, out, dev);
+    eerr_kernel<<<1, 256, 0, st>>>(W, N, dev, gram, 0);
+    dim3 g((N3 + 31) / 32, (N3 + 31) / 32);
+    gram_kernel<<<g, 256, 0, st>>>(W, N, dev, gram + 1, 1.0);
+}
+
+void launch_shard_finish(int N, const double* sums, const double* gram, double* out, cudaStream_t st) {
+    shard_finish_kernel<<<64, 256, 0, st>>>(N, sums, gram, out);
 }
 
 }  // namespace qmc

@@ -23,12 +23,12 @@ struct SweepSmem {
     static constexpr int VE = 16 / sizeof(T);   // elements per 16-byte vector
     __host__ __device__ static int nv(int n) { return (n + VE - 1) / VE * VE; }
     __host__ __device__ static int ld(int n) { return nv(n) + VE; }
-    // per warp: G^T [n][ld], old row [nv], phi' [nv], trig [6N], and for the
-    // e-e-n-n Jastrow term three [N] vectors (sum over electrons of chi_a,
-    // chi_a at the moving electron and at its proposal)
-    __host__ __device__ static size_t warp_bytes(int N, int n) {
+    // per warp: G^T [n][ld], old row [nv], phi' [nv], trig [6N], and only with
+    // the e-e-n-n Jastrow term (j34) three [N] vectors (sum over electrons of
+    // chi_a, chi_a at the moving electron and at its proposal)
+    __host__ __device__ static size_t warp_bytes(int N, int n, bool j34) {
         size_t b = ((size_t)n * ld(n) + 2 * (size_t)nv(n)) * sizeof(T);
-        b += (size_t)9 * N * sizeof(T);
+        b += (size_t)(j34 ? 9 : 6) * N * sizeof(T);
         return (b + 15) & ~size_t(15);
     }
 };
@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(512) sweep_kernel(SysView<T> s, double* __rest
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     T* ptr_s = (T*)smraw;                                    // [N][6] proton trig
     size_t off = ((size_t)6 * N * sizeof(T) + 15) & ~size_t(15);
-    unsigned char* mine = smraw + off + (size_t)warp * SweepSmem<T>::warp_bytes(N, n);
+    const bool j34 = sizeof(T) == 8 && s.fj != nullptr;
+    unsigned char* mine = smraw + off + (size_t)warp * SweepSmem<T>::warp_bytes(N, n, j34);
     T* Gs = (T*)mine;
     T* rowb = Gs + (size_t)n * ld;
     T* phi = rowb + nv;
@@ -116,7 +117,6 @@ __global__ void __launch_bounds__(512) sweep_kernel(SysView<T> s, double* __rest
         et[6 * i + 3 + mu] = cs;
     }
     __syncwarp();
-    const bool j34 = sizeof(T) == 8 && s.fj != nullptr;
     const T zj = (T)s.zeta_j;
     if (j34) {
         for (int a = lane; a < N; a += 32) {
@@ -189,9 +189,11 @@ __global__ void __launch_bounds__(512) sweep_kernel(SysView<T> s, double* __rest
                 }
                 __syncwarp();
                 for (int a = lane; a < N; a += 32) {
-                    const double* fa = s.fj + (size_t)a * N;
+                    // f is symmetric (checked at qmc_init): column a = row a,
+                    // and the lanes' loads of a column element are consecutive
+                    const double* fa = s.fj + a;
                     T wa = 0;
-                    for (int b = 0; b < N; ++b) wa += (T)fa[b] * (c34[b] - cho[b]);
+                    for (int b = 0; b < N; ++b) wa += (T)fa[(size_t)b * N] * (c34[b] - cho[b]);
                     du += (chn[a] - cho[a]) * wa;
                 }
             }
@@ -411,7 +413,7 @@ void launch_sweep(const SysView<T>& s, double* X, const double* Xp, const T* ptp
             return;
         }
     }
-    const size_t wb = SweepSmem<T>::warp_bytes(s.N, s.n);
+    const size_t wb = SweepSmem<T>::warp_bytes(s.N, s.n, sizeof(T) == 8 && s.fj != nullptr);
     const size_t head = ((size_t)6 * s.N * sizeof(T) + 15) & ~size_t(15);
     // as many walkers per CTA as the shared memory of one SM holds (one CTA per SM)
     int wpb = (int)((226 * 1024 - head) / wb);

@@ -9,8 +9,8 @@ template <typename T>
 void launch_orbitals(const SysView<T>& s, const double* pos, int nrows, T* val, T* grad, T* lap, cudaStream_t st);
 template <typename T>
 void launch_propose(int W, int N, double L, double* X, double* Xp, T* ptp, T* uacc, Key key, uint32_t md,
-                    uint32_t sweep, double sigma, cudaStream_t st);
-void launch_init_walkers(int W, int N, double L, const double* R, double* X, Key key, cudaStream_t st);
+                    uint32_t sweep, double sigma, uint32_t w0, cudaStream_t st);
+void launch_init_walkers(int W, int N, double L, const double* R, double* X, Key key, uint32_t w0, cudaStream_t st);
 
 // k_orbitals_tc.cu (tensor-core form of the value-only contraction)
 bool tc_orbitals_supported(int n, int B);
@@ -58,9 +58,20 @@ void launch_setup(int N, double L, double kappa, int nk, const int4* kvec, const
 void launch_recforce_table(int N, int nk, double L, const int4* kvec, const double* kw, const double2* eikR, float* T,
                            cudaStream_t st);
 
+// k_recforce.cu: F[W][M] = rho[W][K] . T[K][M] (reciprocal-space force of every walker sample).
+void launch_recforce_gemm(int W, int M, int K, const float* rho, const float* T, float* F, cudaStream_t st);
+
 // k_reduce.cu: walker reductions and the covariance matrix.
 void launch_reduce(int W, int N, double moves, const double* acc, const unsigned long long* nacc,
                    double* colsum, double* dev, double* out, int* err, cudaStream_t st);
+// k_reduce.cu: walker-sharded form of the same reduction (see there): local
+// sums [3 + 9N + 3], then E, f and local deviation sums gram [1 + 9N^2] from
+// the summed sums, then E_err and S from the summed gram.
+void launch_shard_sums(int W, int N, double moves, const double* acc, const unsigned long long* nacc, double* sums,
+                       cudaStream_t st);
+void launch_shard_reduce(int W, int N, const double* acc, const double* sums, double* dev, double* out, double* gram,
+                         int* err, cudaStream_t st);
+void launch_shard_finish(int N, const double* sums, const double* gram, double* out, cudaStream_t st);
 
 // k_langevin.cu (scheme: kLvAdopted, kLvFast or kLvNorogna)
 enum : int { kLvAdopted = 0, kLvFast = 1, kLvNorogna = 2 };

@@ -23,6 +23,9 @@ QMC_FP64, QMC_MIXED = 0, 1
 QMC_S_IDENTITY, QMC_S_COV = 0, 1
 NKERNEL = 9
 QMC_OPT_TENSOR_CORES, QMC_OPT_TC_ADJOINT, QMC_OPT_INTEGRATOR, QMC_OPT_NOISE_CORRECTION = 1, 2, 3, 4
+QMC_OPT_RECOMPUTE = 5
+QMC_RECOMPUTE_FP64, QMC_RECOMPUTE_NEWTON = 0, 1
+QMC_OPT_WALKER_OFFSET = 6
 QMC_LV_ADOPTED, QMC_LV_FAST, QMC_LV_NOROGNA = 0, 1, 2
 QMC_TOY_PLAIN, QMC_TOY_STANDARD, QMC_TOY_FIRST, QMC_TOY_FAST, QMC_TOY_ADOPTED, QMC_TOY_NOROGNA = range(6)
 QMC_TOY_S_G, QMC_TOY_S_HG = 0, 1
@@ -117,6 +120,9 @@ def lib():
         L.qmc_server_progress.argtypes = [vp]
         L.qmc_server_fetch.argtypes = [vp, C.c_longlong, C.POINTER(Served)]
         L.qmc_server_stats.argtypes = [vp, C.POINTER(C.c_longlong)]
+        L.qmc_shard_sample_device.argtypes = [vp, vp, vp]
+        L.qmc_shard_reduce_device.argtypes = [vp, vp, vp, vp]
+        L.qmc_shard_finish_device.argtypes = [vp, vp, vp, vp, C.c_longlong]
         L.qmc_launch_count.argtypes = [vp]
         L.qmc_launch_count.restype = C.c_longlong
         L.qmc_kernel_name.argtypes = [C.c_int]
@@ -295,6 +301,28 @@ class QMCSystem:
     def set_noise_correction(self, on: bool):
         _chk(lib().qmc_set_option(self._h, QMC_OPT_NOISE_CORRECTION, int(on)), "qmc_set_option")
 
+    def set_recompute(self, mode: int):
+        """QMC_RECOMPUTE_FP64 (default) or QMC_RECOMPUTE_NEWTON (mixed form only)."""
+        _chk(lib().qmc_set_option(self._h, QMC_OPT_RECOMPUTE, int(mode)), "qmc_set_option")
+
+    def set_walker_offset(self, w0: int):
+        """Philox stream of walker 0 (walker sharding); places the walkers again."""
+        _chk(lib().qmc_set_option(self._h, QMC_OPT_WALKER_OFFSET, int(w0)), "qmc_set_option")
+
+    # walker-sharded reduction (device tensors, asynchronous): see ShardGroup
+    def shard_sample_device(self, R_dev, sums_dev):
+        _chk(lib().qmc_shard_sample_device(self._h, C.c_void_p(R_dev.data_ptr()), C.c_void_p(sums_dev.data_ptr())),
+             "qmc_shard_sample_device")
+
+    def shard_reduce_device(self, sums_dev, out_dev, gram_dev):
+        _chk(lib().qmc_shard_reduce_device(self._h, C.c_void_p(sums_dev.data_ptr()), C.c_void_p(out_dev.data_ptr()),
+                                           C.c_void_p(gram_dev.data_ptr())), "qmc_shard_reduce_device")
+
+    def shard_finish_device(self, sums_dev, gram_dev, out_dev, walkers_total: int):
+        _chk(lib().qmc_shard_finish_device(self._h, C.c_void_p(sums_dev.data_ptr()), C.c_void_p(gram_dev.data_ptr()),
+                                           C.c_void_p(out_dev.data_ptr()), int(walkers_total)),
+             "qmc_shard_finish_device")
+
     def set_tc_adjoint(self, on: bool):
         """Orbital force terms in the separate tensor-core kernel (True) or in
         the SIMT measure kernel (False); effective while tensor cores are on."""
@@ -447,3 +475,42 @@ def energy_forces_function():
             return -f * grad_out, None
 
     return EnergyForces
+
+
+def shard_sizes(walkers_total: int, world: int) -> list[int]:
+    """Walkers per process when walkers_total is split over `world` processes
+    (consecutive slices, the first walkers_total % world one larger)."""
+    base, extra = divmod(int(walkers_total), int(world))
+    return [base + (1 if r < extra else 0) for r in range(world)]
+
+
+class ShardGroup:
+    """One energy/force evaluation with the walkers split over the processes of
+    a torch.distributed group (one GPU each): each process holds a consecutive
+    slice of the walker population (its handle's walker offset is the slice's
+    first walker), and the reduction exchanges two buffers per evaluation --
+    the column sums of the per-walker accumulators, then the sums of the
+    per-walker deviations about the global mean (the covariance S) -- by
+    all-reduce.  Every process ends with the E, f, S the single handle over all
+    walkers would give (up to the order of the FP64 sums) and applies the same
+    Langevin step.  `system` is the process's QMCSystem (or any object with the
+    shard_* methods and N); the buffers are tensors on its device."""
+
+    def __init__(self, system, walkers_total: int, group=None):
+        import torch
+        import torch.distributed as dist
+        self.system, self.group, self.dist = system, group, dist
+        self.walkers_total = int(walkers_total)
+        N = system.N
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        self.sums = torch.zeros(3 + 9 * N + 3, dtype=torch.float64, device=dev)
+        self.gram = torch.zeros(1 + 9 * N * N, dtype=torch.float64, device=dev)
+
+    def energy_forces_device(self, R_dev, out_dev):
+        """out_dev: [E, E_err, N_c, accept, f(3N), S(3N x 3N)], the layout of qmc_energy_forces_device."""
+        op = self.dist.ReduceOp.SUM
+        self.system.shard_sample_device(R_dev, self.sums)
+        self.dist.all_reduce(self.sums, op=op, group=self.group)
+        self.system.shard_reduce_device(self.sums, out_dev, self.gram)
+        self.dist.all_reduce(self.gram, op=op, group=self.group)
+        self.system.shard_finish_device(self.sums, self.gram, out_dev, self.walkers_total)

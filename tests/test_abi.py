@@ -58,6 +58,18 @@ def test_invalid_parameters_rejected_without_gpu(lib):
     assert q.footprint_bytes(q.Config.from_workload(wl, fj=fj)) > 0
     assert q.footprint_bytes(q.Config.from_workload(wl, fj=fj, precision=q.QMC_MIXED)) == 0
     assert q.footprint_bytes(q.Config.from_workload(wl, fj=fj, zeta_j=0.0)) == 0
+    # f must be exactly symmetric: the kernels read its row a as its column a
+    A = np.random.default_rng(3).uniform(-0.3, 0.3, (wl.N, wl.N))
+    assert q.footprint_bytes(q.Config.from_workload(wl, fj=0.5 * (A + A.T))) > 0
+    assert q.footprint_bytes(q.Config.from_workload(wl, fj=A)) == 0
+    h = C.c_void_p()
+    asym = q.Config.from_workload(wl, fj=A)
+    assert lib.qmc_init(C.byref(asym.cparams()), (C.c_double * 48)(), C.byref(h)) == -1
+
+
+def test_recompute_option_values(lib):
+    assert q.QMC_OPT_RECOMPUTE == 5 and (q.QMC_RECOMPUTE_FP64, q.QMC_RECOMPUTE_NEWTON) == (0, 1)
+    assert lib.qmc_set_option(None, q.QMC_OPT_RECOMPUTE, 0) == -1      # no handle
 
 
 def test_footprint_scales_with_walkers(lib):

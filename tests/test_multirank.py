@@ -46,3 +46,92 @@ def test_two_gloo_ranks_independent_replicas_and_max_time():
     assert out[0][0] == out[1][0] == 15.0
     assert out[0][1] != out[1][1]                      # different synthetic replicas
     assert out[0][2] == (2, 0, 0) and out[1][2][:2] == (2, 1)
+
+
+class _FakeShard:
+    """Host stand-in for one process's QMCSystem in the walker-sharded
+    reduction: its accumulator slice (from the oracle's chains) and the three
+    shard_* steps written out in numpy, with the buffer layouts of
+    include/qmcmd.h.  The CUDA kernels of these steps are checked against the
+    single-handle reduction on the GPU (tests/test_gpu_shard.py); this checks
+    the exchange around them with real gloo collectives."""
+
+    def __init__(self, acc, N):
+        self.acc, self.N = acc, N
+
+    def shard_sample_device(self, R_dev, sums):
+        import torch
+        W = self.acc.shape[0]
+        s = self.acc.sum(axis=0)
+        sums.copy_(torch.tensor(list(s) + [0.0, float(W), 1.0], dtype=torch.float64))
+
+    def shard_reduce_device(self, sums, out, gram):
+        import numpy as np
+        import torch
+        N3 = 3 * self.N
+        c = sums.numpy()
+        cnt, E = c[0], c[1] / c[0]
+        f = -c[3 + 2 * N3:3 + 3 * N3] / cnt - 2.0 * (c[3 + N3:3 + 2 * N3] / cnt - E * c[3:3 + N3] / cnt)
+        a = self.acc
+        fw = -a[:, 3 + 2 * N3:3 + 3 * N3] / a[:, :1] - 2.0 * (a[:, 3 + N3:3 + 2 * N3] / a[:, :1]
+                                                             - E * a[:, 3:3 + N3] / a[:, :1])
+        d = fw - f
+        e = a[:, 1] / a[:, 0] - E
+        o = out.numpy()
+        o[0], o[2], o[4:4 + N3] = E, cnt, f
+        gram.copy_(torch.tensor(np.concatenate([[np.sum(e * e)], (d.T @ d).ravel()])))
+
+    def shard_finish_device(self, sums, gram, out, walkers_total):
+        N3 = 3 * self.N
+        W = float(sums.numpy()[3 + 9 * self.N + 1])
+        assert W == walkers_total
+        g = gram.numpy()
+        o = out.numpy()
+        o[1] = (g[0] / (W * (W - 1))) ** 0.5
+        o[4 + N3:] = g[1:] / (W * (W - 1))
+
+
+def _shard_worker(rank, ws, port, out):
+    import numpy as np
+    import torch
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    from oracle import oracle as orc
+    from paper_1605_08423_gb300 import qmcmd as q
+    from paper_1605_08423_gb300 import synth
+    wl = synth.workload("h16")
+    osys = orc.System(N=wl.N, L=wl.L, zeta=np.array(wl.zeta), coeff=wl.C)
+    _, acc, _ = orc.vmc(osys, wl.R, W=11, n_sweeps=3, n_warmup=2, sigma=wl.sigma, seed=wl.seed)
+    sizes = q.shard_sizes(11, ws)
+    lo = sum(sizes[:rank])
+    grp = q.ShardGroup(_FakeShard(acc[lo:lo + sizes[rank]], wl.N), 11)
+    o = torch.zeros(4 + 3 * wl.N + 9 * wl.N * wl.N, dtype=torch.float64)
+    grp.energy_forces_device(torch.zeros(wl.N, 3, dtype=torch.float64), o)
+    ref = orc.reduce(acc, wl.N)
+    r = o.numpy()
+    N3 = 3 * wl.N
+    out[rank] = (abs(r[0] - ref["E"]) / abs(ref["E"]), abs(r[1] - ref["E_err"]) / ref["E_err"],
+                 float(np.max(np.abs(r[4:4 + N3] - ref["f"])) / np.max(np.abs(ref["f"]))),
+                 float(np.max(np.abs(r[4 + N3:].reshape(N3, N3) - ref["S"])) / np.max(np.abs(ref["S"]))),
+                 sizes)
+    dist.destroy_process_group()
+
+
+@pytest.mark.timeout(180)
+def test_two_gloo_ranks_walker_sharded_reduction_equals_single_process():
+    """11 walkers split 6 + 5 over two gloo ranks: the sharded E, E_err, f and S
+    equal the oracle's reduction over all 11 walkers."""
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(150)
+        assert p.exitcode == 0
+    for r in range(2):
+        eE, eErr, ef, eS, sizes = out[r]
+        assert sizes == [6, 5]
+        assert eE < 1e-13 and eErr < 1e-10 and ef < 1e-12 and eS < 1e-11, out[r]
