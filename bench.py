@@ -42,7 +42,11 @@ def _args():
     ap.add_argument("--sweeps", type=int, default=None)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--recompute-every", type=int, default=8)
-    ap.add_argument("--fp64-sweeps", type=int, default=4, help="sweeps per step of the FP64-form comparison (0: skip)")
+    ap.add_argument("--fp64-sweeps", type=int, default=50,
+                    help="measured sweeps of the timed FP64-form call (0: skip the FP64-form comparison)")
+    ap.add_argument("--rs-sweep", default="1.3,1.4,1.5",
+                    help="other densities r_s timed at the headline size (comma list; empty: skip)")
+    ap.add_argument("--rs-sweeps", type=int, default=200, help="sweeps per timed call of the r_s sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--serve-requests", type=int, default=200, help="served-form requests (0: skip)")
@@ -53,6 +57,10 @@ def _args():
     ap.add_argument("--toy-steps", type=int, default=None, help="steps per trajectory of the timed toy launch")
     ap.add_argument("--no-jastrow34", action="store_true", help="skip the e-e-n-n Jastrow (FP64 form) leg")
     ap.add_argument("--jastrow34-only", action="store_true", help="run only that leg (one JSON line)")
+    ap.add_argument("--trajectory", type=int, default=0,
+                    help="run only an MD trajectory of this many Langevin steps (S = Cov(f) rebuilt every step) "
+                         "at the headline size and print one JSON line")
+    ap.add_argument("--traj-sweeps", type=int, default=100, help="measured sweeps per MD step of --trajectory")
     return ap.parse_args()
 
 
@@ -124,14 +132,32 @@ class ClockSampler:
 #   reciprocal space: structure factor 14 per (electron, k),
 #     force 12 per (nucleus, k)
 #   g_i, l_i: 8 n per electron;  K = G Y G: 8 n^3 per walker
-# DRAM bytes per walker sample of the measure kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum of one ncu capture at 2048 walkers, scaled by walkers:
-# traffic grows with the walker count); profiles/measure_kernel_h128_w2048_mixed.md.
-# None once the kernel has changed since that capture.
-MEASURE_DRAM_BYTES_PER_WALKER = (593.609216e6 + 85.250816e6) / 2048
-
+# DRAM traffic of a kernel comes from the committed ncu summaries under
+# profiles/: a line "machine: kernel=<class> traffic_bytes_per_<unit>=<bytes>
+# source=<file> sha256=<hex>" written from one capture.  It is used only while
+# the kernel's source file still has that hash (null once the kernel changed).
 MEASURE_UNIT = {"ee_jas": 55.0, "ep_jas": 55.0, "ee_ewald": 6.0 + 10.0 * 4.19, "ep": 130.0 + 6.0 + 19.0 * 4.19,
                 "sk": 14.0, "fk": 12.0}
+
+
+def _profile_traffic(cls: str):
+    """(bytes per unit, unit, summary file) of kernel class `cls` from profiles/, or None."""
+    import glob
+    import hashlib
+    import re
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            m = re.match(r"\s*machine:\s*kernel=(\S+)\s+traffic_bytes_per_(\S+?)=(\S+)\s+source=(\S+)\s+sha256=(\S+)",
+                         line)
+            if not m or m.group(1) != cls:
+                continue
+            src = os.path.join(ROOT, m.group(4))
+            if not os.path.exists(src):
+                continue
+            if hashlib.sha256(open(src, "rb").read()).hexdigest() != m.group(5):
+                return None
+            return float(m.group(3)), m.group(2), os.path.relpath(path, ROOT)
+    return None
 
 
 def _nk(mmax: int) -> int:
@@ -260,9 +286,11 @@ def _toy_bench(stream, steps, rank, n_steps=None, table=True):
             "mean_U_vs_delta": rows or None}
 
 
-def _jastrow34_bench(stream):
+def _jastrow34_bench(stream, calls=8):
     """The FP64 form with and without the e-e-n-n Jastrow term (N = 64, 1024 walkers,
-    4 measured sweeps + 1 continuation per call, a sample every sweep)."""
+    4 measured sweeps + 1 continuation per call, a sample every sweep): after a
+    warm-up call, `calls` calls timed one by one; the median, min and max and the
+    median SM clock over them."""
     import numpy as np
     import torch
     from paper_1605_08423_gb300 import qmcmd as q
@@ -281,18 +309,26 @@ def _jastrow34_bench(stream):
         sysq = q.QMCSystem(cfg, wl.R)
         sysq.set_stream(stream.cuda_stream)
         o = torch.zeros(4 + 3 * wl.N + 9 * wl.N * wl.N, dtype=torch.float64, device="cuda")
-        sysq.energy_forces_device(R_dev, o)
+        sysq.energy_forces_device(R_dev, o)          # warm-up call
         sysq.sync()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sysq.energy_forces_device(R_dev, o)
-        e1.record(stream)
-        torch.cuda.synchronize()
+        clocks = ClockSampler(torch.cuda.current_device())
+        ts = []
+        for _ in range(calls):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sysq.energy_forces_device(R_dev, o)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        clk = clocks.stop()
         sysq.sync()
-        t = e0.elapsed_time(e1) / 1e3
-        out[tag] = {"electron_moves_per_s": wl.walkers * wl.N * (cfg.sweeps + cfg.warmup_cont) / t,
-                    "force_evals_per_s": wl.walkers * cfg.sweeps / t, "ms_per_call": 1e3 * t,
+        ts.sort()
+        t = ts[len(ts) // 2]
+        moves = wl.walkers * wl.N * (cfg.sweeps + cfg.warmup_cont)
+        out[tag] = {"electron_moves_per_s": moves / t, "force_evals_per_s": wl.walkers * cfg.sweeps / t,
+                    "ms_per_call_median": 1e3 * t, "ms_per_call_min": 1e3 * ts[0], "ms_per_call_max": 1e3 * ts[-1],
+                    "calls_timed": calls, "sm_mhz_median": clk.get("sm_mhz"), "clock_reasons": clk.get("reasons"),
                     "E": float(o[0].item())}
         sysq.close()
     return out
@@ -354,6 +390,79 @@ def run_toy_only(args, rank, local):
     if rank == 0:
         print(json.dumps({**toy, "n_gpus": 1, "steps": args.steps, "warmup": 3, "higher_is_better": True,
                           "dtype": "f64", "data": "synthetic"}), flush=True)
+
+
+def run_trajectory(args, rank, local):
+    """A Langevin trajectory at T = 1500 K (the headline system's temperature),
+    Delta = 0.1, S = Cov(f) rebuilt by every step's energy/force call, walkers
+    carried over between steps; the whole trajectory timed with CUDA events on
+    the library's stream (device API, R resident on the device)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_1605_08423_gb300 import qmcmd as q
+    from paper_1605_08423_gb300 import synth
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    over = {"rs": args.rs, "seed": 1002 + rank, "sweeps": args.traj_sweeps}
+    if args.walkers:
+        over["walkers"] = args.walkers
+    wl = synth.workload(args.workload, **over)
+    prec = q.QMC_MIXED if args.precision == "mixed" else q.QMC_FP64
+    cfg = q.Config.from_workload(wl, precision=prec, warmup=20, warmup_cont=5, measure_every=1,
+                                 recompute_every=args.recompute_every)
+    N, W, N3 = wl.N, wl.walkers, 3 * wl.N
+    system = q.QMCSystem(cfg, wl.R)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    system.set_stream(stream.cuda_stream)
+    R_dev = torch.tensor(wl.R, dtype=torch.float64, device="cuda")
+    steps = args.trajectory
+    outs = torch.zeros((steps, 4 + N3 + N3 * N3), dtype=torch.float64, device="cuda")
+    Rs = torch.zeros((steps + 1, N3), dtype=torch.float64, device="cuda")
+    Rs[0] = R_dev.reshape(-1)
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        system.energy_forces_device(R_dev, outs[k])
+        system.langevin_step_device(R_dev, outs[k, 4:4 + N3], outs[k, 4 + N3:], wl.T_kelvin, wl.delta, q.QMC_S_COV)
+        Rs[k + 1].copy_(R_dev.reshape(-1))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    system.sync()
+    ms = e0.elapsed_time(e1)
+    o = outs.cpu().numpy()
+    E, Eerr = o[:, 0], o[:, 1]
+    R = Rs.cpu().numpy()
+    d = R[1:] - R[:-1]
+    d -= wl.L * np.round(d / wl.L)
+    step_rms = np.sqrt(np.mean(d ** 2, axis=1))
+    half = steps // 2
+    slope = float(np.polyfit(np.arange(steps), E, 1)[0]) if steps > 1 else 0.0
+    moves = W * N * (cfg.sweeps + cfg.warmup_cont) * steps
+    out = {"metric": "MD steps/s of the accelerated Langevin dynamics (VMC E, f, S = Cov(f) every step)",
+           "value": steps / (ms / 1e3), "unit": "MD steps/s", "steps": steps, "ms_per_md_step": ms / steps,
+           "electron_moves_per_s": moves / (ms / 1e3), "force_evals_per_s": W * cfg.sweeps * steps / (ms / 1e3),
+           "dtype": "f32" if prec == q.QMC_MIXED else "f64", "data": "synthetic", "clocks": clk,
+           "config": {"workload": f"{args.workload}: N={N} H, r_s={wl.rs}, L={wl.L:.3f} bohr, {wl.n_gauss} "
+                                  f"s-Gaussians/proton, {W} walkers x {cfg.sweeps} sweeps (+{cfg.warmup_cont} "
+                                  f"continuation) per MD step, T={wl.T_kelvin} K, Delta={wl.delta}, adopted scheme, "
+                                  f"alpha = 0.122 N_c, S = Cov(f) rebuilt every step",
+                      "walkers": W, "sweeps_per_step": cfg.sweeps},
+           "E_first": float(E[0]), "E_last": float(E[-1]),
+           "E_mean_first_half": float(E[:half].mean()) if half else None,
+           "E_mean_second_half": float(E[half:].mean()),
+           "E_err_median": float(np.median(Eerr)), "E_slope_per_step": slope,
+           "accept_mean": float(o[:, 3].mean()), "rms_nuclear_step_bohr": float(step_rms.mean()),
+           "E_series": [float(x) for x in E]}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    system.close()
 
 
 def run_ours(args, ws, rank, local):
@@ -466,23 +575,33 @@ def run_ours(args, ws, rank, local):
                           "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock",
                           "flops_per_launch": fl, "avg_launch_ms": avg}
     dom = max(kt, key=lambda k: kt[k][0])
-    if "measure" in roofs and use_tc and N == 128 and G == 4 and MEASURE_DRAM_BYTES_PER_WALKER:
-        roofs["measure"]["traffic"] = MEASURE_DRAM_BYTES_PER_WALKER * W
-        roofs["measure"]["traffic_source"] = "ncu dram bytes, 2048-walker capture scaled to the launch"
+    for cls in roofs:
+        tr = _profile_traffic(cls) if use_tc and N == 128 and G == 4 else None
+        if tr is not None:
+            per_unit, unit, src = tr
+            units = {"walker": W, "row": W * N}.get(unit)
+            if units:
+                roofs[cls]["traffic"] = per_unit * units
+                roofs[cls]["traffic_source"] = (f"ncu dram__bytes_read.sum + dram__bytes_write.sum per {unit} "
+                                                f"({src}), scaled to the launch; same kernel source")
     roof = roofs.get(dom, {"kernel": dom, "bound": "alu", "achieved": None, "peak": fp32_peak,
                            "unit": "TFLOP/s", "frac": None, "traffic": None})
     breakdown = {k: {"ms": v[0] / args.steps, "launches": v[1] // max(args.steps, 1)} for k, v in kt.items()}
 
-    # FP64 form on the same system (short burst) for the "vs FP64 form" comparison
+    # FP64 form on the same system, like for like: the same walkers, sample
+    # every sweep, the same continuation and recompute schedule; one warm-up
+    # call (walker warm-up plus code paths), then one timed call of
+    # args.fp64_sweeps measured sweeps (+ the continuation sweeps), CUDA events
+    # on the same stream.
     fp64 = None
     if args.fp64_sweeps > 0 and prec == q.QMC_MIXED and rank == 0:
         wl64 = synth.workload(args.workload, **{**over, "sweeps": args.fp64_sweeps})
-        cfg64 = q.Config.from_workload(wl64, precision=q.QMC_FP64, warmup=0, warmup_cont=0, measure_every=1,
-                                       recompute_every=args.recompute_every)
+        cfg64 = q.Config.from_workload(wl64, precision=q.QMC_FP64, warmup=cfg.warmup_cont, warmup_cont=cfg.warmup_cont,
+                                       measure_every=1, recompute_every=args.recompute_every)
         s64 = q.QMCSystem(cfg64, wl.R)
         s64.set_stream(stream.cuda_stream)
         out64 = torch.zeros_like(out_dev)
-        s64.energy_forces_device(R_dev, out64)       # first call (warms code paths)
+        s64.energy_forces_device(R_dev, out64)       # warm-up call
         s64.sync()
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -492,11 +611,46 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         s64.sync()
         t64 = f0.elapsed_time(f1) / 1e3
-        fp64 = {"value": W * N * args.fp64_sweeps / t64, "unit": "electron moves/s",
-                "force_evals_per_s": W * args.fp64_sweeps / t64,
-                "sample": f"{args.fp64_sweeps} sweeps + {args.fp64_sweeps} samples, {W} walkers",
-                "mixed_over_fp64": value / (W * N * args.fp64_sweeps / t64)}
+        sw64 = args.fp64_sweeps + cfg64.warmup_cont
+        fp64 = {"value": W * N * sw64 / t64, "unit": "electron moves/s",
+                "force_evals_per_s": W * args.fp64_sweeps / t64, "ms_per_call": 1e3 * t64,
+                "sample": f"one call after a warm-up call: {args.fp64_sweeps} sweeps (+{cfg64.warmup_cont} "
+                          f"continuation), a sample every sweep, {W} walkers, FP64 inverse recompute every "
+                          f"{args.recompute_every} sweeps",
+                "mixed_over_fp64_moves": value / (W * N * sw64 / t64),
+                "mixed_over_fp64_force_evals": fevals / (W * args.fp64_sweeps / t64)}
         s64.close()
+
+    # the other densities of the headline size: one warm-up call, one timed call each
+    rs_rows = None
+    if args.rs_sweep and prec == q.QMC_MIXED and rank == 0 and args.workload == "h128":
+        rs_rows = {}
+        for rs in [float(x) for x in args.rs_sweep.split(",") if x.strip()]:
+            wlr = synth.workload(args.workload, **{**over, "rs": rs, "sweeps": args.rs_sweeps})
+            cfgr = q.Config.from_workload(wlr, precision=prec, warmup=20, warmup_cont=cfg.warmup_cont,
+                                          measure_every=1, recompute_every=args.recompute_every)
+            sr = q.QMCSystem(cfgr, wlr.R)
+            sr.set_stream(stream.cuda_stream)
+            Rr = torch.tensor(wlr.R, dtype=torch.float64, device="cuda")
+            outr = torch.zeros_like(out_dev)
+            sr.energy_forces_device(Rr, outr)
+            sr.sync()
+            torch.cuda.synchronize()
+            r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            r0.record(stream)
+            sr.energy_forces_device(Rr, outr)
+            r1.record(stream)
+            torch.cuda.synchronize()
+            sr.sync()
+            tr = r0.elapsed_time(r1) / 1e3
+            o = outr.cpu().numpy()
+            rs_rows[f"{rs:g}"] = {"L": wlr.L, "electron_moves_per_s": W * N * (args.rs_sweeps + cfgr.warmup_cont) / tr,
+                                  "force_evals_per_s": W * args.rs_sweeps / tr, "ms_per_call": 1e3 * tr,
+                                  "E": float(o[0]), "E_err": float(o[1]), "accept": float(o[3])}
+            sr.close()
+        rs_rows[f"{wl.rs:g}"] = {"L": wl.L, "electron_moves_per_s": value, "force_evals_per_s": fevals,
+                                 "ms_per_call": ms / args.steps, "E": res["E"], "E_err": res["E_err"],
+                                 "accept": res["accept"], "note": "headline timed steps"}
 
     # served form: many concurrent trajectories, Poisson arrivals, continuous batching
     serving = None
@@ -541,9 +695,15 @@ def run_ours(args, ws, rank, local):
                                       f"{G} s-Gaussians/proton, {W} walkers x {cfg.sweeps} sweeps "
                                       f"(+{cfg.warmup_cont} continuation), sample every sweep, "
                                       f"{'mixed' if prec == q.QMC_MIXED else 'FP64'} form, "
-                                      f"FP64 inverse every {cfg.recompute_every} sweeps, "
+                                      f"FP64 Gauss-Jordan inverse recompute every {cfg.recompute_every} sweeps, "
                                       "adjoint forces, Langevin step with S = Cov(f)",
                           "walkers": W, "sweeps": cfg.sweeps, "parallelism": f"replicas x{ws}",
+                          "force_evals_per_s": fevals,
+                          "fp64_form_force_evals_per_s": fp64["force_evals_per_s"] if fp64 else None,
+                          "fp64_form_electron_moves_per_s": fp64["value"] if fp64 else None,
+                          "mixed_over_fp64_force_evals": fp64["mixed_over_fp64_force_evals"] if fp64 else None,
+                          "rs_sweep_electron_moves_per_s": ({k: v["electron_moves_per_s"] for k, v in rs_rows.items()}
+                                                            if rs_rows else None),
                           "l2": "inputs larger than L2 (walker state "
                                 f"{q.footprint_bytes(cfg) / 1e9:.1f} GB per replica)"},
                "force_evals_per_s": fevals,
@@ -555,6 +715,7 @@ def run_ours(args, ws, rank, local):
                "rooflines": roofs,
                "kernel_ms_per_step": breakdown,
                "fp64_form": fp64,
+               "rs_sweep": rs_rows,
                "cpu_baseline": cpu,
                "serving": serving,
                "toy_langevin": toy,
@@ -576,6 +737,9 @@ def main():
         return
     if args.toy_only:
         run_toy_only(args, rank, local)
+        return
+    if args.trajectory > 0:
+        run_trajectory(args, rank, local)
         return
     if args.jastrow34_only:
         import torch
