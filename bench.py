@@ -8,8 +8,10 @@ workload is the N=128 dense-hydrogen system (r_s = 1.2, 4 s-Gaussians per
 proton, 16384 walkers, 1000 sweeps) in the mixed-precision form.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-Under torchrun each rank runs an independent replica (weak scaling, no
-collective on the data path); rank 0 prints one JSON line.
+Under torchrun the walkers of one MD trajectory are sharded over the ranks
+(each rank keeps the per-GPU walker count: weak scaling); every energy/force
+evaluation exchanges its walker sums by two all-reduces and every rank applies
+the same Langevin step; rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -476,9 +478,10 @@ def run_ours(args, ws, rank, local):
 
     __graft_entry__.build()
     torch.cuda.set_device(local)
-    if ws > 1:
+    shard = ws > 1
+    if shard:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    over = {"rs": args.rs, "seed": 1002 + rank}
+    over = {"rs": args.rs, "seed": 1002}     # one system; under torchrun its walkers are split over the ranks
     if args.walkers:
         over["walkers"] = args.walkers
     if args.sweeps:
@@ -490,16 +493,25 @@ def run_ours(args, ws, rank, local):
     N, n, G = wl.N, wl.N // 2, wl.n_gauss
     B, W, N3 = N * G, wl.walkers, 3 * wl.N
     system = q.QMCSystem(cfg, wl.R)
+    if shard:
+        system.set_walker_offset(rank * W)   # rank r holds walkers [r W, (r + 1) W) of W x ranks
     # a dedicated stream: the library launches on it and the timing events are recorded on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     system.set_stream(stream.cuda_stream)
+    group = q.ShardGroup(system, W * ws) if shard else None
     R_dev = torch.tensor(wl.R, dtype=torch.float64, device="cuda")
     out_dev = torch.zeros(4 + N3 + N3 * N3, dtype=torch.float64, device="cuda")
     T_K, delta = wl.T_kelvin, wl.delta
 
+    def evaluate():
+        if group is not None:
+            group.energy_forces_device(R_dev, out_dev)
+        else:
+            system.energy_forces_device(R_dev, out_dev)
+
     def step():
-        system.energy_forces_device(R_dev, out_dev)
+        evaluate()
         system.langevin_step_device(R_dev, out_dev[4:4 + N3], out_dev[4 + N3:], T_K, delta, q.QMC_S_COV)
 
     for _ in range(args.warmup):
@@ -537,13 +549,27 @@ def run_ours(args, ws, rank, local):
     value = ws * moves_per_step * args.steps / (ms / 1e3)
     fevals = ws * fevals_per_step * args.steps / (ms / 1e3)
 
-    # end to end through the host-pointer C ABI (R, f, S host buffers; copies inside)
+    # end to end through the public API with host buffers: one GPU, the
+    # host-pointer C ABI (R, f, S copied in and out inside the calls); sharded,
+    # R copied in from pinned host memory, the sharded evaluation and Langevin
+    # step, the result (E, E_err, N_c, accept, f, S and R') copied back
     Rh = wl.R.copy()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        r = system.energy_forces(Rh)
-        Rh = system.langevin_step(Rh, r["f"], r["S"], T_K, delta, q.QMC_S_COV).reshape(N, 3)
+    if group is None:
+        for _ in range(args.e2e_steps):
+            r = system.energy_forces(Rh)
+            Rh = system.langevin_step(Rh, r["f"], r["S"], T_K, delta, q.QMC_S_COV).reshape(N, 3)
+    else:
+        R_pin = torch.tensor(Rh, dtype=torch.float64).pin_memory()
+        out_pin = torch.zeros(out_dev.numel() + N3, dtype=torch.float64).pin_memory()
+        for _ in range(args.e2e_steps):
+            R_dev.copy_(R_pin.reshape(N, 3), non_blocking=True)
+            step()
+            out_pin[:out_dev.numel()].copy_(out_dev, non_blocking=True)
+            out_pin[out_dev.numel():].copy_(R_dev.reshape(-1), non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            R_pin.copy_(out_pin[out_dev.numel():])
     t_e2e = time.perf_counter() - t0
     e2e = ws * moves_per_step * args.e2e_steps / t_e2e
     h2d = 8 * (N3 + N3 + N3 + N3 * N3)
@@ -664,6 +690,16 @@ def run_ours(args, ws, rank, local):
         sres, swall = serve.run_poisson(srv, tids, trajs, n_requests=args.serve_requests, mean_ms=2.0,
                                         seed=13 + rank)
         serving = serve.summarize(sres, swall)
+        # the same mix offered below its measured capacity (60 %): latency is then
+        # service time plus little queueing
+        cap = serving["completed_per_s"]
+        if cap > 0:
+            mean_lo = 1e3 / (0.6 * cap)
+            n_lo = max(20, args.serve_requests // 4)
+            lres, lwall = serve.run_poisson(srv, tids, trajs, n_requests=n_lo, mean_ms=mean_lo, seed=17 + rank)
+            lo = serve.summarize(lres, lwall)
+            lo["mean_interarrival_ms"] = mean_lo
+            serving["below_capacity"] = lo
         serving.update({"trajectories": len(trajs), "mean_interarrival_ms": 2.0, "max_active": args.serve_active,
                         "hbm_budget_gb": srv.stats()["budget"] / 1e9, "stats": srv.stats(),
                         "workload": "N in {32,64,128}, r_s~U(1.2,1.5), T~U(600,3000) K, 1024-8192 walkers, "
@@ -697,7 +733,8 @@ def run_ours(args, ws, rank, local):
                                       f"{'mixed' if prec == q.QMC_MIXED else 'FP64'} form, "
                                       f"FP64 Gauss-Jordan inverse recompute every {cfg.recompute_every} sweeps, "
                                       "adjoint forces, Langevin step with S = Cov(f)",
-                          "walkers": W, "sweeps": cfg.sweeps, "parallelism": f"replicas x{ws}",
+                          "walkers": W, "walkers_total": W * ws, "sweeps": cfg.sweeps,
+                          "parallelism": f"walker shards x{ws} (two all-reduces per MD step)" if shard else "one GPU",
                           "force_evals_per_s": fevals,
                           "fp64_form_force_evals_per_s": fp64["force_evals_per_s"] if fp64 else None,
                           "fp64_form_electron_moves_per_s": fp64["value"] if fp64 else None,
@@ -705,7 +742,7 @@ def run_ours(args, ws, rank, local):
                           "rs_sweep_electron_moves_per_s": ({k: v["electron_moves_per_s"] for k, v in rs_rows.items()}
                                                             if rs_rows else None),
                           "l2": "inputs larger than L2 (walker state "
-                                f"{q.footprint_bytes(cfg) / 1e9:.1f} GB per replica)"},
+                                f"{q.footprint_bytes(cfg) / 1e9:.1f} GB per GPU)"},
                "force_evals_per_s": fevals,
                "clocks": clk,
                "e2e": {"value": e2e, "unit": "electron moves/s", "h2d_bytes_per_step": h2d,

@@ -75,8 +75,8 @@ typedef struct {
     /* 3- and 4-body e-e-n-n Jastrow term of the SI, one periodised Gaussian
      * chi_a(r) = exp(-zeta_j |d(r - R_a)|^2) per proton:
      *   U += sum_{i<j} sum_{a,b} fj[a][b] chi_a(r_i) chi_b(r_j).
-     * fj = NULL switches it off.  FP64 form with N <= 64 only, and fj must be
-     * exactly symmetric (fj[a][b] == fj[b][a]); INVALID otherwise. */
+     * fj = NULL switches it off.  Both forms (the mixed form in FP32), and fj
+     * must be exactly symmetric (fj[a][b] == fj[b][a]); INVALID otherwise. */
     double zeta_j;            /* Jastrow-orbital exponent, bohr^-2 (the SI uses 0.7933844) */
     const double* fj;         /* [N][N] symmetric coefficients (copied), or NULL         */
 } qmc_params;
@@ -105,7 +105,8 @@ void qmc_destroy(qmc_system* h);
 /* Bytes of device memory a handle with parameters p holds (admission control). */
 size_t qmc_footprint_bytes(const qmc_params* p);
 
-/* Launch subsequent work of h on `stream` (a cudaStream_t; NULL = handle's own). */
+/* Launch subsequent work of h on `stream` (a cudaStream_t; NULL = the handle's
+ * own stream, so pass cudaStreamLegacy for the legacy default stream). */
 int qmc_set_stream(qmc_system* h, void* stream);
 
 /* Wait for h's stream and return the device-side error status (QMC_OK or a code). */
@@ -125,6 +126,24 @@ int qmc_energy_forces(qmc_system* h, const double* R, qmc_result* out);
 /* Same, device pointers, asynchronous: R_dev [N][3]; out_dev receives
  * [E, E_err, n_samples, accept, f(3N), S(3N*3N)] as FP64. */
 int qmc_energy_forces_device(qmc_system* h, const double* R_dev, double* out_dev);
+
+/*
+ * Pressure of the last qmc_energy_forces call (the paper's equations of state;
+ * the paper does not state its estimator).  The Coulomb potential, including
+ * its Ewald sum with kappa L and the k cutoff in units of 2 pi / L held fixed,
+ * is homogeneous of degree -1 in all lengths, so for the trial state scaled
+ * with the box E(lambda) = T / lambda^2 + V / lambda and the virial gives
+ *   P = (2 <T_L> + <V_L>) / (3 L^3) + N k_B T / L^3
+ * (electrons, then the ideal-gas term of classical nuclei at temperature
+ * T_kelvin; pass 0 for the electronic part alone).  out [5] = [P, its error bar
+ * from walker blocks, the electronic part, <V_L>, <T_L>], hartree / bohr^3
+ * (1 Ha/bohr^3 = 29421.0 GPa) and hartree.  qmc_pressure takes a host array and
+ * returns after the result is there; qmc_pressure_device writes device memory
+ * asynchronously.  For this handle's walkers only (a sharded evaluation would
+ * need its per-walker sums combined).  Errors: INVALID, CUDA.
+ */
+int qmc_pressure(qmc_system* h, double T_kelvin, double* out);
+int qmc_pressure_device(qmc_system* h, double T_kelvin, double* out_dev);
 
 /*
  * Walker sharding.  Walkers are independent Markov chains, so one energy/force
@@ -377,6 +396,9 @@ int qmc_checkpoint_load(qmc_system* h, const void* buf);
  * qmc_server_progress never blocks: the caller's loop calls it to retire
  * finished requests and start queued ones, and qmc_server_fetch collects a
  * finished request (1 = done, 0 = still pending).
+ * The budget is allocated as one device arena by qmc_server_create (OOM if it
+ * cannot be); trajectories are carved from it, so admission and eviction
+ * allocate and free no device memory.
  */
 typedef struct qmc_server qmc_server;
 typedef struct {
@@ -386,6 +408,9 @@ typedef struct {
     double* cov;                         /* [3N][3N] or NULL                        */
     double* R_next;                      /* [3N] nuclei after the Langevin step, or NULL */
     double latency_ms, wait_ms, run_ms;  /* submit->done, submit->start, start->done */
+    double gpu_start_ms, gpu_end_ms;     /* the request's work on the device: from its start
+                                            event to its end event, ms after the server was
+                                            created (-1 if not timed) */
 } qmc_served;
 int qmc_server_create(size_t hbm_budget_bytes, int max_active, qmc_server** out);
 void qmc_server_destroy(qmc_server* s);

@@ -85,6 +85,13 @@ def lib():
         L.orc_init_walkers.argtypes = [C.POINTER(Params), _dp, C.c_int, C.c_uint64, _dp]
         L.orc_jastrow_delta.restype = C.c_double
         L.orc_jastrow_delta.argtypes = [C.POINTER(Params), _dp, _dp, C.c_int, _dp]
+        L.orc_vmc_v.restype = None
+        L.orc_vmc_v.argtypes = [C.POINTER(Params), _dp, C.POINTER(ChainArgs), _dp, _dp, _dp, C.POINTER(C.c_longlong),
+                                C.POINTER(C.c_longlong)]
+        L.orc_pressure.restype = None
+        L.orc_pressure.argtypes = [C.c_int, C.c_int, _dp, _dp, C.c_double, C.c_double, _dp]
+        L.orc_slater_matrices.restype = None
+        L.orc_slater_matrices.argtypes = [C.POINTER(Params), _dp, _dp, _dp]
         L.orc_vmc.argtypes = [C.POINTER(Params), _dp, C.POINTER(ChainArgs), _dp, _dp,
                               C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
         L.orc_reduce.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
@@ -197,6 +204,22 @@ def eval_configs(sys: System, R, X, derivs=True):
     return lp, el, dl, de
 
 
+def slater_matrices(sys: System, R, X):
+    """The two Slater blocks (A_up, A_dn), A[i][j] = phi_j(r_i), at one configuration X [Ne, 3]."""
+    p = sys.cparams()
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    nu = p.n_up
+    out = np.zeros((sys.n_elec, p.n_orb))
+    lib().orc_slater_matrices(C.byref(p), _ptr(R), _ptr(X), _ptr(out))
+    return out[:nu], out[nu:]
+
+
+def slater_condition(sys: System, R, X) -> float:
+    """Largest 2-norm condition number of the two Slater blocks at X [Ne, 3]."""
+    return max(float(np.linalg.cond(A)) for A in slater_matrices(sys, R, X))
+
+
 def jastrow_delta(sys: System, R, X, i, xn) -> float:
     """U(X with electron i at xn) - U(X), as the oracle's Metropolis step computes it."""
     p = sys.cparams()
@@ -213,17 +236,29 @@ def init_walkers(sys: System, R, W, seed):
 
 
 def vmc(sys: System, R, *, W, n_sweeps, n_warmup, measure_every=1, sigma=0.3, seed=1, md_step=0,
-        X=None, forces=True):
-    """Run W Metropolis chains; returns (X, acc[W, 3+9N], accept_ratio)."""
+        X=None, forces=True, potential=False):
+    """Run W Metropolis chains; returns (X, acc[W, 3+9N], accept_ratio), and with
+    potential=True also vacc[W] (each walker's sum of the sampled V_L) as a fourth item."""
     p = sys.cparams()
     R = np.ascontiguousarray(R, dtype=np.float64)
     init = X is None
     Xa = np.zeros((W, sys.n_elec, 3)) if init else np.array(X, dtype=np.float64, copy=True)
     acc = np.zeros((W, 3 + 9 * sys.N))
+    vacc = np.zeros(W)
     ca = ChainArgs(W, n_sweeps, n_warmup, measure_every, int(init), int(forces), md_step, 0, sigma, seed)
     na = C.c_longlong(0); nt = C.c_longlong(0)
-    lib().orc_vmc(C.byref(p), _ptr(R), C.byref(ca), _ptr(Xa), _ptr(acc), C.byref(na), C.byref(nt))
-    return Xa, acc, (na.value / nt.value if nt.value else 0.0)
+    lib().orc_vmc_v(C.byref(p), _ptr(R), C.byref(ca), _ptr(Xa), _ptr(acc), _ptr(vacc), C.byref(na), C.byref(nt))
+    ar = na.value / nt.value if nt.value else 0.0
+    return (Xa, acc, ar, vacc) if potential else (Xa, acc, ar)
+
+
+def pressure(acc, vacc, N, omega, T_nuc=0.0) -> dict:
+    """Virial pressure of a cubic cell from the chains' accumulators (hartree / bohr^3)."""
+    acc = np.ascontiguousarray(acc, dtype=np.float64)
+    vacc = np.ascontiguousarray(vacc, dtype=np.float64)
+    out = np.zeros(5)
+    lib().orc_pressure(acc.shape[0], N, _ptr(acc), _ptr(vacc), omega, T_nuc, _ptr(out))
+    return dict(P=out[0], P_err=out[1], P_el=out[2], V=out[3], T=out[4])
 
 
 def reduce(acc, N):

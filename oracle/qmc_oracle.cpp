@@ -622,7 +622,7 @@ static void init_walker(const Params& p, const Rng& rng, uint32_t w, const doubl
 }
 
 static void run_walker(const Params& p, const ChainArgs& c, const Rng& rng, uint32_t w, const double* R,
-                       double* X, double* acc, long long* n_acc, long long* n_try) {
+                       double* X, double* acc, double* vacc, long long* n_acc, long long* n_try) {
     const int Ne = p.n_up + p.n_dn, N3 = 3 * p.N;
     if (c.init_walkers) init_walker(p, rng, w, R, X);
     // Slater matrices of both spin blocks, rows = electrons
@@ -660,6 +660,7 @@ static void run_walker(const Params& p, const ChainArgs& c, const Rng& rng, uint
         if (sw >= c.n_warmup && ((sw - c.n_warmup + 1) % c.measure_every) == 0) {
             ConfigResult r = eval_config(p, R, X, c.forces != 0);
             acc[0] += 1; acc[1] += r.el; acc[2] += r.el * r.el;
+            if (vacc) vacc[0] += r.epot;
             if (c.forces)
                 for (int k = 0; k < N3; ++k) {
                     acc[3 + k] += r.dlnpsi[k];
@@ -1148,6 +1149,14 @@ int orc_eval_configs(const orc::Params* p, const double* R, int nconf, const dou
     return bad ? -1 : 0;
 }
 
+// Slater matrices at one configuration X [Ne][3]: out [Ne][n_orb], row i =
+// phi_j(r_i) for j < n_orb (spin-up rows first, then spin-down rows); used by
+// the tests to state the condition numbers of their inputs.
+void orc_slater_matrices(const orc::Params* p, const double* R, const double* X, double* out) {
+    const int Ne = p->n_up + p->n_dn;
+    for (int i = 0; i < Ne; ++i) orc::slater_row(*p, R, X + 3 * i, p->n_orb, out + (size_t)i * p->n_orb);
+}
+
 // Change of U when electron i of X moves to xn (the Metropolis Jastrow ratio's exponent).
 double orc_jastrow_delta(const orc::Params* p, const double* R, const double* X, int i, const double* xn) {
     return orc::jastrow_delta(*p, R, X, i, xn);
@@ -1162,18 +1171,53 @@ void orc_init_walkers(const orc::Params* p, const double* R, int W, uint64_t see
 
 // VMC chains of W walkers; X [W][Ne][3] in/out; acc [W][3 + 9N] accumulated
 // (caller zeroes it); n_accept / n_try summed over walkers.
-void orc_vmc(const orc::Params* p, const double* R, const orc::ChainArgs* c, double* X, double* acc,
-             long long* n_accept, long long* n_try) {
+// vacc [W] (or null) accumulates each walker's sum of the sampled potential energy V_L.
+void orc_vmc_v(const orc::Params* p, const double* R, const orc::ChainArgs* c, double* X, double* acc, double* vacc,
+               long long* n_accept, long long* n_try) {
     const int Ne = p->n_up + p->n_dn, stride = 3 + 9 * p->N;
     orc::Rng rng(c->seed);
     long long na = 0, nt = 0;
 #pragma omp parallel for schedule(dynamic) reduction(+ : na, nt)
     for (int w = 0; w < c->W; ++w) {
         long long a = 0, t = 0;
-        orc::run_walker(*p, *c, rng, (uint32_t)w, R, X + (size_t)w * 3 * Ne, acc + (size_t)w * stride, &a, &t);
+        orc::run_walker(*p, *c, rng, (uint32_t)w, R, X + (size_t)w * 3 * Ne, acc + (size_t)w * stride,
+                        vacc ? vacc + w : nullptr, &a, &t);
         na += a; nt += t;
     }
     *n_accept = na; *n_try = nt;
+}
+
+void orc_vmc(const orc::Params* p, const double* R, const orc::ChainArgs* c, double* X, double* acc,
+             long long* n_accept, long long* n_try) {
+    orc_vmc_v(p, R, c, X, acc, nullptr, n_accept, n_try);
+}
+
+// Pressure of a cubic cell of volume omega from the chains' accumulators (the
+// paper reports P(rho) along isotherms but does not state its estimator;
+// reading: the virial of the Coulomb system).  Every term of the Hamiltonian
+// is a kinetic term (degree -2) or a Coulomb term (degree -1) in the lengths,
+// so the trial state scaled with the cell has E(lambda) = <T>/lambda^2 +
+// <V>/lambda, and -dE/dOmega = (2<T> + <V>)/(3 Omega), with <T> = <E_L> - <V_L>.
+// Classical nuclei at temperature T_nuc add the ideal-gas term N T_nuc / Omega.
+// out = [P, error bar from walker blocks, electronic part, <V_L>, <T_L>].
+void orc_pressure(int W, int N, const double* acc, const double* vacc, double omega, double T_nuc, double* out) {
+    const int stride = 3 + 9 * N;
+    double c = 0, e = 0, v = 0;
+    for (int w = 0; w < W; ++w) { c += acc[(size_t)w * stride]; e += acc[(size_t)w * stride + 1]; v += vacc[w]; }
+    const double E = e / c, V = v / c, T = E - V;
+    const double Pel = (2.0 * T + V) / (3.0 * omega);
+    double d2 = 0;
+    for (int w = 0; w < W; ++w) {
+        const double cw = acc[(size_t)w * stride];
+        const double Ew = acc[(size_t)w * stride + 1] / cw, Vw = vacc[w] / cw;
+        const double pw = (2.0 * (Ew - Vw) + Vw) / (3.0 * omega);
+        d2 += (pw - Pel) * (pw - Pel);
+    }
+    out[0] = Pel + N * T_nuc / omega;
+    out[1] = W > 1 ? std::sqrt(d2 / ((double)W * (W - 1))) : 0.0;
+    out[2] = Pel;
+    out[3] = V;
+    out[4] = T;
 }
 
 void orc_reduce(int W, int N3, const double* acc, double* E, double* Eerr, double* f, double* S, double* Nc) {

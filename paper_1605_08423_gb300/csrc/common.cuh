@@ -145,7 +145,9 @@ struct SysView {
     const double* vconst;   // [1] proton-proton real-space + self energy
     const double* dvpp;     // [3N] d(proton-proton real-space energy)/dR
     int* err;
-    const double* fj;       // [N][N] e-e-n-n Jastrow coefficients (FP64 form), or null
+    double* vacc;           // [W] per-walker sums of the sample's potential energy V_L (pressure), or null
+    const double* fj;       // [N][N] e-e-n-n Jastrow coefficients (symmetric), or null
+    const T* fjt;           // the same in the working precision, or null
     double zeta_j;          // their Gaussians' exponent
 };
 

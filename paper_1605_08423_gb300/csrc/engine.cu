@@ -10,6 +10,7 @@
 #include "../../include/qmcmd.h"
 #include "common.cuh"
 #include "kernels.cuh"
+#include "pool.h"
 
 using namespace qmc;
 
@@ -30,7 +31,8 @@ struct EventPair { cudaEvent_t a, b; int cls; };
 struct qmc_system {
     qmc_params p;
     std::vector<double> zeta_h, coeff_h, fj_h;
-    double* d_fj = nullptr;    // e-e-n-n Jastrow coefficients [N][N] (FP64 form)
+    double* d_fj = nullptr;    // e-e-n-n Jastrow coefficients [N][N]
+    float* d_fj32 = nullptr;   // the same in FP32 (mixed form)
     int N, n, G, B, W, nk, mmax;
     bool mixed;
     cudaStream_t stream = nullptr, own_stream = nullptr;
@@ -59,6 +61,8 @@ struct qmc_system {
     void *d_uacc = nullptr, *d_Phi = nullptr, *d_Gt = nullptr, *d_D = nullptr, *d_Lp = nullptr;
     double* d_logdet = nullptr;
     double* d_acc = nullptr;
+    double* d_vacc = nullptr;    // per-walker sums of V_L (virial pressure)
+    double* d_pout = nullptr;    // pressure output [5]
     unsigned long long* d_nacc = nullptr;
     // reductions and output
     double *d_colsum = nullptr, *d_dev = nullptr, *d_out = nullptr;
@@ -71,6 +75,9 @@ struct qmc_system {
     double fs_delta = 0.0;
     int* d_err = nullptr;
     std::vector<void*> allocs;
+    // device block the handle's arrays are carved from (server admission), or none
+    unsigned char* pool = nullptr;
+    size_t pool_bytes = 0, pool_off = 0;
     uint32_t md_step = 0;
     uint32_t w0 = 0;                     // QMC_OPT_WALKER_OFFSET: Philox stream of walker 0
     bool first_call = true;
@@ -96,6 +103,13 @@ T* dalloc(qmc_system* h, size_t count, int* rc) {
     void* p = nullptr;
     if (*rc != QMC_OK) return nullptr;
     if (count == 0) count = 1;
+    if (h->pool) {   // carve from the caller's block, 256-byte aligned
+        const size_t bytes = (count * sizeof(T) + kPoolAlign - 1) & ~(kPoolAlign - 1);
+        if (h->pool_off + bytes > h->pool_bytes) { *rc = QMC_ERR_OOM; return nullptr; }
+        p = h->pool + h->pool_off;
+        h->pool_off += bytes;
+        return (T*)p;
+    }
     if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
         *rc = QMC_ERR_OOM;
         cudaGetLastError();
@@ -124,7 +138,7 @@ int validate(const qmc_params* p) {
     if (p->precision != QMC_FP64 && p->precision != QMC_MIXED) return QMC_ERR_INVALID;
     if (p->ewald_mmax < 1 || p->ewald_mmax > 12) return QMC_ERR_INVALID;
     if (!(p->L > 0) || !(p->ewald_kappa > 0) || !(p->sigma > 0) || p->b_ee < 0 || p->b_ep < 0) return QMC_ERR_INVALID;
-    if (p->fj && (p->precision != QMC_FP64 || p->n_protons > 64 || !(p->zeta_j > 0))) return QMC_ERR_INVALID;
+    if (p->fj && !(p->zeta_j > 0)) return QMC_ERR_INVALID;
     if (p->n_sweeps / p->measure_every < 1) return QMC_ERR_INVALID;
     if (p->fj) {   // the kernels use row a of f as its column a: f must be exactly symmetric
         const int N = p->n_protons;
@@ -148,14 +162,18 @@ size_t footprint(const qmc_params* p) {
     const size_t nk = nkc;
     size_t b = 0;
     b += 8 * (3 * N + G + B * n + 6 * N + 3 * N + 2) + 4 * (B * n + 6 * N) + 16 * nk + 8 * nk + 16 * (N * nk + nk);
+    b += 4 * (3 * N + G + nk) + 8 * N * nk + 4;      // FP32 copies of R, zeta, kw, exp(i k.R); error word
+    b += t * W * N * 6;                              // proposal trig
     b += 8 * 2 * W * 3 * N;                          // X, Xp
     b += t * (W * N + W * N * n + 2 * W * n * n + 3 * W * N * n + W * N * n);   // uacc, Phi, Gt, D, Lp
     b += 8 * 2 * W + 8 * W * (3 + 9 * N) + 8 * W;   // logdet, acc, nacc
+    b += 8 * W + 8 * 5;                              // V_L sums, pressure output
     b += 8 * (4 + 9 * N) + 8 * W * (3 * N + 1) + 8 * (4 + 3 * N + 9 * N * N);   // colsum, dev, out
     b += 8 * (2 * W + 6 * W * N);                    // eval outputs
     b += 8 * (3 * 3 * N + 3 * 9 * N * N);           // Langevin
     b += 8 * (2 * 3 * N + 2 * 9 * N * N);           // first simplified scheme between its halves
-    if (p->fj) b += 8 * N * N;                       // e-e-n-n Jastrow coefficients
+    if (p->fj) b += (t == 4 ? 12 : 8) * N * N;       // e-e-n-n Jastrow coefficients (+ FP32 copy)
+    b += (size_t)kPoolAllocs * kPoolAlign;           // alignment slack of a carved handle
     if (t == 4) {                                    // tensor-core operands (mixed form)
         b += tc_coeff_bytes((int)B, (int)n);
         b += tc_adjoint_coeff_bytes((int)n, (int)G) + 4 * (2 * W * n * n + 9 * W * N) + 8 * W;
@@ -201,8 +219,9 @@ SysView<T> view(qmc_system* h, int W) {
     s.ptrig = (const T*)(sizeof(T) == 8 ? (const void*)h->d_ptrig64 : (const void*)h->d_ptrig32);
     s.nk = h->nk; s.mmax = h->mmax;
     s.kvec = h->d_kvec; s.kw = h->d_kw; s.eikR = h->d_eikR; s.rho_p = h->d_rhop;
-    s.vconst = h->d_vconst; s.dvpp = h->d_dvpp; s.err = h->d_err;
+    s.vconst = h->d_vconst; s.dvpp = h->d_dvpp; s.err = h->d_err; s.vacc = h->d_vacc;
     s.fj = h->d_fj; s.zeta_j = h->p.zeta_j;
+    s.fjt = (const T*)(sizeof(T) == 8 ? (const void*)h->d_fj : (const void*)h->d_fj32);
     return s;
 }
 
@@ -296,6 +315,7 @@ double run_sampling(qmc_system* h) {
     const Key key = make_key(h->p.seed);
     const uint32_t md = h->md_step;
     cudaMemsetAsync(h->d_acc, 0, sizeof(double) * (size_t)W * (3 + 9 * N), h->stream);
+    cudaMemsetAsync(h->d_vacc, 0, sizeof(double) * (size_t)W, h->stream);
     cudaMemsetAsync(h->d_nacc, 0, sizeof(unsigned long long) * W, h->stream);
     recompute<T>(h, W);
     const int nw = h->first_call ? h->p.n_warmup : h->p.n_warmup_cont;
@@ -354,6 +374,15 @@ extern "C" {
 size_t qmc_footprint_bytes(const qmc_params* p) { return validate(p) == QMC_OK ? footprint(p) : 0; }
 
 int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
+    return qmc::init_handle(p, R, nullptr, 0, nullptr, true, out);
+}
+
+}  // extern "C"
+
+namespace qmc {
+
+int init_handle(const qmc_params* p, const double* R, void* block, size_t block_bytes, cudaStream_t stream,
+                bool wait, qmc_system** out) {
     if (!out || !R) return QMC_ERR_INVALID;
     *out = nullptr;
     int rc = validate(p);
@@ -362,6 +391,8 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return QMC_ERR_CUDA; }
     qmc_system* h = new (std::nothrow) qmc_system();
     if (!h) return QMC_ERR_OOM;
+    h->pool = (unsigned char*)block;
+    h->pool_bytes = block ? block_bytes : 0;
     h->p = *p;
     h->N = p->n_protons; h->n = h->N / 2; h->G = p->n_gauss; h->B = h->N * h->G; h->W = p->n_walkers;
     h->mmax = p->ewald_mmax;
@@ -377,11 +408,15 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
     std::vector<int4> kv;
     enumerate_kvec(h->mmax, kv);
     h->nk = (int)kv.size();
-    if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
-        delete h;
-        return QMC_ERR_CUDA;
+    if (stream) {
+        h->stream = stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete h;
+            return QMC_ERR_CUDA;
+        }
+        h->stream = h->own_stream;
     }
-    h->stream = h->own_stream;
     const int N = h->N, n = h->n, W = h->W, B = h->B, nk = h->nk;
     const size_t t = h->mixed ? sizeof(float) : sizeof(double);
     h->d_R = dalloc<double>(h, 3 * N, &rc);
@@ -410,6 +445,8 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
     h->d_Lp = dalloc<unsigned char>(h, t * W * N * n, &rc);
     h->d_logdet = dalloc<double>(h, 2 * (size_t)W, &rc);
     h->d_acc = dalloc<double>(h, (size_t)W * (3 + 9 * N), &rc);
+    h->d_vacc = dalloc<double>(h, W, &rc);
+    h->d_pout = dalloc<double>(h, 5, &rc);
     h->d_nacc = dalloc<unsigned long long>(h, W, &rc);
     h->d_colsum = dalloc<double>(h, 4 + 9 * N, &rc);
     h->d_dev = dalloc<double>(h, (size_t)W * (3 * N + 1), &rc);
@@ -426,7 +463,10 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
     h->d_fsS = dalloc<double>(h, 9 * (size_t)N * N, &rc);
     h->d_fsL = dalloc<double>(h, 9 * (size_t)N * N, &rc);
     h->d_err = dalloc<int>(h, 1, &rc);
-    if (!h->fj_h.empty()) h->d_fj = dalloc<double>(h, (size_t)N * N, &rc);
+    if (!h->fj_h.empty()) {
+        h->d_fj = dalloc<double>(h, (size_t)N * N, &rc);
+        if (h->mixed) h->d_fj32 = dalloc<float>(h, (size_t)N * N, &rc);
+    }
     if (h->mixed && tc_orbitals_supported(n, B)) {
         h->d_chat = dalloc<unsigned char>(h, tc_coeff_bytes(B, n), &rc);
         h->use_tc = true;
@@ -449,6 +489,8 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
     cudaMemcpyAsync(h->d_zeta, h->zeta_h.data(), sizeof(double) * h->G, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(h->d_C64, h->coeff_h.data(), sizeof(double) * B * n, cudaMemcpyHostToDevice, st);
     if (h->d_fj) cudaMemcpyAsync(h->d_fj, h->fj_h.data(), sizeof(double) * N * N, cudaMemcpyHostToDevice, st);
+    std::vector<float> fj32(h->fj_h.begin(), h->fj_h.end());
+    if (h->d_fj32) cudaMemcpyAsync(h->d_fj32, fj32.data(), sizeof(float) * N * N, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(h->d_C32, c32.data(), sizeof(float) * B * n, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(h->d_zeta32, z32.data(), sizeof(float) * h->G, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(h->d_kvec, kv.data(), sizeof(int4) * nk, cudaMemcpyHostToDevice, st);
@@ -459,16 +501,21 @@ int qmc_init(const qmc_params* p, const double* R, qmc_system** out) {
     setup_tables(h);
     launch_init_walkers(W, N, p->L, h->d_R, h->d_X, make_key(p->seed), 0u, st);
     rc = check_launch();
-    if (rc == QMC_OK) rc = cuda_rc(cudaStreamSynchronize(st));
+    // host arrays above are pageable, so their copies have been staged already
+    if (rc == QMC_OK && wait) rc = cuda_rc(cudaStreamSynchronize(st));
     if (rc != QMC_OK) { qmc_destroy(h); return rc; }
     *out = h;
     return QMC_OK;
 }
 
+}  // namespace qmc
+
+extern "C" {
+
 void qmc_destroy(qmc_system* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    for (void* a : h->allocs) cudaFree(a);
+    for (void* a : h->allocs) cudaFree(a);      // none for a handle carved from a block
     for (auto& e : h->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (auto& e : h->free_events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
@@ -521,6 +568,25 @@ int qmc_energy_forces(qmc_system* h, const double* R, qmc_result* out) {
     std::memcpy(out->f, o.data() + 4, sizeof(double) * 3 * N);
     std::memcpy(out->cov, o.data() + 4 + 3 * N, sizeof(double) * 9 * (size_t)N * N);
     return QMC_OK;
+}
+
+int qmc_pressure_device(qmc_system* h, double T_kelvin, double* out_dev) {
+    if (!h || !out_dev || T_kelvin < 0) return QMC_ERR_INVALID;
+    const double L = h->p.L;
+    EventPair ep;
+    prof_begin(h, KC_REDUCE, ep);
+    h->nlaunch += 1;
+    launch_pressure(h->W, h->N, h->d_acc, h->d_vacc, L * L * L, T_kelvin * kBoltzmannHaPerK, out_dev, h->stream);
+    prof_end(h, ep);
+    return check_launch();
+}
+
+int qmc_pressure(qmc_system* h, double T_kelvin, double* out) {
+    if (!h || !out) return QMC_ERR_INVALID;
+    int rc = qmc_pressure_device(h, T_kelvin, h->d_pout);
+    if (rc != QMC_OK) return rc;
+    cudaMemcpyAsync(out, h->d_pout, sizeof(double) * 5, cudaMemcpyDeviceToHost, h->stream);
+    return read_err(h);
 }
 
 int qmc_shard_sample_device(qmc_system* h, const double* R_dev, double* sums_dev) {
@@ -663,6 +729,7 @@ int qmc_eval_config(qmc_system* h, int n_conf, const double* X, const double* R,
     cudaMemcpyAsync(h->d_X, X, sizeof(double) * (size_t)n_conf * N3, cudaMemcpyHostToDevice, st);
     setup_tables(h);
     cudaMemsetAsync(h->d_acc, 0, sizeof(double) * (size_t)n_conf * (3 + 9 * N), st);
+    cudaMemsetAsync(h->d_vacc, 0, sizeof(double) * (size_t)n_conf, st);
     double* el = h->d_eval;
     double* lp = el + n_conf;
     double* dl = lp + n_conf;

@@ -50,8 +50,8 @@ struct MLayout {
         while (np < n) np *= 2;
         const size_t spin = split ? sizeof(T) * 2 * (size_t)np * (np + 4) : sizeof(T) * (size_t)np * (3 * (np + 4) + 68);
         const size_t jpart = sizeof(T) * 5 * 256;   // P1 partials: nparts * N <= 256 rows of 5
-        // e-e-n-n Jastrow work space of the FP64 form: c [N], S [N][3], 8 warps x 5N
-        const size_t j34 = sizeof(T) == 8 ? sizeof(T) * 44 * (size_t)N : 0;
+        // e-e-n-n Jastrow work space: c [N], S [N][3], 8 warps x 5N
+        const size_t j34 = sizeof(T) * 44 * (size_t)N;
         size_t u = etab > spin ? etab : spin;
         u = u > j34 ? u : j34;
         uni = take(u > jpart ? u : jpart);
@@ -334,8 +334,8 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
     T* j34c = (T*)uni;               // [N]
     T* j34S = j34c + N;              // [N][3]
     T* j34w = j34S + 3 * N;          // per warp: chi_i [N], grad chi_i [N][3], lap chi_i [N]
-    if constexpr (sizeof(T) == 8) {
-        if (s.fj) {
+    {
+        if (s.fjt) {
             const T zj = (T)s.zeta_j;
             for (int a = tid; a < N; a += nt) {
                 T c = 0, g[3] = {0, 0, 0};
@@ -359,9 +359,9 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
                 for (int a = lane; a < N; a += 32) {
                     RadialDerivs<T> rd;
                     const T chi = jas34_orbital(et + 6 * i, s.ptrig + 6 * a, ell, zj, k2, rd);
-                    const double* fa = s.fj + a;   // column a = row a (f symmetric): coalesced over lanes
+                    const T* fa = s.fjt + a;   // column a = row a (f symmetric): coalesced over lanes
                     T w = 0;
-                    for (int b = 0; b < N; ++b) w += (T)fa[(size_t)b * N] * (j34c[b] - stc[b]);
+                    for (int b = 0; b < N; ++b) w += fa[(size_t)b * N] * (j34c[b] - stc[b]);
                     for (int mu = 0; mu < 3; ++mu) g[mu] += rd.g[mu] * w;
                     l += rd.lap * w;
                     u += chi * w;
@@ -396,15 +396,15 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
     const double kin = block_sum(kin_p, red);
     const double Utot = block_sum(u_p, red + 32);
 
-    // ---- P3b (FP64 form with the e-e-n-n Jastrow term): its terms of d ln psi / dR_a
+    // ---- P3b (with the e-e-n-n Jastrow term): its terms of d ln psi / dR_a
     // and dE_L / dR_a.  With s_a^(i) = S_a - grad chi_a(r_i), v_ia = sum_b grad chi_b(r_i) f_ba,
     // lam_ia = sum_b lap chi_b(r_i) f_ba and vv_i = g_i + grad_i U:
     //   dlnpsi/dR_a += -sum_i grad chi_a(r_i) w_ia
     //   dE_L/dR_a   += sum_i [ 1/2 (grad lap chi_a(r_i) w_ia + lam_ia s_a^(i))
     //                          + (Hess chi_a(r_i) vv_i) w_ia + (vv_i . v_ia) s_a^(i) ]
     // (the R_a-derivative of -1/2 sum_i [lap_i U34 + 2 vv_i . grad_i U34]).
-    if constexpr (sizeof(T) == 8) {
-        if (s.fj) {
+    {
+        if (s.fjt) {
             const T zj = (T)s.zeta_j;
             T* st = j34w + (size_t)warp * 5 * N;   // chi_i [N], grad chi_i [N][3], lap chi_i [N]
             for (int i = warp; i < N; i += nw) {
@@ -420,10 +420,10 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
                 for (int a = lane; a < N; a += 32) {
                     RadialDerivs<T> rd;
                     jas34_orbital(et + 6 * i, s.ptrig + 6 * a, ell, zj, k2, rd);
-                    const double* fa = s.fj + a;   // column a = row a (f symmetric): coalesced over lanes
+                    const T* fa = s.fjt + a;   // column a = row a (f symmetric): coalesced over lanes
                     T w = 0, v[3] = {0, 0, 0}, lam = 0;
                     for (int b = 0; b < N; ++b) {
-                        const T f = (T)fa[(size_t)b * N];
+                        const T f = fa[(size_t)b * N];
                         w += f * (j34c[b] - st[b]);
                         for (int mu = 0; mu < 3; ++mu) v[mu] += st[N + 3 * b + mu] * f;
                         lam += st[4 * N + b] * f;
@@ -951,6 +951,7 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
     }
     if (tid == 0) {
         aw[0] += 1.0; aw[1] += EL; aw[2] += EL * EL;
+        if (s.vacc) s.vacc[w] += vee + vep + vrec + s.vconst[0];   // V_L, for the virial pressure
         if (out_el) { out_el[w] = EL; out_lnpsi[w] = logdet[2 * w] + logdet[2 * w + 1] + Utot; }
     }
     if (bad) raise_err(s.err, kErrNonfinite);

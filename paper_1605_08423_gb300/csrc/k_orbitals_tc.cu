@@ -13,8 +13,18 @@
 //   D += A1 B0 + A0 B1 + A0 B0,
 // the dropped A1 B1 is below 2^-22 relative: FP32-level, which is what the
 // results are stored in.  (P = 3, six products, reaches 2^-33.)
-// B = C^T chunk, prepared once per handle in the same swizzled layout.  After
-// the last chunk the accumulators go TMEM -> registers -> shared -> HBM.
+// B = C^T chunk, prepared once per handle in the same swizzled layout.
+//
+// Accumulation per chunk.  The tensor core's FP32 accumulation over all B
+// basis functions of a row is the largest error of the contraction (the
+// diffuse Gaussians make every nucleus contribute, and the Slater inverse
+// amplifies the error of the orbital values and derivatives alike).  So chunk
+// 0 accumulates into the running total T and every later chunk into a fresh
+// TMEM block C (reset by its first product), which the threads then add into
+// T (tcgen05.ld of C and T, FP32 add, tcgen05.st to T): a chunk's 32 products
+// are summed by the tensor core, the 16 chunk sums at N = 128 by the threads
+// with round-to-nearest.  After the last chunk T goes TMEM -> registers ->
+// shared -> HBM.
 #include "common.cuh"
 #include "kernels.cuh"
 #include "tc.cuh"
@@ -91,7 +101,22 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
     const int row0 = blockIdx.x * kRows;
     const int n = s.n, B = s.B, G = s.G, N = s.N;
     const float ell = (float)s.ell;
-    constexpr uint32_t kCols = (Q == 1) ? 64u : 256u;      // TMEM columns (power of two >= Q * NM)
+    constexpr uint32_t kSub = (Q == 1) ? 64u : 256u;       // columns of one accumulator block (>= Q * NM)
+    constexpr uint32_t kCols = 2 * kSub;                   // running total T at 0, chunk block C at kSub
+    // Add the chunk block C into the running total T: warps split by TMEM lane
+    // quarter (warp % 4) and 16-column groups; warp-collective.
+    auto fold_chunk = [&](int nwarps) {
+        const int quarter = warp & 3, cg = warp >> 2, ngr = nwarps >> 2;
+        const uint32_t tl = tbase + ((uint32_t)(quarter * 32) << 16);
+        for (int c0 = cg * 16; c0 < Q * NM; c0 += 16 * ngr) {
+            float cv[16], tv[16];
+            tc::tmem_ld16(tl + kSub + (uint32_t)c0, cv);
+            tc::tmem_ld16(tl + (uint32_t)c0, tv);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) tv[j] += cv[j];
+            tc::tmem_st16(tl + (uint32_t)c0, tv);
+        }
+    };
 
     if (warp == 0) { tc::tmem_alloc(&tbase, kCols); tc::tmem_relinquish(); }
     if (tid == 0) {
@@ -171,7 +196,8 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
 #pragma unroll
                     for (int q = 0; q < Q; ++q) {
                         const uint32_t a0 = tc::smem_addr(sA + (size_t)(P * q) * kTileA);
-                        const uint32_t d = tmem + (uint32_t)(q * NM);
+                        // chunk 0 into the running total, later chunks into the chunk block
+                        const uint32_t d = tmem + (c > 0 ? kSub : 0u) + (uint32_t)(q * NM);
 #pragma unroll
                         for (int kh = 0; kh < 2; ++kh) {
                             const int ks = 2 * h + kh;
@@ -183,7 +209,7 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
                             for (int m = 6 - np; m < 6; ++m)
                                 tc::mma_tf32(d, tc::desc_sw128(a0 + pi[m] * kTileA + o),
                                              tc::desc_sw128(b0 + pj[m] * bstep + o), idesc,
-                                             (c > 0 || ks > 0 || m > 6 - np) ? 1u : 0u);
+                                             (ks > 0 || m > 6 - np) ? 1u : 0u);
                         }
                     }
                     tc::mma_commit(&mbarh[h]);
@@ -252,6 +278,16 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
                 *(float4*)(tq) = x0;
                 *(float4*)(tq + kTileA) = x1;
             }
+            // chunk c - 1 (c >= 2; chunk 0 went straight into T) is folded into
+            // T once all its MMAs are done and before the first MMA of chunk c,
+            // which resets the chunk block: the fold precedes this warp's
+            // arrival for half 0
+            if (h == 0 && c >= 2) {
+                if (!tc::mbar_wait(&mbarh[1], (uint32_t)((c - 1) & 1), 1ll << 26)) ok = false;
+                tc::fence_after_sync();
+                fold_chunk(kProd / 32);
+                tc::fence_before_sync();
+            }
             // this warp's share of half h is in shared memory
             tc::fence_proxy_async();
             __syncwarp();
@@ -261,7 +297,12 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
     // all MMAs done (they complete in order) before TMEM and sA are read
     if (!tc::mbar_wait(&mbarh[1], (uint32_t)((nch - 1) & 1), 1ll << 26)) ok = false;
     tc::fence_after_sync();
+    if (nch >= 2 && tid < kProd) {
+        fold_chunk(kProd / 32);
+        tc::fence_before_sync();
+    }
     __syncthreads();
+    tc::fence_after_sync();
     } else {
     // B operand: the first P pieces of each prepared C^T chunk (16-byte
     // vectors).  Q = 4 (one CTA per SM): fetched into registers one chunk
@@ -402,7 +443,8 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
                 const uint32_t a0 = tc::smem_addr(sA + (size_t)(P * q) * kTileA);
-                const uint32_t d = tmem + (uint32_t)(q * NM);
+                // chunk 0 into the running total, later chunks into the chunk block
+                const uint32_t d = tmem + (c > 0 ? kSub : 0u) + (uint32_t)(q * NM);
 #pragma unroll
                 for (int ks = 0; ks < kKc / 8; ++ks) {
                     const uint32_t o = 32u * ks;
@@ -412,7 +454,7 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
 #pragma unroll
                     for (int m = 6 - np; m < 6; ++m)
                         tc::mma_tf32(d, tc::desc_sw128(a0 + pi[m] * kTileA + o), tc::desc_sw128(b0 + pj[m] * bstep + o),
-                                     idesc, (c > 0 || ks > 0 || m > 6 - np) ? 1u : 0u);
+                                     idesc, (ks > 0 || m > 6 - np) ? 1u : 0u);
                 }
             }
             tc::mma_commit(&mbarh[0]);
@@ -422,6 +464,10 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
         __syncwarp();
         if (!tc::mbar_wait(&mbarh[0], (uint32_t)(c & 1), 1ll << 26)) ok = false;
         tc::fence_after_sync();
+        if (c > 0) {                             // chunk c into the running total
+            fold_chunk(nt / 32);
+            tc::fence_before_sync();
+        }
         if (Q == 4 && c + 1 < nch) store_b();   // the MMAs of chunk c have read sB
         if (Q == 1 && tid == 0 && c + 1 < nch) {
             tc::mbar_arrive_expect_tx(&bbar, bcopy);

@@ -148,6 +148,50 @@ __global__ void shard_finish_kernel(int N, const double* __restrict__ sums, cons
     if (blockIdx.x == 0 && threadIdx.x == 0) out[1] = sqrt(gram[0] * scale);
 }
 
+// Virial pressure of the last call's samples (the potential is homogeneous of
+// degree -1 in all lengths -- the Ewald sum with kappa L and the k cutoff in
+// units of 2 pi / L fixed included -- so for the trial state scaled with the
+// box, E(lambda) = T / lambda^2 + V / lambda and -dE/dOmega = (2 T + V) / (3 Omega)):
+//   P_w = (2 E_w - V_w) / (3 Omega)   per walker (T = E - V),
+//   P   = (2 E - V) / (3 Omega) + N T_nuc / Omega   (classical nuclei, ideal-gas term),
+//   P_err^2 = sum_w (P_w - P_el)^2 / (W (W - 1)).
+// out = [P, P_err, P_el, <V_L>, <T_L>] (hartree / bohr^3, hartree).
+__global__ void pressure_kernel(int W, int N, const double* __restrict__ acc, const double* __restrict__ vacc,
+                                double omega, double T_nuc, double* out) {
+    __shared__ double red[32];
+    const int ncol = 3 + 9 * N;
+    double c = 0.0, e = 0.0, v = 0.0;
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        c += acc[(size_t)w * ncol];
+        e += acc[(size_t)w * ncol + 1];
+        v += vacc[w];
+    }
+    c = block_sum(c, red);
+    e = block_sum(e, red);
+    v = block_sum(v, red);
+    const double E = e / c, V = v / c;
+    const double Pel = (2.0 * E - V) / (3.0 * omega);
+    double d2 = 0.0;
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        const double cw = acc[(size_t)w * ncol];
+        const double pw = (2.0 * acc[(size_t)w * ncol + 1] / cw - vacc[w] / cw) / (3.0 * omega);
+        d2 += (pw - Pel) * (pw - Pel);
+    }
+    d2 = block_sum(d2, red);
+    if (threadIdx.x == 0) {
+        out[0] = Pel + N * T_nuc / omega;
+        out[1] = W > 1 ? sqrt(d2 / ((double)W * (W - 1))) : 0.0;
+        out[2] = Pel;
+        out[3] = V;
+        out[4] = E - V;
+    }
+}
+
+void launch_pressure(int W, int N, const double* acc, const double* vacc, double omega, double T_nuc, double* out,
+                     cudaStream_t st) {
+    pressure_kernel<<<1, 256, 0, st>>>(W, N, acc, vacc, omega, T_nuc, out);
+}
+
 void launch_shard_sums(int W, int N, double moves, const double* acc, const unsigned long long* nacc, double* sums,
                        cudaStream_t st) {
     const int ncol = 3 + 9 * N;

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(512) sweep_kernel(SysView<T> s, double* __rest
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     T* ptr_s = (T*)smraw;                                    // [N][6] proton trig
     size_t off = ((size_t)6 * N * sizeof(T) + 15) & ~size_t(15);
-    const bool j34 = sizeof(T) == 8 && s.fj != nullptr;
+    const bool j34 = sizeof(T) == 8 && s.fjt != nullptr;
     unsigned char* mine = smraw + off + (size_t)warp * SweepSmem<T>::warp_bytes(N, n, j34);
     T* Gs = (T*)mine;
     T* rowb = Gs + (size_t)n * ld;
@@ -191,9 +191,9 @@ __global__ void __launch_bounds__(512) sweep_kernel(SysView<T> s, double* __rest
                 for (int a = lane; a < N; a += 32) {
                     // f is symmetric (checked at qmc_init): column a = row a,
                     // and the lanes' loads of a column element are consecutive
-                    const double* fa = s.fj + a;
+                    const T* fa = s.fjt + a;
                     T wa = 0;
-                    for (int b = 0; b < N; ++b) wa += (T)fa[(size_t)b * N] * (c34[b] - cho[b]);
+                    for (int b = 0; b < N; ++b) wa += fa[(size_t)b * N] * (c34[b] - cho[b]);
                     du += (chn[a] - cho[a]) * wa;
                 }
             }
@@ -256,8 +256,19 @@ __global__ void __launch_bounds__(512) sweep_kernel(SysView<T> s, double* __rest
 // partners each).  The two warps of a walker meet at a named barrier (one
 // per walker of the CTA).  Same proposals, uniforms and acceptance rule as
 // sweep_kernel; the mixed form keeps accepted proposals unwrapped.
+// With the e-e-n-n Jastrow term (s.fjt set) the CTA stages f (FP32, N x N) in
+// shared memory and each walker keeps c_a = sum_j chi_a(r_j); a move of
+// electron i changes U by sum_a (chi_a(r'_i) - chi_a(r_i)) w_a with
+// w_a = sum_b f_ab (c_b - chi_b(r_i)), each thread taking nuclei tw and
+// tw + 64 (one more barrier per move to publish chi_b(r_i)).
 constexpr int kSwWalkers = 4;   // walkers per CTA (8 warps)
 constexpr int kSwRow = 64;      // register row length (n <= 64)
+
+// Shared-memory floats per walker of sweep_reg_kernel: phi [64], row [64],
+// red [8], trig [6N], and with the e-e-n-n term c [N] and chi(r_i) [N].
+__host__ __device__ inline size_t sweep_reg_walker_floats(int N, bool j34) {
+    return 2 * kSwRow + 8 + 6 * (size_t)N + (j34 ? 2 * (size_t)N : 0);
+}
 
 __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<float> s, double* __restrict__ X,
                                                                   const double* __restrict__ Xp,
@@ -270,13 +281,19 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
     const int N = s.N, n = s.n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int p = warp >> 1, h = warp & 1, tw = tid & 63;
+    const bool j34 = s.fjt != nullptr;
     float* ptr_s = (float*)smraw;                                       // [N][6] proton trig
-    float* mine = ptr_s + ((6 * N + 3) & ~3) + (size_t)p * (2 * kSwRow + 6 * N + 8);
+    float* f_s = ptr_s + ((6 * N + 3) & ~3);                            // [N][N] e-e-n-n coefficients (j34)
+    float* mine = f_s + (j34 ? (size_t)N * N : 0) + (size_t)p * sweep_reg_walker_floats(N, j34);
     float* phi = mine;                  // [64] orbital row at the proposal (zero beyond n)
     float* rowb = phi + kSwRow;         // [64] row il of G^T on acceptance
     float* red = rowb + kSwRow;         // [8] du halves, ratio
     float* et = red + 8;                // [N][6] (sin, cos)(pi x / L) of the current positions
+    float* c34 = et + 6 * N;            // [N] sum_j chi_a(r_j) (j34)
+    float* cho = c34 + N;               // [N] chi_a at the moving electron (j34)
     for (int idx = tid; idx < 6 * N; idx += blockDim.x) ptr_s[idx] = s.ptrig[idx];
+    if (j34)
+        for (int idx = tid; idx < N * N; idx += blockDim.x) f_s[idx] = s.fjt[idx];
     __syncthreads();
     const int w = blockIdx.x * kSwWalkers + p;
     if (w >= s.W) return;              // whole walkers only: both of its warps leave
@@ -291,6 +308,15 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
         sincospif((float)(Xw[idx] * iL), &sn, &cs);
         et[6 * i + mu] = sn;
         et[6 * i + 3 + mu] = cs;
+    }
+    const float zj = (float)s.zeta_j;
+    if (j34) {
+        bar();   // et complete
+        for (int a = tw; a < N; a += 64) {
+            float c = 0.f;
+            for (int j = 0; j < N; ++j) c += jas_orbital(et + 6 * j, ptr_s + 6 * a, ell, zj);
+            c34[a] = c;
+        }
     }
     float pt_nx[6], ph_nx, u_nx;
     auto fetch = [&](int i) {
@@ -361,6 +387,29 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
                     du += u1 - u0;
                 }
             }
+            float chn_r[2] = {0.f, 0.f}, cho_r[2] = {0.f, 0.f};
+            if (j34) {
+                // chi_a at the electron and at its proposal for this thread's nuclei
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int a = tw + 64 * k;
+                    if (a < N) {
+                        chn_r[k] = jas_orbital(pt, ptr_s + 6 * a, ell, zj);
+                        cho_r[k] = jas_orbital(ei, ptr_s + 6 * a, ell, zj);
+                        cho[a] = cho_r[k];
+                    }
+                }
+                bar();   // chi_b(r_i) of every nucleus visible
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int a = tw + 64 * k;
+                    if (a < N) {
+                        float wa = 0.f;
+                        for (int b = 0; b < N; ++b) wa += f_s[(size_t)b * N + a] * (c34[b] - cho[b]);
+                        du += (chn_r[k] - cho_r[k]) * wa;
+                    }
+                }
+            }
             du = warp_sum(du);
             if (lane == 0) red[h] = du;
             if (tw == il) red[2] = wl;
@@ -388,6 +437,13 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
                     et[6 * i + tw] = tw == 0 ? pt[0] : (tw == 1 ? pt[1] : pt[2]);
                     et[6 * i + 3 + tw] = tw == 0 ? pt[3] : (tw == 1 ? pt[4] : pt[5]);
                 }
+                if (j34) {      // c_a of this thread's nuclei (read by others only after the next barrier)
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const int a = tw + 64 * k;
+                        if (a < N) c34[a] += chn_r[k] - cho_r[k];
+                    }
+                }
                 ++naccept;
             }
         }
@@ -406,14 +462,21 @@ void launch_sweep(const SysView<T>& s, double* X, const double* Xp, const T* ptp
                   unsigned long long* nacc, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
         if (s.n <= kSwRow) {   // mixed form: inverse rows in registers
-            const size_t smem = sizeof(float) * (((6 * s.N + 3) & ~3) + kSwWalkers * (2 * kSwRow + 6 * s.N + 8));
+            const bool j34 = s.fjt != nullptr;
+            const size_t smem = sizeof(float) * (((6 * s.N + 3) & ~3) + (j34 ? (size_t)s.N * s.N : 0) +
+                                                 kSwWalkers * sweep_reg_walker_floats(s.N, j34));
+            static size_t attr = 0;
+            if (smem > attr &&
+                cudaFuncSetAttribute(sweep_reg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+                    cudaSuccess)
+                attr = smem;
             sweep_reg_kernel<<<(s.W + kSwWalkers - 1) / kSwWalkers, 64 * kSwWalkers, smem, st>>>(
                 *(const SysView<float>*)&s, X, Xp, (const float*)ptp, (const float*)uacc, (const float*)Phi,
                 (float*)Gt, nacc);
             return;
         }
     }
-    const size_t wb = SweepSmem<T>::warp_bytes(s.N, s.n, sizeof(T) == 8 && s.fj != nullptr);
+    const size_t wb = SweepSmem<T>::warp_bytes(s.N, s.n, sizeof(T) == 8 && s.fjt != nullptr);
     const size_t head = ((size_t)6 * s.N * sizeof(T) + 15) & ~size_t(15);
     // as many walkers per CTA as the shared memory of one SM holds (one CTA per SM)
     int wpb = (int)((226 * 1024 - head) / wb);

@@ -64,6 +64,9 @@ void launch_recforce_gemm(int W, int M, int K, const float* rho, const float* T,
 // k_reduce.cu: walker reductions and the covariance matrix.
 void launch_reduce(int W, int N, double moves, const double* acc, const unsigned long long* nacc,
                    double* colsum, double* dev, double* out, int* err, cudaStream_t st);
+// k_reduce.cu: virial pressure of the last call's samples, out [5].
+void launch_pressure(int W, int N, const double* acc, const double* vacc, double omega, double T_nuc, double* out,
+                     cudaStream_t st);
 // k_reduce.cu: walker-sharded form of the same reduction (see there): local
 // sums [3 + 9N + 3], then E, f and local deviation sums gram [1 + 9N^2] from
 // the summed sums, then E_err and S from the summed gram.

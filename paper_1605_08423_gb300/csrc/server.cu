@@ -15,6 +15,16 @@
 //     sampler and MD state go to host memory (qmc_checkpoint_save) and come back
 //     on re-admission, so a result does not depend on evictions or on which
 //     other requests ran alongside it.
+//   * The budget is one device arena allocated when the server is created; a
+//     trajectory's handle is carved from one block of it (first fit), so
+//     admission and eviction call no cudaMalloc / cudaFree (which may
+//     synchronise the device and stall the requests in flight).  Streams and
+//     pinned buffers are made when a trajectory is added, events when a
+//     request is submitted; qmc_server_progress itself only launches, queries
+//     events and moves checkpoints.
+//   * Every request records a start and an end event on its stream, so the
+//     device-side interval of each request is reported (qmc_served) and the
+//     overlap of requests on the GPU can be checked.
 #include <chrono>
 #include <cstring>
 #include <deque>
@@ -25,6 +35,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/qmcmd.h"
+#include "pool.h"
 
 namespace {
 
@@ -33,11 +44,50 @@ double now_ms() {
     return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
+// First-fit arena over one device allocation; offsets and sizes are multiples
+// of qmc::kPoolAlign, free blocks are coalesced.
+struct Arena {
+    unsigned char* base = nullptr;
+    size_t size = 0;
+    std::map<size_t, size_t> free_;   // offset -> bytes
+    static size_t round(size_t b) { return (b + qmc::kPoolAlign - 1) & ~(qmc::kPoolAlign - 1); }
+    bool fits(size_t bytes) const {
+        bytes = round(bytes);
+        for (const auto& kv : free_)
+            if (kv.second >= bytes) return true;
+        return false;
+    }
+    bool take(size_t bytes, size_t* off) {
+        bytes = round(bytes);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < bytes) continue;
+            *off = it->first;
+            const size_t rest = it->second - bytes, roff = it->first + bytes;
+            free_.erase(it);
+            if (rest) free_[roff] = rest;
+            return true;
+        }
+        return false;
+    }
+    void give(size_t off, size_t bytes) {
+        bytes = round(bytes);
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) { it->second += nx->second; free_.erase(nx); }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) { pv->second += it->second; free_.erase(it); }
+        }
+    }
+};
+
 struct Traj {
     qmc_params p;
     std::vector<double> zeta, coeff;
     int N = 0;
-    size_t footprint = 0;
+    size_t footprint = 0;             // handle + d_R + d_out, the arena block's size
+    size_t handle_bytes = 0;          // the handle's part of the block
+    size_t block_off = 0;             // offset of the block in the arena (resident only)
     double T_kelvin = 0, delta = 0;
     int s_mode = QMC_S_COV;
     std::vector<double> R;            // current nuclei [3N]
@@ -60,7 +110,9 @@ struct Req {
     int status = QMC_OK;
     bool done = false;
     double t_submit = 0, t_start = 0, t_done = 0;
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev = nullptr;          // end of the request's work on its stream
+    cudaEvent_t ev0 = nullptr;         // start of it
+    double gpu_start = -1, gpu_end = -1;
     std::vector<double> out, R_next;
 };
 
@@ -68,6 +120,8 @@ struct Req {
 
 struct qmc_server {
     size_t budget = 0, used = 0;
+    Arena arena;
+    cudaEvent_t ref = nullptr;             // device time origin of the served intervals
     int max_active = 1;
     std::vector<Traj> trajs;
     std::deque<long long> queue;           // submitted, not started (FIFO)
@@ -79,14 +133,14 @@ struct qmc_server {
 
 namespace {
 
-void release_device(Traj& t) {
-    if (t.h) qmc_destroy(t.h);
+// Give a resident trajectory's block back to the arena (its stream stays).
+void release_device(qmc_server* s, Traj& t) {
+    if (!t.h) return;
+    qmc_destroy(t.h);    // waits for the stream; frees nothing carved from the block
     t.h = nullptr;
-    if (t.d_R) cudaFree(t.d_R);
-    if (t.d_out) cudaFree(t.d_out);
     t.d_R = t.d_out = nullptr;
-    if (t.stream) cudaStreamDestroy(t.stream);
-    t.stream = nullptr;
+    s->arena.give(t.block_off, t.footprint);
+    s->used -= t.footprint;
 }
 
 int evict(qmc_server* s, Traj& t) {
@@ -94,35 +148,38 @@ int evict(qmc_server* s, Traj& t) {
     int rc = qmc_checkpoint_save(t.h, t.ckpt.data());
     if (rc != QMC_OK) return rc;
     t.has_ckpt = true;
-    release_device(t);
-    s->used -= t.footprint;
+    release_device(s, t);
     ++s->n_evict;
     return QMC_OK;
 }
 
 int make_resident(qmc_server* s, Traj& t) {
-    if (cudaStreamCreateWithFlags(&t.stream, cudaStreamNonBlocking) != cudaSuccess) return QMC_ERR_CUDA;
-    int rc = qmc_init(&t.p, t.R.data(), &t.h);
-    if (rc != QMC_OK) { release_device(t); return rc; }
-    qmc_set_stream(t.h, t.stream);
-    if (cudaMalloc(&t.d_R, sizeof(double) * 3 * t.N) != cudaSuccess ||
-        cudaMalloc(&t.d_out, sizeof(double) * t.out_len()) != cudaSuccess) {
-        cudaGetLastError();
-        release_device(t);
-        return QMC_ERR_OOM;
+    size_t off = 0;
+    if (!s->arena.take(t.footprint, &off)) return QMC_ERR_OOM;
+    unsigned char* blk = s->arena.base + off;
+    t.block_off = off;
+    s->used += t.footprint;
+    int rc = qmc::init_handle(&t.p, t.R.data(), blk, t.handle_bytes, t.stream, false, &t.h);
+    if (rc != QMC_OK) {
+        t.h = nullptr;
+        s->arena.give(off, t.footprint);
+        s->used -= t.footprint;
+        return rc;
     }
+    t.d_R = (double*)(blk + t.handle_bytes);
+    t.d_out = t.d_R + Arena::round(sizeof(double) * 3 * t.N) / sizeof(double);
     if (t.has_ckpt) {
         rc = qmc_checkpoint_load(t.h, t.ckpt.data());
-        if (rc != QMC_OK) { release_device(t); return rc; }
+        if (rc != QMC_OK) { release_device(s, t); return rc; }
     }
-    s->used += t.footprint;
     ++s->n_admit;
     return QMC_OK;
 }
 
-// Make room for `need` bytes by evicting idle resident trajectories, LRU first.
+// Make room for `need` bytes by evicting idle resident trajectories, LRU first,
+// until the budget allows it and one free block of the arena holds it.
 bool make_room(qmc_server* s, size_t need, int keep) {
-    while (s->used + need > s->budget) {
+    while (s->used + need > s->budget || !s->arena.fits(need)) {
         int victim = -1;
         for (int k = 0; k < (int)s->trajs.size(); ++k) {
             const Traj& t = s->trajs[k];
@@ -138,6 +195,7 @@ bool make_room(qmc_server* s, size_t need, int keep) {
 int launch(qmc_server* s, Req& r) {
     Traj& t = s->trajs[r.traj];
     const int N3 = 3 * t.N;
+    if (cudaEventRecord(r.ev0, t.stream) != cudaSuccess) return QMC_ERR_CUDA;
     std::memcpy(t.h_R, t.R.data(), sizeof(double) * N3);
     cudaMemcpyAsync(t.d_R, t.h_R, sizeof(double) * N3, cudaMemcpyHostToDevice, t.stream);
     int rc = qmc_energy_forces_device(t.h, t.d_R, t.d_out);
@@ -146,7 +204,6 @@ int launch(qmc_server* s, Req& r) {
     if (rc != QMC_OK) return rc;
     cudaMemcpyAsync(t.h_out, t.d_out, sizeof(double) * t.out_len(), cudaMemcpyDeviceToHost, t.stream);
     cudaMemcpyAsync(t.h_R, t.d_R, sizeof(double) * N3, cudaMemcpyDeviceToHost, t.stream);
-    if (cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming) != cudaSuccess) return QMC_ERR_CUDA;
     if (cudaEventRecord(r.ev, t.stream) != cudaSuccess) return QMC_ERR_CUDA;
     t.busy = true;
     r.t_start = now_ms();
@@ -161,22 +218,41 @@ int qmc_server_create(size_t hbm_budget_bytes, int max_active, qmc_server** out)
     if (!out || max_active < 1 || hbm_budget_bytes == 0) return QMC_ERR_INVALID;
     qmc_server* s = new (std::nothrow) qmc_server();
     if (!s) return QMC_ERR_OOM;
-    s->budget = hbm_budget_bytes;
+    s->budget = Arena::round(hbm_budget_bytes);
     s->max_active = max_active;
+    if (cudaMalloc(&s->arena.base, s->budget) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return QMC_ERR_OOM;
+    }
+    s->arena.size = s->budget;
+    s->arena.free_[0] = s->budget;
+    if (cudaEventCreate(&s->ref) != cudaSuccess || cudaEventRecord(s->ref, 0) != cudaSuccess ||
+        cudaEventSynchronize(s->ref) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(s->arena.base);
+        delete s;
+        return QMC_ERR_CUDA;
+    }
     *out = s;
     return QMC_OK;
 }
 
 void qmc_server_destroy(qmc_server* s) {
     if (!s) return;
-    for (auto& kv : s->reqs)
-        if (kv.second.ev) cudaEventDestroy(kv.second.ev);
     for (auto& t : s->trajs) {
         if (t.stream) cudaStreamSynchronize(t.stream);
-        release_device(t);
+        release_device(s, t);
+        if (t.stream) cudaStreamDestroy(t.stream);
         if (t.h_out) cudaFreeHost(t.h_out);
         if (t.h_R) cudaFreeHost(t.h_R);
     }
+    for (auto& kv : s->reqs) {
+        if (kv.second.ev) cudaEventDestroy(kv.second.ev);
+        if (kv.second.ev0) cudaEventDestroy(kv.second.ev0);
+    }
+    if (s->ref) cudaEventDestroy(s->ref);
+    if (s->arena.base) cudaFree(s->arena.base);
     delete s;
 }
 
@@ -192,16 +268,20 @@ int qmc_server_add_trajectory(qmc_server* s, const qmc_params* p, const double* 
     t.N = p->n_protons;
     t.zeta.assign(p->zeta, p->zeta + p->n_gauss);
     t.coeff.assign(p->coeff, p->coeff + (size_t)t.N * p->n_gauss * (t.N / 2));
-    t.footprint = fp + sizeof(double) * (3 * (size_t)t.N + t.out_len());
+    t.handle_bytes = Arena::round(fp);
+    t.footprint = t.handle_bytes + Arena::round(sizeof(double) * 3 * (size_t)t.N) +
+                  Arena::round(sizeof(double) * t.out_len());
     if (t.footprint > s->budget) return QMC_ERR_OOM;
     t.T_kelvin = T_kelvin;
     t.delta = delta;
     t.s_mode = s_mode;
     t.R.assign(R0, R0 + 3 * t.N);
     if (cudaHostAlloc((void**)&t.h_out, sizeof(double) * t.out_len(), cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc((void**)&t.h_R, sizeof(double) * 3 * t.N, cudaHostAllocDefault) != cudaSuccess) {
+        cudaHostAlloc((void**)&t.h_R, sizeof(double) * 3 * t.N, cudaHostAllocDefault) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&t.stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         if (t.h_out) cudaFreeHost(t.h_out);
+        if (t.h_R) cudaFreeHost(t.h_R);
         return QMC_ERR_CUDA;
     }
     s->trajs.push_back(std::move(t));
@@ -215,6 +295,11 @@ int qmc_server_add_trajectory(qmc_server* s, const qmc_params* p, const double* 
 int qmc_server_submit(qmc_server* s, int traj, long long* ticket) {
     if (!s || !ticket || traj < 0 || traj >= (int)s->trajs.size()) return QMC_ERR_INVALID;
     Req r;
+    if (cudaEventCreate(&r.ev0) != cudaSuccess || cudaEventCreate(&r.ev) != cudaSuccess) {
+        cudaGetLastError();
+        if (r.ev0) cudaEventDestroy(r.ev0);
+        return QMC_ERR_CUDA;
+    }
     r.ticket = s->next_ticket++;
     r.traj = traj;
     r.t_submit = now_ms();
@@ -241,8 +326,16 @@ int qmc_server_progress(qmc_server* s) {
         if (r.status == QMC_OK) t.R = r.R_next;
         r.t_done = now_ms();
         r.done = true;
+        float a = 0.f, b = 0.f;
+        if (q == cudaSuccess && cudaEventElapsedTime(&a, s->ref, r.ev0) == cudaSuccess &&
+            cudaEventElapsedTime(&b, s->ref, r.ev) == cudaSuccess) {
+            r.gpu_start = a;
+            r.gpu_end = b;
+        }
+        cudaGetLastError();
         cudaEventDestroy(r.ev);
-        r.ev = nullptr;
+        cudaEventDestroy(r.ev0);
+        r.ev = r.ev0 = nullptr;
         t.busy = false;
         t.last_used = s->tick;
         s->active.erase(s->active.begin() + k);
@@ -293,6 +386,8 @@ int qmc_server_fetch(qmc_server* s, long long ticket, qmc_served* out) {
     out->latency_ms = r.t_done - r.t_submit;
     out->wait_ms = (r.t_start > 0 ? r.t_start : r.t_done) - r.t_submit;
     out->run_ms = r.t_start > 0 ? r.t_done - r.t_start : 0.0;
+    out->gpu_start_ms = r.gpu_start;
+    out->gpu_end_ms = r.gpu_end;
     if (!r.out.empty()) {
         out->E = r.out[0]; out->E_err = r.out[1]; out->n_samples = r.out[2]; out->accept = r.out[3];
         if (out->f) std::memcpy(out->f, r.out.data() + 4, sizeof(double) * N3);

@@ -26,6 +26,7 @@ QMC_OPT_TENSOR_CORES, QMC_OPT_TC_ADJOINT, QMC_OPT_INTEGRATOR, QMC_OPT_NOISE_CORR
 QMC_OPT_RECOMPUTE = 5
 QMC_RECOMPUTE_FP64, QMC_RECOMPUTE_NEWTON = 0, 1
 QMC_OPT_WALKER_OFFSET = 6
+HA_PER_BOHR3_IN_GPA = 29421.02648438959    # 1 hartree / bohr^3 in GPa (CODATA)
 QMC_LV_ADOPTED, QMC_LV_FAST, QMC_LV_NOROGNA = 0, 1, 2
 QMC_TOY_PLAIN, QMC_TOY_STANDARD, QMC_TOY_FIRST, QMC_TOY_FAST, QMC_TOY_ADOPTED, QMC_TOY_NOROGNA = range(6)
 QMC_TOY_S_G, QMC_TOY_S_HG = 0, 1
@@ -56,7 +57,8 @@ class Served(C.Structure):
     _fields_ = [("traj", C.c_int), ("status", C.c_int), ("E", C.c_double), ("E_err", C.c_double),
                 ("n_samples", C.c_double), ("accept", C.c_double), ("f", C.POINTER(C.c_double)),
                 ("cov", C.POINTER(C.c_double)), ("R_next", C.POINTER(C.c_double)),
-                ("latency_ms", C.c_double), ("wait_ms", C.c_double), ("run_ms", C.c_double)]
+                ("latency_ms", C.c_double), ("wait_ms", C.c_double), ("run_ms", C.c_double),
+                ("gpu_start_ms", C.c_double), ("gpu_end_ms", C.c_double)]
 
 
 class Result(C.Structure):
@@ -120,6 +122,8 @@ def lib():
         L.qmc_server_progress.argtypes = [vp]
         L.qmc_server_fetch.argtypes = [vp, C.c_longlong, C.POINTER(Served)]
         L.qmc_server_stats.argtypes = [vp, C.POINTER(C.c_longlong)]
+        L.qmc_pressure.argtypes = [vp, C.c_double, _dp]
+        L.qmc_pressure_device.argtypes = [vp, C.c_double, vp]
         L.qmc_shard_sample_device.argtypes = [vp, vp, vp]
         L.qmc_shard_reduce_device.argtypes = [vp, vp, vp, vp]
         L.qmc_shard_finish_device.argtypes = [vp, vp, vp, vp, C.c_longlong]
@@ -244,6 +248,19 @@ class QMCSystem:
         _chk(lib().qmc_eval_config(self._h, nc, _p(X), _p(_f64(R)), _p(lp), _p(el), _p(dl), _p(de)),
              "qmc_eval_config")
         return dict(lnpsi=lp, el=el, dlnpsi=dl, del_=de)
+
+    def pressure(self, T_kelvin: float = 0.0) -> dict:
+        """Virial pressure of the last energy_forces call (hartree / bohr^3):
+        P (electrons + classical nuclei at T_kelvin), its error bar, the
+        electronic part, <V_L> and <T_L>."""
+        o = np.zeros(5)
+        _chk(lib().qmc_pressure(self._h, float(T_kelvin), _p(o)), "qmc_pressure")
+        return dict(P=o[0], P_err=o[1], P_el=o[2], V=o[3], T=o[4])
+
+    def pressure_device(self, T_kelvin, out_dev):
+        """The same into a float64 cuda tensor [5] (asynchronous)."""
+        _chk(lib().qmc_pressure_device(self._h, float(T_kelvin), C.c_void_p(out_dev.data_ptr())),
+             "qmc_pressure_device")
 
     def walkers(self) -> np.ndarray:
         X = np.zeros((self.cfg.walkers, self.N, 3))
@@ -433,14 +450,15 @@ class Server:
         """Finished request as a dict, or None while it is pending."""
         N3 = 3 * self._N[traj]
         f = np.zeros(N3); S = np.zeros((N3, N3)); Rn = np.zeros(N3)
-        o = Served(0, 0, 0.0, 0.0, 0.0, 0.0, _p(f), _p(S), _p(Rn), 0.0, 0.0, 0.0)
+        o = Served(0, 0, 0.0, 0.0, 0.0, 0.0, _p(f), _p(S), _p(Rn), 0.0, 0.0, 0.0, -1.0, -1.0)
         rc = lib().qmc_server_fetch(self._s, ticket, C.byref(o))
         if rc < 0:
             raise QMCError(rc, "qmc_server_fetch")
         if rc == 0:
             return None
         return dict(traj=o.traj, status=o.status, E=o.E, E_err=o.E_err, Nc=o.n_samples, accept=o.accept, f=f,
-                    S=S, R_next=Rn, latency_ms=o.latency_ms, wait_ms=o.wait_ms, run_ms=o.run_ms)
+                    S=S, R_next=Rn, latency_ms=o.latency_ms, wait_ms=o.wait_ms, run_ms=o.run_ms,
+                    gpu_start_ms=o.gpu_start_ms, gpu_end_ms=o.gpu_end_ms)
 
     def stats(self) -> dict:
         st = (C.c_longlong * 8)()
@@ -494,7 +512,9 @@ class ShardGroup:
     all-reduce.  Every process ends with the E, f, S the single handle over all
     walkers would give (up to the order of the FP64 sums) and applies the same
     Langevin step.  `system` is the process's QMCSystem (or any object with the
-    shard_* methods and N); the buffers are tensors on its device."""
+    shard_* methods and N); the buffers are tensors on its device.  The
+    collectives run on torch's current stream, so the handle is put on that
+    stream too (its kernels and the all-reduces are then ordered)."""
 
     def __init__(self, system, walkers_total: int, group=None):
         import torch
@@ -503,6 +523,10 @@ class ShardGroup:
         self.walkers_total = int(walkers_total)
         N = system.N
         dev = "cuda" if torch.cuda.is_available() else "cpu"
+        if dev == "cuda" and hasattr(system, "set_stream"):
+            # torch's default stream has handle 0, which qmc_set_stream reads as
+            # "the handle's own stream": name the legacy default stream (1) instead
+            system.set_stream(torch.cuda.current_stream().cuda_stream or 1)
         self.sums = torch.zeros(3 + 9 * N + 3, dtype=torch.float64, device=dev)
         self.gram = torch.zeros(1 + 9 * N * N, dtype=torch.float64, device=dev)
 

@@ -90,6 +90,30 @@ def run_poisson(server: "q.Server", tids: list[int], trajs: list[Trajectory], n_
     return results, time.perf_counter() - t0
 
 
+def device_concurrency(results) -> dict:
+    """From the requests' device intervals: the mean number of requests running
+    on the GPU while any runs (sum of durations / length of their union) and the
+    fraction of requests that overlapped another one."""
+    iv = sorted((r["gpu_start_ms"], r["gpu_end_ms"]) for r in results
+                if r.get("gpu_start_ms", -1) >= 0 and r.get("gpu_end_ms", -1) > r.get("gpu_start_ms", -1))
+    if not iv:
+        return {"mean_concurrency": None, "overlapped_fraction": None}
+    total = sum(b - a for a, b in iv)
+    union, cur_a, cur_b = 0.0, iv[0][0], iv[0][1]
+    for a, b in iv[1:]:
+        if a > cur_b:
+            union += cur_b - cur_a
+            cur_a, cur_b = a, b
+        else:
+            cur_b = max(cur_b, b)
+    union += cur_b - cur_a
+    over = 0
+    for i, (a, b) in enumerate(iv):
+        if any(max(a, c) < min(b, d) for j, (c, d) in enumerate(iv) if j != i):
+            over += 1
+    return {"mean_concurrency": total / union if union > 0 else None, "overlapped_fraction": over / len(iv)}
+
+
 def summarize(results, wall_s) -> dict:
     lat = [r["latency_ms"] for r in results if r["status"] == 0]
     fe = sum(r["samples"] for r in results if r["status"] == 0)
@@ -99,4 +123,4 @@ def summarize(results, wall_s) -> dict:
             "service_p50_ms": percentile(run, 50), "service_p99_ms": percentile(run, 99),
             "completed_per_s": len(lat) / wall_s,
             "mean_wait_ms": float(np.mean([r["wait_ms"] for r in results])) if results else float("nan"),
-            "force_evals_per_s": fe / wall_s, "wall_s": wall_s}
+            "force_evals_per_s": fe / wall_s, "wall_s": wall_s, **device_concurrency(results)}

@@ -39,6 +39,8 @@ def test_struct_layouts_match_header(lib):
     # qmc_params: 10 int32, 5 double, uint64, 2 pointers, then the e-e-n-n Jastrow double and pointer
     assert C.sizeof(q.Params) == 10 * 4 + 5 * 8 + 8 + 2 * 8 + 8 + 8
     assert C.sizeof(q.Result) == 6 * 8
+    # qmc_served: 2 int, 4 double, 3 pointers, 5 double
+    assert C.sizeof(q.Served) == 2 * 4 + 4 * 8 + 3 * 8 + 5 * 8
 
 
 def test_invalid_parameters_rejected_without_gpu(lib):
@@ -53,10 +55,10 @@ def test_invalid_parameters_rejected_without_gpu(lib):
     rc = lib.qmc_init(C.byref(odd.cparams()), (C.c_double * 48)(), C.byref(h))
     assert rc == -1
     assert q.strerror(-7) == "singular Slater matrix"
-    # the e-e-n-n Jastrow term: FP64 form, N <= 64, positive exponent
+    # the e-e-n-n Jastrow term: both forms, positive exponent
     fj = np.eye(wl.N) * 0.1
     assert q.footprint_bytes(q.Config.from_workload(wl, fj=fj)) > 0
-    assert q.footprint_bytes(q.Config.from_workload(wl, fj=fj, precision=q.QMC_MIXED)) == 0
+    assert q.footprint_bytes(q.Config.from_workload(wl, fj=fj, precision=q.QMC_MIXED)) > 0
     assert q.footprint_bytes(q.Config.from_workload(wl, fj=fj, zeta_j=0.0)) == 0
     # f must be exactly symmetric: the kernels read its row a as its column a
     A = np.random.default_rng(3).uniform(-0.3, 0.3, (wl.N, wl.N))

@@ -60,15 +60,15 @@ def test_eval_config_matches_oracle(name, nconf, prec):
     assert np.all(_rel_vec(g["del_"], de) <= tol), _rel_vec(g["del_"], de)
 
 
-@pytest.mark.parametrize("prec", [q.QMC_FP64, q.QMC_MIXED])
-def test_eval_config_full_size_sampled(prec):
-    """The N=128, 4-Gaussian headline system: sampled configurations."""
+def test_eval_config_full_size_fp64():
+    """The N=128, 4-Gaussian headline system in the FP64 form, any configuration
+    (the mixed form at this size: tests/test_gpu_h128_mixed.py)."""
     wl = synth.workload("h128", walkers=2)
-    X = _configs(wl, 2, 17) if prec == q.QMC_FP64 else _sampled(wl, 2, 17, sweeps=4)
-    sysg = q.QMCSystem(q.Config.from_workload(wl, precision=prec), wl.R)
+    X = _configs(wl, 2, 17)
+    sysg = q.QMCSystem(q.Config.from_workload(wl, precision=q.QMC_FP64), wl.R)
     g = sysg.eval_config(X, wl.R)
     lp, el, dl, de = orc.eval_configs(_oracle_sys(wl), wl.R, X, derivs=True)
-    tol = TOL[prec]
+    tol = TOL[q.QMC_FP64]
     assert np.all(np.abs(g["el"] - el) <= tol * np.abs(el)), (g["el"], el)
     assert np.all(np.abs(g["lnpsi"] - lp) <= tol * np.abs(lp))
     assert np.all(_rel_vec(g["dlnpsi"], dl) <= tol), _rel_vec(g["dlnpsi"], dl)
@@ -152,10 +152,12 @@ def test_mixed_chain_statistically_matches_fp64():
     r64 = q.QMCSystem(q.Config.from_workload(wl, precision=q.QMC_FP64), wl.R).energy_forces(wl.R)
     r32 = q.QMCSystem(q.Config.from_workload(wl, precision=q.QMC_MIXED), wl.R).energy_forces(wl.R)
     err = np.hypot(r64["E_err"], r32["E_err"])
-    assert abs(r64["E"] - r32["E"]) < 4 * err, (r64["E"], r32["E"], err)
+    assert abs(r64["E"] - r32["E"]) < 3 * err, (r64["E"], r32["E"], err)
+    # 48 force components: every |z| below the Sidak threshold of a 0.27 %
+    # family-wise rate (|z| < 4.03), at least 95 % within 3 sigma
     sig = np.sqrt(np.diag(r64["S"]) + np.diag(r32["S"]))
     z = np.abs(r64["f"] - r32["f"]) / sig
-    assert np.mean(z < 3) > 0.95 and np.max(z) < 5.5, z
+    assert np.mean(z < 3) >= 0.95 and np.max(z) < 4.03, z
 
 
 def _spd(n, seed):
@@ -327,4 +329,4 @@ def test_small_system_md_end_to_end_both_forms_and_both_S():
     # first MD step (same nuclei): FP64 and mixed forms agree within their error bars
     for mode in (q.QMC_S_IDENTITY, q.QMC_S_COV):
         (e64, s64), (e32, s32) = res[(q.QMC_FP64, mode)][0], res[(q.QMC_MIXED, mode)][0]
-        assert abs(e64 - e32) < 4 * np.hypot(s64, s32)
+        assert abs(e64 - e32) < 3 * np.hypot(s64, s32)

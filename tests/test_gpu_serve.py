@@ -126,3 +126,40 @@ def test_served_poisson_loop_reports_latency():
     srv.close()
     assert s["requests"] == 30 and s["failed"] == 0
     assert 0 < s["p50_ms"] <= s["p99_ms"] and s["force_evals_per_s"] > 0
+
+
+def test_requests_overlap_on_the_device():
+    """Continuous batching, not a queue: requests of different trajectories
+    admitted together run at the same time on the GPU (their start-to-end
+    event intervals on their streams intersect)."""
+    trajs = [_traj(k, 32, 1024) for k in range(4)]
+    srv = q.Server(1 << 34, 4)
+    tids = [srv.add_trajectory(c, R, T, 0.1) for c, R, T in trajs]
+    res = _run(srv, tids, 1, [0, 1, 2, 3, 0, 1, 2, 3])
+    srv.close()
+    iv = [(r["gpu_start_ms"], r["gpu_end_ms"]) for k in res for r in res[k]]
+    assert all(0 <= a < b for a, b in iv), iv
+    pairs = [(i, j) for i in range(len(iv)) for j in range(i + 1, len(iv))
+             if max(iv[i][0], iv[j][0]) < min(iv[i][1], iv[j][1])]
+    assert pairs, iv
+
+
+def test_no_device_allocation_while_serving():
+    """The budget is one arena taken at creation: admissions (also after
+    evictions under a tight budget) allocate no device memory."""
+    import torch
+    trajs = [_traj(0, 16, 512), _traj(1, 32, 512), _traj(2, 16, 512), _traj(3, 32, 512)]
+    budget = int(2.2 * max(q.footprint_bytes(c) for c, _, _ in trajs))
+    srv = q.Server(budget, 2)
+    tids = [srv.add_trajectory(c, R, T, 0.1) for c, R, T in trajs]
+    _run(srv, tids, 1, [0, 1, 2, 3])            # every kernel loaded once
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    ev0 = srv.stats()["evictions"]
+    _run(srv, tids, 2, [3, 2, 1, 0, 0, 1, 2, 3])
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    st = srv.stats()
+    srv.close()
+    assert st["evictions"] > ev0 and st["admissions"] > 4
+    assert free1 == free0, (free0, free1)

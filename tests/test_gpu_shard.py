@@ -20,12 +20,18 @@ def test_two_shards_equal_one_handle(name, W, W1, prec):
     N, N3 = wl.N, 3 * wl.N
     cfg = q.Config.from_workload(wl, precision=prec, warmup=2, warmup_cont=1, recompute_every=2)
     one = q.QMCSystem(cfg, wl.R)
+    # the library's work and the sums below (torch) on one stream
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    st = stream.cuda_stream
+    one.set_stream(st)
     R_dev = torch.tensor(wl.R, dtype=torch.float64, device="cuda")
     nout = 4 + N3 + N3 * N3
     shards = []
     for lo, hi in ((0, W1), (W1, W)):
         s = q.QMCSystem(q.Config.from_workload(wl, precision=prec, warmup=2, warmup_cont=1, recompute_every=2,
                                                walkers=hi - lo), wl.R)
+        s.set_stream(st)
         s.set_walker_offset(lo)
         shards.append(s)
     ref_out = torch.zeros(nout, dtype=torch.float64, device="cuda")

@@ -1,5 +1,6 @@
-"""The multi-rank bench path on CPU: two gloo ranks run independent replicas
-(different seeds, no data-path collective) and agree on the max-over-ranks time."""
+"""The multi-rank paths on CPU with gloo ranks: the bench's rank set-up (one
+system on every rank, walkers split by offset, max-over-ranks time) and the
+walker-sharded reduction's exchange."""
 import os
 import socket
 
@@ -22,17 +23,17 @@ def _worker(rank, ws, port, out):
     dist.init_process_group("gloo", rank=rank, world_size=ws)
     from paper_1605_08423_gb300 import synth
     import bench
-    wl = synth.workload("h16", seed=1002 + rank)     # per-rank replica, as bench.run_ours seeds it
+    wl = synth.workload("h16", seed=1002)     # one system on every rank, as bench.run_ours builds it
     ms = 10.0 + 5.0 * rank
     t = torch.tensor([ms])
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.barrier()
-    out[rank] = (float(t.item()), float(wl.R.sum()), bench._dist())
+    out[rank] = (float(t.item()), float(wl.R.sum()), bench._dist(), rank * wl.walkers)
     dist.destroy_process_group()
 
 
 @pytest.mark.timeout(120)
-def test_two_gloo_ranks_independent_replicas_and_max_time():
+def test_two_gloo_ranks_one_system_walker_offsets_and_max_time():
     ctx = mp.get_context("spawn")
     mgr = ctx.Manager()
     out = mgr.dict()
@@ -44,7 +45,8 @@ def test_two_gloo_ranks_independent_replicas_and_max_time():
         p.join(90)
         assert p.exitcode == 0
     assert out[0][0] == out[1][0] == 15.0
-    assert out[0][1] != out[1][1]                      # different synthetic replicas
+    assert out[0][1] == out[1][1]                      # the same nuclei on every rank
+    assert out[0][3] == 0 and out[1][3] == 256         # rank r's walkers start at r W
     assert out[0][2] == (2, 0, 0) and out[1][2][:2] == (2, 1)
 
 
