@@ -1134,19 +1134,33 @@ int orc_eval_config(const orc::Params* p, const double* R, const double* X, int 
 }
 
 // Many configurations at once (walker-parallel): X [nconf][Ne][3].
+// The R-derivatives take one dual-number pass per (configuration, nucleus);
+// the passes are independent, so the threads share them out over both indices
+// (each pass is the same computation as in eval_config).
 int orc_eval_configs(const orc::Params* p, const double* R, int nconf, const double* X, int derivs,
                      double* lnpsi, double* el, double* dlnpsi, double* del) {
-    const int Ne = p->n_up + p->n_dn, N3 = 3 * p->N;
+    const int Ne = p->n_up + p->n_dn, N3 = 3 * p->N, N = p->N;
     int bad = 0;
 #pragma omp parallel for schedule(dynamic) reduction(+ : bad)
     for (int c = 0; c < nconf; ++c) {
-        orc::ConfigResult r = orc::eval_config(*p, R, X + (size_t)c * 3 * Ne, derivs != 0);
+        orc::ConfigResult r = orc::eval_config(*p, R, X + (size_t)c * 3 * Ne, false);
         if (!r.ok) { ++bad; continue; }
         lnpsi[c] = r.lnpsi; el[c] = r.el;
-        if (derivs)
-            for (int k = 0; k < N3; ++k) { dlnpsi[(size_t)c * N3 + k] = r.dlnpsi[k]; del[(size_t)c * N3 + k] = r.del[k]; }
     }
-    return bad ? -1 : 0;
+    if (bad || !derivs) return bad ? -1 : 0;
+#pragma omp parallel for schedule(dynamic) collapse(2)
+    for (int c = 0; c < nconf; ++c)
+        for (int a = 0; a < N; ++a) {
+            std::vector<orc::D3> Rd((size_t)N3);
+            for (int k = 0; k < N3; ++k) Rd[k] = orc::D3(R[k]);
+            for (int mu = 0; mu < 3; ++mu) Rd[3 * a + mu].d[mu] = 1.0;
+            orc::WfOut<orc::D3> wd = orc::wavefunction<orc::D3>(*p, Rd.data(), X + (size_t)c * 3 * Ne);
+            for (int mu = 0; mu < 3; ++mu) {
+                dlnpsi[(size_t)c * N3 + 3 * a + mu] = wd.lnpsi.d[mu];
+                del[(size_t)c * N3 + 3 * a + mu] = wd.el.d[mu];
+            }
+        }
+    return 0;
 }
 
 // Slater matrices at one configuration X [Ne][3]: out [Ne][n_orb], row i =

@@ -95,7 +95,7 @@ def test_sampler_inverse_after_eight_sweeps_h128(recompute):
     configuration (every 8 sweeps, FP64 Gauss-Jordan or Newton-Schulz).  The
     sample's E_L and forces, taken with that inverse, against the oracle at the
     walkers' positions."""
-    W = 24
+    W = 16
     wl = synth.workload("h128", walkers=W, sweeps=8, warmup=0)
     cfg = q.Config.from_workload(wl, precision=q.QMC_MIXED, warmup=0, measure_every=8,
                                  recompute_every=1000 if recompute == "none" else 8)
