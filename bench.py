@@ -190,6 +190,25 @@ def _flops_per_launch(cls: str, W, N, n, B, G, acc_ratio, use_tc, nk=462):
     return None
 
 
+def _hbm_bytes_per_launch(cls: str, W, N, n, nk, acc_ratio, t=4):
+    """Algorithmic HBM bytes of one launch (state that must come from or go to
+    HBM once; working precision t bytes), for the kernels whose HBM rate is
+    reported beside their ALU roofline:
+      sweep    per walker: G^T of both spins read and written (2 x 2 n^2 t), the
+               proposals' orbital rows (N n t), their trig (6 N t) and uniforms
+               (N t), positions read (24 N) and accepted ones written (24 N p_acc);
+      measure  per walker: D (3 N n t), Lp (N n t), G^T (2 n^2 t), positions
+               (24 N), accumulators read and written (2 x 8 (3 + 9 N)); out to
+               the adjoint kernel K^T (2 n^2 t), electron data (9 N t),
+               E_L (8) and the structure factor (2 nk t)."""
+    if cls == "sweep":
+        return W * (2 * 2 * n * n * t + N * n * t + 6 * N * t + N * t + 24 * N + 24 * N * acc_ratio)
+    if cls == "measure":
+        return W * (3 * N * n * t + N * n * t + 2 * n * n * t + 24 * N + 2 * 8 * (3 + 9 * N)
+                    + 2 * n * n * t + 9 * N * t + 8 + 2 * nk * t)
+    return None
+
+
 def _cpu_baseline(wl, walkers_per_core=1):
     """The FP64 oracle on the host cores: one sweep plus one local-energy and
     force sample per walker, W = threads x walkers_per_core."""
@@ -289,24 +308,37 @@ def _toy_bench(stream, steps, rank, n_steps=None, table=True):
 
 
 def _jastrow34_bench(stream, calls=8):
-    """The FP64 form with and without the e-e-n-n Jastrow term (N = 64, 1024 walkers,
-    4 measured sweeps + 1 continuation per call, a sample every sweep): after a
+    """Both forms with and without the e-e-n-n Jastrow term: the FP64 form at
+    N = 64 (1024 walkers) and the mixed form at N = 128 (4096 walkers), 4
+    measured sweeps + 1 continuation per call, a sample every sweep: after a
     warm-up call, `calls` calls timed one by one; the median, min and max and the
     median SM clock over them."""
     import numpy as np
     import torch
     from paper_1605_08423_gb300 import qmcmd as q
     from paper_1605_08423_gb300 import synth
-    wl = synth.workload("h64", walkers=1024, sweeps=4, warmup=2)
+    out = {"metric": "electron moves/s and force-evals/s with and without U_{3+4}",
+           "config": {"workload": "FP64 form: h64 (N=64, r_s=1.4, 2 s-Gaussians/proton), 1024 walkers; mixed "
+                                  "form: h128 (N=128, r_s=1.2, 4 s-Gaussians/proton), 4096 walkers; 4 sweeps "
+                                  "(+1 continuation) per call, sample every sweep, U_{3+4} coefficients "
+                                  "symmetric U(-0.3, 0.3), exponent 0.7933844"}}
+    for form, name, walkers in (("fp64", "h64", 1024), ("mixed", "h128", 4096)):
+        _jastrow34_legs(stream, calls, out, form, name, walkers)
+    return out
+
+
+def _jastrow34_legs(stream, calls, out, form, name, walkers):
+    import numpy as np
+    import torch
+    from paper_1605_08423_gb300 import qmcmd as q
+    from paper_1605_08423_gb300 import synth
+    wl = synth.workload(name, walkers=walkers, sweeps=4, warmup=2)
     A = np.random.default_rng(5).uniform(-0.3, 0.3, (wl.N, wl.N))
     fj = 0.5 * (A + A.T)
     R_dev = torch.tensor(wl.R, dtype=torch.float64, device="cuda")
-    out = {"metric": "FP64-form electron moves/s and force-evals/s with and without U_{3+4}",
-           "config": {"workload": f"h64: N={wl.N} H, r_s={wl.rs}, {wl.n_gauss} s-Gaussians/proton, FP64 form, "
-                                  f"{wl.walkers} walkers x {wl.sweeps} sweeps (+1 continuation), sample every "
-                                  "sweep, U_{3+4} coefficients symmetric U(-0.3, 0.3), exponent 0.7933844"}}
-    for tag, f in (("without", None), ("with", fj)):
-        cfg = q.Config.from_workload(wl, precision=q.QMC_FP64, warmup=2, warmup_cont=1, measure_every=1,
+    prec = q.QMC_FP64 if form == "fp64" else q.QMC_MIXED
+    for tag, f in ((f"{form}_without", None), (f"{form}_with", fj)):
+        cfg = q.Config.from_workload(wl, precision=prec, warmup=2, warmup_cont=1, measure_every=1,
                                      recompute_every=4, fj=f)
         sysq = q.QMCSystem(cfg, wl.R)
         sysq.set_stream(stream.cuda_stream)
@@ -333,7 +365,6 @@ def _jastrow34_bench(stream, calls=8):
                     "calls_timed": calls, "sm_mhz_median": clk.get("sm_mhz"), "clock_reasons": clk.get("reasons"),
                     "E": float(o[0].item())}
         sysq.close()
-    return out
 
 
 def _toy_cpu_baseline():
@@ -600,6 +631,12 @@ def run_ours(args, ws, rank, local):
                           "frac": ach / fp32_peak, "traffic": None,
                           "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock",
                           "flops_per_launch": fl, "avg_launch_ms": avg}
+            hb = _hbm_bytes_per_launch(cls, W, N, n, _nk(cfg.mmax), float(res["accept"]),
+                                       4 if prec == q.QMC_MIXED else 8)
+            if hb:
+                gbs = hb / (avg / 1e3) / 1e9
+                roofs[cls].update({"hbm_bytes_per_launch_algorithmic": hb, "hbm_gbs_achieved": gbs,
+                                   "hbm_frac_of_measured_copy": gbs / float(peaks.get("hbm_gbs", 6800.0))})
     dom = max(kt, key=lambda k: kt[k][0])
     for cls in roofs:
         tr = _profile_traffic(cls) if use_tc and N == 128 and G == 4 else None

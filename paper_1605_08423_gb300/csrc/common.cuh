@@ -297,6 +297,16 @@ __device__ __forceinline__ float ex2_fast(float x) {
     return y;
 }
 
+// Nearest integer of x (|x| < 2^22) in FP32 arithmetic: adding and removing
+// 1.5 * 2^23 leaves no fraction bits, and round-to-nearest-even does the
+// rounding (IEEE rounding of each addition; no reassociation in this build).
+// The FMA pipe does it, where rintf's rounding instruction runs on the FP64
+// pipe, a fraction of whose rate this part has.
+__device__ __forceinline__ float rint_fma(float x) {
+    const float m = 12582912.0f;   // 1.5 * 2^23
+    return __fsub_rn(__fadd_rn(x, m), m);
+}
+
 // Mixed-form real-space Ewald sum of one pair: the images of the minimum-image
 // vector inside the FP32-level cutoff (skip_min: leave out the minimum image),
 // phi(r) = erfc(kappa r) / r and, when grad, its gradient added to grad.
@@ -304,7 +314,7 @@ __device__ __forceinline__ float ex2_fast(float x) {
 template <bool kGrad>
 __device__ __forceinline__ float ewald_real_cut(float dx, float dy, float dz, bool skip_min, float Lt, float iL,
                                                 float rc2, float kappa, float* grad) {
-    dx -= Lt * rintf(dx * iL); dy -= Lt * rintf(dy * iL); dz -= Lt * rintf(dz * iL);
+    dx -= Lt * rint_fma(dx * iL); dy -= Lt * rint_fma(dy * iL); dz -= Lt * rint_fma(dz * iL);
     // moving component m of the minimum image by L away from zero adds
     // L (L - 2 |d_m|) > 0 to r^2 (so only the minimum image can sit at r = 0)
     const float r0 = dx * dx + dy * dy + dz * dz;

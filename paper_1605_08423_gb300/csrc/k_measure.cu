@@ -683,6 +683,7 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
     //   M1 = Y G,  K = G M1  (= G Y G),  Z = C G,  P = C K  (per 64-row tile of C)
     // and the basis-derivative contraction is fused onto each Z/P tile.
     const int np = s.np, ldt = np + 4, ng = np / 4;
+    const int lnp = __ffs(np) - 1;   // np is a power of two: index arithmetic by shifts (no integer division)
     if constexpr (kSplit) {
         // K = G Y G per spin block for the adjoint kernel, in two buffers: the
         // 4 x 4 register tiles of M1 = Y G overwrite Y^T once every thread has
@@ -694,7 +695,7 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
         for (int sp = 0; sp < 2; ++sp) {
             const T* Gsp = Gt + ((size_t)w * 2 + sp) * n * n;
             for (int idx = tid; idx < np * np; idx += nt) {
-                const int il = idx / np, j = idx - il * np;
+                const int il = idx >> lnp, j = idx & (np - 1);
                 T g = 0, y = 0;
                 if (il < n && j < n) {
                     const int i = sp * n + il;
@@ -751,9 +752,9 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
                     for (int b_ = 0; b_ < 4; ++b_) bufG2[(c0 + b_) * ldt + r0 + a_] = acc4[a_][b_];
             __syncthreads();
             float* ko = kt_out + ((size_t)w * 2 + sp) * n * n;
-            for (int idx = tid; idx < n * n; idx += nt) {
-                const int i = idx / n, j = idx - i * n;
-                ko[idx] = (float)bufG2[i * ldt + j];
+            for (int idx = tid; idx < np * np; idx += nt) {
+                const int i = idx >> lnp, j = idx & (np - 1);
+                if (i < n && j < n) ko[i * n + j] = (float)bufG2[i * ldt + j];
             }
             __syncthreads();
         }
@@ -765,7 +766,7 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
     for (int sp = 0; sp < 2; ++sp) {
         const T* Gsp = Gt + ((size_t)w * 2 + sp) * n * n;
         for (int idx = tid; idx < np * np; idx += nt) {
-            const int il = idx / np, j = idx - il * np;
+            const int il = idx >> lnp, j = idx & (np - 1);
             T g = 0, y = 0;
             if (il < n && j < n) {
                 const int i = sp * n + il;
@@ -818,7 +819,7 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
         const int B = s.B;
         for (int b0 = 0; b0 < B; b0 += 64) {
             for (int idx = tid; idx < 64 * np; idx += nt) {   // C^T tile
-                const int bl = idx / np, j = idx - bl * np;
+                const int bl = idx >> lnp, j = idx & (np - 1);
                 bufS[j * 68 + bl] = (b0 + bl < B && j < n) ? s.C[(size_t)(b0 + bl) * n + j] : T(0);
             }
             __syncthreads();

@@ -226,8 +226,14 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
                 if (c + 2 < nch) fetch_b4(c + 2);
             }
             // one item = (row, 4 consecutive basis functions of the half); the
-            // displacement to a nucleus is computed once for its Gaussians
-            const int r = tid >> 2, k0 = 16 * h + 4 * (tid & 3);
+            // displacement to a nucleus is computed once for its Gaussians.
+            // Warp wp owns rows 8 wp .. 8 wp + 7 (one swizzle block); each
+            // quarter-warp (the 8 lanes of one phase of a 16-byte store) takes
+            // rows q and q + 4 of the block, whose swizzled 16-byte chunks of
+            // this half lie in opposite halves of the 128-byte row: the phase
+            // covers all 32 banks once (no bank conflict).
+            const int wl = tid & 31;
+            const int r = 8 * (tid >> 5) + ((wl >> 3) & 3) + 4 * ((wl >> 2) & 1), k0 = 16 * h + 4 * (wl & 3);
             float v[Q][4];
             int a_prev = -1;
             float t = 0.f, pp = 0.f, sq = 0.f, pv[3] = {0.f, 0.f, 0.f};

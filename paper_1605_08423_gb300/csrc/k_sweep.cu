@@ -264,10 +264,16 @@ __global__ void __launch_bounds__(512) sweep_kernel(SysView<T> s, double* __rest
 constexpr int kSwWalkers = 4;   // walkers per CTA (8 warps)
 constexpr int kSwRow = 64;      // register row length (n <= 64)
 
+// Stride of one point's (sin, cos)(pi x / L) triples in sweep_reg_kernel's
+// shared memory: 7 floats, so that the 32 lanes reading 32 consecutive points
+// hit 32 distinct banks (a stride of 6 pairs them up).
+constexpr int kTS = 7;
+
 // Shared-memory floats per walker of sweep_reg_kernel: phi [64], row [64],
-// red [8], trig [6N], and with the e-e-n-n term c [N] and chi(r_i) [N].
+// red [8], trig [kTS N], and with the e-e-n-n term c [N] and chi(r_i) [N];
+// rounded up to whole 16-byte vectors (phi and the row are read as float4).
 __host__ __device__ inline size_t sweep_reg_walker_floats(int N, bool j34) {
-    return 2 * kSwRow + 8 + 6 * (size_t)N + (j34 ? 2 * (size_t)N : 0);
+    return (2 * kSwRow + 8 + kTS * (size_t)N + (j34 ? 2 * (size_t)N : 0) + 3) & ~size_t(3);
 }
 
 __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<float> s, double* __restrict__ X,
@@ -282,16 +288,16 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int p = warp >> 1, h = warp & 1, tw = tid & 63;
     const bool j34 = s.fjt != nullptr;
-    float* ptr_s = (float*)smraw;                                       // [N][6] proton trig
-    float* f_s = ptr_s + ((6 * N + 3) & ~3);                            // [N][N] e-e-n-n coefficients (j34)
+    float* ptr_s = (float*)smraw;                                       // [N][kTS] proton trig
+    float* f_s = ptr_s + ((kTS * N + 3) & ~3);                            // [N][N] e-e-n-n coefficients (j34)
     float* mine = f_s + (j34 ? (size_t)N * N : 0) + (size_t)p * sweep_reg_walker_floats(N, j34);
     float* phi = mine;                  // [64] orbital row at the proposal (zero beyond n)
     float* rowb = phi + kSwRow;         // [64] row il of G^T on acceptance
     float* red = rowb + kSwRow;         // [8] du halves, ratio
-    float* et = red + 8;                // [N][6] (sin, cos)(pi x / L) of the current positions
-    float* c34 = et + 6 * N;            // [N] sum_j chi_a(r_j) (j34)
+    float* et = red + 8;                // [N][kTS] (sin, cos)(pi x / L) of the current positions
+    float* c34 = et + kTS * N;            // [N] sum_j chi_a(r_j) (j34)
     float* cho = c34 + N;               // [N] chi_a at the moving electron (j34)
-    for (int idx = tid; idx < 6 * N; idx += blockDim.x) ptr_s[idx] = s.ptrig[idx];
+    for (int idx = tid; idx < 6 * N; idx += blockDim.x) ptr_s[kTS * (idx / 6) + idx % 6] = s.ptrig[idx];
     if (j34)
         for (int idx = tid; idx < N * N; idx += blockDim.x) f_s[idx] = s.fjt[idx];
     __syncthreads();
@@ -306,15 +312,15 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
         const int i = idx / 3, mu = idx % 3;
         float sn, cs;
         sincospif((float)(Xw[idx] * iL), &sn, &cs);
-        et[6 * i + mu] = sn;
-        et[6 * i + 3 + mu] = cs;
+        et[kTS * i + mu] = sn;
+        et[kTS * i + 3 + mu] = cs;
     }
     const float zj = (float)s.zeta_j;
     if (j34) {
         bar();   // et complete
         for (int a = tw; a < N; a += 64) {
             float c = 0.f;
-            for (int j = 0; j < N; ++j) c += jas_orbital(et + 6 * j, ptr_s + 6 * a, ell, zj);
+            for (int j = 0; j < N; ++j) c += jas_orbital(et + kTS * j, ptr_s + kTS * a, ell, zj);
             c34[a] = c;
         }
     }
@@ -370,17 +376,17 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
             const float wl = (a4[0] + a4[1]) + (a4[2] + a4[3]);
             // Jastrow difference: partners tw and tw + 64
             float du = 0.f;
-            const float* ei = et + 6 * i;
+            const float* ei = et + kTS * i;
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 const int j = tw + 64 * k;
                 if (j < N) {
-                    const float* ej = et + 6 * j;
+                    const float* ej = et + kTS * j;
                     float u1, u0, d1, d2;
                     pade_ee(bee, pair_dist(pt, ej, ell), u1, d1, d2);
                     pade_ee(bee, pair_dist(ei, ej, ell), u0, d1, d2);
                     du += (j != i) ? u1 - u0 : 0.f;
-                    const float* pa = ptr_s + 6 * j;
+                    const float* pa = ptr_s + kTS * j;
                     float d3;
                     pade_ep(bep, Zj, pair_dist(pt, pa, ell), u1, d1, d2, d3);
                     pade_ep(bep, Zj, pair_dist(ei, pa, ell), u0, d1, d2, d3);
@@ -394,8 +400,8 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
                 for (int k = 0; k < 2; ++k) {
                     const int a = tw + 64 * k;
                     if (a < N) {
-                        chn_r[k] = jas_orbital(pt, ptr_s + 6 * a, ell, zj);
-                        cho_r[k] = jas_orbital(ei, ptr_s + 6 * a, ell, zj);
+                        chn_r[k] = jas_orbital(pt, ptr_s + kTS * a, ell, zj);
+                        cho_r[k] = jas_orbital(ei, ptr_s + kTS * a, ell, zj);
                         cho[a] = cho_r[k];
                     }
                 }
@@ -434,8 +440,8 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
                 }
                 if (tw < 3) {   // keep the proposal as is (periodic functions; the next proposal pass wraps)
                     Xw[3 * i + tw] = Xp[row * 3 + tw];
-                    et[6 * i + tw] = tw == 0 ? pt[0] : (tw == 1 ? pt[1] : pt[2]);
-                    et[6 * i + 3 + tw] = tw == 0 ? pt[3] : (tw == 1 ? pt[4] : pt[5]);
+                    et[kTS * i + tw] = tw == 0 ? pt[0] : (tw == 1 ? pt[1] : pt[2]);
+                    et[kTS * i + 3 + tw] = tw == 0 ? pt[3] : (tw == 1 ? pt[4] : pt[5]);
                 }
                 if (j34) {      // c_a of this thread's nuclei (read by others only after the next barrier)
 #pragma unroll
@@ -463,7 +469,7 @@ void launch_sweep(const SysView<T>& s, double* X, const double* Xp, const T* ptp
     if constexpr (sizeof(T) == 4) {
         if (s.n <= kSwRow) {   // mixed form: inverse rows in registers
             const bool j34 = s.fjt != nullptr;
-            const size_t smem = sizeof(float) * (((6 * s.N + 3) & ~3) + (j34 ? (size_t)s.N * s.N : 0) +
+            const size_t smem = sizeof(float) * (((kTS * s.N + 3) & ~3) + (j34 ? (size_t)s.N * s.N : 0) +
                                                  kSwWalkers * sweep_reg_walker_floats(s.N, j34));
             static size_t attr = 0;
             if (smem > attr &&
