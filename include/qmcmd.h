@@ -61,8 +61,8 @@ typedef struct {
     int32_t n_warmup;         /* sweeps before the first measurement of the first call   */
     int32_t n_warmup_cont;    /* same, for later calls (walkers carried over)            */
     int32_t measure_every;    /* sweeps between samples, >= 1                           */
-    int32_t recompute_every;  /* sweeps between periodic inverse recomputes, >= 1 (FP64  */
-                              /* Gauss-Jordan unless QMC_OPT_RECOMPUTE says otherwise)   */
+    int32_t recompute_every;  /* sweeps between periodic inverse recomputes, >= 1 (see   */
+                              /* QMC_OPT_RECOMPUTE for how each form recomputes)         */
     int32_t precision;        /* QMC_FP64 or QMC_MIXED                                   */
     int32_t ewald_mmax;       /* reciprocal cutoff |m| <= mmax (k = 2 pi m / L)          */
     double L;                 /* box side, bohr                                          */
@@ -282,13 +282,17 @@ enum { QMC_LV_ADOPTED = 0, QMC_LV_FAST = 1, QMC_LV_NOROGNA = 2 };
 /* QMC_OPT_RECOMPUTE selects the periodic inverse recompute inside a call
  * (every recompute_every sweeps; the recompute at the start of every call is
  * always the FP64 one):
- *   QMC_RECOMPUTE_FP64 (default)  Slater blocks at the current positions, then
- *                                 FP64 Gauss-Jordan inverse and ln|det| (resets the
- *                                 drift of the Sherman-Morrison updates);
- *   QMC_RECOMPUTE_NEWTON          mixed form only: one FP32 Newton-Schulz step
- *                                 G <- G + G (I - A G) on the carried inverse, FP64
- *                                 Gauss-Jordan for blocks with max|I - A G| >= 0.01
- *                                 (faster on parts with a slow FP64 pipe; FP32-level).
+ *   QMC_RECOMPUTE_FP64            the FP64 form's only choice: Slater blocks at
+ *                                 the current positions, then FP64 Gauss-Jordan
+ *                                 inverse and ln|det| (resets the drift of the
+ *                                 Sherman-Morrison updates);
+ *   QMC_RECOMPUTE_NEWTON          the mixed form's default: one Newton-Schulz step
+ *                                 G <- G + G (I - A G) on the carried inverse, the
+ *                                 residual I - A G formed with a compensated (error-
+ *                                 free product, TwoSum) FP32 dot product, so that G
+ *                                 becomes the inverse of the FP32 Slater block to
+ *                                 FP32 rounding; FP64 Gauss-Jordan for blocks with
+ *                                 max|I - A G| >= 0.01.  ln|det| is not updated.
  * INVALID for other values, and for QMC_RECOMPUTE_NEWTON in the FP64 form. */
 enum { QMC_OPT_RECOMPUTE = 5 };
 /* QMC_OPT_WALKER_OFFSET (value >= 0, default 0): the handle's walker w draws

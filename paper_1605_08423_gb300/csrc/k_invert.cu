@@ -132,13 +132,21 @@ __global__ void __launch_bounds__(256) invert_kernel(int N, int n, const T* __re
 }
 
 // Mixed form, periodic recompute inside a call: one Newton-Schulz step
-//   R = I - A G,  G <- G + G R   (FP32, error O(|R|^2))
+//   R = I - A G,  G <- G + G R
 // on the inverse the Sherman-Morrison updates have carried since the last
 // recompute; A = the Slater block just evaluated at the current positions.
-// The rank-1 updates leave |R| near FP32 rounding, so one step restores the
-// inverse to FP32 accuracy at the cost of two n^3 FP32 products (the FP64
-// Gauss-Jordan runs at 1/64 of that rate on this part).  If max |R_ij| >= 0.01
-// (or is not finite) the block is inverted from scratch by Gauss-Jordan in
+// With E = G - A^-1 the step leaves G' - A^-1 = -E A E, second order in the
+// drift.  The residual is formed without rounding error of consequence: each
+// product a*g is split exactly into its FP32 value and error (one FMA) and the
+// sum is carried as an unevaluated pair hi + lo with Knuth's TwoSum (the
+// compensated dot product of Ogita, Rump and Oishi, SIAM J. Sci. Comput. 26,
+// 2005), so R is the residual of the FP32 A and G to FP32 relative accuracy
+// although A G agrees with I to a few units of FP32 rounding.  G R is small
+// and formed in plain FP32.  The result is the inverse of the FP32 Slater
+// block to FP32 rounding (what FP64 Gauss-Jordan rounded to FP32 gives) from
+// about ten FP32 operations per term of one n^3 product plus one plain n^3
+// product; FP64 runs at 1/64 of the FP32 rate on this part.  If max |R_ij| >=
+// 0.01 (or is not finite) the block is inverted from scratch by Gauss-Jordan in
 // FP64 instead.  ln|det| is not updated here (nothing in a call reads it
 // after the first recompute, which is always Gauss-Jordan).
 __global__ void __launch_bounds__(256) refine_kernel(int N, int n, int np, const float* __restrict__ Phi,
@@ -164,21 +172,34 @@ __global__ void __launch_bounds__(256) refine_kernel(int N, int n, int np, const
     const bool act = tid < ng * ng;
     float acc[4][4] = {};
     float rm = 0.f;
-    if (act) {                               // (A G)[i][k] = sum_j A[i][j] G[j][k]
+    if (act) {                               // (A G)[i][k] = sum_j A[i][j] G[j][k] as hi + lo
+        float lo[4][4] = {};
         for (int j = 0; j < np; ++j) {
             const float4 a4 = *(const float4*)(AT + j * ld + r0), g4 = *(const float4*)(Gm + j * ld + c0);
             const float av[4] = {a4.x, a4.y, a4.z, a4.w}, gv[4] = {g4.x, g4.y, g4.z, g4.w};
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * gv[b];
+                for (int b = 0; b < 4; ++b) {
+                    // explicit-rounding intrinsics: no contraction into FMAs,
+                    // which would void the error-free transformations
+                    const float p = __fmul_rn(av[a], gv[b]);
+                    const float e = __fmaf_rn(av[a], gv[b], -p);     // a g - p exactly
+                    const float s = acc[a][b], t = __fadd_rn(s, p);
+                    const float z = __fsub_rn(t, s);
+                    const float d = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));   // s + p - t exactly
+                    lo[a][b] = __fadd_rn(lo[a][b], __fadd_rn(d, e));
+                    acc[a][b] = t;
+                }
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const int i = r0 + a, k = c0 + b;
-                const float r = (i < n && k < n) ? (i == k ? 1.f : 0.f) - acc[a][b] : 0.f;
+                // (delta - hi) is exact (hi is within a few units of rounding
+                // of delta); one rounding when lo is taken off
+                const float r = (i < n && k < n) ? __fsub_rn(__fsub_rn(i == k ? 1.f : 0.f, acc[a][b]), lo[a][b]) : 0.f;
                 R[i * ld + k] = r;
                 rm = fmaxf(rm, isfinite(r) ? fabsf(r) : 1e30f);
             }

@@ -92,16 +92,15 @@ def test_sampler_inverse_after_eight_sweeps_h128(recompute):
     """The inverse the sampler carries: one sample after 8 sweeps (1024 moves)
     of Sherman-Morrison updates from the call's FP64 inverse (no recompute in
     between), or right after the periodic recompute of the bench
-    configuration (every 8 sweeps, FP64 Gauss-Jordan or Newton-Schulz).  The
-    sample's E_L and forces, taken with that inverse, against the oracle at the
-    walkers' positions."""
+    configuration (every 8 sweeps, FP64 Gauss-Jordan or the default
+    compensated Newton-Schulz step).  The sample's E_L and forces,
+    taken with that inverse, against the oracle at the walkers' positions."""
     W = 16
     wl = synth.workload("h128", walkers=W, sweeps=8, warmup=0)
     cfg = q.Config.from_workload(wl, precision=q.QMC_MIXED, warmup=0, measure_every=8,
                                  recompute_every=1000 if recompute == "none" else 8)
     s = q.QMCSystem(cfg, wl.R)
-    if recompute == "newton":
-        s.set_recompute(q.QMC_RECOMPUTE_NEWTON)
+    s.set_recompute(q.QMC_RECOMPUTE_FP64 if recompute == "fp64" else q.QMC_RECOMPUTE_NEWTON)
     s.energy_forces(wl.R)
     X, acc = s.walkers(), s.accumulators()
     N3 = 3 * wl.N
@@ -121,8 +120,36 @@ def test_sampler_inverse_after_eight_sweeps_h128(recompute):
     assert np.all(r_dl <= TOL) and np.all(r_de <= TOL), (r_dl.max(), r_de.max())
 
 
+def test_newton_recompute_matches_fp64_recompute_h128():
+    """The compensated Newton-Schulz recompute yields the inverse of the FP32
+    Slater block to FP32 rounding, as FP64 Gauss-Jordan does: the same chains
+    (the recompute falls on the measured eighth sweep, so the positions agree),
+    the samples taken with either inverse agree far below the mixed form's
+    error against the oracle."""
+    W = 16
+    wl = synth.workload("h128", walkers=W, sweeps=8, warmup=0)
+    out = {}
+    for mode in (q.QMC_RECOMPUTE_FP64, q.QMC_RECOMPUTE_NEWTON):
+        cfg = q.Config.from_workload(wl, precision=q.QMC_MIXED, warmup=0, measure_every=8, recompute_every=8)
+        s = q.QMCSystem(cfg, wl.R)
+        s.set_recompute(mode)
+        s.energy_forces(wl.R)
+        out[mode] = (s.walkers(), s.accumulators())
+        s.close()
+    (Xa, a), (Xb, b) = out[q.QMC_RECOMPUTE_FP64], out[q.QMC_RECOMPUTE_NEWTON]
+    assert np.array_equal(Xa, Xb)
+    N3 = 3 * wl.N
+    de_el = np.abs(a[:, 1] - b[:, 1]).max() / np.abs(a[:, 1]).max()
+    r_dl = _rel_vec(b[:, 3:3 + N3].reshape(W, wl.N, 3), a[:, 3:3 + N3].reshape(W, wl.N, 3))
+    r_de = _rel_vec(b[:, 3 + 2 * N3:].reshape(W, wl.N, 3), a[:, 3 + 2 * N3:].reshape(W, wl.N, 3))
+    print(f"newton vs fp64 recompute: E_L norm-wise {de_el:.2e}, d ln psi/dR {r_dl.max():.2e}, "
+          f"dE_L/dR {r_de.max():.2e}")
+    assert de_el <= 2e-6
+    assert r_dl.max() <= 5e-6 and r_de.max() <= 5e-6
+
+
 def test_headline_sampler_statistically_matches_fp64_form():
-    """The bench's mixed configuration (tensor cores, FP64 recompute every 8
+    """The bench's mixed configuration (tensor cores, inverse recompute every 8
     sweeps) against the FP64 GPU form -- which reproduces the oracle's chains
     exactly -- on the same Philox key: 1024 walkers x 100 sweeps, a sample
     every sweep, after 30 warm-up sweeps.  E within 3 sigma.  Forces: 384
