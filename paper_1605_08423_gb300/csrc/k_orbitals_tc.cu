@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
     float* ptr_s = (float*)(sB + (size_t)kBbuf * P * NM * 128);  // [N][6] proton trig
     __shared__ float rtrig[kRows][6];
     __shared__ float zs[16];   // zeta_g and zeta_g log2(e), g < 8
-    __shared__ uint64_t mbarh[2], fullh[2], bbar;
+    __shared__ uint64_t mbarh[2], fullh[2], bbar, freeh0, foldab[2];
     __shared__ uint32_t tbase;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nt = blockDim.x;
     const int row0 = blockIdx.x * kRows;
@@ -123,6 +123,8 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
         tc::mbar_init(&mbarh[0], 1); tc::mbar_init(&mbarh[1], 1);
         tc::mbar_init(&fullh[0], 16); tc::mbar_init(&fullh[1], 16);   // one arrival per producer warp
         tc::mbar_init(&bbar, 1);                                         // B chunk bulk copies (value kernel)
+        tc::mbar_init(&freeh0, 1);                                       // derivative kernel: half 0 read
+        tc::mbar_init(&foldab[0], 16); tc::mbar_init(&foldab[1], 16);   // derivative kernel: folds done
         tc::fence_mbar_init();
     }
     for (int idx = tid; idx < kRows * 3; idx += nt) {
@@ -150,15 +152,25 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
     bool ok = true;
 
     if constexpr (Q == 4 && P == 2) {
-    // Derivative kernel (Q = 4): a chunk of 32 basis functions is produced in
-    // two halves (basis 0-15 and 16-31 = k-steps 0-1 and 2-3, disjoint 64-byte
-    // column ranges of every A row).  Warps 0-15 produce and arrive on
-    // fullh[h]; warp 16 waits on it and issues the half's MMAs, which commit to
-    // mbarh[h] (one completion per chunk), so the tensor core works on one half
-    // while the producers fill the other.  Half h of chunk c is overwritten
-    // only after the MMAs of (c - 1, h) are done.  B is double-buffered: chunk
-    // c + 1 is fetched into registers a chunk ahead and stored once the MMAs of
-    // chunk c - 1, the buffer's last reader, are done.
+    // Derivative kernel (Q = 4).  A chunk of 32 basis functions is produced in
+    // two halves (basis 0-15 and 16-31 = k-steps 0-1 and 2-3, disjoint 16-byte
+    // pieces of every A row) by warps 0-15, which arrive on fullh[h]; warp 16
+    // issues the MMAs.  Each later chunk accumulates into the chunk block C,
+    // split by quantity group: C_a (d/dx, d/dy) and C_b (d/dz, Laplacian).  The
+    // MMAs of chunk c run in four steps
+    //   S1 half 0 into C_a, S2 half 0 into C_b (commit freeh0),
+    //   S3 half 1 into C_a (commit doneA = mbarh[0]), S4 half 1 into C_b (commit doneB = mbarh[1]).
+    // Producer order for chunk c >= 1: half 0 of c (once freeh0 of c - 1 says
+    // S1, S2 of c - 1 have read half 0), fold C_a of c - 1 into T (after doneA),
+    // fold C_b of c - 1 (after doneB), store the B chunk c + 1 into the buffer
+    // chunk c - 1 used, half 1 of c.  S1 of chunk c also waits for the fold of
+    // C_a of c - 1 (folda), S2 for that of C_b (foldb).  So the production of
+    // half 0 runs under S3, S4 of the previous chunk and the folds under S1 of
+    // this one: the tensor core does not wait for a fold.  Every barrier
+    // completes once per chunk (folds: once per chunk >= 1) and cannot complete
+    // again before its waiters have seen the previous completion (each
+    // completion needs work that follows that wait), so parity waits are
+    // unambiguous.
     constexpr int kProd = 512;                 // producer threads
     constexpr int kBv4 = 2;                    // P * NM * 8 <= 1024 vectors over 512 producers
     const int nbv4 = P * NM * 8;
@@ -180,131 +192,176 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
             if (idx < nbv4) dst[idx] = bnx[v];
         }
     };
+    // C of quantity group grp added into T (columns grp * 2 NM .. + 2 NM) by
+    // the 16 producer warps: warp % 4 picks the TMEM lane quarter, warp / 4 a
+    // 16-column group; all loads of a warp are issued before one wait, the
+    // stores before one wait.
+    auto fold_group = [&](int grp) {
+        const int quarter = warp & 3, cg = warp >> 2;
+        const uint32_t tl = tbase + ((uint32_t)(quarter * 32) << 16);
+        const int c_lo = grp * 2 * NM, c_hi = c_lo + 2 * NM;
+        for (int c0 = c_lo + cg * 16; c0 < c_hi; c0 += 64) {
+            float cv[16], tv[16];
+            tc::tmem_ld16(tl + kSub + (uint32_t)c0, cv);
+            tc::tmem_ld16(tl + (uint32_t)c0, tv);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) tv[j] += cv[j];
+            tc::tmem_st16(tl + (uint32_t)c0, tv);
+        }
+    };
+    // one item = (row, 4 consecutive basis functions of half h of chunk c);
+    // the displacement to a nucleus is computed once for its Gaussians.  Warp
+    // wp owns rows 8 wp .. 8 wp + 7 (one swizzle block); each quarter-warp (the
+    // 8 lanes of one phase of a 16-byte store) takes rows q and q + 4 of the
+    // block, whose swizzled 16-byte pieces of this half lie in opposite halves
+    // of the 128-byte row: the phase covers all 32 banks once.
+    auto produce = [&](int c, int h) {
+        const int wl = tid & 31;
+        const int r = 8 * (tid >> 5) + ((wl >> 3) & 3) + 4 * ((wl >> 2) & 1), k0 = 16 * h + 4 * (wl & 3);
+        float v[Q][4];
+        int a_prev = -1;
+        float t = 0.f, pp = 0.f, sq = 0.f, pv[3] = {0.f, 0.f, 0.f};
+        const int b0 = c * kKc + k0;
+        int a0, g0;
+        if (gshift >= 0) { a0 = b0 >> gshift; g0 = b0 & (G - 1); }
+        else { a0 = b0 / G; g0 = b0 - a0 * G; }
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const int b = b0 + kk;
+            int a = a0, g = g0 + kk;
+            while (g >= G) { g -= G; ++a; }
+#pragma unroll
+            for (int q = 0; q < Q; ++q) v[q][kk] = 0.f;
+            if (b >= B || row0 + r >= nrows) continue;
+            if (a != a_prev) {
+                a_prev = a;
+                const float* pt = ptr_s + 6 * a;
+                t = 0.f; pp = 0.f; sq = 0.f;
+#pragma unroll
+                for (int mu = 0; mu < 3; ++mu) {
+                    const float sx = rtrig[r][mu], cx = rtrig[r][3 + mu];
+                    const float sd = sx * pt[3 + mu] - cx * pt[mu];
+                    const float cd = cx * pt[3 + mu] + sx * pt[mu];
+                    t += sd * sd;
+                    pv[mu] = ell * sd * cd;
+                    pp += pv[mu] * pv[mu];
+                    sq += cd * cd - sd * sd;
+                }
+                t *= ell * ell;
+            }
+            const float z = zs[g];
+            const float e = tc_ex2(-zs[8 + g] * t);
+            const float f1 = -z * e, f2 = z * z * e;
+#pragma unroll
+            for (int mu = 0; mu < 3; ++mu) v[mu][kk] = 2.f * f1 * pv[mu];
+            v[Q - 1][kk] = 4.f * f2 * pp + 2.f * f1 * sq;
+        }
+        const uint32_t off = tc::sw128_off(r, k0);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            unsigned char* tq = sA + (size_t)(P * q) * kTileA + off;
+            float4 x0, x1;
+            tc::split_tf32_fast(v[q][0], x0.x, x1.x);
+            tc::split_tf32_fast(v[q][1], x0.y, x1.y);
+            tc::split_tf32_fast(v[q][2], x0.z, x1.z);
+            tc::split_tf32_fast(v[q][3], x0.w, x1.w);
+            *(float4*)(tq) = x0;
+            *(float4*)(tq + kTileA) = x1;
+        }
+        // this warp's share of half h is in shared memory
+        tc::fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&fullh[h]);
+    };
+    // a fold is complete in this warp: make its TMEM stores visible to the MMAs
+    auto arrive_fold = [&](uint64_t* bar) {
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(bar);
+    };
     if (tid < kProd) {
         fetch_b4(0);
         store_b4(0);
         if (nch > 1) fetch_b4(1);
     }
     const bool issuer = warp == kProd / 32;
-    for (int c = 0; c < nch; ++c) {
-        for (int h = 0; h < 2; ++h) {
-            if (issuer) {
-                if (lane == 0) {
-                    if (!tc::mbar_wait(&fullh[h], (uint32_t)(c & 1), 1ll << 26)) ok = false;
-                    tc::fence_after_sync();
-                    const uint32_t b0 = tc::smem_addr(sB + (size_t)(c & 1) * bbytes), bstep = (uint32_t)NM * 128;
+    if (issuer) {
+        if (lane == 0) {
+            // MMAs of half h of chunk c for quantities q0, q0 + 1: chunk 0 into
+            // the running total, later chunks into the chunk block
+            auto issue = [&](int c, int h, int q0) {
+                const uint32_t b0 = tc::smem_addr(sB + (size_t)(c & 1) * bbytes), bstep = (uint32_t)NM * 128;
 #pragma unroll
-                    for (int q = 0; q < Q; ++q) {
-                        const uint32_t a0 = tc::smem_addr(sA + (size_t)(P * q) * kTileA);
-                        // chunk 0 into the running total, later chunks into the chunk block
-                        const uint32_t d = tmem + (c > 0 ? kSub : 0u) + (uint32_t)(q * NM);
+                for (int q = q0; q < q0 + 2; ++q) {
+                    const uint32_t a0 = tc::smem_addr(sA + (size_t)(P * q) * kTileA);
+                    const uint32_t d = tmem + (c > 0 ? kSub : 0u) + (uint32_t)(q * NM);
 #pragma unroll
-                        for (int kh = 0; kh < 2; ++kh) {
-                            const int ks = 2 * h + kh;
-                            const uint32_t o = 32u * ks;
-                            // products A_i B_j with i + j <= P - 1, smallest first
-                            constexpr int np = P == 3 ? 6 : 3;
-                            const int pi[6] = {2, 1, 0, 1, 0, 0}, pj[6] = {0, 1, 2, 0, 1, 0};
+                    for (int kh = 0; kh < 2; ++kh) {
+                        const int ks = 2 * h + kh;
+                        const uint32_t o = 32u * ks;
+                        // products A_i B_j with i + j <= 1, smallest first
+                        const int pi[3] = {1, 0, 0}, pj[3] = {0, 1, 0};
 #pragma unroll
-                            for (int m = 6 - np; m < 6; ++m)
-                                tc::mma_tf32(d, tc::desc_sw128(a0 + pi[m] * kTileA + o),
-                                             tc::desc_sw128(b0 + pj[m] * bstep + o), idesc,
-                                             (ks > 0 || m > 6 - np) ? 1u : 0u);
-                        }
+                        for (int m = 0; m < 3; ++m)
+                            tc::mma_tf32(d, tc::desc_sw128(a0 + pi[m] * kTileA + o),
+                                         tc::desc_sw128(b0 + pj[m] * bstep + o), idesc, (ks > 0 || m > 0) ? 1u : 0u);
                     }
-                    tc::mma_commit(&mbarh[h]);
                 }
-                __syncwarp();
-                continue;
+            };
+            for (int c = 0; c < nch; ++c) {
+                const uint32_t par = (uint32_t)(c & 1);
+                // S1: half 0 of (d/dx, d/dy), once the half is produced and C_a folded
+                if (!tc::mbar_wait(&fullh[0], par, 1ll << 26)) ok = false;
+                if (c >= 2 && !tc::mbar_wait(&foldab[0], par, 1ll << 26)) ok = false;
+                tc::fence_after_sync();
+                issue(c, 0, 0);
+                // S2: half 0 of (d/dz, Laplacian), once C_b is folded; half 0 is then read
+                if (c >= 2 && !tc::mbar_wait(&foldab[1], par, 1ll << 26)) ok = false;
+                tc::fence_after_sync();
+                issue(c, 0, 2);
+                tc::mma_commit(&freeh0);
+                // S3: half 1 of (d/dx, d/dy); C_a of this chunk complete
+                if (!tc::mbar_wait(&fullh[1], par, 1ll << 26)) ok = false;
+                tc::fence_after_sync();
+                issue(c, 1, 0);
+                tc::mma_commit(&mbarh[0]);
+                // S4: half 1 of (d/dz, Laplacian); the chunk is read, C_b complete
+                issue(c, 1, 2);
+                tc::mma_commit(&mbarh[1]);
             }
-            if (c > 0) {
-                if (!tc::mbar_wait(&mbarh[h], (uint32_t)((c - 1) & 1), 1ll << 26)) ok = false;
+        }
+        __syncwarp();
+    } else {
+        for (int c = 0; c < nch; ++c) {
+            const uint32_t pp_ = (uint32_t)((c - 1) & 1);
+            if (c >= 1) {
+                if (!tc::mbar_wait(&freeh0, pp_, 1ll << 26)) ok = false;     // S2 of c - 1 done
                 tc::fence_after_sync();
             }
-            if (h == 1 && c + 1 < nch) {
+            produce(c, 0);
+            if (c >= 1) {
+                if (!tc::mbar_wait(&mbarh[0], pp_, 1ll << 26)) ok = false;   // S3 of c - 1 done
+                tc::fence_after_sync();
+                if (c >= 2) { fold_group(0); arrive_fold(&foldab[0]); }
+                if (!tc::mbar_wait(&mbarh[1], pp_, 1ll << 26)) ok = false;   // S4 of c - 1 done
+                tc::fence_after_sync();
+                if (c >= 2) { fold_group(1); arrive_fold(&foldab[1]); }
+            }
+            // the B buffer of chunk c + 1 was last read by chunk c - 1, done
+            if (c + 1 < nch) {
                 store_b4((c + 1) & 1);
                 if (c + 2 < nch) fetch_b4(c + 2);
             }
-            // one item = (row, 4 consecutive basis functions of the half); the
-            // displacement to a nucleus is computed once for its Gaussians.
-            // Warp wp owns rows 8 wp .. 8 wp + 7 (one swizzle block); each
-            // quarter-warp (the 8 lanes of one phase of a 16-byte store) takes
-            // rows q and q + 4 of the block, whose swizzled 16-byte chunks of
-            // this half lie in opposite halves of the 128-byte row: the phase
-            // covers all 32 banks once (no bank conflict).
-            const int wl = tid & 31;
-            const int r = 8 * (tid >> 5) + ((wl >> 3) & 3) + 4 * ((wl >> 2) & 1), k0 = 16 * h + 4 * (wl & 3);
-            float v[Q][4];
-            int a_prev = -1;
-            float t = 0.f, pp = 0.f, sq = 0.f, pv[3] = {0.f, 0.f, 0.f};
-            const int b0 = c * kKc + k0;
-            int a0, g0;
-            if (gshift >= 0) { a0 = b0 >> gshift; g0 = b0 & (G - 1); }
-            else { a0 = b0 / G; g0 = b0 - a0 * G; }
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const int b = b0 + kk;
-                int a = a0, g = g0 + kk;
-                while (g >= G) { g -= G; ++a; }
-#pragma unroll
-                for (int q = 0; q < Q; ++q) v[q][kk] = 0.f;
-                if (b >= B || row0 + r >= nrows) continue;
-                if (a != a_prev) {
-                    a_prev = a;
-                    const float* pt = ptr_s + 6 * a;
-                    t = 0.f; pp = 0.f; sq = 0.f;
-#pragma unroll
-                    for (int mu = 0; mu < 3; ++mu) {
-                        const float sx = rtrig[r][mu], cx = rtrig[r][3 + mu];
-                        const float sd = sx * pt[3 + mu] - cx * pt[mu];
-                        const float cd = cx * pt[3 + mu] + sx * pt[mu];
-                        t += sd * sd;
-                        pv[mu] = ell * sd * cd;
-                        pp += pv[mu] * pv[mu];
-                        sq += cd * cd - sd * sd;
-                    }
-                    t *= ell * ell;
-                }
-                const float z = zs[g];
-                const float e = tc_ex2(-zs[8 + g] * t);
-                const float f1 = -z * e, f2 = z * z * e;
-#pragma unroll
-                for (int mu = 0; mu < 3; ++mu) v[mu][kk] = 2.f * f1 * pv[mu];
-                v[Q - 1][kk] = 4.f * f2 * pp + 2.f * f1 * sq;
-            }
-            const uint32_t off = tc::sw128_off(r, k0);
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                unsigned char* tq = sA + (size_t)(P * q) * kTileA + off;
-                float4 x0, x1;
-                tc::split_tf32_fast(v[q][0], x0.x, x1.x);
-                tc::split_tf32_fast(v[q][1], x0.y, x1.y);
-                tc::split_tf32_fast(v[q][2], x0.z, x1.z);
-                tc::split_tf32_fast(v[q][3], x0.w, x1.w);
-                *(float4*)(tq) = x0;
-                *(float4*)(tq + kTileA) = x1;
-            }
-            // chunk c - 1 (c >= 2; chunk 0 went straight into T) is folded into
-            // T once all its MMAs are done and before the first MMA of chunk c,
-            // which resets the chunk block: the fold precedes this warp's
-            // arrival for half 0
-            if (h == 0 && c >= 2) {
-                if (!tc::mbar_wait(&mbarh[1], (uint32_t)((c - 1) & 1), 1ll << 26)) ok = false;
-                tc::fence_after_sync();
-                fold_chunk(kProd / 32);
-                tc::fence_before_sync();
-            }
-            // this warp's share of half h is in shared memory
-            tc::fence_proxy_async();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&fullh[h]);
+            produce(c, 1);
         }
-    }
-    // all MMAs done (they complete in order) before TMEM and sA are read
-    if (!tc::mbar_wait(&mbarh[1], (uint32_t)((nch - 1) & 1), 1ll << 26)) ok = false;
-    tc::fence_after_sync();
-    if (nch >= 2 && tid < kProd) {
-        fold_chunk(kProd / 32);
+        // the last chunk's blocks (chunk 0 went straight into T)
+        const uint32_t pl = (uint32_t)((nch - 1) & 1);
+        if (!tc::mbar_wait(&mbarh[0], pl, 1ll << 26)) ok = false;
+        tc::fence_after_sync();
+        if (nch >= 2) fold_group(0);
+        if (!tc::mbar_wait(&mbarh[1], pl, 1ll << 26)) ok = false;
+        tc::fence_after_sync();
+        if (nch >= 2) fold_group(1);
         tc::fence_before_sync();
     }
     __syncthreads();
