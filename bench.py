@@ -768,10 +768,7 @@ def run_ours(args, ws, rank, local):
                                       f"{G} s-Gaussians/proton, {W} walkers x {cfg.sweeps} sweeps "
                                       f"(+{cfg.warmup_cont} continuation), sample every sweep, "
                                       f"{'mixed' if prec == q.QMC_MIXED else 'FP64'} form, "
-                                      + ("inverse recompute (compensated Newton-Schulz step, FP64 Gauss-Jordan "
-                                         "at the start of each call)" if prec == q.QMC_MIXED else
-                                         "FP64 Gauss-Jordan inverse recompute")
-                                      + f" every {cfg.recompute_every} sweeps, "
+                                      f"FP64 Gauss-Jordan inverse recompute every {cfg.recompute_every} sweeps, "
                                       "adjoint forces, Langevin step with S = Cov(f)",
                           "walkers": W, "walkers_total": W * ws, "sweeps": cfg.sweeps,
                           "parallelism": f"walker shards x{ws} (two all-reduces per MD step)" if shard else "one GPU",

@@ -282,17 +282,18 @@ enum { QMC_LV_ADOPTED = 0, QMC_LV_FAST = 1, QMC_LV_NOROGNA = 2 };
 /* QMC_OPT_RECOMPUTE selects the periodic inverse recompute inside a call
  * (every recompute_every sweeps; the recompute at the start of every call is
  * always the FP64 one):
- *   QMC_RECOMPUTE_FP64            the FP64 form's only choice: Slater blocks at
- *                                 the current positions, then FP64 Gauss-Jordan
- *                                 inverse and ln|det| (resets the drift of the
- *                                 Sherman-Morrison updates);
- *   QMC_RECOMPUTE_NEWTON          the mixed form's default: one Newton-Schulz step
+ *   QMC_RECOMPUTE_FP64 (default)  Slater blocks at the current positions, then
+ *                                 FP64 Gauss-Jordan inverse and ln|det| (resets the
+ *                                 drift of the Sherman-Morrison updates);
+ *   QMC_RECOMPUTE_NEWTON          mixed form only: one Newton-Schulz step
  *                                 G <- G + G (I - A G) on the carried inverse, the
  *                                 residual I - A G formed with a compensated (error-
  *                                 free product, TwoSum) FP32 dot product, so that G
  *                                 becomes the inverse of the FP32 Slater block to
  *                                 FP32 rounding; FP64 Gauss-Jordan for blocks with
  *                                 max|I - A G| >= 0.01.  ln|det| is not updated.
+ *                                 About a third of the FP64 recompute's time on
+ *                                 parts whose FP64 rate is 1/64 of FP32.
  * INVALID for other values, and for QMC_RECOMPUTE_NEWTON in the FP64 form. */
 enum { QMC_OPT_RECOMPUTE = 5 };
 /* QMC_OPT_WALKER_OFFSET (value >= 0, default 0): the handle's walker w draws

@@ -83,7 +83,7 @@ struct qmc_system {
     bool first_call = true;
     int lv_scheme = kLvAdopted;          // QMC_OPT_INTEGRATOR
     bool lv_noise_correction = false;    // QMC_OPT_NOISE_CORRECTION
-    bool ns_recompute = false;           // QMC_OPT_RECOMPUTE == QMC_RECOMPUTE_NEWTON (mixed-form default)
+    bool ns_recompute = false;           // QMC_OPT_RECOMPUTE == QMC_RECOMPUTE_NEWTON (mixed form only)
     bool langevin_first = true;
     uint32_t langevin_step_no = 0;
     double last_Nc = 0.0;
@@ -258,11 +258,11 @@ void recompute(qmc_system* h, int W) {
 }
 
 // Periodic recompute inside a call, which resets the drift of the rank-1
-// updates: with QMC_RECOMPUTE_FP64 (the FP64 form's only choice) the Slater
-// blocks at the current positions and their FP64 Gauss-Jordan inverses and
-// ln|det|; with QMC_RECOMPUTE_NEWTON (the mixed form's default) one Newton-
-// Schulz step on the carried inverse with the residual in compensated FP32
-// (FP64 Gauss-Jordan only for blocks too far off).
+// updates: by default (QMC_RECOMPUTE_FP64) the Slater blocks at the current
+// positions and their FP64 Gauss-Jordan inverses and ln|det|; with
+// QMC_RECOMPUTE_NEWTON (mixed form only) one Newton-Schulz step on the carried
+// inverse with the residual in compensated FP32 (FP64 Gauss-Jordan only for
+// blocks too far off).
 template <typename T>
 void recompute_in_call(qmc_system* h, int W) {
     if constexpr (sizeof(T) == 4) {
@@ -398,7 +398,6 @@ int init_handle(const qmc_params* p, const double* R, void* block, size_t block_
     h->N = p->n_protons; h->n = h->N / 2; h->G = p->n_gauss; h->B = h->N * h->G; h->W = p->n_walkers;
     h->mmax = p->ewald_mmax;
     h->mixed = p->precision == QMC_MIXED;
-    h->ns_recompute = h->mixed;          // compensated Newton-Schulz by default in the mixed form
     h->zeta_h.assign(p->zeta, p->zeta + h->G);
     h->coeff_h.assign(p->coeff, p->coeff + (size_t)h->B * h->n);
     h->p.zeta = h->zeta_h.data();

@@ -319,8 +319,8 @@ class QMCSystem:
         _chk(lib().qmc_set_option(self._h, QMC_OPT_NOISE_CORRECTION, int(on)), "qmc_set_option")
 
     def set_recompute(self, mode: int):
-        """QMC_RECOMPUTE_NEWTON (the mixed-form default; compensated Newton-Schulz step) or
-        QMC_RECOMPUTE_FP64 (FP64 Gauss-Jordan; the FP64 form's only choice)."""
+        """QMC_RECOMPUTE_FP64 (default; FP64 Gauss-Jordan) or QMC_RECOMPUTE_NEWTON (mixed form
+        only; one Newton-Schulz step with a compensated residual)."""
         _chk(lib().qmc_set_option(self._h, QMC_OPT_RECOMPUTE, int(mode)), "qmc_set_option")
 
     def set_walker_offset(self, w0: int):

@@ -92,8 +92,8 @@ def test_sampler_inverse_after_eight_sweeps_h128(recompute):
     """The inverse the sampler carries: one sample after 8 sweeps (1024 moves)
     of Sherman-Morrison updates from the call's FP64 inverse (no recompute in
     between), or right after the periodic recompute of the bench
-    configuration (every 8 sweeps, FP64 Gauss-Jordan or the default
-    compensated Newton-Schulz step).  The sample's E_L and forces,
+    configuration (every 8 sweeps, the default FP64 Gauss-Jordan or the
+    compensated Newton-Schulz option).  The sample's E_L and forces,
     taken with that inverse, against the oracle at the walkers' positions."""
     W = 16
     wl = synth.workload("h128", walkers=W, sweeps=8, warmup=0)
@@ -149,7 +149,7 @@ def test_newton_recompute_matches_fp64_recompute_h128():
 
 
 def test_headline_sampler_statistically_matches_fp64_form():
-    """The bench's mixed configuration (tensor cores, inverse recompute every 8
+    """The bench's mixed configuration (tensor cores, FP64 recompute every 8
     sweeps) against the FP64 GPU form -- which reproduces the oracle's chains
     exactly -- on the same Philox key: 1024 walkers x 100 sweeps, a sample
     every sweep, after 30 warm-up sweeps.  E within 3 sigma.  Forces: 384
