@@ -219,42 +219,71 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
         const int wl = tid & 31;
         const int r = 8 * (tid >> 5) + ((wl >> 3) & 3) + 4 * ((wl >> 2) & 1), k0 = 16 * h + 4 * (wl & 3);
         float v[Q][4];
-        int a_prev = -1;
-        float t = 0.f, pp = 0.f, sq = 0.f, pv[3] = {0.f, 0.f, 0.f};
-        const int b0 = c * kKc + k0;
-        int a0, g0;
-        if (gshift >= 0) { a0 = b0 >> gshift; g0 = b0 & (G - 1); }
-        else { a0 = b0 / G; g0 = b0 - a0 * G; }
+        if (G == 4) {
+            // 4 Gaussians per nucleus: the item is the 4 Gaussians of nucleus
+            // (c * 32 + k0) / 4, one geometry and four exponentials
+            const int a = (c * kKc + k0) >> 2;
+            const bool on = a < N && row0 + r < nrows;
+            const float* pt = ptr_s + 6 * (on ? a : 0);
+            float t = 0.f, pp = 0.f, sq = 0.f, pv[3];
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            const int b = b0 + kk;
-            int a = a0, g = g0 + kk;
-            while (g >= G) { g -= G; ++a; }
-#pragma unroll
-            for (int q = 0; q < Q; ++q) v[q][kk] = 0.f;
-            if (b >= B || row0 + r >= nrows) continue;
-            if (a != a_prev) {
-                a_prev = a;
-                const float* pt = ptr_s + 6 * a;
-                t = 0.f; pp = 0.f; sq = 0.f;
-#pragma unroll
-                for (int mu = 0; mu < 3; ++mu) {
-                    const float sx = rtrig[r][mu], cx = rtrig[r][3 + mu];
-                    const float sd = sx * pt[3 + mu] - cx * pt[mu];
-                    const float cd = cx * pt[3 + mu] + sx * pt[mu];
-                    t += sd * sd;
-                    pv[mu] = ell * sd * cd;
-                    pp += pv[mu] * pv[mu];
-                    sq += cd * cd - sd * sd;
-                }
-                t *= ell * ell;
+            for (int mu = 0; mu < 3; ++mu) {
+                const float sx = rtrig[r][mu], cx = rtrig[r][3 + mu];
+                const float sd = sx * pt[3 + mu] - cx * pt[mu];
+                const float cd = cx * pt[3 + mu] + sx * pt[mu];
+                t += sd * sd;
+                pv[mu] = ell * sd * cd;
+                pp += pv[mu] * pv[mu];
+                sq += cd * cd - sd * sd;
             }
-            const float z = zs[g];
-            const float e = tc_ex2(-zs[8 + g] * t);
-            const float f1 = -z * e, f2 = z * z * e;
+            t *= ell * ell;
 #pragma unroll
-            for (int mu = 0; mu < 3; ++mu) v[mu][kk] = 2.f * f1 * pv[mu];
-            v[Q - 1][kk] = 4.f * f2 * pp + 2.f * f1 * sq;
+            for (int kk = 0; kk < 4; ++kk) {
+                const float z = zs[kk];
+                const float e = tc_ex2(-zs[8 + kk] * t);
+                const float f1 = -z * e, f2 = z * z * e;
+#pragma unroll
+                for (int mu = 0; mu < 3; ++mu) v[mu][kk] = on ? 2.f * f1 * pv[mu] : 0.f;
+                v[Q - 1][kk] = on ? 4.f * f2 * pp + 2.f * f1 * sq : 0.f;
+            }
+        } else {
+            int a_prev = -1;
+            float t = 0.f, pp = 0.f, sq = 0.f, pv[3] = {0.f, 0.f, 0.f};
+            const int b0 = c * kKc + k0;
+            int a0, g0;
+            if (gshift >= 0) { a0 = b0 >> gshift; g0 = b0 & (G - 1); }
+            else { a0 = b0 / G; g0 = b0 - a0 * G; }
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const int b = b0 + kk;
+                int a = a0, g = g0 + kk;
+                while (g >= G) { g -= G; ++a; }
+#pragma unroll
+                for (int q = 0; q < Q; ++q) v[q][kk] = 0.f;
+                if (b >= B || row0 + r >= nrows) continue;
+                if (a != a_prev) {
+                    a_prev = a;
+                    const float* pt = ptr_s + 6 * a;
+                    t = 0.f; pp = 0.f; sq = 0.f;
+#pragma unroll
+                    for (int mu = 0; mu < 3; ++mu) {
+                        const float sx = rtrig[r][mu], cx = rtrig[r][3 + mu];
+                        const float sd = sx * pt[3 + mu] - cx * pt[mu];
+                        const float cd = cx * pt[3 + mu] + sx * pt[mu];
+                        t += sd * sd;
+                        pv[mu] = ell * sd * cd;
+                        pp += pv[mu] * pv[mu];
+                        sq += cd * cd - sd * sd;
+                    }
+                    t *= ell * ell;
+                }
+                const float z = zs[g];
+                const float e = tc_ex2(-zs[8 + g] * t);
+                const float f1 = -z * e, f2 = z * z * e;
+#pragma unroll
+                for (int mu = 0; mu < 3; ++mu) v[mu][kk] = 2.f * f1 * pv[mu];
+                v[Q - 1][kk] = 4.f * f2 * pp + 2.f * f1 * sq;
+            }
         }
         const uint32_t off = tc::sw128_off(r, k0);
 #pragma unroll
@@ -445,8 +474,38 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
                 }
             }
         };
+        // Value kernel with 4 Gaussians per nucleus (256 threads): the items of
+        // a thread are rows tid / 8 + 32 u of the one nucleus c * 8 + tid % 8,
+        // so its trig values are loaded once per chunk and the exponent needs
+        // only the squared periodised distance.
+        const bool fast4 = Q == 1 && G == 4 && nt == 256;
+        if (fast4) {
+            const int a = c * (kKc / 4) + (tid & 7);
+            const bool a_ok = a < N;
+            float ps[3], pc[3];
 #pragma unroll
-        for (int u = 0; u < IT; ++u) {
+            for (int mu = 0; mu < 3; ++mu) {
+                ps[mu] = a_ok ? ptr_s[6 * a + mu] : 0.f;
+                pc[mu] = a_ok ? ptr_s[6 * a + 3 + mu] : 1.f;
+            }
+            const float ell2 = ell * ell;
+#pragma unroll
+            for (int u = 0; u < IT; ++u) {
+                const int r = (tid >> 3) + 32 * u;
+                float t = 0.f;
+#pragma unroll
+                for (int mu = 0; mu < 3; ++mu) {
+                    const float sd = rtrig[r][mu] * pc[mu] - rtrig[r][3 + mu] * ps[mu];
+                    t += sd * sd;
+                }
+                t *= ell2;
+                const bool on = a_ok && row0 + r < nrows;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) vv[u][0][kk] = on ? tc_ex2(-zs[8 + kk] * t) : 0.f;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < (fast4 ? 0 : IT); ++u) {
             const int item = tid + u * nt;
             const int r = item / (kKc / 4), k0 = 4 * (item - r * (kKc / 4));
             int a_prev = -1;
@@ -523,9 +582,12 @@ __global__ void __launch_bounds__(Q == 1 ? 256 : 544, Q == 1 ? 4 : 1)
             tc::mma_commit(&mbarh[0]);
         }
         // the other lanes of the issuing warp wait here, not in the mbarrier
-        // poll below, so they do not hold up the single issuing lane
+        // poll below, so they do not hold up the single issuing lane; one warp
+        // polls for the MMAs, the others wait at the block barrier and take no
+        // issue slots from the other CTAs on the SM meanwhile
         __syncwarp();
-        if (!tc::mbar_wait(&mbarh[0], (uint32_t)(c & 1), 1ll << 26)) ok = false;
+        if (warp == 0 && !tc::mbar_wait(&mbarh[0], (uint32_t)(c & 1), 1ll << 26)) ok = false;
+        __syncthreads();
         tc::fence_after_sync();
         if (c > 0) {                             // chunk c into the running total
             fold_chunk(nt / 32);
