@@ -250,11 +250,16 @@ __global__ void __launch_bounds__(512) sweep_kernel(SysView<T> s, double* __rest
 // Thread tw (0..63) of a walker owns row tw of the staged inverse (G^T row,
 // zero-padded to 64 columns), so a move touches no shared-memory copy of G:
 //   w_l = sum_j phi'_j G^T[l][j] for every row (the ratio is w_il),
-//   on acceptance the owner of row il puts it in shared memory and every
-//   thread applies G^T[l] -= (w_l - delta_{l,il}) / R * G^T[il].
+//   on acceptance every thread applies G^T[l] -= (w_l - delta_{l,il}) / R * G^T[il].
 // The Jastrow difference is split over the 64 threads (two e-e and two e-n
 // partners each).  The two warps of a walker meet at a named barrier (one
-// per walker of the CTA).  Same proposals, uniforms and acceptance rule as
+// per walker of the CTA), once per move: before it every thread has put its
+// share of the Jastrow difference, the owner of row il its row and w_il, and
+// every thread its element of the next move's orbital row into shared
+// buffers that alternate between moves; after it the acceptance decision and
+// the update need nothing else.  Electron i's (sin, cos) after an accepted
+// move are written by the thread that has i among its partners (tw = i mod
+// 64), the only thread that reads them later in the sweep.  Same proposals, uniforms and acceptance rule as
 // sweep_kernel; the mixed form keeps accepted proposals unwrapped.
 // With the e-e-n-n Jastrow term (s.fjt set) the CTA stages f (FP32, N x N) in
 // shared memory and each walker keeps c_a = sum_j chi_a(r_j); a move of
@@ -269,11 +274,12 @@ constexpr int kSwRow = 64;      // register row length (n <= 64)
 // hit 32 distinct banks (a stride of 6 pairs them up).
 constexpr int kTS = 7;
 
-// Shared-memory floats per walker of sweep_reg_kernel: phi [64], row [64],
-// red [8], trig [kTS N], and with the e-e-n-n term c [N] and chi(r_i) [N];
-// rounded up to whole 16-byte vectors (phi and the row are read as float4).
+// Shared-memory floats per walker of sweep_reg_kernel: phi [2][64], row
+// [2][64], red [2][4], trig [kTS N], and with the e-e-n-n term c [N] and
+// chi(r_i) [N]; rounded up to whole 16-byte vectors (phi and the row are read
+// as float4).
 __host__ __device__ inline size_t sweep_reg_walker_floats(int N, bool j34) {
-    return (2 * kSwRow + 8 + kTS * (size_t)N + (j34 ? 2 * (size_t)N : 0) + 3) & ~size_t(3);
+    return (4 * kSwRow + 8 + kTS * (size_t)N + (j34 ? 2 * (size_t)N : 0) + 3) & ~size_t(3);
 }
 
 __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<float> s, double* __restrict__ X,
@@ -291,9 +297,9 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
     float* ptr_s = (float*)smraw;                                       // [N][kTS] proton trig
     float* f_s = ptr_s + ((kTS * N + 3) & ~3);                            // [N][N] e-e-n-n coefficients (j34)
     float* mine = f_s + (j34 ? (size_t)N * N : 0) + (size_t)p * sweep_reg_walker_floats(N, j34);
-    float* phi = mine;                  // [64] orbital row at the proposal (zero beyond n)
-    float* rowb = phi + kSwRow;         // [64] row il of G^T on acceptance
-    float* red = rowb + kSwRow;         // [8] du halves, ratio
+    float* phi = mine;                  // [2][64] orbital row at the proposal (zero beyond n)
+    float* rowb = phi + 2 * kSwRow;     // [2][64] row il of G^T
+    float* red = rowb + 2 * kSwRow;     // [2][4] du halves, ratio
     float* et = red + 8;                // [N][kTS] (sin, cos)(pi x / L) of the current positions
     float* c34 = et + kTS * N;            // [N] sum_j chi_a(r_j) (j34)
     float* cho = c34 + N;               // [N] chi_a at the moving electron (j34)
@@ -324,15 +330,14 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
             c34[a] = c;
         }
     }
-    float pt_nx[6], ph_nx, u_nx;
-    auto fetch = [&](int i) {
+    // proposal trig and uniform of a row; the orbital value phi_tw of a row
+    auto ld_pt = [&](int i, float* pt_, float& u_) {
         const size_t row = (size_t)w * N + i;
 #pragma unroll
-        for (int mu = 0; mu < 6; ++mu) pt_nx[mu] = ptp[row * 6 + mu];
-        ph_nx = tw < n ? Phi[row * n + tw] : 0.f;
-        u_nx = uacc[row];
+        for (int mu = 0; mu < 6; ++mu) pt_[mu] = ptp[row * 6 + mu];
+        u_ = uacc[row];
     };
-    fetch(0);
+    auto ld_ph = [&](int i) { return tw < n ? Phi[((size_t)w * N + i) * n + tw] : 0.f; };
     unsigned long long naccept = 0;
     const bool vec4 = (n & 3) == 0;
     for (int sp = 0; sp < 2; ++sp) {
@@ -354,18 +359,24 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
             }
             g[j] = v.x; g[j + 1] = v.y; g[j + 2] = v.z; g[j + 3] = v.w;
         }
+        const int i0 = sp * n;
+        phi[tw] = ld_ph(i0);                      // the spin's first move: buffer 0
+        float ph_nx = n > 1 ? ld_ph(i0 + 1) : 0.f;   // the next move's value, stored during this move
+        float pt_nx[6], u_nx;
+        ld_pt(i0, pt_nx, u_nx);
+        bar();   // buffer 0 and the positions visible; the previous spin's reads done
         for (int il = 0; il < n; ++il) {
-            const int i = sp * n + il;
+            const int i = i0 + il, buf = il & 1;
             const size_t row = (size_t)w * N + i;
             float pt[6];
 #pragma unroll
             for (int mu = 0; mu < 6; ++mu) pt[mu] = pt_nx[mu];
-            phi[tw] = ph_nx;
             const float u = u_nx;
-            if (i + 1 < N) fetch(i + 1);
-            bar();   // phi and the previous move's position updates are visible
+            const float ph_wr = ph_nx;
+            if (il + 1 < n) ld_pt(i + 1, pt_nx, u_nx);
+            if (il + 2 < n) ph_nx = ld_ph(i + 2);
             // w_l for this thread's row: four partial sums
-            const float4* phv = (const float4*)phi;
+            const float4* phv = (const float4*)(phi + buf * kSwRow);
             float a4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int jv = 0; jv < kSwRow / 4; ++jv) {
@@ -405,7 +416,7 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
                         cho[a] = cho_r[k];
                     }
                 }
-                bar();   // chi_b(r_i) of every nucleus visible
+                bar();   // chi_b(r_i) of every nucleus and the previous move's c_b visible
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     const int a = tw + 64 * k;
@@ -417,31 +428,34 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
                 }
             }
             du = warp_sum(du);
-            if (lane == 0) red[h] = du;
-            if (tw == il) red[2] = wl;
+            float* rd = red + 4 * buf;
+            float* rb = rowb + buf * kSwRow;
+            if (lane == 0) rd[h] = du;
+            if (tw == il) {
+                rd[2] = wl;
+#pragma unroll
+                for (int jv = 0; jv < kSwRow / 4; ++jv)
+                    ((float4*)rb)[jv] = make_float4(g[4 * jv], g[4 * jv + 1], g[4 * jv + 2], g[4 * jv + 3]);
+            }
+            if (il + 1 < n) phi[(buf ^ 1) * kSwRow + tw] = ph_wr;
             bar();
-            const float ratio = red[2];
-            const float dut = red[0] + red[1];
+            const float ratio = rd[2];
+            const float dut = rd[0] + rd[1];
             const float prob = ratio * ratio * expf(2.f * dut);
             if (u < prob) {
-                if (tw == il) {
-#pragma unroll
-                    for (int jv = 0; jv < kSwRow / 4; ++jv)
-                        ((float4*)rowb)[jv] = make_float4(g[4 * jv], g[4 * jv + 1], g[4 * jv + 2], g[4 * jv + 3]);
-                }
-                bar();
                 const float coef = (wl - (tw == il ? 1.f : 0.f)) * __fdividef(1.f, ratio);
-                const float4* rbv = (const float4*)rowb;
+                const float4* rbv = (const float4*)rb;
 #pragma unroll
                 for (int jv = 0; jv < kSwRow / 4; ++jv) {
-                    const float4 rb = rbv[jv];
-                    g[4 * jv] -= coef * rb.x; g[4 * jv + 1] -= coef * rb.y;
-                    g[4 * jv + 2] -= coef * rb.z; g[4 * jv + 3] -= coef * rb.w;
+                    const float4 r4 = rbv[jv];
+                    g[4 * jv] -= coef * r4.x; g[4 * jv + 1] -= coef * r4.y;
+                    g[4 * jv + 2] -= coef * r4.z; g[4 * jv + 3] -= coef * r4.w;
                 }
-                if (tw < 3) {   // keep the proposal as is (periodic functions; the next proposal pass wraps)
-                    Xw[3 * i + tw] = Xp[row * 3 + tw];
-                    et[kTS * i + tw] = tw == 0 ? pt[0] : (tw == 1 ? pt[1] : pt[2]);
-                    et[kTS * i + 3 + tw] = tw == 0 ? pt[3] : (tw == 1 ? pt[4] : pt[5]);
+                // keep the proposal as is (periodic functions; the next proposal pass wraps)
+                if (tw < 3) Xw[3 * i + tw] = Xp[row * 3 + tw];
+                if (tw == (i & 63)) {
+#pragma unroll
+                    for (int mu = 0; mu < 6; ++mu) et[kTS * i + mu] = pt[mu];
                 }
                 if (j34) {      // c_a of this thread's nuclei (read by others only after the next barrier)
 #pragma unroll
@@ -458,7 +472,6 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
             for (int j = 0; j < kSwRow; ++j)
                 if (j < n) G[(size_t)tw * n + j] = g[j];
         }
-        bar();
     }
     if (tw == 0) nacc[w] += naccept;
 }
