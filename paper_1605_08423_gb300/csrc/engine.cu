@@ -62,6 +62,7 @@ struct qmc_system {
     double* d_logdet = nullptr;
     double* d_acc = nullptr;
     double* d_vacc = nullptr;    // per-walker sums of V_L (virial pressure)
+    float* d_vep = nullptr;      // per-electron e-n Jastrow sums carried by the mixed sweep
     double* d_pout = nullptr;    // pressure output [5]
     unsigned long long* d_nacc = nullptr;
     // reductions and output
@@ -178,6 +179,7 @@ size_t footprint(const qmc_params* p) {
         b += tc_coeff_bytes((int)B, (int)n);
         b += tc_adjoint_coeff_bytes((int)n, (int)G) + 4 * (2 * W * n * n + 9 * W * N) + 8 * W;
         b += 4 * (3 * N * 2 * nk + W * 2 * nk + W * 3 * N);   // reciprocal-force GEMM operands
+        b += 4 * W * N;                                        // carried e-n Jastrow sums of the sweep
     }
     return b;
 }
@@ -333,7 +335,7 @@ double run_sampling(qmc_system* h) {
         prof_end(h, ep);
         prof_begin(h, KC_SWEEP, ep);
         launch_sweep<T>(s, h->d_X, h->d_Xp, (const T*)h->d_ptp, (const T*)h->d_uacc, (const T*)h->d_Phi,
-                        (T*)h->d_Gt, h->d_nacc, h->stream);
+                        (T*)h->d_Gt, h->d_nacc, h->d_vep, sw == 0, h->stream);
         prof_end(h, ep);
         if ((sw + 1) % h->p.recompute_every == 0) recompute_in_call<T>(h, W);
         if (sw >= nw && ((sw - nw + 1) % h->p.measure_every) == 0) measure<T>(h, W, nullptr, nullptr, nullptr, nullptr);
@@ -447,6 +449,7 @@ int init_handle(const qmc_params* p, const double* R, void* block, size_t block_
     h->d_logdet = dalloc<double>(h, 2 * (size_t)W, &rc);
     h->d_acc = dalloc<double>(h, (size_t)W * (3 + 9 * N), &rc);
     h->d_vacc = dalloc<double>(h, W, &rc);
+    if (h->mixed) h->d_vep = dalloc<float>(h, (size_t)W * N, &rc);
     h->d_pout = dalloc<double>(h, 5, &rc);
     h->d_nacc = dalloc<unsigned long long>(h, W, &rc);
     h->d_colsum = dalloc<double>(h, 4 + 9 * N, &rc);

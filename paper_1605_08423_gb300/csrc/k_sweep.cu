@@ -275,11 +275,11 @@ constexpr int kSwRow = 64;      // register row length (n <= 64)
 constexpr int kTS = 7;
 
 // Shared-memory floats per walker of sweep_reg_kernel: phi [2][64], row
-// [2][64], red [2][4], trig [kTS N], and with the e-e-n-n term c [N] and
-// chi(r_i) [N]; rounded up to whole 16-byte vectors (phi and the row are read
-// as float4).
+// [2][64], red [2][8], trig [kTS N], V [N], and with the e-e-n-n term c [N]
+// and chi(r_i) [N]; rounded up to whole 16-byte vectors (phi and the row are
+// read as float4).
 __host__ __device__ inline size_t sweep_reg_walker_floats(int N, bool j34) {
-    return (4 * kSwRow + 8 + kTS * (size_t)N + (j34 ? 2 * (size_t)N : 0) + 3) & ~size_t(3);
+    return (4 * kSwRow + 16 + (kTS + 1) * (size_t)N + (j34 ? 2 * (size_t)N : 0) + 3) & ~size_t(3);
 }
 
 __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<float> s, double* __restrict__ X,
@@ -288,7 +288,8 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
                                                                   const float* __restrict__ uacc,
                                                                   const float* __restrict__ Phi,
                                                                   float* __restrict__ Gt,
-                                                                  unsigned long long* __restrict__ nacc) {
+                                                                  unsigned long long* __restrict__ nacc,
+                                                                  float* __restrict__ Vep, int vep_init) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = s.N, n = s.n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -299,9 +300,10 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
     float* mine = f_s + (j34 ? (size_t)N * N : 0) + (size_t)p * sweep_reg_walker_floats(N, j34);
     float* phi = mine;                  // [2][64] orbital row at the proposal (zero beyond n)
     float* rowb = phi + 2 * kSwRow;     // [2][64] row il of G^T
-    float* red = rowb + 2 * kSwRow;     // [2][4] du halves, ratio
-    float* et = red + 8;                // [N][kTS] (sin, cos)(pi x / L) of the current positions
-    float* c34 = et + kTS * N;            // [N] sum_j chi_a(r_j) (j34)
+    float* red = rowb + 2 * kSwRow;     // [2][8] e-e du halves, ratio, new e-n sum halves
+    float* et = red + 16;               // [N][kTS] (sin, cos)(pi x / L) of the current positions
+    float* vj = et + kTS * N;           // [N] V_i = sum_a u_en(r_i, R_a) at the current positions
+    float* c34 = vj + N;                // [N] sum_j chi_a(r_j) (j34)
     float* cho = c34 + N;               // [N] chi_a at the moving electron (j34)
     for (int idx = tid; idx < 6 * N; idx += blockDim.x) ptr_s[kTS * (idx / 6) + idx % 6] = s.ptrig[idx];
     if (j34)
@@ -322,8 +324,25 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
         et[kTS * i + 3 + mu] = cs;
     }
     const float zj = (float)s.zeta_j;
+    bar();   // et complete
+    // V_i: computed from the positions in the first sweep of a call, carried
+    // in Vep between the call's sweeps (an accepted move sets V_i to the sum
+    // of its new e-n terms), so a move evaluates the e-n Pade terms only at
+    // the proposal
+    for (int i = tw; i < N; i += 64) {
+        float v = 0.f;
+        if (vep_init) {
+            for (int a = 0; a < N; ++a) {
+                float u0, d1, d2, d3;
+                pade_ep(bep, Zj, pair_dist(et + kTS * i, ptr_s + kTS * a, ell), u0, d1, d2, d3);
+                v += u0;
+            }
+        } else {
+            v = Vep[(size_t)w * N + i];
+        }
+        vj[i] = v;
+    }
     if (j34) {
-        bar();   // et complete
         for (int a = tw; a < N; a += 64) {
             float c = 0.f;
             for (int j = 0; j < N; ++j) c += jas_orbital(et + kTS * j, ptr_s + kTS * a, ell, zj);
@@ -385,8 +404,9 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
                 a4[2] += ph.z * g[4 * jv + 2]; a4[3] += ph.w * g[4 * jv + 3];
             }
             const float wl = (a4[0] + a4[1]) + (a4[2] + a4[3]);
-            // Jastrow difference: partners tw and tw + 64
-            float du = 0.f;
+            // Jastrow difference: partners tw and tw + 64 (e-e: new minus old
+            // pair terms; e-n: the new terms, less V_i after the barrier)
+            float du = 0.f, vnew = 0.f;
             const float* ei = et + kTS * i;
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
@@ -400,8 +420,7 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
                     const float* pa = ptr_s + kTS * j;
                     float d3;
                     pade_ep(bep, Zj, pair_dist(pt, pa, ell), u1, d1, d2, d3);
-                    pade_ep(bep, Zj, pair_dist(ei, pa, ell), u0, d1, d2, d3);
-                    du += u1 - u0;
+                    vnew += u1;
                 }
             }
             float chn_r[2] = {0.f, 0.f}, cho_r[2] = {0.f, 0.f};
@@ -428,9 +447,10 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
                 }
             }
             du = warp_sum(du);
-            float* rd = red + 4 * buf;
+            vnew = warp_sum(vnew);
+            float* rd = red + 8 * buf;
             float* rb = rowb + buf * kSwRow;
-            if (lane == 0) rd[h] = du;
+            if (lane == 0) { rd[h] = du; rd[4 + h] = vnew; }
             if (tw == il) {
                 rd[2] = wl;
 #pragma unroll
@@ -438,9 +458,11 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
                     ((float4*)rb)[jv] = make_float4(g[4 * jv], g[4 * jv + 1], g[4 * jv + 2], g[4 * jv + 3]);
             }
             if (il + 1 < n) phi[(buf ^ 1) * kSwRow + tw] = ph_wr;
+            const float v_old = vj[i];   // before the barrier: an accepted move rewrites it after
             bar();
             const float ratio = rd[2];
-            const float dut = rd[0] + rd[1];
+            const float vin = rd[4] + rd[5];
+            const float dut = (rd[0] + rd[1]) + (vin - v_old);
             const float prob = ratio * ratio * expf(2.f * dut);
             if (u < prob) {
                 const float coef = (wl - (tw == il ? 1.f : 0.f)) * __fdividef(1.f, ratio);
@@ -456,6 +478,7 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
                 if (tw == (i & 63)) {
 #pragma unroll
                     for (int mu = 0; mu < 6; ++mu) et[kTS * i + mu] = pt[mu];
+                    vj[i] = vin;   // read again only in the next sweep
                 }
                 if (j34) {      // c_a of this thread's nuclei (read by others only after the next barrier)
 #pragma unroll
@@ -473,12 +496,14 @@ __global__ void __launch_bounds__(64 * kSwWalkers) sweep_reg_kernel(SysView<floa
                 if (j < n) G[(size_t)tw * n + j] = g[j];
         }
     }
+    bar();   // the last accepted moves' V_i
+    for (int i = tw; i < N; i += 64) Vep[(size_t)w * N + i] = vj[i];
     if (tw == 0) nacc[w] += naccept;
 }
 
 template <typename T>
 void launch_sweep(const SysView<T>& s, double* X, const double* Xp, const T* ptp, const T* uacc, const T* Phi, T* Gt,
-                  unsigned long long* nacc, cudaStream_t st) {
+                  unsigned long long* nacc, float* vep, bool vep_init, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
         if (s.n <= kSwRow) {   // mixed form: inverse rows in registers
             const bool j34 = s.fjt != nullptr;
@@ -491,7 +516,7 @@ void launch_sweep(const SysView<T>& s, double* X, const double* Xp, const T* ptp
                 attr = smem;
             sweep_reg_kernel<<<(s.W + kSwWalkers - 1) / kSwWalkers, 64 * kSwWalkers, smem, st>>>(
                 *(const SysView<float>*)&s, X, Xp, (const float*)ptp, (const float*)uacc, (const float*)Phi,
-                (float*)Gt, nacc);
+                (float*)Gt, nacc, vep, vep_init ? 1 : 0);
             return;
         }
     }
@@ -512,8 +537,8 @@ void launch_sweep(const SysView<T>& s, double* X, const double* Xp, const T* ptp
 }
 
 template void launch_sweep<double>(const SysView<double>&, double*, const double*, const double*, const double*,
-                                   const double*, double*, unsigned long long*, cudaStream_t);
+                                   const double*, double*, unsigned long long*, float*, bool, cudaStream_t);
 template void launch_sweep<float>(const SysView<float>&, double*, const double*, const float*, const float*,
-                                  const float*, float*, unsigned long long*, cudaStream_t);
+                                  const float*, float*, unsigned long long*, float*, bool, cudaStream_t);
 
 }  // namespace qmc

@@ -38,8 +38,11 @@ void launch_refine(int W, int N, int n, const float* Phi, float* Gt, double* log
 
 // k_sweep.cu: one Metropolis sweep per walker (warp per walker).
 template <typename T>
+// vep: [W][N] per-electron e-n Jastrow sums carried between the sweeps of a
+// call by the mixed-form register sweep (computed when vep_init, i.e. in the
+// call's first sweep); unused by the other sweep kernels.
 void launch_sweep(const SysView<T>& s, double* X, const double* Xp, const T* ptp, const T* uacc, const T* Phi, T* Gt,
-                  unsigned long long* nacc, cudaStream_t st);
+                  unsigned long long* nacc, float* vep, bool vep_init, cudaStream_t st);
 
 // k_measure.cu: local energy, d ln psi / dR and dE_L / dR per walker.
 template <typename T>
