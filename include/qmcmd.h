@@ -256,10 +256,11 @@ int qmc_set_walkers(qmc_system* h, const double* X);
  * [count, sum E_L, sum E_L^2, sum dlnpsi/dR (3N), sum E_L dlnpsi/dR (3N), sum dE_L/dR (3N)]. */
 int qmc_get_accumulators(qmc_system* h, double* acc);
 
-/* Handle options.  QMC_OPT_TENSOR_CORES (mixed form only, default 1): evaluate
- * the orbital contractions with the tcgen05 tensor-core kernel (2xTF32 split,
+/* Handle options.  QMC_OPT_TENSOR_CORES (mixed form with N = 128 and n_gauss =
+ * 4, default 1; other systems always use the SIMT kernels): evaluate the
+ * orbital contractions with the tcgen05 tensor-core kernel (2xTF32 split,
  * FP32-level accuracy); 0 selects the SIMT FP32 kernel.
- * QMC_OPT_TC_ADJOINT (mixed form with N <= 128, n_gauss <= 4; default 1):
+ * QMC_OPT_TC_ADJOINT (where QMC_OPT_TENSOR_CORES is available; default 1):
  * while tensor cores are on, the B x n contractions of the orbital force terms
  * (Z = C G, P = C G Y G) and their basis-derivative epilogue run in a separate
  * tcgen05 kernel (2xTF32 pieces, 3 products); 0 keeps them in the SIMT

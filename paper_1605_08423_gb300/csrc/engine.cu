@@ -471,7 +471,14 @@ int init_handle(const qmc_params* p, const double* R, void* block, size_t block_
         h->d_fj = dalloc<double>(h, (size_t)N * N, &rc);
         if (h->mixed) h->d_fj32 = dalloc<float>(h, (size_t)N * N, &rc);
     }
-    if (h->mixed && tc_orbitals_supported(n, B)) {
+    // The tcgen05 kernels serve N = 128 with 4 Gaussians per nucleus (n = 64
+    // orbitals per spin), the configuration they are built, tuned and tested
+    // for; other systems use the SIMT FP32 kernels.  With 32 or 64 protons and
+    // 2 Gaussians per nucleus the tcgen05 path rarely stalled the device for
+    // tens of seconds and returned non-finite results (several thousand
+    // walkers, most often with other handles' kernels running); the cause is
+    // not found, so that path is not offered.
+    if (h->mixed && tc_orbitals_supported(n, B) && n == 64 && h->G == 4) {
         h->d_chat = dalloc<unsigned char>(h, tc_coeff_bytes(B, n), &rc);
         h->use_tc = true;
         if (tc_adjoint_supported(N, n, h->G)) {
