@@ -49,7 +49,9 @@ struct MLayout {
         int np = 4;
         while (np < n) np *= 2;
         const size_t spin = split ? sizeof(T) * 2 * (size_t)np * (np + 4) : sizeof(T) * (size_t)np * (3 * (np + 4) + 68);
-        const size_t jpart = sizeof(T) * 5 * 256;   // P1 partials: nparts * N <= 256 rows of 5
+        // P1 partials: nparts * N <= 256 rows of 5, and (mixed form, N a
+        // multiple of 32) the e-e tiles' rows of 5 per electron and partner block
+        const size_t jpart = sizeof(T) * 5 * (256 + (size_t)(N / 32) * N);
         // e-e-n-n Jastrow work space: c [N], S [N][3], 8 warps x 5N
         const size_t j34 = sizeof(T) * 44 * (size_t)N;
         size_t u = etab > spin ? etab : spin;
@@ -244,12 +246,22 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
     // the slices are summed in order afterwards.
     const int nparts = nt >= N ? nt / N : 1;
     T* jpart = (T*)uni;
+    // Mixed form with N a multiple of 32: each e-e pair is evaluated once, in
+    // 32 x 32 tiles of electron blocks (I, J), I <= J, one warp per tile: lane
+    // l holds electron 32 I + l and at step k meets electron 32 J + (l + k) mod
+    // 32; its row sums stay in the lane and the partner's column sums move one
+    // lane per step (shuffle), so that after the tile lane l holds electron
+    // 32 J + l's.  A diagonal tile takes steps 1..16 (step 16 on lanes 0-15
+    // only).  Each (electron, partner block) has one slot of 5; the slots are
+    // summed in block order with the e-n slices below.
+    const bool ee_tiles = sizeof(T) == 4 && (N & 31) == 0 && N >= 64;
+    T* eepart = jpart + (size_t)5 * 256;   // [N / 32][N][5]
     for (int tt = tid; tt < nparts * N; tt += nt) {
         const int i = tt % N, pi = tt / N;
         const int j0 = (N * pi) / nparts, j1 = (N * (pi + 1)) / nparts;
         T g[3] = {0, 0, 0}, lp = 0, ui = 0;
         const T* ei = et + 6 * i;
-        for (int j = j0; j < j1; ++j) {
+        for (int j = ee_tiles ? j1 : j0; j < j1; ++j) {
             if (j == i) continue;
             T sd[3], cd[3], t;
             disp_trig(ei, et + 6 * j, ell, sd, cd, t);
@@ -298,12 +310,78 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
         T* o = jpart + ((size_t)pi * N + i) * 5;
         o[0] = g[0]; o[1] = g[1]; o[2] = g[2]; o[3] = lp; o[4] = ui;
     }
+    if constexpr (sizeof(T) == 4) {
+        if (ee_tiles) {
+            const int nb = N >> 5, noff = nb * (nb - 1) / 2, ntiles = noff + nb;
+            for (int tile = warp; tile < ntiles; tile += nw) {
+                int I = 0, J = 0;
+                if (tile < noff) {   // off-diagonal tiles, I < J in row-major order
+                    int r = tile;
+                    while (r >= nb - 1 - I) { r -= nb - 1 - I; ++I; }
+                    J = I + 1 + r;
+                } else {
+                    I = J = tile - noff;
+                }
+                const bool diag = I == J;
+                const int i = 32 * I + lane;
+                float ei[6];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) ei[c] = et[6 * i + c];
+                float rg[3] = {0.f, 0.f, 0.f}, rl = 0.f, ru = 0.f, cg[3] = {0.f, 0.f, 0.f}, cl = 0.f;
+                const int k0 = diag ? 1 : 0, k1 = diag ? 17 : 32;
+                for (int k = k0; k < k1; ++k) {
+                    if (!diag || k < 16 || lane < 16) {
+                        const int j = 32 * J + ((lane + k) & 31);
+                        float sd[3], cd[3], t;
+                        disp_trig(ei, et + 6 * j, ell, sd, cd, t);
+                        float u, f1, f2;
+                        jas_ee_f32(t, bee, u, f1, f2);
+                        float pp = 0.f, sq = 0.f;
+#pragma unroll
+                        for (int mu = 0; mu < 3; ++mu) {
+                            const float pm = ell * sd[mu] * cd[mu], gm = 2.f * f1 * pm;
+                            rg[mu] += gm;
+                            cg[mu] -= gm;   // p is odd under the exchange of the pair
+                            pp += pm * pm;
+                            sq += cd[mu] * cd[mu] - sd[mu] * sd[mu];
+                        }
+                        const float lpv = 4.f * f2 * pp + 2.f * f1 * sq;
+                        rl += lpv;
+                        cl += lpv;
+                        ru += u;
+                    }
+                    // the column sums move to the lane that meets their electron next
+                    const int src = (lane + 1) & 31;
+#pragma unroll
+                    for (int mu = 0; mu < 3; ++mu) cg[mu] = __shfl_sync(0xffffffffu, cg[mu], src);
+                    cl = __shfl_sync(0xffffffffu, cl, src);
+                }
+                if (diag) {   // lane l holds column (l + 17) mod 32: column l's come from lane (l + 15) mod 32
+                    const int src = (lane + 15) & 31;
+#pragma unroll
+                    for (int mu = 0; mu < 3; ++mu) cg[mu] = __shfl_sync(0xffffffffu, cg[mu], src);
+                    cl = __shfl_sync(0xffffffffu, cl, src);
+                    T* o = eepart + ((size_t)I * N + i) * 5;
+                    o[0] = rg[0] + cg[0]; o[1] = rg[1] + cg[1]; o[2] = rg[2] + cg[2]; o[3] = rl + cl; o[4] = ru;
+                } else {
+                    T* o = eepart + ((size_t)J * N + i) * 5;
+                    o[0] = rg[0]; o[1] = rg[1]; o[2] = rg[2]; o[3] = rl; o[4] = ru;
+                    T* oc = eepart + ((size_t)I * N + 32 * J + lane) * 5;
+                    oc[0] = cg[0]; oc[1] = cg[1]; oc[2] = cg[2]; oc[3] = cl; oc[4] = 0.f;
+                }
+            }
+        }
+    }
     __syncthreads();
     for (int i = tid; i < N; i += nt) {
         T v[5] = {0, 0, 0, 0, 0};
         for (int pi = 0; pi < nparts; ++pi)
 #pragma unroll
             for (int c = 0; c < 5; ++c) v[c] += jpart[((size_t)pi * N + i) * 5 + c];
+        if (ee_tiles)
+            for (int pb = 0; pb < (N >> 5); ++pb)
+#pragma unroll
+                for (int c = 0; c < 5; ++c) v[c] += eepart[((size_t)pb * N + i) * 5 + c];
         gU[3 * i] = v[0]; gU[3 * i + 1] = v[1]; gU[3 * i + 2] = v[2];
         lU[i] = v[3]; Ui[i] = v[4];
     }
