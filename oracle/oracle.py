@@ -43,6 +43,7 @@ class Params(C.Structure):
         ("Zj", C.c_double), ("kappa", C.c_double),
         ("zeta", C.POINTER(C.c_double)), ("coeff", C.POINTER(C.c_double)),
         ("zeta_j", C.c_double), ("fj", C.POINTER(C.c_double)),
+        ("twist", C.POINTER(C.c_double)),
     ]
 
 
@@ -110,6 +111,18 @@ def lib():
         L.orc_toy_run.argtypes = [C.POINTER(ToyArgs), C.c_int, _dp, _dp]
         L.orc_toy_noise.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, _dp]
         L.orc_toy_run_ids.argtypes = [C.POINTER(ToyArgs), C.c_int, C.POINTER(C.c_int), _dp, _dp]
+        L.orc_reduce_twists.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.orc_bloch_images.restype = C.c_int
+        L.orc_bloch_images.argtypes = [C.POINTER(Params)]
+        L.orc_bloch_gaussian.argtypes = [C.c_double, _dp, _dp, C.c_double, _dp, C.c_int, _dp]
+        L.orc_eval_config_twist.restype = C.c_int
+        L.orc_eval_config_twist.argtypes = [C.POINTER(Params), _dp, _dp, C.c_int, _dp, _dp, _dp, _dp]
+        L.orc_eval_configs_twist.restype = C.c_int
+        L.orc_eval_configs_twist.argtypes = [C.POINTER(Params), _dp, C.c_int, _dp, C.c_int, _dp, C.c_int, _dp, _dp,
+                                             _dp, _dp]
+        L.orc_vmc_twists.restype = C.c_int
+        L.orc_vmc_twists.argtypes = [C.POINTER(Params), _dp, C.POINTER(ChainArgs), C.c_int, _dp, _dp, _dp, _dp,
+                                     C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
         _lib = L
     return _lib
 
@@ -137,6 +150,7 @@ class System:
     periodic: bool = True
     zeta_j: float = 0.7933844        # exponent of the U_{3+4} Jastrow orbitals (SI's Z_1 = Z_2)
     fj: np.ndarray | None = None     # [N][N] symmetric U_{3+4} coefficients; None: term off
+    twist: np.ndarray | None = None  # [3] twist theta of the spin-up orbitals (Bloch Gaussians); None: real form
 
     def cparams(self) -> Params:
         self._zeta = np.ascontiguousarray(self.zeta, dtype=np.float64)
@@ -145,11 +159,13 @@ class System:
         n_up = self.N // 2 if self.n_up is None else self.n_up
         n_dn = self.N - n_up if self.n_dn is None else self.n_dn
         kappa = 5.0 / self.L if self.kappa is None else self.kappa
+        self._twist = None if self.twist is None else np.ascontiguousarray(self.twist, dtype=np.float64).reshape(3)
         return Params(self.N, n_up, n_dn, self._coeff.shape[1], len(self._zeta), int(self.periodic),
                       self.mmax, 0, self.L, self.b_ee, self.b_ep, self.Z,
                       self.Z if self.Zj is None else self.Zj, kappa,
                       _ptr(self._zeta), _ptr(self._coeff), self.zeta_j,
-                      _ptr(self._fj) if self._fj is not None else C.cast(None, _dp))
+                      _ptr(self._fj) if self._fj is not None else C.cast(None, _dp),
+                      _ptr(self._twist) if self._twist is not None else C.cast(None, _dp))
 
     @property
     def n_elec(self) -> int:
@@ -269,6 +285,87 @@ def reduce(acc, N):
     f = np.zeros(N3); S = np.zeros((N3, N3))
     lib().orc_reduce(W, N3, _ptr(acc), C.byref(E), C.byref(Ee), _ptr(f), _ptr(S), C.byref(Nc))
     return dict(E=E.value, E_err=Ee.value, f=f, S=S, Nc=Nc.value)
+
+
+def reduce_twists(acc, N, K):
+    """Twist average of K contiguous walker blocks (each reduced on its own)."""
+    acc = np.ascontiguousarray(acc, dtype=np.float64)
+    W = acc.shape[0]
+    N3 = 3 * N
+    E = C.c_double(); Ee = C.c_double(); Nc = C.c_double()
+    f = np.zeros(N3); S = np.zeros((N3, N3))
+    lib().orc_reduce_twists(K, W, N3, _ptr(acc), C.byref(E), C.byref(Ee), _ptr(f), _ptr(S), C.byref(Nc))
+    return dict(E=E.value, E_err=Ee.value, f=f, S=S, Nc=Nc.value)
+
+
+# ---- twisted boundary conditions ----
+
+def bloch_images(sys: System) -> int:
+    """Images per axis M of the Bloch-summed Gaussians of this system."""
+    return lib().orc_bloch_images(C.byref(sys.cparams()))
+
+
+def bloch_gaussian(L, x, Rc, zeta, theta, M):
+    """Bloch-summed Gaussian at x: (chi, grad chi [3], lap chi), complex."""
+    x, Rc, th = (np.ascontiguousarray(a, dtype=np.float64).reshape(3) for a in (x, Rc, theta))
+    o = np.zeros(10)
+    lib().orc_bloch_gaussian(L, _ptr(x), _ptr(Rc), zeta, _ptr(th), int(M), _ptr(o))
+    return complex(o[0], o[1]), o[2:8:2] + 1j * o[3:8:2], complex(o[8], o[9])
+
+
+def eval_config_twist(sys: System, R, X, derivs=False):
+    """Twisted orbitals (sys.twist set): dict(lnpsi, phase, el, ekin, ekin_im, epot, grad, dlnpsi, del_)."""
+    assert sys.twist is not None
+    p = sys.cparams()
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    sc = np.zeros(6)
+    grad = np.zeros((sys.n_elec, 3))
+    dl = np.zeros((sys.N, 3))
+    de = np.zeros((sys.N, 3))
+    rc = lib().orc_eval_config_twist(C.byref(p), _ptr(R), _ptr(X), int(derivs), _ptr(sc), _ptr(grad), _ptr(dl),
+                                     _ptr(de))
+    if rc != 0:
+        raise ValueError("singular Slater block")
+    out = dict(lnpsi=sc[0], phase=sc[1], el=sc[2], ekin=sc[3], ekin_im=sc[4], epot=sc[5], grad=grad)
+    if derivs:
+        out.update(dlnpsi=dl, del_=de)
+    return out
+
+
+def eval_configs_twist(sys: System, R, X, twists, derivs=True):
+    """X [nconf, Ne, 3]; configuration c takes twists[c // (nconf // K)]: lnpsi, el, dlnpsi, del."""
+    twists = np.ascontiguousarray(twists, dtype=np.float64).reshape(-1, 3)
+    p = sys.cparams()
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    n = X.shape[0]
+    lp = np.zeros(n); el = np.zeros(n)
+    dl = np.zeros((n, sys.N, 3)); de = np.zeros((n, sys.N, 3))
+    rc = lib().orc_eval_configs_twist(C.byref(p), _ptr(R), n, _ptr(X), twists.shape[0], _ptr(twists), int(derivs),
+                                      _ptr(lp), _ptr(el), _ptr(dl), _ptr(de))
+    if rc != 0:
+        raise ValueError("singular Slater block" if rc == -1 else "configurations not a multiple of the twists")
+    return lp, el, dl, de
+
+
+def vmc_twists(sys: System, R, twists, *, W, n_sweeps, n_warmup, measure_every=1, sigma=0.3, seed=1, md_step=0,
+               X=None, forces=True):
+    """Chains with twisted orbitals, walker w on twists[w // (W // K)]; returns (X, acc, accept_ratio, vacc)."""
+    twists = np.ascontiguousarray(twists, dtype=np.float64).reshape(-1, 3)
+    p = sys.cparams()
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    init = X is None
+    Xa = np.zeros((W, sys.n_elec, 3)) if init else np.array(X, dtype=np.float64, copy=True)
+    acc = np.zeros((W, 3 + 9 * sys.N))
+    vacc = np.zeros(W)
+    ca = ChainArgs(W, n_sweeps, n_warmup, measure_every, int(init), int(forces), md_step, 0, sigma, seed)
+    na = C.c_longlong(0); nt = C.c_longlong(0)
+    rc = lib().orc_vmc_twists(C.byref(p), _ptr(R), C.byref(ca), twists.shape[0], _ptr(twists), _ptr(Xa), _ptr(acc),
+                              _ptr(vacc), C.byref(na), C.byref(nt))
+    if rc != 0:
+        raise ValueError("walkers not a multiple of the twists")
+    return Xa, acc, (na.value / nt.value if nt.value else 0.0), vacc
 
 
 LV_ADOPTED, LV_FAST, LV_NOROGNA = 0, 1, 2

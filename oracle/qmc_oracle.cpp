@@ -28,6 +28,12 @@
 //   langevin_step ........ harmonic closed forms (steepest descent, Newton step,
 //                          stationary covariance, autocorrelation); fast and
 //                          simple-rule variants against their closed forms
+//   twisted form ......... Bloch Gaussians against their Fourier series
+//                          (Poisson summation) and the Bloch property; psi's
+//                          Bloch phases and time reversal; the complex kinetic
+//                          energy and the R-derivatives against finite
+//                          differences; the plane-wave limit; the chain against
+//                          a brute-force integral; the twist-average rule
 //   toy model ............ finite differences of U, H, S^{-1}; the S-difference
 //                          corrections against the cumbersome term (Gauss-Hermite
 //                          averages); stationary <U> against quadratures of the
@@ -132,6 +138,30 @@ static inline D3 cos(const D3& x) { return chain(x, std::cos(x.v), -std::sin(x.v
 static inline D3 sqrt(const D3& x) { double s = std::sqrt(x.v); return chain(x, s, 0.5 / s); }
 static inline D3 log(const D3& x) { return chain(x, std::log(x.v), 1.0 / x.v); }
 static inline D3 erfc(const D3& x) { return chain(x, std::erfc(x.v), -2.0 / std::sqrt(M_PI) * std::exp(-x.v * x.v)); }
+
+// ---------------------------------------------------------------------------
+// Complex number over a real scalar S (double or D3), for the twisted
+// (complex) orbitals; only the operations the determinant algebra needs.
+// ---------------------------------------------------------------------------
+template <class S>
+struct Cx {
+    S re, im;
+    Cx() : re(0.0), im(0.0) {}
+    Cx(const S& r, const S& i) : re(r), im(i) {}
+};
+template <class S> static inline Cx<S> operator+(const Cx<S>& a, const Cx<S>& b) { return Cx<S>(a.re + b.re, a.im + b.im); }
+template <class S> static inline Cx<S> operator-(const Cx<S>& a, const Cx<S>& b) { return Cx<S>(a.re - b.re, a.im - b.im); }
+template <class S> static inline Cx<S> operator*(const Cx<S>& a, const Cx<S>& b) {
+    return Cx<S>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <class S> static inline Cx<S> operator/(const Cx<S>& a, const Cx<S>& b) {
+    const S q = b.re * b.re + b.im * b.im;
+    return Cx<S>((a.re * b.re + a.im * b.im) / q, (a.im * b.re - a.re * b.im) / q);
+}
+template <class S> static inline Cx<S> scale(const Cx<S>& a, double r) { return Cx<S>(a.re * r, a.im * r); }
+template <class S> static inline Cx<S>& operator+=(Cx<S>& a, const Cx<S>& b) { a = a + b; return a; }
+template <class S> static inline Cx<S>& operator-=(Cx<S>& a, const Cx<S>& b) { a = a - b; return a; }
+template <class S> static inline double abs2v(const Cx<S>& a) { return val(a.re) * val(a.re) + val(a.im) * val(a.im); }
 using std::exp; using std::sin; using std::cos; using std::sqrt; using std::log; using std::erfc;
 
 // ---------------------------------------------------------------------------
@@ -157,6 +187,10 @@ struct Params {
     // periodised Gaussian exp(-zeta_j |d|^2) per nucleus; fj = null: term off
     double zeta_j;
     const double* fj;     // [N][N] symmetric coefficients f^{ab}
+    // Twisted boundary conditions (SI, basis section): null keeps the real
+    // sin-periodised orbitals; otherwise the twist vector theta [3] of the
+    // spin-up determinant (spin down: -theta) and Bloch-summed Gaussians
+    const double* twist;
 };
 
 // ---------------------------------------------------------------------------
@@ -401,30 +435,14 @@ static void slater_block(const Params& p, const S* R, const double* X, int i0, i
         }
 }
 
+// Jastrow exponent U with grad_i U and lap_i U of every electron (SI, J = e^U:
+// the Pade e-e and e-n terms and, with p.fj, the e-e-n-n term).
 template <class S>
-static WfOut<S> wavefunction(const Params& p, const S* R, const double* X) {
-    WfOut<S> out;
+static void jastrow_all(const Params& p, const S* R, const double* X, S& U, std::vector<S>& gU, std::vector<S>& lU) {
     const int Ne = p.n_up + p.n_dn;
-    out.ok = true;
-    out.sign = 1;
-    out.lnpsi = S(0.0);
-    std::vector<S> g((size_t)Ne * 3, S(0.0)), l(Ne, S(0.0));
-    for (int s = 0; s < 2; ++s) {
-        int i0 = s ? p.n_up : 0, ne = s ? p.n_dn : p.n_up;
-        if (ne == 0) continue;
-        S ld; int sg; bool ok;
-        std::vector<S> gs, ls;
-        slater_block(p, R, X, i0, ne, ld, sg, gs, ls, ok);
-        if (!ok) { out.ok = false; return out; }
-        out.lnpsi += ld; out.sign *= sg;
-        for (int i = 0; i < ne; ++i) {
-            for (int mu = 0; mu < 3; ++mu) g[(i0 + i) * 3 + mu] = gs[i * 3 + mu];
-            l[i0 + i] = ls[i];
-        }
-    }
-    // Jastrow U, grad_i U, lap_i U
-    std::vector<S> gU((size_t)Ne * 3, S(0.0)), lU(Ne, S(0.0));
-    S U(0.0);
+    gU.assign((size_t)Ne * 3, S(0.0));
+    lU.assign(Ne, S(0.0));
+    U = S(0.0);
     auto fee = [&](const S& r, S& u, S& up, S& upp) {
         double uu, a, b; u_ee(p.b_ee, val(r), uu, a, b); u = S(uu); up = S(a); upp = S(b);
     };
@@ -472,6 +490,45 @@ static WfOut<S> wavefunction(const Params& p, const S* R, const double* X) {
                 }
             }
     }
+}
+
+// Potential energy of all 2N charges (Ewald sum in the periodic box).
+template <class S>
+static S potential(const Params& p, const S* R, const double* X) {
+    const int Ne = p.n_up + p.n_dn;
+    std::vector<double> q;
+    std::vector<S> pos;
+    for (int i = 0; i < Ne; ++i) { q.push_back(-1.0); for (int mu = 0; mu < 3; ++mu) pos.push_back(S(X[3 * i + mu])); }
+    for (int a = 0; a < p.N; ++a) { q.push_back(p.Z); for (int mu = 0; mu < 3; ++mu) pos.push_back(R[3 * a + mu]); }
+    if (p.periodic) return ewald((int)q.size(), q.data(), pos.data(), p.L, p.kappa, p.mmax, false);
+    return coulomb_open((int)q.size(), q.data(), pos.data());
+}
+
+template <class S>
+static WfOut<S> wavefunction(const Params& p, const S* R, const double* X) {
+    WfOut<S> out;
+    const int Ne = p.n_up + p.n_dn;
+    out.ok = true;
+    out.sign = 1;
+    out.lnpsi = S(0.0);
+    std::vector<S> g((size_t)Ne * 3, S(0.0)), l(Ne, S(0.0));
+    for (int s = 0; s < 2; ++s) {
+        int i0 = s ? p.n_up : 0, ne = s ? p.n_dn : p.n_up;
+        if (ne == 0) continue;
+        S ld; int sg; bool ok;
+        std::vector<S> gs, ls;
+        slater_block(p, R, X, i0, ne, ld, sg, gs, ls, ok);
+        if (!ok) { out.ok = false; return out; }
+        out.lnpsi += ld; out.sign *= sg;
+        for (int i = 0; i < ne; ++i) {
+            for (int mu = 0; mu < 3; ++mu) g[(i0 + i) * 3 + mu] = gs[i * 3 + mu];
+            l[i0 + i] = ls[i];
+        }
+    }
+    // Jastrow U, grad_i U, lap_i U
+    std::vector<S> gU, lU;
+    S U;
+    jastrow_all(p, R, X, U, gU, lU);
     out.lnpsi += U;
     // kinetic energy: lap_i ln psi = (l_i - |g_i|^2) + lap_i U ; grad_i ln psi = g_i + grad_i U
     S kin(0.0);
@@ -489,12 +546,7 @@ static WfOut<S> wavefunction(const Params& p, const S* R, const double* X) {
     }
     out.ekin = -0.5 * kin;
     // potential energy of all 2N charges
-    std::vector<double> q;
-    std::vector<S> pos;
-    for (int i = 0; i < Ne; ++i) { q.push_back(-1.0); for (int mu = 0; mu < 3; ++mu) pos.push_back(S(X[3 * i + mu])); }
-    for (int a = 0; a < p.N; ++a) { q.push_back(p.Z); for (int mu = 0; mu < 3; ++mu) pos.push_back(R[3 * a + mu]); }
-    if (p.periodic) out.epot = ewald((int)q.size(), q.data(), pos.data(), p.L, p.kappa, p.mmax, false);
-    else out.epot = coulomb_open((int)q.size(), q.data(), pos.data());
+    out.epot = potential(p, R, X);
     out.el = out.ekin + out.epot;
     return out;
 }
@@ -672,6 +724,310 @@ static void run_walker(const Params& p, const ChainArgs& c, const Rng& rng, uint
 }
 
 // ---------------------------------------------------------------------------
+// Twisted boundary conditions (SI, basis section: the orbitals obey
+// phi(r + n L) = exp(i theta.n) phi(r) for integer vectors n).  Reading: the
+// Gaussians are turned into Bloch functions by the standard lattice sum
+//   chi_{a,g}(r) = sum_n exp(i theta.n) exp(-zeta_g |r - R_a - n L|^2),
+// which has that property for every n; the spin-up determinant uses theta and
+// the spin-down one -theta (the SI's opposite twists for opposite spins) with
+// the same real coefficients, so the down orbitals are the complex conjugates
+// of the up ones and psi(-theta) = conj psi(theta).  The Jastrow factor stays
+// the real sin-periodised one.  Truncation (part of the definition): with k
+// the nearest integer vector to (r - R_a)/L, the images n = k + m with m in
+// [-M, M]^3 and
+//   M = max(1, ceil(sqrt(40 / zeta_min) / L - 1/2)),
+// so that every omitted image lies more than sqrt(40 / zeta_min) away (each
+// omitted term below e^-40 of the largest one).
+// With complex psi the sampled density is |psi|^2, and the estimators take the
+// real parts: E_L = Re(H psi / psi), d ln|psi| / dR = Re(d ln psi / dR) and
+// d E_L / dR = Re(d (H psi / psi) / dR) (H is Hermitian, so
+// E = <|psi|^2 Re E_L> / <|psi|^2> and its R-derivative take these forms).
+// ---------------------------------------------------------------------------
+static int bloch_images(const Params& p) {
+    double zmin = p.zeta[0];
+    for (int g = 1; g < p.n_gauss; ++g) zmin = std::min(zmin, p.zeta[g]);
+    const int M = (int)std::ceil(std::sqrt(40.0 / zmin) / p.L - 0.5);
+    return M < 1 ? 1 : M;
+}
+
+// Bloch-summed Gaussian, its gradient and its Laplacian in the electron
+// coordinate x, as the plain sum over the (2M+1)^3 images.
+template <class S>
+static void bloch_gaussian(double L, const double x[3], const S Rc[3], double zeta, const double th[3], int M,
+                           Cx<S>& chi, Cx<S> grad[3], Cx<S>& lap) {
+    chi = Cx<S>(); lap = Cx<S>();
+    for (int mu = 0; mu < 3; ++mu) grad[mu] = Cx<S>();
+    S d[3];
+    int k[3];
+    for (int mu = 0; mu < 3; ++mu) {
+        d[mu] = x[mu] - Rc[mu];
+        k[mu] = (int)std::nearbyint(val(d[mu]) / L);
+    }
+    for (int m0 = -M; m0 <= M; ++m0)
+        for (int m1 = -M; m1 <= M; ++m1)
+            for (int m2 = -M; m2 <= M; ++m2) {
+                const int n[3] = {k[0] + m0, k[1] + m1, k[2] + m2};
+                S u[3], r2(0.0);
+                for (int mu = 0; mu < 3; ++mu) { u[mu] = d[mu] - (double)n[mu] * L; r2 += u[mu] * u[mu]; }
+                const S e = exp(-zeta * r2);
+                const double ph = th[0] * n[0] + th[1] * n[1] + th[2] * n[2];
+                const double c = std::cos(ph), s = std::sin(ph);
+                chi += Cx<S>(c * e, s * e);
+                for (int mu = 0; mu < 3; ++mu) {
+                    const S gm = -2.0 * zeta * u[mu] * e;
+                    grad[mu] += Cx<S>(c * gm, s * gm);
+                }
+                const S lp = (4.0 * zeta * zeta * r2 - 6.0 * zeta) * e;
+                lap += Cx<S>(c * lp, s * lp);
+            }
+}
+
+// Complex LU with partial pivoting (largest modulus; Golub & Van Loan,
+// Alg. 3.4.1) and the inverse; returns ln|det| and arg det (value only).
+template <class S>
+static bool lu_inverse_c(int n, std::vector<Cx<S>> A, std::vector<Cx<S>>& inv, S& logabs, double& phase) {
+    std::vector<int> perm(n);
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    logabs = S(0.0);
+    phase = 0.0;
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < n; ++i)
+            if (abs2v(A[i * n + k]) > abs2v(A[piv * n + k])) piv = i;
+        if (abs2v(A[piv * n + k]) == 0.0) return false;
+        if (piv != k) {
+            for (int j = 0; j < n; ++j) std::swap(A[k * n + j], A[piv * n + j]);
+            std::swap(perm[k], perm[piv]);
+            phase += M_PI;
+        }
+        const Cx<S> pivot = A[k * n + k];
+        logabs += 0.5 * log(pivot.re * pivot.re + pivot.im * pivot.im);
+        phase += std::atan2(val(pivot.im), val(pivot.re));
+        for (int i = k + 1; i < n; ++i) {
+            A[i * n + k] = A[i * n + k] / pivot;
+            for (int j = k + 1; j < n; ++j) A[i * n + j] -= A[i * n + k] * A[k * n + j];
+        }
+    }
+    phase = std::remainder(phase, 2.0 * M_PI);
+    inv.assign((size_t)n * n, Cx<S>());
+    for (int col = 0; col < n; ++col) {
+        std::vector<Cx<S>> y(n);
+        for (int i = 0; i < n; ++i) {
+            Cx<S> s = (perm[i] == col) ? Cx<S>(S(1.0), S(0.0)) : Cx<S>();
+            for (int j = 0; j < i; ++j) s -= A[i * n + j] * y[j];
+            y[i] = s;
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            Cx<S> s = y[i];
+            for (int j = i + 1; j < n; ++j) s -= A[i * n + j] * inv[j * n + col];
+            inv[i * n + col] = s / A[i * n + i];
+        }
+    }
+    return true;
+}
+
+// Twisted Slater block of electrons i0..i0+ne-1 with twist th: ln|det|,
+// arg det, and per electron g_i = grad_i det / det, l_i = lap_i det / det.
+template <class S>
+static void slater_block_twist(const Params& p, const S* R, const double* X, int i0, int ne, const double th[3],
+                               S& logabs, double& phase, std::vector<Cx<S>>& g, std::vector<Cx<S>>& l, bool& ok) {
+    const int G = p.n_gauss, nb = p.N * G, no = p.n_orb, M = bloch_images(p);
+    std::vector<Cx<S>> A((size_t)ne * ne), D[3], Lp((size_t)ne * ne);
+    for (int mu = 0; mu < 3; ++mu) D[mu].assign((size_t)ne * ne, Cx<S>());
+    for (int i = 0; i < ne; ++i) {
+        const double* x = X + 3 * (i0 + i);
+        std::vector<Cx<S>> chi(nb), dchi[3], lchi(nb);
+        for (int mu = 0; mu < 3; ++mu) dchi[mu].resize(nb);
+        for (int a = 0; a < p.N; ++a)
+            for (int gg = 0; gg < G; ++gg) {
+                Cx<S> c, gr[3], lp;
+                bloch_gaussian(p.L, x, R + 3 * a, p.zeta[gg], th, M, c, gr, lp);
+                const int b = a * G + gg;
+                chi[b] = c; lchi[b] = lp;
+                for (int mu = 0; mu < 3; ++mu) dchi[mu][b] = gr[mu];
+            }
+        for (int j = 0; j < ne; ++j) {
+            Cx<S> v, lv, dv[3];
+            for (int b = 0; b < nb; ++b) {
+                const double cbj = p.coeff[(size_t)b * no + j];
+                v += scale(chi[b], cbj); lv += scale(lchi[b], cbj);
+                for (int mu = 0; mu < 3; ++mu) dv[mu] += scale(dchi[mu][b], cbj);
+            }
+            A[i * ne + j] = v; Lp[i * ne + j] = lv;
+            for (int mu = 0; mu < 3; ++mu) D[mu][i * ne + j] = dv[mu];
+        }
+    }
+    std::vector<Cx<S>> inv;
+    ok = lu_inverse_c(ne, A, inv, logabs, phase);
+    g.assign((size_t)ne * 3, Cx<S>()); l.assign(ne, Cx<S>());
+    if (!ok) return;
+    for (int i = 0; i < ne; ++i)
+        for (int j = 0; j < ne; ++j) {
+            for (int mu = 0; mu < 3; ++mu) g[i * 3 + mu] += D[mu][i * ne + j] * inv[j * ne + i];
+            l[i] += Lp[i * ne + j] * inv[j * ne + i];
+        }
+}
+
+template <class S>
+struct WfTwist {
+    S lnpsi;          // ln |psi|
+    double phase;     // arg psi (value only)
+    S ekin, epot, el; // Re of the kinetic and local energies
+    double ekin_im;   // Im of the kinetic energy (value only)
+    std::vector<double> grad;  // Re grad_i ln psi, [Ne][3]
+    bool ok;
+};
+
+// Twisted wavefunction psi = det(Phi_up(theta)) det(Phi_dn(-theta)) e^U and
+//   H psi / psi = -1/2 sum_i [ l_i + 2 g_i . grad_i U + lap_i U + |grad_i U|^2 ] + V
+// (complex l_i, g_i of the blocks; U real), E_L its real part.
+template <class S>
+static WfTwist<S> wavefunction_twist(const Params& p, const S* R, const double* X) {
+    WfTwist<S> out;
+    const int Ne = p.n_up + p.n_dn;
+    out.ok = true;
+    out.lnpsi = S(0.0);
+    out.phase = 0.0;
+    std::vector<Cx<S>> g((size_t)Ne * 3), l(Ne);
+    for (int s = 0; s < 2; ++s) {
+        const int i0 = s ? p.n_up : 0, ne = s ? p.n_dn : p.n_up;
+        if (ne == 0) continue;
+        const double sg = s ? -1.0 : 1.0;
+        const double th[3] = {sg * p.twist[0], sg * p.twist[1], sg * p.twist[2]};
+        S la; double ph; bool ok;
+        std::vector<Cx<S>> gs, ls;
+        slater_block_twist(p, R, X, i0, ne, th, la, ph, gs, ls, ok);
+        if (!ok) { out.ok = false; return out; }
+        out.lnpsi += la; out.phase += ph;
+        for (int i = 0; i < ne; ++i) {
+            for (int mu = 0; mu < 3; ++mu) g[(i0 + i) * 3 + mu] = gs[i * 3 + mu];
+            l[i0 + i] = ls[i];
+        }
+    }
+    out.phase = std::remainder(out.phase, 2.0 * M_PI);
+    std::vector<S> gU, lU;
+    S U;
+    jastrow_all(p, R, X, U, gU, lU);
+    out.lnpsi += U;
+    S kin(0.0);
+    double kin_im = 0.0;
+    out.grad.assign((size_t)Ne * 3, 0.0);
+    for (int i = 0; i < Ne; ++i) {
+        S re = l[i].re + lU[i];
+        double im = val(l[i].im);
+        for (int mu = 0; mu < 3; ++mu) {
+            re += 2.0 * g[i * 3 + mu].re * gU[i * 3 + mu] + gU[i * 3 + mu] * gU[i * 3 + mu];
+            im += 2.0 * val(g[i * 3 + mu].im) * val(gU[i * 3 + mu]);
+            out.grad[i * 3 + mu] = val(g[i * 3 + mu].re + gU[i * 3 + mu]);
+        }
+        kin += re;
+        kin_im += im;
+    }
+    out.ekin = -0.5 * kin;
+    out.ekin_im = -0.5 * kin_im;
+    out.epot = potential(p, R, X);
+    out.el = out.ekin + out.epot;
+    return out;
+}
+
+struct TwistResult {
+    double lnpsi, phase, el, ekin, ekin_im, epot; bool ok;
+    std::vector<double> grad, dlnpsi, del;
+};
+static TwistResult eval_config_twist(const Params& p, const double* R, const double* X, bool derivs) {
+    TwistResult res;
+    WfTwist<double> w = wavefunction_twist<double>(p, R, X);
+    res.ok = w.ok; res.lnpsi = w.lnpsi; res.phase = w.phase; res.el = w.el; res.ekin = w.ekin;
+    res.ekin_im = w.ekin_im; res.epot = w.epot; res.grad = w.grad;
+    if (!derivs || !w.ok) return res;
+    res.dlnpsi.assign((size_t)3 * p.N, 0.0);
+    res.del.assign((size_t)3 * p.N, 0.0);
+    std::vector<D3> Rd((size_t)3 * p.N);
+    for (int a = 0; a < p.N; ++a) {
+        for (int k = 0; k < 3 * p.N; ++k) Rd[k] = D3(R[k]);
+        for (int mu = 0; mu < 3; ++mu) Rd[3 * a + mu].d[mu] = 1.0;
+        WfTwist<D3> wd = wavefunction_twist<D3>(p, Rd.data(), X);
+        for (int mu = 0; mu < 3; ++mu) {
+            res.dlnpsi[3 * a + mu] = wd.lnpsi.d[mu];
+            res.del[3 * a + mu] = wd.el.d[mu];
+        }
+    }
+    return res;
+}
+
+// Row of twisted orbitals at x (values only).
+static void slater_row_twist(const Params& p, const double* R, const double* x, int ne, const double th[3],
+                             Cx<double>* row) {
+    const int G = p.n_gauss, no = p.n_orb, M = bloch_images(p);
+    for (int j = 0; j < ne; ++j) row[j] = Cx<double>();
+    for (int a = 0; a < p.N; ++a)
+        for (int gg = 0; gg < G; ++gg) {
+            Cx<double> c, gr[3], lp;
+            bloch_gaussian<double>(p.L, x, R + 3 * a, p.zeta[gg], th, M, c, gr, lp);
+            const int b = a * G + gg;
+            for (int j = 0; j < ne; ++j) row[j] += scale(c, p.coeff[(size_t)b * no + j]);
+        }
+}
+
+// The Metropolis chain of run_walker with twisted orbitals (the spin-up block
+// with twist theta = p.twist, spin down with -theta): acceptance |psi'/psi|^2
+// from ln|det| of fresh complex LUs; the same Philox draws, sweep order and
+// sampling rule; samples from eval_config_twist.
+static void run_walker_twist(const Params& p, const ChainArgs& c, const Rng& rng, uint32_t w, const double* R,
+                             double* X, double* acc, double* vacc, long long* n_acc, long long* n_try) {
+    const int Ne = p.n_up + p.n_dn, N3 = 3 * p.N;
+    if (c.init_walkers) init_walker(p, rng, w, R, X);
+    std::vector<Cx<double>> A[2];
+    double ld[2] = {0, 0};
+    double th[2][3];
+    for (int s = 0; s < 2; ++s) {
+        const double sg = s ? -1.0 : 1.0;
+        for (int mu = 0; mu < 3; ++mu) th[s][mu] = sg * p.twist[mu];
+        const int i0 = s ? p.n_up : 0, ne = s ? p.n_dn : p.n_up;
+        A[s].assign((size_t)ne * ne, Cx<double>());
+        for (int i = 0; i < ne; ++i) slater_row_twist(p, R, X + 3 * (i0 + i), ne, th[s], &A[s][(size_t)i * ne]);
+        std::vector<Cx<double>> inv; double ph;
+        if (ne) lu_inverse_c(ne, A[s], inv, ld[s], ph);
+    }
+    const int total = c.n_warmup + c.n_sweeps;
+    for (int sw = 0; sw < total; ++sw) {
+        for (int i = 0; i < Ne; ++i) {
+            const int s = i < p.n_up ? 0 : 1;
+            const int i0 = s ? p.n_up : 0, ne = s ? p.n_dn : p.n_up, il = i - i0;
+            const uint32_t idx = (uint32_t)(sw * Ne + i);
+            double xn[3];
+            for (int mu = 0; mu < 3; ++mu) xn[mu] = X[3 * i + mu] + c.sigma * rng.normal(w, c.md_step, idx, P_PROP_X + mu);
+            std::vector<Cx<double>> An = A[s];
+            slater_row_twist(p, R, xn, ne, th[s], &An[(size_t)il * ne]);
+            std::vector<Cx<double>> inv; double ldn, ph;
+            const bool ok = lu_inverse_c(ne, An, inv, ldn, ph);
+            const double du = jastrow_delta(p, R, X, i, xn);
+            const double prob = ok ? std::exp(2.0 * (ldn - ld[s]) + 2.0 * du) : 0.0;
+            const double u = rng.uniform(w, c.md_step, idx, P_ACCEPT);
+            ++*n_try;
+            if (u < prob) {
+                ++*n_acc;
+                for (int mu = 0; mu < 3; ++mu) X[3 * i + mu] = p.periodic ? wrap(xn[mu], p.L) : xn[mu];
+                // the row of the wrapped position differs from An's by a phase only
+                slater_row_twist(p, R, X + 3 * i, ne, th[s], &An[(size_t)il * ne]);
+                A[s] = An; ld[s] = ldn;
+            }
+        }
+        if (sw >= c.n_warmup && ((sw - c.n_warmup + 1) % c.measure_every) == 0) {
+            TwistResult r = eval_config_twist(p, R, X, c.forces != 0);
+            acc[0] += 1; acc[1] += r.el; acc[2] += r.el * r.el;
+            if (vacc) vacc[0] += r.epot;
+            if (c.forces)
+                for (int k = 0; k < N3; ++k) {
+                    acc[3 + k] += r.dlnpsi[k];
+                    acc[3 + N3 + k] += r.el * r.dlnpsi[k];
+                    acc[3 + 2 * N3 + k] += r.del[k];
+                }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Statistics (covariance matrix definition of the paper):
 //   E = mean E_L;  f = -<dE_L/dR> - 2(<E_L dlnpsi/dR> - E <dlnpsi/dR>)
 //   per-walker block forces f_w (same formula with walker means and the global E)
@@ -708,6 +1064,33 @@ static void reduce(int W, int N3, const double* acc, double* E, double* Eerr, do
             for (int w = 0; w < W; ++w) s += (fw[(size_t)w * N3 + i] - f[i]) * (fw[(size_t)w * N3 + j] - f[j]);
             S[(size_t)i * N3 + j] = W > 1 ? s / ((double)W * (W - 1)) : 0.0;
         }
+}
+
+// ---------------------------------------------------------------------------
+// Twist average (main text: k-point sampling of the Brillouin zone on a
+// Monkhorst-Pack mesh, whose points have equal weights).  Walkers come in K
+// contiguous blocks of W/K, block t sampling twist t; each block is reduced on
+// its own (its force with its own energy E_t, the estimator holding per twist)
+// and the K independent estimates are averaged:
+//   E = (1/K) sum_t E_t,  f = (1/K) sum_t f_t,  S = (1/K^2) sum_t S_t,
+//   E_err^2 = (1/K^2) sum_t E_err,t^2,  N_c = sum_t N_c,t.
+// ---------------------------------------------------------------------------
+static void reduce_twists(int K, int W, int N3, const double* acc, double* E, double* Eerr, double* f, double* S,
+                          double* Nc) {
+    const int Wk = W / K, stride = 3 + 3 * N3;
+    *E = 0; *Nc = 0;
+    double e2 = 0;
+    for (int k = 0; k < N3; ++k) f[k] = 0;
+    for (size_t k = 0; k < (size_t)N3 * N3; ++k) S[k] = 0;
+    std::vector<double> ft(N3), St((size_t)N3 * N3);
+    for (int t = 0; t < K; ++t) {
+        double Et, Eet, Nct;
+        reduce(Wk, N3, acc + (size_t)t * Wk * stride, &Et, &Eet, ft.data(), St.data(), &Nct);
+        *E += Et / K; e2 += Eet * Eet; *Nc += Nct;
+        for (int k = 0; k < N3; ++k) f[k] += ft[k] / K;
+        for (size_t k = 0; k < (size_t)N3 * N3; ++k) S[k] += St[k] / ((double)K * K);
+    }
+    *Eerr = std::sqrt(e2) / K;
 }
 
 // ---------------------------------------------------------------------------
@@ -1236,6 +1619,91 @@ void orc_pressure(int W, int N, const double* acc, const double* vacc, double om
 
 void orc_reduce(int W, int N3, const double* acc, double* E, double* Eerr, double* f, double* S, double* Nc) {
     orc::reduce(W, N3, acc, E, Eerr, f, S, Nc);
+}
+
+void orc_reduce_twists(int K, int W, int N3, const double* acc, double* E, double* Eerr, double* f, double* S,
+                       double* Nc) {
+    orc::reduce_twists(K, W, N3, acc, E, Eerr, f, S, Nc);
+}
+
+// ---- twisted boundary conditions (p->twist set) ----
+
+int orc_bloch_images(const orc::Params* p) { return orc::bloch_images(*p); }
+
+// One Bloch-summed Gaussian at x for a nucleus at Rc: out [10] = chi (re, im),
+// grad chi (re, im per component), lap chi (re, im).
+void orc_bloch_gaussian(double L, const double* x, const double* Rc, double zeta, const double* th, int M,
+                        double* out) {
+    orc::Cx<double> c, g[3], l;
+    orc::bloch_gaussian<double>(L, x, Rc, zeta, th, M, c, g, l);
+    out[0] = c.re; out[1] = c.im;
+    for (int mu = 0; mu < 3; ++mu) { out[2 + 2 * mu] = g[mu].re; out[3 + 2 * mu] = g[mu].im; }
+    out[8] = l.re; out[9] = l.im;
+}
+
+// One configuration with twisted orbitals: out_scalars = {ln|psi|, arg psi,
+// E_L, Re E_kin, Im E_kin, E_pot}; grad = Re grad_i ln psi; dlnpsi, del as in
+// orc_eval_config.  Returns 0, or -1 for a singular Slater block.
+int orc_eval_config_twist(const orc::Params* p, const double* R, const double* X, int derivs, double* out_scalars,
+                          double* grad, double* dlnpsi, double* del) {
+    if (!p->twist) return -2;
+    orc::TwistResult r = orc::eval_config_twist(*p, R, X, derivs != 0);
+    if (!r.ok) return -1;
+    out_scalars[0] = r.lnpsi; out_scalars[1] = r.phase; out_scalars[2] = r.el;
+    out_scalars[3] = r.ekin; out_scalars[4] = r.ekin_im; out_scalars[5] = r.epot;
+    const int Ne = p->n_up + p->n_dn;
+    if (grad) std::memcpy(grad, r.grad.data(), sizeof(double) * 3 * Ne);
+    if (derivs) {
+        std::memcpy(dlnpsi, r.dlnpsi.data(), sizeof(double) * 3 * p->N);
+        std::memcpy(del, r.del.data(), sizeof(double) * 3 * p->N);
+    }
+    return 0;
+}
+
+// Many configurations, twist twists[3 * (c / (nconf / K))] for configuration c
+// (K contiguous blocks); outputs as orc_eval_configs.
+int orc_eval_configs_twist(const orc::Params* p, const double* R, int nconf, const double* X, int K,
+                           const double* twists, int derivs, double* lnpsi, double* el, double* dlnpsi, double* del) {
+    const int Ne = p->n_up + p->n_dn, N3 = 3 * p->N;
+    if (K < 1 || nconf % K) return -2;
+    const int per = nconf / K;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic) reduction(+ : bad)
+    for (int c = 0; c < nconf; ++c) {
+        orc::Params q = *p;
+        q.twist = twists + 3 * (c / per);
+        orc::TwistResult r = orc::eval_config_twist(q, R, X + (size_t)c * 3 * Ne, derivs != 0);
+        if (!r.ok) { ++bad; continue; }
+        lnpsi[c] = r.lnpsi; el[c] = r.el;
+        if (derivs)
+            for (int k = 0; k < N3; ++k) {
+                dlnpsi[(size_t)c * N3 + k] = r.dlnpsi[k];
+                del[(size_t)c * N3 + k] = r.del[k];
+            }
+    }
+    return bad ? -1 : 0;
+}
+
+// VMC chains with twisted orbitals: walker w samples twist
+// twists[3 * (w / (W / K))] (K contiguous blocks, W a multiple of K); the
+// rest as orc_vmc_v.
+int orc_vmc_twists(const orc::Params* p, const double* R, const orc::ChainArgs* c, int K, const double* twists,
+                   double* X, double* acc, double* vacc, long long* n_accept, long long* n_try) {
+    if (K < 1 || c->W % K) return -2;
+    const int Ne = p->n_up + p->n_dn, stride = 3 + 9 * p->N, per = c->W / K;
+    orc::Rng rng(c->seed);
+    long long na = 0, nt = 0;
+#pragma omp parallel for schedule(dynamic) reduction(+ : na, nt)
+    for (int w = 0; w < c->W; ++w) {
+        orc::Params q = *p;
+        q.twist = twists + 3 * (w / per);
+        long long a = 0, t = 0;
+        orc::run_walker_twist(q, *c, rng, (uint32_t)w, R, X + (size_t)w * 3 * Ne, acc + (size_t)w * stride,
+                              vacc ? vacc + w : nullptr, &a, &t);
+        na += a; nt += t;
+    }
+    *n_accept = na; *n_try = nt;
+    return 0;
 }
 
 int orc_langevin(int n, const double* R, const double* Rprev, const double* f, const double* S,
