@@ -79,6 +79,25 @@ typedef struct {
      * must be exactly symmetric (fj[a][b] == fj[b][a]); INVALID otherwise. */
     double zeta_j;            /* Jastrow-orbital exponent, bohr^-2 (the SI uses 0.7933844) */
     const double* fj;         /* [N][N] symmetric coefficients (copied), or NULL         */
+    /* Twisted boundary conditions (SI, basis section: phi(r + nL) = e^{i theta.n} phi(r))
+     * and the k-point average of the main text.  n_twist = 0: the real
+     * Gamma-point form above.  n_twist = K > 0: FP64 form only, no fj, W a
+     * multiple of K with W/K >= 2 (INVALID otherwise).  The orbitals are then
+     * Bloch-summed Gaussians
+     *   chi_{a,g}(r) = sum_n e^{i theta.n} exp(-zeta_g |r - R_a - nL|^2)
+     * (images n = k + m, m in [-M, M]^3 around the nearest one k, with
+     * M = max(1, ceil(sqrt(40 / zeta_min) / L - 1/2))), complex, with the same
+     * real coefficients; the spin-up determinant carries theta and the
+     * spin-down one -theta; the Jastrow factor is unchanged.  Walkers come in K
+     * contiguous blocks of W/K, block t sampling |psi_t|^2 with twist
+     * twist[3t..3t+2]; E_L and the estimators take real parts.  Each block is
+     * reduced on its own and the results averaged with equal weights:
+     * E, f and the acceptance are the means over the twists, n_samples the
+     * sum, E_err = sqrt(sum E_err_t^2) / K and S = sum S_t / K^2.  The served
+     * form and the walker-sharded calls reject twisted handles. */
+    int32_t n_twist;          /* K, number of twists (0: Gamma point)                    */
+    int32_t pad_twist;        /* unused, 0                                               */
+    const double* twist;      /* [K][3] twist vectors theta, radians (copied), or NULL   */
 } qmc_params;
 
 /* Result of one energy/force evaluation.  f and cov are caller-allocated host

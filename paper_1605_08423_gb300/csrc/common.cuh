@@ -149,6 +149,22 @@ struct SysView {
     const double* fj;       // [N][N] e-e-n-n Jastrow coefficients (symmetric), or null
     const T* fjt;           // the same in the working precision, or null
     double zeta_j;          // their Gaussians' exponent
+    // Complex (twisted) orbitals, FP64 form only, else null: the measure
+    // kernel takes Re g_i, Re l_i from ext_gl [W][N][4] instead of forming
+    // them, leaves the orbital force terms to the twisted Pulay kernel and
+    // writes grad U (ext_gu [W][N][3]) and E_L (ext_el [W]) for it
+    const double* ext_gl;
+    double* ext_gu;
+    double* ext_el;
+};
+
+// Twisted boundary conditions: walker w samples twist t = w / Wk (K contiguous
+// blocks); the spin-up orbitals carry theta_t, the spin-down ones -theta_t.
+struct TwistView {
+    int K, Wk;              // twists, walkers per twist
+    int M;                  // Bloch-sum images per axis: m = -M..M around the nearest one
+    const double* theta;    // [K][3]
+    const double2* ph;      // [K][3][2M+1]: exp(i theta_mu m), m = -M..M
 };
 
 // Radial-function chain for f(t), t = |d|^2 with d the sin-periodised

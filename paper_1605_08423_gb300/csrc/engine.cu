@@ -88,6 +88,16 @@ struct qmc_system {
     bool langevin_first = true;
     uint32_t langevin_step_no = 0;
     double last_Nc = 0.0;
+    // twisted boundary conditions (FP64 form): K twists, walker blocks of W/K;
+    // the twist vectors and their phase table, Re g and Re l per electron,
+    // grad U and E_L per walker (measure kernel -> twisted Pulay kernel) and
+    // the per-twist results before the average
+    int K = 0;
+    TwistView tv{};
+    std::vector<double> twist_h;
+    double* d_theta = nullptr;
+    double2* d_tph = nullptr;
+    double *d_gl = nullptr, *d_gU = nullptr, *d_elt = nullptr, *d_tout = nullptr;
     long long nlaunch = 0;  // kernels launched by this handle
     bool profiling = false;
     std::vector<EventPair> events, free_events;
@@ -130,6 +140,15 @@ void enumerate_kvec(int mmax, std::vector<int4>& kv) {
             }
 }
 
+// Images per axis of the Bloch-summed Gaussians (twisted orbitals): every
+// omitted image lies more than sqrt(40 / zeta_min) away from the electron.
+int bloch_images(const qmc_params* p) {
+    double zmin = p->zeta[0];
+    for (int g = 1; g < p->n_gauss; ++g) zmin = p->zeta[g] < zmin ? p->zeta[g] : zmin;
+    const int M = (int)std::ceil(std::sqrt(40.0 / zmin) / p->L - 0.5);
+    return M < 1 ? 1 : M;
+}
+
 int validate(const qmc_params* p) {
     if (!p || !p->zeta || !p->coeff) return QMC_ERR_INVALID;
     if (p->n_protons < 2 || p->n_protons > 128 || (p->n_protons & 1)) return QMC_ERR_INVALID;
@@ -141,6 +160,15 @@ int validate(const qmc_params* p) {
     if (!(p->L > 0) || !(p->ewald_kappa > 0) || !(p->sigma > 0) || p->b_ee < 0 || p->b_ep < 0) return QMC_ERR_INVALID;
     if (p->fj && !(p->zeta_j > 0)) return QMC_ERR_INVALID;
     if (p->n_sweeps / p->measure_every < 1) return QMC_ERR_INVALID;
+    if (p->n_twist < 0) return QMC_ERR_INVALID;
+    if (p->n_twist > 0) {   // twisted boundary conditions: FP64 form, no e-e-n-n term, whole walker blocks
+        if (!p->twist || p->precision != QMC_FP64 || p->fj) return QMC_ERR_INVALID;
+        if (p->n_walkers % p->n_twist || p->n_walkers / p->n_twist < 2) return QMC_ERR_INVALID;
+        for (int k = 0; k < 3 * p->n_twist; ++k)
+            if (!std::isfinite(p->twist[k])) return QMC_ERR_INVALID;
+        for (int g = 0; g < p->n_gauss; ++g)
+            if (!(p->zeta[g] > 0)) return QMC_ERR_INVALID;
+    }
     if (p->fj) {   // the kernels use row a of f as its column a: f must be exactly symmetric
         const int N = p->n_protons;
         for (int a = 0; a < N; ++a)
@@ -166,7 +194,8 @@ size_t footprint(const qmc_params* p) {
     b += 4 * (3 * N + G + nk) + 8 * N * nk + 4;      // FP32 copies of R, zeta, kw, exp(i k.R); error word
     b += t * W * N * 6;                              // proposal trig
     b += 8 * 2 * W * 3 * N;                          // X, Xp
-    b += t * (W * N + W * N * n + 2 * W * n * n + 3 * W * N * n + W * N * n);   // uacc, Phi, Gt, D, Lp
+    const size_t tc = p->n_twist > 0 ? 16 : t;     // complex orbitals of the twisted form
+    b += t * W * N + tc * (W * N * n + 2 * W * n * n + 3 * W * N * n + W * N * n);   // uacc, Phi, Gt, D, Lp
     b += 8 * 2 * W + 8 * W * (3 + 9 * N) + 8 * W;   // logdet, acc, nacc
     b += 8 * W + 8 * 5;                              // V_L sums, pressure output
     b += 8 * (4 + 9 * N) + 8 * W * (3 * N + 1) + 8 * (4 + 3 * N + 9 * N * N);   // colsum, dev, out
@@ -174,6 +203,10 @@ size_t footprint(const qmc_params* p) {
     b += 8 * (3 * 3 * N + 3 * 9 * N * N);           // Langevin
     b += 8 * (2 * 3 * N + 2 * 9 * N * N);           // first simplified scheme between its halves
     if (p->fj) b += (t == 4 ? 12 : 8) * N * N;       // e-e-n-n Jastrow coefficients (+ FP32 copy)
+    if (p->n_twist > 0) {                            // twists, phase table, Re g / Re l, grad U, E_L, per-twist results
+        const size_t K = p->n_twist, M = bloch_images(p);
+        b += 8 * 3 * K + 16 * 3 * K * (2 * M + 1) + 8 * W * N * 4 + 8 * W * N * 3 + 8 * W + 8 * K * (4 + 3 * N + 9 * N * N);
+    }
     b += (size_t)kPoolAllocs * kPoolAlign;           // alignment slack of a carved handle
     if (t == 4) {                                    // tensor-core operands (mixed form)
         b += tc_coeff_bytes((int)B, (int)n);
@@ -224,6 +257,7 @@ SysView<T> view(qmc_system* h, int W) {
     s.vconst = h->d_vconst; s.dvpp = h->d_dvpp; s.err = h->d_err; s.vacc = h->d_vacc;
     s.fj = h->d_fj; s.zeta_j = h->p.zeta_j;
     s.fjt = (const T*)(sizeof(T) == 8 ? (const void*)h->d_fj : (const void*)h->d_fj32);
+    s.ext_gl = nullptr; s.ext_gu = nullptr; s.ext_el = nullptr;
     return s;
 }
 
@@ -345,8 +379,99 @@ double run_sampling(qmc_system* h) {
     return (double)W * total * N;
 }
 
+// ---- twisted boundary conditions (FP64 form, complex orbitals) ----
+
+// Complex Slater blocks at the current walker positions and their inverses.
+void recompute_twist(qmc_system* h, int W) {
+    EventPair ep;
+    prof_begin(h, KC_RECOMPUTE, ep);
+    SysView<double> s = view<double>(h, W);
+    h->nlaunch += 2;
+    launch_twist_orbitals(s, h->tv, h->d_X, W * h->N, (double2*)h->d_Phi, nullptr, nullptr, h->stream);
+    launch_twist_invert(W, h->N, h->n, (const double2*)h->d_Phi, (double2*)h->d_Gt, h->d_logdet, h->d_err, h->stream);
+    prof_end(h, ep);
+}
+
+// Local energy and force sample of every walker: complex orbital rows, Re g and
+// Re l, the measure kernel for everything real (Jastrow, Ewald, E_L), then the
+// complex orbital (Pulay) force terms.
+void measure_twist(qmc_system* h, int W, double* el, double* lnpsi, double* dl, double* de) {
+    SysView<double> s = view<double>(h, W);
+    const int N = h->N, n = h->n;
+    EventPair ep;
+    h->nlaunch += 4;
+    prof_begin(h, KC_ORB_MEAS, ep);
+    launch_twist_orbitals(s, h->tv, h->d_X, W * N, (double2*)h->d_Phi, (double2*)h->d_D, (double2*)h->d_Lp,
+                          h->stream);
+    launch_twist_gl(W * N, N, n, (const double2*)h->d_D, (const double2*)h->d_Lp, (const double2*)h->d_Gt, h->d_gl,
+                    h->stream);
+    prof_end(h, ep);
+    s.ext_gl = h->d_gl; s.ext_gu = h->d_gU; s.ext_el = h->d_elt;
+    prof_begin(h, KC_MEASURE, ep);
+    launch_measure<double>(s, h->d_X, (const double*)h->d_D, (const double*)h->d_Lp, (const double*)h->d_Gt,
+                           h->d_logdet, h->d_acc, el, lnpsi, dl, de, nullptr, nullptr, nullptr, nullptr, h->stream);
+    prof_end(h, ep);
+    prof_begin(h, KC_ADJOINT, ep);
+    launch_twist_pulay(s, h->tv, h->d_X, (const double2*)h->d_D, (const double2*)h->d_Lp, (const double2*)h->d_Gt,
+                       h->d_gU, h->d_elt, h->d_acc, dl, de, h->stream);
+    prof_end(h, ep);
+}
+
+double run_sampling_twist(qmc_system* h) {
+    const int W = h->W, N = h->N;
+    SysView<double> s = view<double>(h, W);
+    const Key key = make_key(h->p.seed);
+    const uint32_t md = h->md_step;
+    cudaMemsetAsync(h->d_acc, 0, sizeof(double) * (size_t)W * (3 + 9 * N), h->stream);
+    cudaMemsetAsync(h->d_vacc, 0, sizeof(double) * (size_t)W, h->stream);
+    cudaMemsetAsync(h->d_nacc, 0, sizeof(unsigned long long) * W, h->stream);
+    recompute_twist(h, W);
+    const int nw = h->first_call ? h->p.n_warmup : h->p.n_warmup_cont;
+    const int total = nw + h->p.n_sweeps;
+    for (int sw = 0; sw < total; ++sw) {
+        EventPair ep;
+        h->nlaunch += 3;
+        prof_begin(h, KC_PROPOSE, ep);
+        launch_propose<double>(W, N, h->p.L, h->d_X, h->d_Xp, (double*)h->d_ptp, (double*)h->d_uacc, key, md,
+                               (uint32_t)sw, h->p.sigma, h->w0, h->stream);
+        prof_end(h, ep);
+        prof_begin(h, KC_ORB_PROP, ep);
+        launch_twist_orbitals(s, h->tv, h->d_Xp, W * N, (double2*)h->d_Phi, nullptr, nullptr, h->stream);
+        prof_end(h, ep);
+        prof_begin(h, KC_SWEEP, ep);
+        launch_twist_sweep(s, h->tv, h->d_X, h->d_Xp, (const double*)h->d_ptp, (const double*)h->d_uacc,
+                           (const double2*)h->d_Phi, (double2*)h->d_Gt, h->d_nacc, h->stream);
+        prof_end(h, ep);
+        if ((sw + 1) % h->p.recompute_every == 0) recompute_twist(h, W);
+        if (sw >= nw && ((sw - nw + 1) % h->p.measure_every) == 0) measure_twist(h, W, nullptr, nullptr, nullptr, nullptr);
+    }
+    h->md_step++;
+    h->first_call = false;
+    return (double)W * total * N;
+}
+
+// Each twist's walker block reduced on its own, then the twist average.
+void reduce_twist(qmc_system* h, double moves) {
+    const int K = h->K, Wk = h->W / K, N = h->N;
+    const size_t stride = 3 + 9 * (size_t)N, olen = 4 + 3 * (size_t)N + 9 * (size_t)N * N;
+    for (int t = 0; t < K; ++t)
+        launch_reduce(Wk, N, moves / K, h->d_acc + (size_t)t * Wk * stride, h->d_nacc + (size_t)t * Wk, h->d_colsum,
+                      h->d_dev, h->d_tout + (size_t)t * olen, h->d_err, h->stream);
+    launch_twist_average(K, N, h->d_tout, h->d_out, h->stream);
+    h->nlaunch += 5 * K + 1;
+}
+
 template <typename T>
 void run_call(qmc_system* h) {
+    if (h->K) {
+        const double moves = run_sampling_twist(h);
+        EventPair ep;
+        prof_begin(h, KC_REDUCE, ep);
+        reduce_twist(h, moves);
+        prof_end(h, ep);
+        h->last_Nc = (double)h->W * (h->p.n_sweeps / h->p.measure_every);
+        return;
+    }
     const double moves = run_sampling<T>(h);
     EventPair ep;
     prof_begin(h, KC_REDUCE, ep);
@@ -408,6 +533,14 @@ int init_handle(const qmc_params* p, const double* R, void* block, size_t block_
         h->fj_h.assign(p->fj, p->fj + (size_t)h->N * h->N);
         h->p.fj = h->fj_h.data();
     }
+    if (p->n_twist > 0) {
+        h->K = p->n_twist;
+        h->twist_h.assign(p->twist, p->twist + 3 * (size_t)h->K);
+        h->p.twist = h->twist_h.data();
+    } else {
+        h->p.n_twist = 0;
+        h->p.twist = nullptr;
+    }
     std::vector<int4> kv;
     enumerate_kvec(h->mmax, kv);
     h->nk = (int)kv.size();
@@ -422,6 +555,7 @@ int init_handle(const qmc_params* p, const double* R, void* block, size_t block_
     }
     const int N = h->N, n = h->n, W = h->W, B = h->B, nk = h->nk;
     const size_t t = h->mixed ? sizeof(float) : sizeof(double);
+    const size_t tc = h->K ? sizeof(double2) : t;   // complex orbitals of the twisted form
     h->d_R = dalloc<double>(h, 3 * N, &rc);
     h->d_zeta = dalloc<double>(h, h->G, &rc);
     h->d_C64 = dalloc<double>(h, (size_t)B * n, &rc);
@@ -442,10 +576,10 @@ int init_handle(const qmc_params* p, const double* R, void* block, size_t block_
     h->d_X = dalloc<double>(h, (size_t)W * 3 * N, &rc);
     h->d_Xp = dalloc<double>(h, (size_t)W * 3 * N, &rc);
     h->d_uacc = dalloc<unsigned char>(h, t * W * N, &rc);
-    h->d_Phi = dalloc<unsigned char>(h, t * W * N * n, &rc);
-    h->d_Gt = dalloc<unsigned char>(h, t * W * 2 * n * n, &rc);
-    h->d_D = dalloc<unsigned char>(h, t * W * N * 3 * n, &rc);
-    h->d_Lp = dalloc<unsigned char>(h, t * W * N * n, &rc);
+    h->d_Phi = dalloc<unsigned char>(h, tc * W * N * n, &rc);
+    h->d_Gt = dalloc<unsigned char>(h, tc * W * 2 * n * n, &rc);
+    h->d_D = dalloc<unsigned char>(h, tc * W * N * 3 * n, &rc);
+    h->d_Lp = dalloc<unsigned char>(h, tc * W * N * n, &rc);
     h->d_logdet = dalloc<double>(h, 2 * (size_t)W, &rc);
     h->d_acc = dalloc<double>(h, (size_t)W * (3 + 9 * N), &rc);
     h->d_vacc = dalloc<double>(h, W, &rc);
@@ -470,6 +604,25 @@ int init_handle(const qmc_params* p, const double* R, void* block, size_t block_
     if (!h->fj_h.empty()) {
         h->d_fj = dalloc<double>(h, (size_t)N * N, &rc);
         if (h->mixed) h->d_fj32 = dalloc<float>(h, (size_t)N * N, &rc);
+    }
+    std::vector<double2> tph;
+    if (h->K) {
+        const int K = h->K, M = bloch_images(p);
+        h->d_theta = dalloc<double>(h, 3 * (size_t)K, &rc);
+        h->d_tph = dalloc<double2>(h, (size_t)K * 3 * (2 * M + 1), &rc);
+        h->d_gl = dalloc<double>(h, (size_t)W * N * 4, &rc);
+        h->d_gU = dalloc<double>(h, (size_t)W * N * 3, &rc);
+        h->d_elt = dalloc<double>(h, W, &rc);
+        h->d_tout = dalloc<double>(h, (size_t)K * (4 + 3 * N + 9 * (size_t)N * N), &rc);
+        // exp(i theta_mu m), m = -M..M, per twist and axis
+        for (int k = 0; k < K; ++k)
+            for (int mu = 0; mu < 3; ++mu)
+                for (int m = -M; m <= M; ++m) {
+                    const double a = h->twist_h[3 * k + mu] * m;
+                    tph.push_back(make_double2(std::cos(a), std::sin(a)));
+                }
+        h->tv.K = K; h->tv.Wk = W / K; h->tv.M = M;
+        h->tv.theta = h->d_theta; h->tv.ph = h->d_tph;
     }
     // The tcgen05 kernels serve N = 128 with 4 Gaussians per nucleus (n = 64
     // orbitals per spin), the configuration they are built, tuned and tested
@@ -500,6 +653,10 @@ int init_handle(const qmc_params* p, const double* R, void* block, size_t block_
     cudaMemcpyAsync(h->d_zeta, h->zeta_h.data(), sizeof(double) * h->G, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(h->d_C64, h->coeff_h.data(), sizeof(double) * B * n, cudaMemcpyHostToDevice, st);
     if (h->d_fj) cudaMemcpyAsync(h->d_fj, h->fj_h.data(), sizeof(double) * N * N, cudaMemcpyHostToDevice, st);
+    if (h->K) {
+        cudaMemcpyAsync(h->d_theta, h->twist_h.data(), sizeof(double) * 3 * h->K, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(h->d_tph, tph.data(), sizeof(double2) * tph.size(), cudaMemcpyHostToDevice, st);
+    }
     std::vector<float> fj32(h->fj_h.begin(), h->fj_h.end());
     if (h->d_fj32) cudaMemcpyAsync(h->d_fj32, fj32.data(), sizeof(float) * N * N, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(h->d_C32, c32.data(), sizeof(float) * B * n, cudaMemcpyHostToDevice, st);
@@ -601,7 +758,7 @@ int qmc_pressure(qmc_system* h, double T_kelvin, double* out) {
 }
 
 int qmc_shard_sample_device(qmc_system* h, const double* R_dev, double* sums_dev) {
-    if (!h || !R_dev || !sums_dev) return QMC_ERR_INVALID;
+    if (!h || !R_dev || !sums_dev || h->K) return QMC_ERR_INVALID;
     const int N = h->N;
     cudaMemcpyAsync(h->d_R, R_dev, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, h->stream);
     setup_tables(h);
@@ -615,7 +772,7 @@ int qmc_shard_sample_device(qmc_system* h, const double* R_dev, double* sums_dev
 }
 
 int qmc_shard_reduce_device(qmc_system* h, const double* sums_dev, double* out_dev, double* gram_dev) {
-    if (!h || !sums_dev || !out_dev || !gram_dev) return QMC_ERR_INVALID;
+    if (!h || !sums_dev || !out_dev || !gram_dev || h->K) return QMC_ERR_INVALID;
     EventPair ep;
     prof_begin(h, KC_REDUCE, ep);
     h->nlaunch += 4;
@@ -626,7 +783,7 @@ int qmc_shard_reduce_device(qmc_system* h, const double* sums_dev, double* out_d
 
 int qmc_shard_finish_device(qmc_system* h, const double* sums_dev, const double* gram_dev, double* out_dev,
                             long long walkers_total) {
-    if (!h || !sums_dev || !gram_dev || !out_dev || walkers_total < 2) return QMC_ERR_INVALID;
+    if (!h || !sums_dev || !gram_dev || !out_dev || walkers_total < 2 || h->K) return QMC_ERR_INVALID;
     EventPair ep;
     prof_begin(h, KC_REDUCE, ep);
     h->nlaunch += 1;
@@ -745,7 +902,8 @@ int qmc_eval_config(qmc_system* h, int n_conf, const double* X, const double* R,
     double* lp = el + n_conf;
     double* dl = lp + n_conf;
     double* de = dl + (size_t)n_conf * N3;
-    if (h->mixed) { recompute<float>(h, n_conf); measure<float>(h, n_conf, el, lp, dl, de); }
+    if (h->K) { recompute_twist(h, n_conf); measure_twist(h, n_conf, el, lp, dl, de); }
+    else if (h->mixed) { recompute<float>(h, n_conf); measure<float>(h, n_conf, el, lp, dl, de); }
     else { recompute<double>(h, n_conf); measure<double>(h, n_conf, el, lp, dl, de); }
     int rc = check_launch();
     if (rc != QMC_OK) return rc;

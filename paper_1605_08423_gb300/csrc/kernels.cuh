@@ -79,6 +79,22 @@ void launch_shard_reduce(int W, int N, const double* acc, const double* sums, do
                          int* err, cudaStream_t st);
 void launch_shard_finish(int N, const double* sums, const double* gram, double* out, cudaStream_t st);
 
+// k_twist.cu: twisted boundary conditions (FP64 form, complex orbitals).
+void launch_twist_orbitals(const SysView<double>& s, const TwistView& tv, const double* pos, int nrows,
+                           double2* val, double2* grad, double2* lap, cudaStream_t st);
+void launch_twist_invert(int W, int N, int n, const double2* Phi, double2* Gt, double* logdet, int* err,
+                         cudaStream_t st);
+void launch_twist_sweep(const SysView<double>& s, const TwistView& tv, double* X, const double* Xp, const double* ptp,
+                        const double* uacc, const double2* Phi, double2* Gt, unsigned long long* nacc,
+                        cudaStream_t st);
+void launch_twist_gl(int rows, int N, int n, const double2* D, const double2* Lp, const double2* Gt, double* gl,
+                     cudaStream_t st);
+void launch_twist_pulay(const SysView<double>& s, const TwistView& tv, const double* X, const double2* D,
+                        const double2* Lp, const double2* Gt, const double* gU, const double* elw, double* acc,
+                        double* out_dl, double* out_de, cudaStream_t st);
+size_t twist_pulay_smem_bytes(int N, int n);
+void launch_twist_average(int K, int N, const double* tout, double* out, cudaStream_t st);
+
 // k_langevin.cu (scheme: kLvAdopted, kLvFast or kLvNorogna)
 enum : int { kLvAdopted = 0, kLvFast = 1, kLvNorogna = 2 };
 void launch_langevin(int n3, double* R, double* Rprev, const double* f, const double* S, double* Sprev,

@@ -259,7 +259,7 @@ void qmc_server_destroy(qmc_server* s) {
 int qmc_server_add_trajectory(qmc_server* s, const qmc_params* p, const double* R0, double T_kelvin, double delta,
                               int s_mode, int* traj) {
     if (!s || !p || !R0 || !traj || !p->zeta || !p->coeff) return QMC_ERR_INVALID;
-    if (p->fj) return QMC_ERR_INVALID;   // the served form carries no e-e-n-n Jastrow term
+    if (p->fj || p->n_twist) return QMC_ERR_INVALID;   // the served form: no e-e-n-n term, Gamma point only
     if (s_mode != QMC_S_IDENTITY && s_mode != QMC_S_COV) return QMC_ERR_INVALID;
     const size_t fp = qmc_footprint_bytes(p);
     if (fp == 0) return QMC_ERR_INVALID;

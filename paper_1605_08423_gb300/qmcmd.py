@@ -50,6 +50,7 @@ class Params(C.Structure):
         ("sigma", C.c_double), ("seed", C.c_uint64),
         ("zeta", C.POINTER(C.c_double)), ("coeff", C.POINTER(C.c_double)),
         ("zeta_j", C.c_double), ("fj", C.POINTER(C.c_double)),
+        ("n_twist", C.c_int32), ("pad_twist", C.c_int32), ("twist", C.POINTER(C.c_double)),
     ]
 
 
@@ -178,6 +179,7 @@ class Config:
     seed: int = 1
     zeta_j: float = 0.7933844         # exponent of the e-e-n-n Jastrow orbitals
     fj: np.ndarray | None = None      # [N][N] symmetric e-e-n-n Jastrow coefficients (FP64 form), or None
+    twists: np.ndarray | None = None  # [K][3] twist vectors (twisted boundary conditions, FP64 form), or None
 
     @classmethod
     def from_workload(cls, wl: "synth.Workload", precision=QMC_FP64, **over):
@@ -192,10 +194,13 @@ class Config:
         self._c = _f64(self.coeff)
         kappa = 5.0 / self.L if self.kappa is None else self.kappa
         self._fj = None if self.fj is None else _f64(np.asarray(self.fj).reshape(self.N, self.N))
+        self._tw = None if self.twists is None else _f64(np.asarray(self.twists).reshape(-1, 3))
         return Params(self.N, len(self._z), self.walkers, self.sweeps, self.warmup, self.warmup_cont,
                       self.measure_every, self.recompute_every, self.precision, self.mmax, self.L, self.b_ee,
                       self.b_ep, kappa, self.sigma, self.seed, _p(self._z), _p(self._c), self.zeta_j,
-                      _p(self._fj) if self._fj is not None else C.cast(None, _dp))
+                      _p(self._fj) if self._fj is not None else C.cast(None, _dp),
+                      0 if self._tw is None else self._tw.shape[0], 0,
+                      _p(self._tw) if self._tw is not None else C.cast(None, _dp))
 
 
 def footprint_bytes(cfg: Config) -> int:

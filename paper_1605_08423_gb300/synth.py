@@ -119,6 +119,15 @@ def workload(name: str, **over) -> Workload:
     return Workload(name=name, **kw)
 
 
+def monkhorst_pack(q: int) -> np.ndarray:
+    """Twist vectors theta [q^3, 3] of the q x q x q Monkhorst-Pack mesh of a
+    cubic cell (the main text's k-point sampling; q = 4 for the 64-atom runs):
+    theta_mu = 2 pi (2 r - q - 1) / (2 q), r = 1..q, i.e. k = theta / L."""
+    u = (2.0 * np.arange(1, q + 1) - q - 1) / (2.0 * q)
+    g = np.stack(np.meshgrid(u, u, u, indexing="ij"), -1).reshape(-1, 3)
+    return 2.0 * math.pi * g
+
+
 def random_electrons(n_conf: int, n_elec: int, L: float, seed: int) -> np.ndarray:
     """Uniform electron configurations [n_conf, n_elec, 3] in the box (for parity inputs)."""
     rng = np.random.default_rng(seed + 104729)

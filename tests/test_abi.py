@@ -36,8 +36,10 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_struct_layouts_match_header(lib):
-    # qmc_params: 10 int32, 5 double, uint64, 2 pointers, then the e-e-n-n Jastrow double and pointer
-    assert C.sizeof(q.Params) == 10 * 4 + 5 * 8 + 8 + 2 * 8 + 8 + 8
+    # qmc_params: 10 int32, 5 double, uint64, 2 pointers, then the e-e-n-n Jastrow double and pointer,
+    # then the twists: 2 int32 and a pointer
+    assert C.sizeof(q.Params) == 10 * 4 + 5 * 8 + 8 + 2 * 8 + 8 + 8 + 2 * 4 + 8
+    assert q.Params.twist.offset == C.sizeof(q.Params) - 8
     assert C.sizeof(q.Result) == 6 * 8
     # qmc_served: 2 int, 4 double, 3 pointers, 5 double
     assert C.sizeof(q.Served) == 2 * 4 + 4 * 8 + 3 * 8 + 5 * 8
@@ -67,6 +69,19 @@ def test_invalid_parameters_rejected_without_gpu(lib):
     h = C.c_void_p()
     asym = q.Config.from_workload(wl, fj=A)
     assert lib.qmc_init(C.byref(asym.cparams()), (C.c_double * 48)(), C.byref(h)) == -1
+
+
+def test_twist_parameters_validated_without_gpu(lib):
+    wl = synth.workload("h16", walkers=8)
+    tw = synth.monkhorst_pack(2)[:4]
+    assert q.footprint_bytes(q.Config.from_workload(wl, twists=tw)) > q.footprint_bytes(q.Config.from_workload(wl))
+    assert q.footprint_bytes(q.Config.from_workload(wl, twists=tw, precision=q.QMC_MIXED)) == 0   # FP64 only
+    assert q.footprint_bytes(q.Config.from_workload(wl, twists=tw[:3])) == 0     # W not a multiple of K
+    assert q.footprint_bytes(q.Config.from_workload(wl, walkers=4, twists=tw)) == 0   # fewer than 2 per twist
+    assert q.footprint_bytes(q.Config.from_workload(wl, twists=tw, fj=np.eye(wl.N) * 0.1)) == 0
+    bad = tw.copy()
+    bad[1, 2] = np.nan
+    assert q.footprint_bytes(q.Config.from_workload(wl, twists=bad)) == 0
 
 
 def test_recompute_option_values(lib):
