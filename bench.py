@@ -59,6 +59,8 @@ def _args():
     ap.add_argument("--toy-steps", type=int, default=None, help="steps per trajectory of the timed toy launch")
     ap.add_argument("--no-jastrow34", action="store_true", help="skip the e-e-n-n Jastrow (FP64 form) leg")
     ap.add_argument("--jastrow34-only", action="store_true", help="run only that leg (one JSON line)")
+    ap.add_argument("--no-twist", action="store_true", help="skip the twisted-boundary-condition (FP64 form) leg")
+    ap.add_argument("--twist-only", action="store_true", help="run only that leg (one JSON line)")
     ap.add_argument("--trajectory", type=int, default=0,
                     help="run only an MD trajectory of this many Langevin steps (S = Cov(f) rebuilt every step) "
                          "at the headline size and print one JSON line")
@@ -365,6 +367,64 @@ def _jastrow34_legs(stream, calls, out, form, name, walkers):
                     "calls_timed": calls, "sm_mhz_median": clk.get("sm_mhz"), "clock_reasons": clk.get("reasons"),
                     "E": float(o[0].item())}
         sysq.close()
+
+
+def _twist_bench(stream, calls=5):
+    """Twisted boundary conditions with the k-point average (FP64 form): the
+    main text's 64-atom cell with its 4 x 4 x 4 Monkhorst-Pack mesh (64 twists),
+    h64 (N = 64, r_s = 1.4, 2 s-Gaussians/proton), 16 walkers per twist (1024),
+    4 measured sweeps + 1 continuation per call, a sample every sweep, inverse
+    recompute every 4 sweeps; after a warm-up call, `calls` calls timed one by
+    one (median, min, max, median SM clock), then one profiled call for the
+    per-kernel split.  The Gamma-point FP64 form at the same size is timed the
+    same way beside it."""
+    import torch
+    from paper_1605_08423_gb300 import qmcmd as q
+    from paper_1605_08423_gb300 import synth
+    tw = synth.monkhorst_pack(4)
+    wl = synth.workload("h64", walkers=16 * len(tw), sweeps=4, warmup=2)
+    R_dev = torch.tensor(wl.R, dtype=torch.float64, device="cuda")
+    out = {"metric": "electron moves/s and force-evals/s, twist-averaged (64 twists) and Gamma point",
+           "config": {"workload": f"h64: N=64 H, r_s=1.4, 2 s-Gaussians/proton, 4x4x4 Monkhorst-Pack twists, "
+                                  f"{wl.walkers} walkers (16 per twist), 4 sweeps (+1 continuation) per call, "
+                                  "sample every sweep, inverse recompute every 4 sweeps, FP64 form"}}
+    for tag, twists in (("twisted", tw), ("gamma", None)):
+        cfg = q.Config.from_workload(wl, precision=q.QMC_FP64, warmup=2, warmup_cont=1, measure_every=1,
+                                     recompute_every=4, twists=twists)
+        sysq = q.QMCSystem(cfg, wl.R)
+        sysq.set_stream(stream.cuda_stream)
+        o = torch.zeros(4 + 3 * wl.N + 9 * wl.N * wl.N, dtype=torch.float64, device="cuda")
+        sysq.energy_forces_device(R_dev, o)          # warm-up call
+        sysq.sync()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(torch.cuda.current_device())
+        ts = []
+        for _ in range(calls):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sysq.energy_forces_device(R_dev, o)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        clk = clocks.stop()
+        sysq.sync()
+        sysq.set_profiling(True)
+        sysq.kernel_times()
+        sysq.energy_forces_device(R_dev, o)
+        kt = sysq.kernel_times()
+        sysq.set_profiling(False)
+        sysq.sync()
+        ts.sort()
+        t = ts[len(ts) // 2]
+        moves = wl.walkers * wl.N * (cfg.sweeps + cfg.warmup_cont)
+        out[tag] = {"electron_moves_per_s": moves / t, "force_evals_per_s": wl.walkers * cfg.sweeps / t,
+                    "ms_per_call_median": 1e3 * t, "ms_per_call_min": 1e3 * ts[0], "ms_per_call_max": 1e3 * ts[-1],
+                    "calls_timed": calls, "sm_mhz_median": clk.get("sm_mhz"), "clock_reasons": clk.get("reasons"),
+                    "kernel_ms_per_call": {k: round(v[0], 3) for k, v in kt.items() if v[1]},
+                    "E": float(o[0].item()), "E_err": float(o[1].item())}
+        sysq.close()
+    out["twisted_over_gamma_time"] = out["twisted"]["ms_per_call_median"] / out["gamma"]["ms_per_call_median"]
+    return out
 
 
 def _toy_cpu_baseline():
@@ -756,6 +816,13 @@ def run_ours(args, ws, rank, local):
         except Exception as exc:   # a secondary leg: report, do not lose the headline line
             j34 = {"error": f"{type(exc).__name__}: {exc}"}
 
+    twl = None
+    if not args.no_twist and rank == 0:
+        try:
+            twl = _twist_bench(stream)
+        except Exception as exc:   # a secondary leg: report, do not lose the headline line
+            twl = {"error": f"{type(exc).__name__}: {exc}"}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = _cpu_baseline(wl)
@@ -794,6 +861,7 @@ def run_ours(args, ws, rank, local):
                "serving": serving,
                "toy_langevin": toy,
                "jastrow34_fp64": j34,
+               "twist_fp64": twl,
                "peaks": peak_kind,
                "result": {"E": res["E"], "E_err": res["E_err"], "accept": res["accept"], "Nc": res["Nc"]}}
         print(json.dumps(out), flush=True)
@@ -815,7 +883,7 @@ def main():
     if args.trajectory > 0:
         run_trajectory(args, rank, local)
         return
-    if args.jastrow34_only:
+    if args.jastrow34_only or args.twist_only:
         import torch
         import __graft_entry__
         __graft_entry__.build()
@@ -823,7 +891,7 @@ def main():
         stream = torch.cuda.Stream()
         torch.cuda.set_stream(stream)
         if rank == 0:
-            print(json.dumps(_jastrow34_bench(stream)), flush=True)
+            print(json.dumps(_jastrow34_bench(stream) if args.jastrow34_only else _twist_bench(stream)), flush=True)
         return
     run_ours(args, ws, rank, local)
 
