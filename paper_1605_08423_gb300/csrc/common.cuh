@@ -149,13 +149,6 @@ struct SysView {
     const double* fj;       // [N][N] e-e-n-n Jastrow coefficients (symmetric), or null
     const T* fjt;           // the same in the working precision, or null
     double zeta_j;          // their Gaussians' exponent
-    // Complex (twisted) orbitals, FP64 form only, else null: the measure
-    // kernel takes Re g_i, Re l_i from ext_gl [W][N][4] instead of forming
-    // them, leaves the orbital force terms to the twisted Pulay kernel and
-    // writes grad U (ext_gu [W][N][3]) and E_L (ext_el [W]) for it
-    const double* ext_gl;
-    double* ext_gu;
-    double* ext_el;
 };
 
 // Twisted boundary conditions: walker w samples twist t = w / Wk (K contiguous

@@ -89,15 +89,17 @@ struct qmc_system {
     uint32_t langevin_step_no = 0;
     double last_Nc = 0.0;
     // twisted boundary conditions (FP64 form): K twists, walker blocks of W/K;
-    // the twist vectors and their phase table, Re g and Re l per electron,
-    // grad U and E_L per walker (measure kernel -> twisted Pulay kernel) and
-    // the per-twist results before the average
+    // the twist vectors and their phase table; the real inputs of the FP64
+    // measure kernel (D', Lp' with Re g, Re l in column 0, unit inverse rows,
+    // zero coefficients); E_L and ln|psi| per walker; the per-twist results
+    // before the average
     int K = 0;
     TwistView tv{};
     std::vector<double> twist_h;
     double* d_theta = nullptr;
     double2* d_tph = nullptr;
-    double *d_gl = nullptr, *d_gU = nullptr, *d_elt = nullptr, *d_tout = nullptr;
+    double *d_Dr = nullptr, *d_Lpr = nullptr, *d_Gtr = nullptr, *d_Czero = nullptr;
+    double *d_elt = nullptr, *d_lpt = nullptr, *d_tout = nullptr;
     long long nlaunch = 0;  // kernels launched by this handle
     bool profiling = false;
     std::vector<EventPair> events, free_events;
@@ -205,7 +207,8 @@ size_t footprint(const qmc_params* p) {
     if (p->fj) b += (t == 4 ? 12 : 8) * N * N;       // e-e-n-n Jastrow coefficients (+ FP32 copy)
     if (p->n_twist > 0) {                            // twists, phase table, Re g / Re l, grad U, E_L, per-twist results
         const size_t K = p->n_twist, M = bloch_images(p);
-        b += 8 * 3 * K + 16 * 3 * K * (2 * M + 1) + 8 * W * N * 4 + 8 * W * N * 3 + 8 * W + 8 * K * (4 + 3 * N + 9 * N * N);
+        b += 8 * 3 * K + 16 * 3 * K * (2 * M + 1) + 8 * (W * N * 4 * n + 2 * W * n * n + B * n) + 8 * 2 * W +
+             8 * K * (4 + 3 * N + 9 * N * N);
     }
     b += (size_t)kPoolAllocs * kPoolAlign;           // alignment slack of a carved handle
     if (t == 4) {                                    // tensor-core operands (mixed form)
@@ -257,7 +260,6 @@ SysView<T> view(qmc_system* h, int W) {
     s.vconst = h->d_vconst; s.dvpp = h->d_dvpp; s.err = h->d_err; s.vacc = h->d_vacc;
     s.fj = h->d_fj; s.zeta_j = h->p.zeta_j;
     s.fjt = (const T*)(sizeof(T) == 8 ? (const void*)h->d_fj : (const void*)h->d_fj32);
-    s.ext_gl = nullptr; s.ext_gu = nullptr; s.ext_el = nullptr;
     return s;
 }
 
@@ -392,9 +394,11 @@ void recompute_twist(qmc_system* h, int W) {
     prof_end(h, ep);
 }
 
-// Local energy and force sample of every walker: complex orbital rows, Re g and
-// Re l, the measure kernel for everything real (Jastrow, Ewald, E_L), then the
-// complex orbital (Pulay) force terms.
+// Local energy and force sample of every walker: complex orbital rows; Re g and
+// Re l into column 0 of D' and Lp'; the FP64 measure kernel on D', Lp', unit
+// inverse rows and zero coefficients (so it computes E_L = Re(H psi / psi), the
+// Jastrow and Ewald force terms with vv = Re g + grad U, and adds nothing from
+// its orbital force phase); then the complex orbital (Pulay) force terms.
 void measure_twist(qmc_system* h, int W, double* el, double* lnpsi, double* dl, double* de) {
     SysView<double> s = view<double>(h, W);
     const int N = h->N, n = h->n;
@@ -403,17 +407,19 @@ void measure_twist(qmc_system* h, int W, double* el, double* lnpsi, double* dl, 
     prof_begin(h, KC_ORB_MEAS, ep);
     launch_twist_orbitals(s, h->tv, h->d_X, W * N, (double2*)h->d_Phi, (double2*)h->d_D, (double2*)h->d_Lp,
                           h->stream);
-    launch_twist_gl(W * N, N, n, (const double2*)h->d_D, (const double2*)h->d_Lp, (const double2*)h->d_Gt, h->d_gl,
-                    h->stream);
+    launch_twist_gl(W * N, N, n, (const double2*)h->d_D, (const double2*)h->d_Lp, (const double2*)h->d_Gt, h->d_Dr,
+                    h->d_Lpr, h->stream);
     prof_end(h, ep);
-    s.ext_gl = h->d_gl; s.ext_gu = h->d_gU; s.ext_el = h->d_elt;
+    SysView<double> s0 = s;
+    s0.C = h->d_Czero;
+    double* elw = el ? el : h->d_elt;
     prof_begin(h, KC_MEASURE, ep);
-    launch_measure<double>(s, h->d_X, (const double*)h->d_D, (const double*)h->d_Lp, (const double*)h->d_Gt,
-                           h->d_logdet, h->d_acc, el, lnpsi, dl, de, nullptr, nullptr, nullptr, nullptr, h->stream);
+    launch_measure<double>(s0, h->d_X, h->d_Dr, h->d_Lpr, h->d_Gtr, h->d_logdet, h->d_acc, elw,
+                           lnpsi ? lnpsi : h->d_lpt, dl, de, nullptr, nullptr, nullptr, nullptr, h->stream);
     prof_end(h, ep);
     prof_begin(h, KC_ADJOINT, ep);
     launch_twist_pulay(s, h->tv, h->d_X, (const double2*)h->d_D, (const double2*)h->d_Lp, (const double2*)h->d_Gt,
-                       h->d_gU, h->d_elt, h->d_acc, dl, de, h->stream);
+                       elw, h->d_acc, dl, de, h->stream);
     prof_end(h, ep);
 }
 
@@ -610,9 +616,12 @@ int init_handle(const qmc_params* p, const double* R, void* block, size_t block_
         const int K = h->K, M = bloch_images(p);
         h->d_theta = dalloc<double>(h, 3 * (size_t)K, &rc);
         h->d_tph = dalloc<double2>(h, (size_t)K * 3 * (2 * M + 1), &rc);
-        h->d_gl = dalloc<double>(h, (size_t)W * N * 4, &rc);
-        h->d_gU = dalloc<double>(h, (size_t)W * N * 3, &rc);
+        h->d_Dr = dalloc<double>(h, (size_t)W * N * 3 * n, &rc);
+        h->d_Lpr = dalloc<double>(h, (size_t)W * N * n, &rc);
+        h->d_Gtr = dalloc<double>(h, (size_t)W * 2 * n * n, &rc);
+        h->d_Czero = dalloc<double>(h, (size_t)B * n, &rc);
         h->d_elt = dalloc<double>(h, W, &rc);
+        h->d_lpt = dalloc<double>(h, W, &rc);
         h->d_tout = dalloc<double>(h, (size_t)K * (4 + 3 * N + 9 * (size_t)N * N), &rc);
         // exp(i theta_mu m), m = -M..M, per twist and axis
         for (int k = 0; k < K; ++k)
@@ -656,6 +665,10 @@ int init_handle(const qmc_params* p, const double* R, void* block, size_t block_
     if (h->K) {
         cudaMemcpyAsync(h->d_theta, h->twist_h.data(), sizeof(double) * 3 * h->K, cudaMemcpyHostToDevice, st);
         cudaMemcpyAsync(h->d_tph, tph.data(), sizeof(double2) * tph.size(), cudaMemcpyHostToDevice, st);
+        cudaMemsetAsync(h->d_Dr, 0, sizeof(double) * (size_t)W * N * 3 * n, st);
+        cudaMemsetAsync(h->d_Lpr, 0, sizeof(double) * (size_t)W * N * n, st);
+        cudaMemsetAsync(h->d_Czero, 0, sizeof(double) * (size_t)B * n, st);
+        launch_twist_unit_rows(W, n, h->d_Gtr, st);
     }
     std::vector<float> fj32(h->fj_h.begin(), h->fj_h.end());
     if (h->d_fj32) cudaMemcpyAsync(h->d_fj32, fj32.data(), sizeof(float) * N * N, cudaMemcpyHostToDevice, st);

@@ -387,16 +387,7 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
     }
 
     // ---- P2: g_i = sum_j D_ij G_ji, l_i = sum_j Lp_ij G_ji (warp per electron,
-    // lanes over the orbitals: coalesced rows of D, Lp and G^T).  Twisted
-    // (complex) orbitals: their real parts, formed by the twist kernels.
-    if (s.ext_gl) {
-        for (int idx = tid; idx < 4 * N; idx += nt) {
-            const int i = idx >> 2, c = idx & 3;
-            const T v = (T)s.ext_gl[((size_t)w * N + i) * 4 + c];
-            if (c < 3) gi[3 * i + c] = v;
-            else li[i] = v;
-        }
-    } else
+    // lanes over the orbitals: coalesced rows of D, Lp and G^T)
     for (int i = warp; i < N; i += nw) {
         const int sp = i / n, il = i - sp * n;
         const T* grow = Gt + (((size_t)w * 2 + sp) * n + il) * n;
@@ -845,7 +836,7 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
             }
             __syncthreads();
         }
-    } else if (!s.ext_gl) {   // (twisted orbitals: the twisted Pulay kernel takes these terms)
+    } else {
     T* bufA = (T*)uni;                       // Y^T [j][i], later K [j][i]
     T* bufG = bufA + (size_t)np * ldt;       // G   [j][i] = G_{j,i}
     T* bufS = bufG + (size_t)np * ldt;       // G^T [i][j], later C^T tile [j][b] (stride 68)
@@ -1036,10 +1027,6 @@ __global__ void __launch_bounds__(256, kSplit ? 3 : 1) measure_kernel(SysView<T>
             eg_out[(size_t)w * 9 * N + idx] = (float)(c < 6 ? et[6 * i + c] : gU[3 * i + c - 6]);
         }
         if (tid == 0) elw[w] = EL;
-    }
-    if (s.ext_gl) {   // for the twisted Pulay kernel
-        for (int idx = tid; idx < 3 * N; idx += nt) s.ext_gu[(size_t)w * 3 * N + idx] = (double)gU[idx];
-        if (tid == 0) s.ext_el[w] = EL;
     }
     if (tid == 0) {
         aw[0] += 1.0; aw[1] += EL; aw[2] += EL * EL;

@@ -425,15 +425,18 @@ void launch_twist_sweep(const SysView<double>& s, const TwistView& tv, double* X
 }
 
 // ---------------------------------------------------------------------------
-// g_i = sum_j D_ij G^T[i][j] and l_i = sum_j Lp_ij G^T[i][j] of every electron;
-// the measure kernel needs their real parts (out [rows][4] = Re g, Re l), the
-// only way the complex determinant enters E_L besides the force terms:
-//   Re(H psi / psi) = -1/2 sum_i [ Re l_i + 2 Re g_i . grad_i U + lap_i U + |grad_i U|^2 ] + V.
-// One warp per electron.
+// g_i = sum_j D_ij G^T[i][j] and l_i = sum_j Lp_ij G^T[i][j] of every electron.
+// Their real parts are the only way the complex determinant enters E_L:
+//   Re(H psi / psi) = -1/2 sum_i [ Re l_i + 2 Re g_i . grad_i U + lap_i U + |grad_i U|^2 ] + V,
+// and the e-n Jastrow force terms take vv_i = Re g_i + grad_i U.  The FP64
+// measure kernel computes all of that from real rows D, Lp and inverse rows
+// G^T: it is handed D' and Lp' whose column 0 holds Re g_i and Re l_i (the
+// other columns stay zero) and G'^T rows e_0 (twist_unit_rows), so its
+// sum_j D'_ij G'^T[i][j] is Re g_i exactly.  One warp per electron.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) twist_gl_kernel(int rows, int N, int n, const double2* __restrict__ D,
+__global__ void __launch_bounds__(256) twist_gl_kernel(int rows, int n, const double2* __restrict__ D,
                                                        const double2* __restrict__ Lp, const double2* __restrict__ Gt,
-                                                       double* __restrict__ gl) {
+                                                       int N, double* __restrict__ Dr, double* __restrict__ Lpr) {
     const int lane = threadIdx.x & 31, r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (r >= rows) return;
     const int w = r / N, i = r - w * N, sp = i / n, il = i - sp * n;
@@ -451,19 +454,35 @@ __global__ void __launch_bounds__(256) twist_gl_kernel(int rows, int N, int n, c
     }
     g0 = warp_sum(g0); g1 = warp_sum(g1); g2 = warp_sum(g2); l = warp_sum(l);
     if (lane == 0) {
-        gl[(size_t)r * 4] = g0; gl[(size_t)r * 4 + 1] = g1; gl[(size_t)r * 4 + 2] = g2; gl[(size_t)r * 4 + 3] = l;
+        Dr[(size_t)r * 3 * n] = g0;
+        Dr[((size_t)r * 3 + 1) * n] = g1;
+        Dr[((size_t)r * 3 + 2) * n] = g2;
+        Lpr[(size_t)r * n] = l;
     }
 }
 
-void launch_twist_gl(int rows, int N, int n, const double2* D, const double2* Lp, const double2* Gt, double* gl,
-                     cudaStream_t st) {
-    twist_gl_kernel<<<(rows + 7) / 8, 256, 0, st>>>(rows, N, n, D, Lp, Gt, gl);
+void launch_twist_gl(int rows, int N, int n, const double2* D, const double2* Lp, const double2* Gt, double* Dr,
+                     double* Lpr, cudaStream_t st) {
+    twist_gl_kernel<<<(rows + 7) / 8, 256, 0, st>>>(rows, n, D, Lp, Gt, N, Dr, Lpr);
+}
+
+// G'^T[w][sp][i][j] = (j == 0) for every walker-spin block (written once per handle).
+__global__ void twist_unit_rows_kernel(size_t total, int n, double* __restrict__ Gtr) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < total) Gtr[k] = (k % (size_t)n) == 0 ? 1.0 : 0.0;
+}
+
+void launch_twist_unit_rows(int W, int n, double* Gtr, cudaStream_t st) {
+    const size_t total = (size_t)W * 2 * n * n;
+    twist_unit_rows_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(total, n, Gtr);
 }
 
 // ---------------------------------------------------------------------------
 // Orbital (Pulay) terms of the force estimators with complex orbitals, one CTA
 // per walker, after the measure kernel has accumulated everything else of the
-// sample (the Jastrow and Ewald terms) and written grad U and E_L.  Per spin
+// sample (the Jastrow and Ewald terms; its own orbital force phase runs on zero
+// coefficients and adds nothing) and written E_L.  grad_i U (the Pade e-e and
+// e-n terms of the sin-periodised Jastrow) is formed here again.  Per spin
 // block, with G the inverse (G[j][i] = G^T[i][j]),
 //   Y_ij = -1/2 Lp_ij - grad_i U . D_ij,  K = G Y G,  Z_bi = sum_j C_bj G_ji,  P_bi = sum_j C_bj K_ji,
 //   d ln|psi| / dR_a += -Re sum_i sum_{b in a} Z_bi grad chi_b(r_i)
@@ -478,7 +497,6 @@ __global__ void __launch_bounds__(256) twist_pulay_kernel(SysView<double> s, Twi
                                                           const double2* __restrict__ D,
                                                           const double2* __restrict__ Lp,
                                                           const double2* __restrict__ Gt,
-                                                          const double* __restrict__ gU_all,
                                                           const double* __restrict__ elw, double* __restrict__ acc,
                                                           double* __restrict__ out_dl, double* __restrict__ out_de) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -489,10 +507,46 @@ __global__ void __launch_bounds__(256) twist_pulay_kernel(SysView<double> s, Twi
     double2* T1 = YK + (size_t)n * n;           // [n][n]  (Y G)[i][i']
     double* fdl = (double*)(T1 + (size_t)n * n); // [3N]
     double* fde = fdl + N3;                      // [3N]
+    double* et = fde + N3;                       // [N][6] (sin, cos)(pi x / L) of the electrons
+    double* gUw = et + 6 * N;                    // [N][3] grad_i U
     const double* th = tv.theta + 3 * (w / tv.Wk);
     const double2* ph = tv.ph + (size_t)(w / tv.Wk) * 3 * (2 * M + 1);
-    for (int c = tid; c < N3; c += nt) { fdl[c] = 0.0; fde[c] = 0.0; }
-    const double* gUw = gU_all + (size_t)w * 3 * N;
+    for (int c = tid; c < N3; c += nt) {
+        fdl[c] = 0.0; fde[c] = 0.0;
+        double sn, cs;
+        sincospi(X[(size_t)w * N3 + c] * s.iL, &sn, &cs);
+        et[6 * (c / 3) + c % 3] = sn;
+        et[6 * (c / 3) + 3 + c % 3] = cs;
+    }
+    __syncthreads();
+    for (int i = tid; i < N; i += nt) {          // grad_i U: d t / dx = 2 p, p = (L/pi) sin cos
+        double g[3] = {0, 0, 0};
+        const double* ei = et + 6 * i;
+        for (int j = 0; j < N; ++j) {
+            if (j == i) continue;
+            double sd[3], cd[3], t;
+            disp_trig(ei, et + 6 * j, s.ell, sd, cd, t);
+            const double r = qsqrt_pair(t);
+            double u, u1, u2, f1, f2, f3;
+            pade_ee(s.b_ee, r, u, u1, u2);
+            rho_to_t(r, u1, u2, 0.0, f1, f2, f3);
+#pragma unroll
+            for (int mu = 0; mu < 3; ++mu) g[mu] += 2.0 * f1 * (s.ell * sd[mu] * cd[mu]);
+        }
+        for (int a = 0; a < N; ++a) {
+            double sd[3], cd[3], t;
+            disp_trig(ei, s.ptrig + 6 * a, s.ell, sd, cd, t);
+            const double r = qsqrt_pair(t);
+            double u, u1, u2, u3, f1, f2, f3;
+            pade_ep(s.b_ep, s.Zj, r, u, u1, u2, u3);
+            rho_to_t(r, u1, u2, 0.0, f1, f2, f3);
+#pragma unroll
+            for (int mu = 0; mu < 3; ++mu) g[mu] += 2.0 * f1 * (s.ell * sd[mu] * cd[mu]);
+        }
+#pragma unroll
+        for (int mu = 0; mu < 3; ++mu) gUw[3 * i + mu] = g[mu];
+    }
+    __syncthreads();
     for (int sp = 0; sp < 2; ++sp) {
         const double sg = sp == 0 ? 1.0 : -1.0;
         const double2* Gsp = Gt + ((size_t)w * 2 + sp) * n * n;
@@ -586,18 +640,18 @@ __global__ void __launch_bounds__(256) twist_pulay_kernel(SysView<double> s, Twi
 }
 
 size_t twist_pulay_smem_bytes(int N, int n) {
-    return (size_t)3 * n * n * sizeof(double2) + (size_t)6 * N * sizeof(double);
+    return (size_t)3 * n * n * sizeof(double2) + (size_t)15 * N * sizeof(double);
 }
 
 void launch_twist_pulay(const SysView<double>& s, const TwistView& tv, const double* X, const double2* D,
-                        const double2* Lp, const double2* Gt, const double* gU, const double* elw, double* acc,
-                        double* out_dl, double* out_de, cudaStream_t st) {
+                        const double2* Lp, const double2* Gt, const double* elw, double* acc, double* out_dl,
+                        double* out_de, cudaStream_t st) {
     const size_t smem = twist_pulay_smem_bytes(s.N, s.n);
     static size_t attr = 0;
     if (smem > attr &&
         cudaFuncSetAttribute(twist_pulay_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess)
         attr = smem;
-    twist_pulay_kernel<<<s.W, 256, smem, st>>>(s, tv, X, D, Lp, Gt, gU, elw, acc, out_dl, out_de);
+    twist_pulay_kernel<<<s.W, 256, smem, st>>>(s, tv, X, D, Lp, Gt, elw, acc, out_dl, out_de);
 }
 
 // ---------------------------------------------------------------------------

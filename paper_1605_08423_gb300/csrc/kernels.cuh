@@ -87,11 +87,12 @@ void launch_twist_invert(int W, int N, int n, const double2* Phi, double2* Gt, d
 void launch_twist_sweep(const SysView<double>& s, const TwistView& tv, double* X, const double* Xp, const double* ptp,
                         const double* uacc, const double2* Phi, double2* Gt, unsigned long long* nacc,
                         cudaStream_t st);
-void launch_twist_gl(int rows, int N, int n, const double2* D, const double2* Lp, const double2* Gt, double* gl,
-                     cudaStream_t st);
+void launch_twist_gl(int rows, int N, int n, const double2* D, const double2* Lp, const double2* Gt, double* Dr,
+                     double* Lpr, cudaStream_t st);
+void launch_twist_unit_rows(int W, int n, double* Gtr, cudaStream_t st);
 void launch_twist_pulay(const SysView<double>& s, const TwistView& tv, const double* X, const double2* D,
-                        const double2* Lp, const double2* Gt, const double* gU, const double* elw, double* acc,
-                        double* out_dl, double* out_de, cudaStream_t st);
+                        const double2* Lp, const double2* Gt, const double* elw, double* acc, double* out_dl,
+                        double* out_de, cudaStream_t st);
 size_t twist_pulay_smem_bytes(int N, int n);
 void launch_twist_average(int K, int N, const double* tout, double* out, cudaStream_t st);
 
