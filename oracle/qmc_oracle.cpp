@@ -1099,6 +1099,10 @@ static void reduce_twists(int K, int W, int N3, const double* acc, double* E, do
 //   <z z^T> = S^{-1},  Dt = (1-e^{-a D})/a,  Db = (1-e^{-2 a D})/(2a)  (Dt = Db = D at a = 0).
 // z = L^{-T} xi with S = L L^T (Cholesky) and xi ~ N(0, I).  Optional noise
 // correction (SI "Noise correction"): T -> T - D/2.  box > 0 wraps R' into [0, box).
+// R_prev - R is the displacement of the previous step: in the periodic box
+// (box > 0) its minimum image, each component reduced by the nearest multiple
+// of box (a position wrapped into the box between the two steps would
+// otherwise enter with a jump of one box side).
 // scheme selects the variant of the SI:
 //   LV_ADOPTED  the equation above;
 //   LV_FAST     the faster iteration scheme (Eq. finaldyn):
@@ -1129,11 +1133,15 @@ static int langevin(int n, const double* R, const double* Rprev, const double* f
             Lc[(size_t)i * n + j] = t / Lc[(size_t)j * n + j];
         }
     }
-    std::vector<double> g(n), y(n), x(n), z(n);
+    std::vector<double> g(n), y(n), x(n), z(n), dR(n);
+    for (int j = 0; j < n; ++j) {
+        dR[j] = Rprev[j] - R[j];
+        if (box > 0) dR[j] -= box * std::nearbyint(dR[j] / box);
+    }
     for (int i = 0; i < n; ++i) {
         double s = 0;
         if (scheme != LV_NOROGNA)
-            for (int j = 0; j < n; ++j) s += (Sprev[(size_t)i * n + j] - S[(size_t)i * n + j]) * (Rprev[j] - R[j]);
+            for (int j = 0; j < n; ++j) s += (Sprev[(size_t)i * n + j] - S[(size_t)i * n + j]) * dR[j];
         g[i] = f[i] - s / (2.0 * Db);
     }
     for (int i = 0; i < n; ++i) {                       // L y = g

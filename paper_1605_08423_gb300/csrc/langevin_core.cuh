@@ -61,6 +61,10 @@ __device__ inline void cta_backward(int n, const double* Lc, double* w, double* 
 // with Dt = (1 - e^{-alpha D})/alpha, Db = (1 - e^{-2 alpha D})/(2 alpha) for
 // the adopted scheme with alpha > 0 and Dt = Db = D otherwise; kLvNorogna drops
 // the S_prev term; identity != 0 takes S = I (no Cholesky, no S_prev term).
+// R_prev - R is the previous step's displacement: in the periodic box (box > 0)
+// its minimum image, each component reduced by the nearest multiple of box (a
+// position wrapped into the box between the steps would otherwise enter with a
+// jump of one box side).
 // xi ~ N(0, I) from Philox (counter = (component, md, 0, kLangevin)).
 //
 // Aliasing: R, Rprev, f, S and Sprev are read, R' is returned in the shared
@@ -85,12 +89,21 @@ __device__ inline bool cta_langevin_step(int n, const double* R, const double* R
         Db = (1.0 - exp(-2.0 * alpha * delta)) / (2.0 * alpha);
     }
     if (!identity && !cta_cholesky(n, S, Lc, red)) return false;
+    const bool two_time = !identity && scheme != kLvNorogna;
+    if (two_time) {   // R_prev - R (minimum image), kept in r1 until R' is formed
+        for (int j = tid; j < n; j += nt) {
+            double dj = Rprev[j] - R[j];
+            if (box > 0.0) dj -= box * rint(dj / box);
+            r1[j] = dj;
+        }
+        __syncthreads();
+    }
     // g = f - (S_prev - S)(R_prev - R) / (2 Db);  xi;  keep R
     for (int i = tid; i < n; i += nt) {
         double t = f[i];
-        if (!identity && scheme != kLvNorogna) {
+        if (two_time) {
             double s = 0.0;
-            for (int j = 0; j < n; ++j) s += (Sprev[(size_t)i * n + j] - S[(size_t)i * n + j]) * (Rprev[j] - R[j]);
+            for (int j = 0; j < n; ++j) s += (Sprev[(size_t)i * n + j] - S[(size_t)i * n + j]) * r1[j];
             t -= s / (2.0 * Db);
         }
         g[i] = t;

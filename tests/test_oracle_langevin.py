@@ -216,3 +216,44 @@ def test_first_simplified_scheme_samples_canonical_with_position_dependent_S():
         if t > 1000:
             acc.append(R ** 2)
     assert abs(float(np.mean(acc)) - 1.0) < 0.15
+
+
+def test_previous_displacement_is_the_minimum_image():
+    """In the periodic box the S_prev term takes the previous step's displacement
+    R_prev - R as a minimum image: shifting R_prev by whole box sides leaves
+    the step unchanged."""
+    n, L = 12, 5.0
+    rng = np.random.default_rng(12)
+    R = rng.uniform(0, L, n)
+    Rprev = R + 0.1 * rng.standard_normal(n)
+    S, Sp = _spd(n, 3), _spd(n, 4)
+    f, xi = rng.standard_normal(n), rng.standard_normal(n)
+    a = orc.langevin(R, Rprev, f, S, Sp, 0.3, 0.05, 2.0, xi, box=L)
+    shift = L * rng.integers(-2, 3, n)
+    b = orc.langevin(R, Rprev + shift, f, S, Sp, 0.3, 0.05, 2.0, xi, box=L)
+    assert np.max(np.abs(a - b)) < 1e-12
+
+
+def test_position_dependent_S_in_a_periodic_box():
+    """V = -A cos(2 pi x / L) with S(x) = 1 + 0.8 sin^2(2 pi x / L) on a periodic
+    box where positions wrap every few hundred steps: the two-time scheme
+    samples the canonical <cos(2 pi x / L)> = I_1(A/T) / I_0(A/T) (a jump of one
+    box side in R_prev - R at each wrap would bias it far outside this band)."""
+    from scipy.special import i0, i1
+    L, A, T, d, n, steps = 4.0, 1.0, 1.0, 0.02, 64, 4000
+    k = 2 * math.pi / L
+    rng = np.random.default_rng(3)
+    R = rng.uniform(0, L, n)
+    Rprev = R.copy()
+    acc = []
+    for t in range(steps):
+        S = np.diag(1 + 0.8 * np.sin(k * R) ** 2)
+        Sp = np.diag(1 + 0.8 * np.sin(k * Rprev) ** 2)
+        Rn = orc.langevin(R, Rprev, -A * k * np.sin(k * R), S, Sp, T, d, 0.0, rng.standard_normal(n), box=L)
+        Rprev, R = R, Rn
+        if t > 500:
+            acc.append(np.cos(k * R))
+    a = np.array(acc)
+    err = a.mean(axis=0).std() / math.sqrt(n)
+    exact = i1(A / T) / i0(A / T)
+    assert abs(a.mean() - exact) < 4 * err + 0.01, (a.mean(), exact, err)
