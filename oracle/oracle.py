@@ -112,6 +112,9 @@ def lib():
         L.orc_toy_noise.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, _dp]
         L.orc_toy_run_ids.argtypes = [C.POINTER(ToyArgs), C.c_int, C.POINTER(C.c_int), _dp, _dp]
         L.orc_reduce_twists.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.orc_empirical_energy.restype = C.c_double
+        L.orc_empirical_energy.argtypes = [C.c_int, C.c_double, _dp, C.c_double]
+        L.orc_empirical_s.argtypes = [C.c_int, C.c_double, _dp, C.c_double, C.c_double, _dp]
         L.orc_bloch_images.restype = C.c_int
         L.orc_bloch_images.argtypes = [C.POINTER(Params)]
         L.orc_bloch_gaussian.argtypes = [C.c_double, _dp, _dp, C.c_double, _dp, C.c_int, _dp]
@@ -296,6 +299,23 @@ def reduce_twists(acc, N, K):
     f = np.zeros(N3); S = np.zeros((N3, N3))
     lib().orc_reduce_twists(K, W, N3, _ptr(acc), C.byref(E), C.byref(Ee), _ptr(f), _ptr(S), C.byref(Nc))
     return dict(E=E.value, E_err=Ee.value, f=f, S=S, Nc=Nc.value)
+
+
+# ---- empirical acceleration matrix ----
+
+def empirical_energy(R, L, lam) -> float:
+    """Screened-Coulomb proton pair energy sum_{a<b} sum_images exp(-r/lam)/r (images within L)."""
+    R = np.ascontiguousarray(R, dtype=np.float64).reshape(-1, 3)
+    return lib().orc_empirical_energy(R.shape[0], L, _ptr(R), lam)
+
+
+def empirical_s(R, L, lam, mu) -> np.ndarray:
+    """S = H + mu I, H the Hessian of empirical_energy ([3N][3N])."""
+    R = np.ascontiguousarray(R, dtype=np.float64).reshape(-1, 3)
+    n3 = 3 * R.shape[0]
+    S = np.zeros((n3, n3))
+    lib().orc_empirical_s(R.shape[0], L, _ptr(R), lam, mu, _ptr(S))
+    return S
 
 
 # ---- twisted boundary conditions ----

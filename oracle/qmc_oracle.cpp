@@ -34,6 +34,9 @@
 //                          energy and the R-derivatives against finite
 //                          differences; the plane-wave limit; the chain against
 //                          a brute-force integral; the twist-average rule
+//   empirical S .......... closed forms of one pair (with and without images
+//                          inside the cutoff), finite differences of the
+//                          energy, symmetry, translation sum rule, mu shift
 //   toy model ............ finite differences of U, H, S^{-1}; the S-difference
 //                          corrections against the cumbersome term (Gauss-Hermite
 //                          averages); stationary <U> against quadratures of the
@@ -1094,6 +1097,83 @@ static void reduce_twists(int K, int W, int N3, const double* acc, double* E, do
 }
 
 // ---------------------------------------------------------------------------
+// Empirical acceleration matrix (main text, conclusions: S = H + mu I with H
+// the Hessian of an accurate and cheap empirical potential, mu > 0 chosen
+// where H is not positive definite; the paper names no potential).  Reading:
+// the screened-Coulomb (Yukawa) pair potential of the protons in the electron
+// gas,
+//   V(R) = sum_{a<b} sum_{n : |d_ab + nL| < L} v(|d_ab + nL|),  v(r) = exp(-r / lambda) / r,
+// with d_ab = R_a - R_b and the images n taken within one box side, lambda the
+// screening length.  H = d^2 V / dR dR by nested forward-mode dual numbers.
+// ---------------------------------------------------------------------------
+template <class V>
+struct D1 {   // value and one tangent over a value type that may itself be a D1
+    V v, d;
+    D1() : v(0.0), d(0.0) {}
+    D1(double c) : v(c), d(0.0) {}
+    D1(const V& a, const V& b) : v(a), d(b) {}
+};
+template <class V> static inline D1<V> operator+(const D1<V>& a, const D1<V>& b) { return D1<V>(a.v + b.v, a.d + b.d); }
+template <class V> static inline D1<V> operator-(const D1<V>& a, const D1<V>& b) { return D1<V>(a.v - b.v, a.d - b.d); }
+template <class V> static inline D1<V> operator*(const D1<V>& a, const D1<V>& b) {
+    return D1<V>(a.v * b.v, a.d * b.v + a.v * b.d);
+}
+template <class V> static inline D1<V> operator/(const D1<V>& a, const D1<V>& b) {
+    const V q = a.v / b.v;
+    return D1<V>(q, (a.d - q * b.d) / b.v);
+}
+template <class V> static inline D1<V> operator*(double c, const D1<V>& a) { return D1<V>(c * a.v, c * a.d); }
+template <class V> static inline D1<V> operator-(const D1<V>& a, double c) { return D1<V>(a.v - c, a.d); }
+template <class V> static inline D1<V>& operator+=(D1<V>& a, const D1<V>& b) { a = a + b; return a; }
+template <class V> static inline D1<V> exp(const D1<V>& a) { const V e = exp(a.v); return D1<V>(e, e * a.d); }
+template <class V> static inline D1<V> sqrt(const D1<V>& a) { const V r = sqrt(a.v); return D1<V>(r, a.d / (2.0 * r)); }
+template <class V> static inline double val(const D1<V>& a) { return val(a.v); }
+
+template <class E>
+static E empirical_energy(int N, double L, const E* R, double lambda) {
+    E V(0.0);
+    for (int a = 0; a < N; ++a)
+        for (int b = a + 1; b < N; ++b) {
+            E d[3];
+            for (int mu = 0; mu < 3; ++mu) {
+                d[mu] = R[3 * a + mu] - R[3 * b + mu];
+                d[mu] = d[mu] - L * std::nearbyint(val(d[mu]) / L);   // minimum image
+            }
+            for (int n0 = -2; n0 <= 2; ++n0)
+                for (int n1 = -2; n1 <= 2; ++n1)
+                    for (int n2 = -2; n2 <= 2; ++n2) {
+                        const int nn[3] = {n0, n1, n2};
+                        E r2(0.0);
+                        for (int mu = 0; mu < 3; ++mu) {
+                            const E x = d[mu] - (-L * nn[mu]);
+                            r2 += x * x;
+                        }
+                        if (!(val(r2) < L * L)) continue;
+                        const E r = sqrt(r2);
+                        V += exp(E(0.0) - (1.0 / lambda) * r) / r;
+                    }
+        }
+    return V;
+}
+
+// S = H + mu I ([3N][3N]); one pass of second-order duals per pair of coordinates.
+static void empirical_s(int N, double L, const double* R, double lambda, double mu, double* S) {
+    typedef D1<D1<double>> E2;
+    const int n3 = 3 * N;
+    std::vector<E2> x(n3);
+    for (int i = 0; i < n3; ++i)
+        for (int j = i; j < n3; ++j) {
+            for (int k = 0; k < n3; ++k) x[k] = E2(R[k]);
+            x[i].d.v = 1.0;     // outer tangent along coordinate i
+            x[j].v.d = 1.0;     // inner tangent along coordinate j
+            const E2 V = empirical_energy<E2>(N, L, x.data(), lambda);
+            const double h = V.d.d;
+            S[(size_t)i * n3 + j] = h + (i == j ? mu : 0.0);
+            S[(size_t)j * n3 + i] = h + (i == j ? mu : 0.0);
+        }
+}
+
+// ---------------------------------------------------------------------------
 // Adopted integrator (SI, "Better integration scheme, the adopted one"):
 //   R' = R + Dt S^{-1} [ f - (S_prev - S)(R_prev - R) / (2 Db) ] + sqrt(2 T Db) z,
 //   <z z^T> = S^{-1},  Dt = (1-e^{-a D})/a,  Db = (1-e^{-2 a D})/(2a)  (Dt = Db = D at a = 0).
@@ -1632,6 +1712,16 @@ void orc_reduce(int W, int N3, const double* acc, double* E, double* Eerr, doubl
 void orc_reduce_twists(int K, int W, int N3, const double* acc, double* E, double* Eerr, double* f, double* S,
                        double* Nc) {
     orc::reduce_twists(K, W, N3, acc, E, Eerr, f, S, Nc);
+}
+
+// ---- empirical acceleration matrix S = H + mu I ----
+
+double orc_empirical_energy(int N, double L, const double* R, double lambda) {
+    return orc::empirical_energy<double>(N, L, R, lambda);
+}
+
+void orc_empirical_s(int N, double L, const double* R, double lambda, double mu, double* S) {
+    orc::empirical_s(N, L, R, lambda, mu, S);
 }
 
 // ---- twisted boundary conditions (p->twist set) ----
