@@ -45,7 +45,7 @@ enum {
 };
 
 enum { QMC_FP64 = 0, QMC_MIXED = 1 };          /* precision forms */
-enum { QMC_S_IDENTITY = 0, QMC_S_COV = 1 };    /* acceleration matrix of langevin_step */
+enum { QMC_S_IDENTITY = 0, QMC_S_COV = 1, QMC_S_EMPIRICAL = 2 };   /* acceleration matrix of langevin_step */
 
 /*
  * System and sampler parameters (the wavefunction of the paper's Eq. for
@@ -202,7 +202,11 @@ int qmc_shard_finish_device(qmc_system* h, const double* sums_dev, const double*
  * with (R_prev, S_prev) the pair of the previous call kept in h (equal to the
  * current pair on the first call).  s_mode QMC_S_IDENTITY: S = I, alpha = 0
  * (conventional first-order Langevin); QMC_S_COV: S as given and
- * alpha = 0.122 N_c of the last qmc_energy_forces call unless alpha > 0.
+ * alpha = 0.122 N_c of the last qmc_energy_forces call unless alpha > 0;
+ * QMC_S_EMPIRICAL: S = H + mu I at the current R built on the device (see
+ * qmc_set_empirical_s; the S argument is ignored), alpha as given (>= 0; 0
+ * gives Dt = Db = Delta).  In the periodic box R_prev - R is taken as the
+ * minimum image (the previous step's displacement).
  * R (host, [3N]) is updated in place and wrapped into [0, L).  Noise from
  * Philox (key = seed, counter = (component, step, 0, 7)).
  * Errors: INVALID, NOT_PD, CUDA.
@@ -213,6 +217,27 @@ int langevin_step(qmc_system* h, double* R, const double* f, const double* S,
 /* Same, device pointers, asynchronous (R_dev in/out). */
 int langevin_step_device(qmc_system* h, double* R_dev, const double* f_dev, const double* S_dev,
                          double T_kelvin, double delta, int s_mode, double alpha);
+
+/*
+ * Empirical acceleration matrix (main text, conclusions: S = H + mu I with H the
+ * Hessian of an accurate and cheap empirical potential and mu > 0 where H is
+ * not positive definite; the paper names no potential).  H here is the Hessian
+ * of the screened-Coulomb (Yukawa) pair potential of the protons,
+ *   V = sum_{a<b} sum_{n : |d_ab + nL| < L} exp(-r/lambda) / r,  r = |d_ab + nL|,
+ * images within one box side.  It has the three uniform translations as zero
+ * modes, so mu > 0 is needed for a positive definite S.
+ * qmc_set_empirical_s sets lambda (bohr; <= 0: the Thomas-Fermi length
+ * 1/sqrt(4 k_F / pi), k_F = (3 pi^2 N / L^3)^(1/3), the default) and mu
+ * (hartree / bohr^2, >= 0; default 0.5) for s_mode QMC_S_EMPIRICAL.  A mu
+ * below minus the lowest eigenvalue of H makes the step fail with NOT_PD (its
+ * Cholesky factorisation of S), and the caller raises mu.
+ * qmc_empirical_s writes S = H + mu I at nuclei R (host [N][3]) into S (host
+ * [3N][3N]); the _device form takes device pointers and is asynchronous.
+ * Errors: INVALID, CUDA.
+ */
+int qmc_set_empirical_s(qmc_system* h, double lambda, double mu);
+int qmc_empirical_s(qmc_system* h, const double* R, double* S);
+int qmc_empirical_s_device(qmc_system* h, const double* R_dev, double* S_dev);
 
 /*
  * First simplified scheme of the SI (Eq. smartMarkov), which needs S at the

@@ -86,6 +86,8 @@ struct qmc_system {
     bool lv_noise_correction = false;    // QMC_OPT_NOISE_CORRECTION
     bool ns_recompute = false;           // QMC_OPT_RECOMPUTE == QMC_RECOMPUTE_NEWTON (mixed form only)
     bool langevin_first = true;
+    // QMC_S_EMPIRICAL: screening length (bohr) and shift (Ha/bohr^2) of S = H + mu I
+    double emp_lambda = 0.0, emp_mu = 0.5;
     uint32_t langevin_step_no = 0;
     double last_Nc = 0.0;
     // twisted boundary conditions (FP64 form): K twists, walker blocks of W/K;
@@ -149,6 +151,13 @@ int bloch_images(const qmc_params* p) {
     for (int g = 1; g < p->n_gauss; ++g) zmin = p->zeta[g] < zmin ? p->zeta[g] : zmin;
     const int M = (int)std::ceil(std::sqrt(40.0 / zmin) / p->L - 0.5);
     return M < 1 ? 1 : M;
+}
+
+// Thomas-Fermi screening length of the electron gas of N electrons in the box:
+// k_F = (3 pi^2 N / L^3)^(1/3), k_TF^2 = 4 k_F / pi (hartree units), lambda = 1 / k_TF.
+double thomas_fermi_length(int N, double L) {
+    const double kF = std::cbrt(3.0 * kPi * kPi * N / (L * L * L));
+    return 1.0 / std::sqrt(4.0 * kF / kPi);
 }
 
 int validate(const qmc_params* p) {
@@ -681,6 +690,7 @@ int init_handle(const qmc_params* p, const double* R, void* block, size_t block_
     if (h->d_ahat) prepare_tc_adjoint_coeff(h->d_C32, N, h->G, n, h->d_ahat, st);
     setup_tables(h);
     launch_init_walkers(W, N, p->L, h->d_R, h->d_X, make_key(p->seed), 0u, st);
+    h->emp_lambda = thomas_fermi_length(N, p->L);
     rc = check_launch();
     // host arrays above are pageable, so their copies have been staged already
     if (rc == QMC_OK && wait) rc = cuda_rc(cudaStreamSynchronize(st));
@@ -809,7 +819,8 @@ int qmc_shard_finish_device(qmc_system* h, const double* sums_dev, const double*
 int langevin_step_device(qmc_system* h, double* R_dev, const double* f_dev, const double* S_dev, double T_kelvin,
                          double delta, int s_mode, double alpha) {
     if (!h || !R_dev || !f_dev || (!S_dev && s_mode == QMC_S_COV)) return QMC_ERR_INVALID;
-    if (s_mode != QMC_S_IDENTITY && s_mode != QMC_S_COV) return QMC_ERR_INVALID;
+    if (s_mode != QMC_S_IDENTITY && s_mode != QMC_S_COV && s_mode != QMC_S_EMPIRICAL) return QMC_ERR_INVALID;
+    if (s_mode == QMC_S_EMPIRICAL && alpha < 0) return QMC_ERR_INVALID;
     if (!(delta > 0) || T_kelvin < 0) return QMC_ERR_INVALID;
     double T_ha = T_kelvin * kBoltzmannHaPerK;
     if (h->lv_noise_correction) {       // SI "Noise correction": 2 T D = 2 T_target D - D^2
@@ -819,8 +830,12 @@ int langevin_step_device(qmc_system* h, double* R_dev, const double* f_dev, cons
     const int n3 = 3 * h->N;
     cudaStream_t st = h->stream;
     const int identity = s_mode == QMC_S_IDENTITY;
-    if (!identity)
+    if (s_mode == QMC_S_COV)
         cudaMemcpyAsync(h->d_S, S_dev, sizeof(double) * n3 * n3, cudaMemcpyDeviceToDevice, st);
+    if (s_mode == QMC_S_EMPIRICAL) {   // S = H + mu I at the current positions
+        h->nlaunch += 1;
+        launch_empirical_s(h->N, h->p.L, R_dev, h->emp_lambda, h->emp_mu, h->d_S, st);
+    }
     if (h->langevin_first) {
         cudaMemcpyAsync(h->d_Rprev, R_dev, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st);
         if (!identity) cudaMemcpyAsync(h->d_Sprev, h->d_S, sizeof(double) * n3 * n3, cudaMemcpyDeviceToDevice, st);
@@ -828,7 +843,8 @@ int langevin_step_device(qmc_system* h, double* R_dev, const double* f_dev, cons
         h->langevin_first = false;
     }
     double a = 0.0;
-    if (!identity) a = alpha > 0 ? alpha : 0.122 * h->last_Nc;
+    if (s_mode == QMC_S_COV) a = alpha > 0 ? alpha : 0.122 * h->last_Nc;
+    if (s_mode == QMC_S_EMPIRICAL) a = alpha;
     EventPair ep;
     prof_begin(h, KC_LANGEVIN, ep);
     h->nlaunch += 1;
@@ -837,6 +853,30 @@ int langevin_step_device(qmc_system* h, double* R_dev, const double* f_dev, cons
     prof_end(h, ep);
     h->langevin_step_no++;
     return check_launch();
+}
+
+int qmc_set_empirical_s(qmc_system* h, double lambda, double mu) {
+    if (!h || !std::isfinite(lambda) || !std::isfinite(mu) || mu < 0) return QMC_ERR_INVALID;
+    h->emp_lambda = lambda > 0 ? lambda : thomas_fermi_length(h->N, h->p.L);
+    h->emp_mu = mu;
+    return QMC_OK;
+}
+
+int qmc_empirical_s_device(qmc_system* h, const double* R_dev, double* S_dev) {
+    if (!h || !R_dev || !S_dev) return QMC_ERR_INVALID;
+    h->nlaunch += 1;
+    launch_empirical_s(h->N, h->p.L, R_dev, h->emp_lambda, h->emp_mu, S_dev, h->stream);
+    return check_launch();
+}
+
+int qmc_empirical_s(qmc_system* h, const double* R, double* S) {
+    if (!h || !R || !S) return QMC_ERR_INVALID;
+    const int n3 = 3 * h->N;
+    cudaMemcpyAsync(h->d_Rl, R, sizeof(double) * n3, cudaMemcpyHostToDevice, h->stream);
+    int rc = qmc_empirical_s_device(h, h->d_Rl, h->d_Lwork);
+    if (rc != QMC_OK) return rc;
+    cudaMemcpyAsync(S, h->d_Lwork, sizeof(double) * n3 * n3, cudaMemcpyDeviceToHost, h->stream);
+    return read_err(h);
 }
 
 int langevin_step(qmc_system* h, double* R, const double* f, const double* S, double T_kelvin, double delta,

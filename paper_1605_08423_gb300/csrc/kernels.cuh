@@ -96,6 +96,9 @@ void launch_twist_pulay(const SysView<double>& s, const TwistView& tv, const dou
 size_t twist_pulay_smem_bytes(int N, int n);
 void launch_twist_average(int K, int N, const double* tout, double* out, cudaStream_t st);
 
+// k_empirical.cu: S = H + mu I, H the Hessian of the screened-Coulomb proton pair potential.
+void launch_empirical_s(int N, double L, const double* R, double lambda, double mu, double* S, cudaStream_t st);
+
 // k_langevin.cu (scheme: kLvAdopted, kLvFast or kLvNorogna)
 enum : int { kLvAdopted = 0, kLvFast = 1, kLvNorogna = 2 };
 void launch_langevin(int n3, double* R, double* Rprev, const double* f, const double* S, double* Sprev,

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libqmcmd.so")
 
 QMC_FP64, QMC_MIXED = 0, 1
-QMC_S_IDENTITY, QMC_S_COV = 0, 1
+QMC_S_IDENTITY, QMC_S_COV, QMC_S_EMPIRICAL = 0, 1, 2
 NKERNEL = 9
 QMC_OPT_TENSOR_CORES, QMC_OPT_TC_ADJOINT, QMC_OPT_INTEGRATOR, QMC_OPT_NOISE_CORRECTION = 1, 2, 3, 4
 QMC_OPT_RECOMPUTE = 5
@@ -98,6 +98,9 @@ def lib():
         L.qmc_energy_forces_device.argtypes = [vp, vp, vp]
         L.langevin_step.argtypes = [vp, _dp, _dp, _dp, C.c_double, C.c_double, C.c_int, C.c_double]
         L.langevin_step_device.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, C.c_int, C.c_double]
+        L.qmc_set_empirical_s.argtypes = [vp, C.c_double, C.c_double]
+        L.qmc_empirical_s.argtypes = [vp, _dp, _dp]
+        L.qmc_empirical_s_device.argtypes = [vp, vp, vp]
         L.langevin_first_predict.argtypes = [vp, _dp, _dp, _dp, C.c_double, C.c_double]
         L.langevin_first_correct.argtypes = [vp, _dp, _dp]
         L.qmc_eval_config.argtypes = [vp, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
@@ -244,6 +247,16 @@ class QMCSystem:
         _chk(lib().langevin_step(self._h, _p(Rn), _p(_f64(f)), _p(Sa), T_kelvin, delta, s_mode, alpha),
              "langevin_step")
         return Rn
+
+    def set_empirical_s(self, lam: float = 0.0, mu: float = 0.5):
+        """Parameters of S = H + mu I for s_mode QMC_S_EMPIRICAL (lam <= 0: Thomas-Fermi length)."""
+        _chk(lib().qmc_set_empirical_s(self._h, float(lam), float(mu)), "qmc_set_empirical_s")
+
+    def empirical_s(self, R) -> np.ndarray:
+        """S = H + mu I at nuclei R ([3N][3N]; the screened-Coulomb proton pair Hessian)."""
+        S = np.zeros((3 * self.N, 3 * self.N))
+        _chk(lib().qmc_empirical_s(self._h, _p(_f64(R)), _p(S)), "qmc_empirical_s")
+        return S
 
     def eval_config(self, X, R) -> dict:
         X = _f64(X)
