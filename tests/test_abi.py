@@ -84,6 +84,14 @@ def test_twist_parameters_validated_without_gpu(lib):
     assert q.footprint_bytes(q.Config.from_workload(wl, twists=bad)) == 0
 
 
+def test_acceleration_matrix_modes(lib):
+    assert (q.QMC_S_IDENTITY, q.QMC_S_COV, q.QMC_S_EMPIRICAL) == (0, 1, 2)
+    src = open(os.path.join(ROOT, "include", "qmcmd.h")).read()
+    assert "QMC_S_EMPIRICAL = 2" in src
+    assert lib.qmc_set_empirical_s(None, 0.7, 0.5) == -1      # no handle
+    assert lib.qmc_empirical_s(None, None, None) == -1
+
+
 def test_recompute_option_values(lib):
     assert q.QMC_OPT_RECOMPUTE == 5 and (q.QMC_RECOMPUTE_FP64, q.QMC_RECOMPUTE_NEWTON) == (0, 1)
     assert lib.qmc_set_option(None, q.QMC_OPT_RECOMPUTE, 0) == -1      # no handle
