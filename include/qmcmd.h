@@ -219,6 +219,22 @@ int langevin_step_device(qmc_system* h, double* R_dev, const double* f_dev, cons
                          double T_kelvin, double delta, int s_mode, double alpha);
 
 /*
+ * Twists sharded over processes (one GPU each; twisted handles only): each
+ * process's handle samples its own K_r of the K twists, all with the same
+ * walkers per twist, and qmc_energy_forces_device gives its average over them
+ * in out_dev.  qmc_twist_partial_device turns that into the process's
+ * contribution part_dev = [K_r E, (K_r E_err)^2, N_c, K_r accept, K_r f, K_r^2 S]
+ * (4 + 3N + 9N^2 doubles); after the caller sums the contributions over the
+ * processes (an all-reduce), qmc_twist_combine_device writes the average over
+ * all K_total twists in the layout of qmc_energy_forces_device (the rule of the
+ * n_twist comment: means, N_c summed, E_err = sqrt(sum E_err_t^2) / K,
+ * S = sum S_t / K^2).  Device pointers, asynchronous.  Errors: INVALID (a
+ * handle without twists, K_total below its K), CUDA.
+ */
+int qmc_twist_partial_device(qmc_system* h, const double* out_dev, double* part_dev);
+int qmc_twist_combine_device(qmc_system* h, const double* part_dev, int K_total, double* out_dev);
+
+/*
  * Empirical acceleration matrix (main text, conclusions: S = H + mu I with H the
  * Hessian of an accurate and cheap empirical potential and mu > 0 where H is
  * not positive definite; the paper names no potential).  H here is the Hessian

@@ -855,6 +855,20 @@ int langevin_step_device(qmc_system* h, double* R_dev, const double* f_dev, cons
     return check_launch();
 }
 
+int qmc_twist_partial_device(qmc_system* h, const double* out_dev, double* part_dev) {
+    if (!h || !out_dev || !part_dev || !h->K) return QMC_ERR_INVALID;
+    h->nlaunch += 1;
+    launch_twist_partial(h->K, h->N, out_dev, part_dev, h->stream);
+    return check_launch();
+}
+
+int qmc_twist_combine_device(qmc_system* h, const double* part_dev, int K_total, double* out_dev) {
+    if (!h || !part_dev || !out_dev || !h->K || K_total < h->K) return QMC_ERR_INVALID;
+    h->nlaunch += 1;
+    launch_twist_combine(K_total, h->N, part_dev, out_dev, h->stream);
+    return check_launch();
+}
+
 int qmc_set_empirical_s(qmc_system* h, double lambda, double mu) {
     if (!h || !std::isfinite(lambda) || !std::isfinite(mu) || mu < 0) return QMC_ERR_INVALID;
     h->emp_lambda = lambda > 0 ? lambda : thomas_fermi_length(h->N, h->p.L);

@@ -684,4 +684,41 @@ void launch_twist_average(int K, int N, const double* tout, double* out, cudaStr
     twist_average_kernel<<<(len + 255) / 256, 256, 0, st>>>(K, 3 * N, tout, out);
 }
 
+// Twists sharded over processes: a process whose handle averaged K_r of the K
+// twists contributes [K_r E, (K_r E_err)^2, N_c, K_r accept, K_r f, K_r^2 S];
+// the sum of the contributions over the processes, divided as below, is the
+// average over all K twists (the same combination rule, since
+// K_r^2 E_err,r^2 = sum_{t in r} E_err,t^2 and K_r^2 S_r = sum_{t in r} S_t).
+__global__ void twist_partial_kernel(double Kr, int N3, const double* __restrict__ out, double* __restrict__ part) {
+    const int len = 4 + N3 + N3 * N3;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= len) return;
+    const double v = out[c];
+    if (c == 1) part[c] = (Kr * v) * (Kr * v);
+    else if (c == 2) part[c] = v;
+    else if (c < 4 + N3) part[c] = Kr * v;
+    else part[c] = Kr * Kr * v;
+}
+
+__global__ void twist_combine_kernel(double K, int N3, const double* __restrict__ part, double* __restrict__ out) {
+    const int len = 4 + N3 + N3 * N3;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= len) return;
+    const double v = part[c];
+    if (c == 1) out[c] = sqrt(v) / K;
+    else if (c == 2) out[c] = v;
+    else if (c < 4 + N3) out[c] = v / K;
+    else out[c] = v / (K * K);
+}
+
+void launch_twist_partial(int Kr, int N, const double* out, double* part, cudaStream_t st) {
+    const int len = 4 + 3 * N + 9 * N * N;
+    twist_partial_kernel<<<(len + 255) / 256, 256, 0, st>>>((double)Kr, 3 * N, out, part);
+}
+
+void launch_twist_combine(int K, int N, const double* part, double* out, cudaStream_t st) {
+    const int len = 4 + 3 * N + 9 * N * N;
+    twist_combine_kernel<<<(len + 255) / 256, 256, 0, st>>>((double)K, 3 * N, part, out);
+}
+
 }  // namespace qmc

@@ -95,6 +95,8 @@ void launch_twist_pulay(const SysView<double>& s, const TwistView& tv, const dou
                         double* out_de, cudaStream_t st);
 size_t twist_pulay_smem_bytes(int N, int n);
 void launch_twist_average(int K, int N, const double* tout, double* out, cudaStream_t st);
+void launch_twist_partial(int Kr, int N, const double* out, double* part, cudaStream_t st);
+void launch_twist_combine(int K, int N, const double* part, double* out, cudaStream_t st);
 
 // k_empirical.cu: S = H + mu I, H the Hessian of the screened-Coulomb proton pair potential.
 void launch_empirical_s(int N, double L, const double* R, double lambda, double mu, double* S, cudaStream_t st);

@@ -99,6 +99,8 @@ def lib():
         L.langevin_step.argtypes = [vp, _dp, _dp, _dp, C.c_double, C.c_double, C.c_int, C.c_double]
         L.langevin_step_device.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, C.c_int, C.c_double]
         L.qmc_set_empirical_s.argtypes = [vp, C.c_double, C.c_double]
+        L.qmc_twist_partial_device.argtypes = [vp, vp, vp]
+        L.qmc_twist_combine_device.argtypes = [vp, vp, C.c_int, vp]
         L.qmc_empirical_s.argtypes = [vp, _dp, _dp]
         L.qmc_empirical_s_device.argtypes = [vp, vp, vp]
         L.langevin_first_predict.argtypes = [vp, _dp, _dp, _dp, C.c_double, C.c_double]
@@ -247,6 +249,15 @@ class QMCSystem:
         _chk(lib().langevin_step(self._h, _p(Rn), _p(_f64(f)), _p(Sa), T_kelvin, delta, s_mode, alpha),
              "langevin_step")
         return Rn
+
+    # twists sharded over processes (device tensors, asynchronous): see TwistGroup
+    def twist_partial_device(self, out_dev, part_dev):
+        _chk(lib().qmc_twist_partial_device(self._h, C.c_void_p(out_dev.data_ptr()), C.c_void_p(part_dev.data_ptr())),
+             "qmc_twist_partial_device")
+
+    def twist_combine_device(self, part_dev, K_total: int, out_dev):
+        _chk(lib().qmc_twist_combine_device(self._h, C.c_void_p(part_dev.data_ptr()), int(K_total),
+                                            C.c_void_p(out_dev.data_ptr())), "qmc_twist_combine_device")
 
     def set_empirical_s(self, lam: float = 0.0, mu: float = 0.5):
         """Parameters of S = H + mu I for s_mode QMC_S_EMPIRICAL (lam <= 0: Thomas-Fermi length)."""
@@ -519,6 +530,46 @@ def shard_sizes(walkers_total: int, world: int) -> list[int]:
     (consecutive slices, the first walkers_total % world one larger)."""
     base, extra = divmod(int(walkers_total), int(world))
     return [base + (1 if r < extra else 0) for r in range(world)]
+
+
+def twist_slice(twists, rank: int, world: int) -> np.ndarray:
+    """The consecutive share of a twist list ([K][3], K a multiple of world) that
+    process `rank` of `world` samples in a TwistGroup."""
+    t = np.asarray(twists, dtype=np.float64).reshape(-1, 3)
+    if t.shape[0] % world:
+        raise ValueError(f"{t.shape[0]} twists do not split evenly over {world} processes")
+    k = t.shape[0] // world
+    return t[rank * k:(rank + 1) * k]
+
+
+class TwistGroup:
+    """One twist-averaged energy/force evaluation with the twist mesh split over
+    the processes of a torch.distributed group (one GPU each): each process's
+    handle samples its own slice of the twists (twist_slice), with the same
+    walkers per twist everywhere, so the sampling exchanges nothing; one
+    all-reduce then sums the processes' weighted averages (qmc_twist_partial),
+    and every process ends with the average over all twists
+    (qmc_twist_combine), the result one handle over the whole mesh would give
+    up to the order of the FP64 sums.  `system` is the process's QMCSystem (or
+    any object with energy_forces_device, the twist_* methods and N)."""
+
+    def __init__(self, system, K_total: int, group=None):
+        import torch
+        import torch.distributed as dist
+        self.system, self.group, self.dist = system, group, dist
+        self.K_total = int(K_total)
+        N = system.N
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        if dev == "cuda" and hasattr(system, "set_stream"):
+            system.set_stream(torch.cuda.current_stream().cuda_stream or 1)
+        self.part = torch.zeros(4 + 3 * N + 9 * N * N, dtype=torch.float64, device=dev)
+
+    def energy_forces_device(self, R_dev, out_dev):
+        """out_dev: [E, E_err, N_c, accept, f(3N), S(3N x 3N)], the layout of qmc_energy_forces_device."""
+        self.system.energy_forces_device(R_dev, out_dev)
+        self.system.twist_partial_device(out_dev, self.part)
+        self.dist.all_reduce(self.part, op=self.dist.ReduceOp.SUM, group=self.group)
+        self.system.twist_combine_device(self.part, self.K_total, out_dev)
 
 
 class ShardGroup:

@@ -16,6 +16,7 @@ from paper_1605_08423_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 MP4 = synth.monkhorst_pack(4)
+DEV = "cuda"
 
 
 def _osys(wl, theta):
@@ -106,6 +107,47 @@ def test_twist_average_of_single_twist_handles():
     assert np.max(np.abs(both["f"] - 0.5 * (parts[0]["f"] + parts[1]["f"]))) < 1e-12 * np.max(np.abs(both["f"]))
     assert np.max(np.abs(both["S"] - 0.25 * (parts[0]["S"] + parts[1]["S"]))) < 1e-12 * np.max(np.abs(both["S"]))
     assert both["Nc"] == parts[0]["Nc"] + parts[1]["Nc"]
+
+
+def test_twist_sharded_partials_combine_to_the_single_handle():
+    """The partial / combine steps of a TwistGroup on one GPU: two two-twist
+    handles on the same walkers (the second one's Philox streams offset by
+    W/2), their contributions summed as the all-reduce would, give the result
+    of one four-twist handle."""
+    import torch
+    wl = synth.workload("h16", walkers=8, sweeps=3, warmup=2)
+    tw = MP4[[3, 20, 44, 61]]
+    n_out = 4 + 3 * wl.N + 9 * wl.N * wl.N
+    R_dev = torch.tensor(wl.R, dtype=torch.float64, device=DEV)
+    ref = torch.zeros(n_out, dtype=torch.float64, device=DEV)
+    one = q.QMCSystem(q.Config.from_workload(wl, twists=tw), wl.R)
+    one.energy_forces_device(R_dev, ref)
+    one.sync()
+    total = torch.zeros(n_out, dtype=torch.float64, device=DEV)
+    systems = []
+    for r in range(2):
+        s = q.QMCSystem(q.Config.from_workload(wl, walkers=4, twists=q.twist_slice(tw, r, 2)), wl.R)
+        s.set_walker_offset(4 * r)
+        o = torch.zeros(n_out, dtype=torch.float64, device=DEV)
+        part = torch.zeros(n_out, dtype=torch.float64, device=DEV)
+        s.energy_forces_device(R_dev, o)
+        s.twist_partial_device(o, part)
+        s.sync()
+        total += part
+        systems.append(s)
+    out = torch.zeros(n_out, dtype=torch.float64, device=DEV)
+    if DEV == "cuda":
+        torch.cuda.synchronize()      # the handles run on their own streams
+    systems[0].twist_combine_device(total, 4, out)
+    systems[0].sync()
+    a, b = out.cpu().numpy(), ref.cpu().numpy()
+    N3 = 3 * wl.N
+    assert abs(a[0] - b[0]) < 1e-12 * max(abs(b[0]), 1.0) and abs(a[1] - b[1]) < 1e-12 * b[1]
+    assert a[2] == b[2] and abs(a[3] - b[3]) < 1e-14
+    assert np.max(np.abs(a[4:4 + N3] - b[4:4 + N3])) < 1e-12 * np.max(np.abs(b[4:4 + N3]))
+    assert np.max(np.abs(a[4 + N3:] - b[4 + N3:])) < 1e-12 * np.max(np.abs(b[4 + N3:]))
+    with pytest.raises(q.QMCError):
+        systems[0].twist_combine_device(total, 1, out)          # fewer twists than the handle's own
 
 
 def test_twisted_handles_reject_sharding():
