@@ -81,8 +81,8 @@ typedef struct {
     const double* fj;         /* [N][N] symmetric coefficients (copied), or NULL         */
     /* Twisted boundary conditions (SI, basis section: phi(r + nL) = e^{i theta.n} phi(r))
      * and the k-point average of the main text.  n_twist = 0: the real
-     * Gamma-point form above.  n_twist = K > 0: FP64 form only, no fj, W a
-     * multiple of K with W/K >= 2 (INVALID otherwise).  The orbitals are then
+     * Gamma-point form above.  n_twist = K > 0: FP64 form only (fj allowed),
+     * W a multiple of K with W/K >= 2 (INVALID otherwise).  The orbitals are then
      * Bloch-summed Gaussians
      *   chi_{a,g}(r) = sum_n e^{i theta.n} exp(-zeta_g |r - R_a - nL|^2)
      * (images n = k + m, m in [-M, M]^3 around the nearest one k, with

@@ -172,8 +172,8 @@ int validate(const qmc_params* p) {
     if (p->fj && !(p->zeta_j > 0)) return QMC_ERR_INVALID;
     if (p->n_sweeps / p->measure_every < 1) return QMC_ERR_INVALID;
     if (p->n_twist < 0) return QMC_ERR_INVALID;
-    if (p->n_twist > 0) {   // twisted boundary conditions: FP64 form, no e-e-n-n term, whole walker blocks
-        if (!p->twist || p->precision != QMC_FP64 || p->fj) return QMC_ERR_INVALID;
+    if (p->n_twist > 0) {   // twisted boundary conditions: FP64 form, whole walker blocks
+        if (!p->twist || p->precision != QMC_FP64) return QMC_ERR_INVALID;
         if (p->n_walkers % p->n_twist || p->n_walkers / p->n_twist < 2) return QMC_ERR_INVALID;
         for (int k = 0; k < 3 * p->n_twist; ++k)
             if (!std::isfinite(p->twist[k])) return QMC_ERR_INVALID;

@@ -277,15 +277,29 @@ void launch_twist_invert(int W, int N, int n, const double2* Phi, double2* Gt, d
 // the moving spin block's G^T staged in shared memory, row stride n + 1):
 //   ratio  R = sum_j phi'_j G^T[i][j],   accept if u < |R|^2 exp(2 dU),
 //   G^T[l] <- G^T[l] - (w_l - delta_{l,i}) / R * G^T[i],  w_l = sum_j phi'_j G^T[l][j].
-// dU is the real Jastrow difference of the Gamma-point form.  An accepted
+// dU is the real Jastrow difference of the Gamma-point form (with the e-e-n-n
+// term when s.fj is set: c_a = sum_j chi_a(r_j) kept per walker, and the pairs
+// (i, j != i) change by sum_a (chi_a(r'_i) - chi_a(r_i)) sum_b f_ab (c_b - chi_b(r_i))).  An accepted
 // position is wrapped into the box, x = x' - kL; the orbital row of x is
 // exp(-i sg theta.k) times that of x', so row i of G^T (column i of the
 // inverse) takes the factor exp(i sg theta.k) to stay the inverse of the
 // Slater block at the stored positions.
 // ---------------------------------------------------------------------------
-__host__ __device__ inline size_t twist_sweep_warp_bytes(int N, int n) {
-    const size_t b = ((size_t)n * (n + 1) + 2 * (size_t)n) * sizeof(double2) + (size_t)6 * N * sizeof(double);
+__host__ __device__ inline size_t twist_sweep_warp_bytes(int N, int n, bool j34) {
+    const size_t b = ((size_t)n * (n + 1) + 2 * (size_t)n) * sizeof(double2) + (size_t)(j34 ? 9 : 6) * N * sizeof(double);
     return (b + 15) & ~size_t(15);
+}
+
+// e-e-n-n Jastrow orbital exp(-zeta |d|^2) between two points given by their
+// (sin, cos)(pi x / L) triples (d the sin-periodised displacement)
+__device__ __forceinline__ double tw_jas_orbital(const double* a, const double* b, double ell, double zeta) {
+    double t = 0;
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) {
+        const double sd = a[mu] * b[3 + mu] - a[3 + mu] * b[mu];
+        t += sd * sd;
+    }
+    return exp(-zeta * ell * ell * t);
 }
 
 __device__ __forceinline__ double tw_pair_dist(const double* a, const double* b, double ell) {
@@ -309,11 +323,15 @@ __global__ void __launch_bounds__(256) twist_sweep_kernel(SysView<double> s, Twi
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     double* ptr_s = (double*)smraw;                                   // [N][6] proton trig
     const size_t off = ((size_t)6 * N * sizeof(double) + 15) & ~size_t(15);
-    unsigned char* mine = smraw + off + (size_t)warp * twist_sweep_warp_bytes(N, n);
+    const bool j34 = s.fj != nullptr;
+    unsigned char* mine = smraw + off + (size_t)warp * twist_sweep_warp_bytes(N, n, j34);
     double2* Gs = (double2*)mine;            // [n][ld]
     double2* rowb = Gs + (size_t)n * ld;     // [n]
     double2* phi = rowb + n;                 // [n]
     double* et = (double*)(phi + n);         // [N][6] electron trig
+    double* c34 = et + 6 * N;                // [N] sum over electrons of chi_a (e-e-n-n term)
+    double* cho = c34 + N;                   // [N] chi_a at the moving electron
+    double* chn = cho + N;                   // [N] chi_a at its proposal
     for (int idx = threadIdx.x; idx < 6 * N; idx += blockDim.x) ptr_s[idx] = s.ptrig[idx];
     __syncthreads();
     const int w = blockIdx.x * wpb + warp;
@@ -329,6 +347,15 @@ __global__ void __launch_bounds__(256) twist_sweep_kernel(SysView<double> s, Twi
         et[6 * i + 3 + mu] = cs;
     }
     __syncwarp();
+    const double zj = s.zeta_j;
+    if (j34) {
+        for (int a = lane; a < N; a += 32) {
+            double c = 0;
+            for (int j = 0; j < N; ++j) c += tw_jas_orbital(et + 6 * j, ptr_s + 6 * a, ell, zj);
+            c34[a] = c;
+        }
+        __syncwarp();
+    }
     const double* th = tv.theta + 3 * (w / tv.Wk);
     unsigned long long naccept = 0;
     for (int sp = 0; sp < 2; ++sp) {
@@ -363,6 +390,19 @@ __global__ void __launch_bounds__(256) twist_sweep_kernel(SysView<double> s, Twi
                 pade_ep(bep, Zj, tw_pair_dist(pt, pa, ell), u1, d1, d2, d3);
                 pade_ep(bep, Zj, tw_pair_dist(ei, pa, ell), u0, d1, d2, d3);
                 du += u1 - u0;
+            }
+            if (j34) {
+                for (int a = lane; a < N; a += 32) {
+                    chn[a] = tw_jas_orbital(pt, ptr_s + 6 * a, ell, zj);
+                    cho[a] = tw_jas_orbital(ei, ptr_s + 6 * a, ell, zj);
+                }
+                __syncwarp();
+                for (int a = lane; a < N; a += 32) {
+                    const double* fa = s.fj + a;   // f symmetric: column a = row a, consecutive over lanes
+                    double wa = 0;
+                    for (int b = 0; b < N; ++b) wa += fa[(size_t)b * N] * (c34[b] - cho[b]);
+                    du += (chn[a] - cho[a]) * wa;
+                }
             }
             du = warp_sum(du);
             const double prob = (ratio.x * ratio.x + ratio.y * ratio.y) * exp(2.0 * du);
@@ -399,6 +439,8 @@ __global__ void __launch_bounds__(256) twist_sweep_kernel(SysView<double> s, Twi
                     const double2 f = make_double2(cs, sn);
                     for (int j = lane; j < n; j += 32) Gs[il * ld + j] = cmul(Gs[il * ld + j], f);
                 }
+                if (j34)
+                    for (int a = lane; a < N; a += 32) c34[a] += chn[a] - cho[a];
                 ++naccept;
             }
             __syncwarp();
@@ -412,7 +454,7 @@ __global__ void __launch_bounds__(256) twist_sweep_kernel(SysView<double> s, Twi
 void launch_twist_sweep(const SysView<double>& s, const TwistView& tv, double* X, const double* Xp, const double* ptp,
                         const double* uacc, const double2* Phi, double2* Gt, unsigned long long* nacc,
                         cudaStream_t st) {
-    const size_t wb = twist_sweep_warp_bytes(s.N, s.n);
+    const size_t wb = twist_sweep_warp_bytes(s.N, s.n, s.fj != nullptr);
     const size_t base = ((size_t)6 * s.N * sizeof(double) + 15) & ~size_t(15);
     int wpb = (int)((200u * 1024u - base) / wb);
     wpb = wpb < 1 ? 1 : (wpb > 8 ? 8 : wpb);
@@ -482,7 +524,9 @@ void launch_twist_unit_rows(int W, int n, double* Gtr, cudaStream_t st) {
 // per walker, after the measure kernel has accumulated everything else of the
 // sample (the Jastrow and Ewald terms; its own orbital force phase runs on zero
 // coefficients and adds nothing) and written E_L.  grad_i U (the Pade e-e and
-// e-n terms of the sin-periodised Jastrow) is formed here again.  Per spin
+// e-n terms of the sin-periodised Jastrow, and with s.fj the e-e-n-n term
+// grad_i U34 = sum_a grad chi_a(r_i) w_ia, w_ia = sum_b f_ab (c_b - chi_b(r_i)),
+// c = sum_j chi(r_j)) is formed here again.  Per spin
 // block, with G the inverse (G[j][i] = G^T[i][j]),
 //   Y_ij = -1/2 Lp_ij - grad_i U . D_ij,  K = G Y G,  Z_bi = sum_j C_bj G_ji,  P_bi = sum_j C_bj K_ji,
 //   d ln|psi| / dR_a += -Re sum_i sum_{b in a} Z_bi grad chi_b(r_i)
@@ -509,6 +553,8 @@ __global__ void __launch_bounds__(256) twist_pulay_kernel(SysView<double> s, Twi
     double* fde = fdl + N3;                      // [3N]
     double* et = fde + N3;                       // [N][6] (sin, cos)(pi x / L) of the electrons
     double* gUw = et + 6 * N;                    // [N][3] grad_i U
+    double* c34 = gUw + 3 * N;                   // [N] sum over electrons of chi_a (e-e-n-n term)
+    double* rows = c34 + N;                      // per warp [N]: chi_b(r_i)
     const double* th = tv.theta + 3 * (w / tv.Wk);
     const double2* ph = tv.ph + (size_t)(w / tv.Wk) * 3 * (2 * M + 1);
     for (int c = tid; c < N3; c += nt) {
@@ -547,6 +593,37 @@ __global__ void __launch_bounds__(256) twist_pulay_kernel(SysView<double> s, Twi
         for (int mu = 0; mu < 3; ++mu) gUw[3 * i + mu] = g[mu];
     }
     __syncthreads();
+    if (s.fj) {   // grad chi = -zeta chi grad t, grad t = 2 p, p = (L/pi) sin cos
+        const double zj = s.zeta_j;
+        for (int a = tid; a < N; a += nt) {
+            double c = 0;
+            for (int j = 0; j < N; ++j) c += tw_jas_orbital(et + 6 * j, s.ptrig + 6 * a, s.ell, zj);
+            c34[a] = c;
+        }
+        __syncthreads();
+        double* row = rows + (size_t)warp * N;
+        for (int i = warp; i < N; i += nw) {
+            for (int b = lane; b < N; b += 32) row[b] = tw_jas_orbital(et + 6 * i, s.ptrig + 6 * b, s.ell, zj);
+            __syncwarp();
+            double g[3] = {0, 0, 0};
+            for (int a = lane; a < N; a += 32) {
+                const double* fa = s.fj + a;   // f symmetric: column a = row a
+                double wa = 0;
+                for (int b = 0; b < N; ++b) wa += fa[(size_t)b * N] * (c34[b] - row[b]);
+                double sd[3], cd[3], t;
+                disp_trig(et + 6 * i, s.ptrig + 6 * a, s.ell, sd, cd, t);
+#pragma unroll
+                for (int mu = 0; mu < 3; ++mu) g[mu] += -2.0 * zj * row[a] * (s.ell * sd[mu] * cd[mu]) * wa;
+            }
+#pragma unroll
+            for (int mu = 0; mu < 3; ++mu) g[mu] = warp_sum(g[mu]);
+            if (lane == 0)
+#pragma unroll
+                for (int mu = 0; mu < 3; ++mu) gUw[3 * i + mu] += g[mu];
+            __syncwarp();
+        }
+        __syncthreads();
+    }
     for (int sp = 0; sp < 2; ++sp) {
         const double sg = sp == 0 ? 1.0 : -1.0;
         const double2* Gsp = Gt + ((size_t)w * 2 + sp) * n * n;
@@ -639,14 +716,14 @@ __global__ void __launch_bounds__(256) twist_pulay_kernel(SysView<double> s, Twi
     if (bad) raise_err(s.err, kErrNonfinite);
 }
 
-size_t twist_pulay_smem_bytes(int N, int n) {
-    return (size_t)3 * n * n * sizeof(double2) + (size_t)15 * N * sizeof(double);
+size_t twist_pulay_smem_bytes(int N, int n, bool j34) {
+    return (size_t)3 * n * n * sizeof(double2) + (size_t)(j34 ? 15 + 1 + 8 : 15) * N * sizeof(double);
 }
 
 void launch_twist_pulay(const SysView<double>& s, const TwistView& tv, const double* X, const double2* D,
                         const double2* Lp, const double2* Gt, const double* elw, double* acc, double* out_dl,
                         double* out_de, cudaStream_t st) {
-    const size_t smem = twist_pulay_smem_bytes(s.N, s.n);
+    const size_t smem = twist_pulay_smem_bytes(s.N, s.n, s.fj != nullptr);
     static size_t attr = 0;
     if (smem > attr &&
         cudaFuncSetAttribute(twist_pulay_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess)

@@ -93,7 +93,7 @@ void launch_twist_unit_rows(int W, int n, double* Gtr, cudaStream_t st);
 void launch_twist_pulay(const SysView<double>& s, const TwistView& tv, const double* X, const double2* D,
                         const double2* Lp, const double2* Gt, const double* elw, double* acc, double* out_dl,
                         double* out_de, cudaStream_t st);
-size_t twist_pulay_smem_bytes(int N, int n);
+size_t twist_pulay_smem_bytes(int N, int n, bool j34);
 void launch_twist_average(int K, int N, const double* tout, double* out, cudaStream_t st);
 void launch_twist_partial(int Kr, int N, const double* out, double* part, cudaStream_t st);
 void launch_twist_combine(int K, int N, const double* part, double* out, cudaStream_t st);

@@ -78,7 +78,7 @@ def test_twist_parameters_validated_without_gpu(lib):
     assert q.footprint_bytes(q.Config.from_workload(wl, twists=tw, precision=q.QMC_MIXED)) == 0   # FP64 only
     assert q.footprint_bytes(q.Config.from_workload(wl, twists=tw[:3])) == 0     # W not a multiple of K
     assert q.footprint_bytes(q.Config.from_workload(wl, walkers=4, twists=tw)) == 0   # fewer than 2 per twist
-    assert q.footprint_bytes(q.Config.from_workload(wl, twists=tw, fj=np.eye(wl.N) * 0.1)) == 0
+    assert q.footprint_bytes(q.Config.from_workload(wl, twists=tw, fj=np.eye(wl.N) * 0.1)) > 0   # with U_{3+4}
     bad = tw.copy()
     bad[1, 2] = np.nan
     assert q.footprint_bytes(q.Config.from_workload(wl, twists=bad)) == 0

@@ -90,6 +90,44 @@ def test_twisted_chain_reproduces_oracle(recompute_every):
     assert abs(res["accept"] - ar) < 1e-12
 
 
+def _fj(N, seed=5):
+    A = np.random.default_rng(seed).uniform(-0.3, 0.3, (N, N))
+    return 0.5 * (A + A.T)
+
+
+def test_twisted_with_jastrow34_eval_config_matches_oracle():
+    """The paper's production wavefunction: twisted orbitals with the e-e-n-n
+    Jastrow term; per configuration as above, two twists."""
+    wl = synth.workload("h16", walkers=8)
+    tw = MP4[[9, 50]]
+    fj = _fj(wl.N)
+    X = _configs(wl, 8, 41)
+    g = q.QMCSystem(q.Config.from_workload(wl, twists=tw, fj=fj), wl.R).eval_config(X, wl.R)
+    osys = orc.System(N=wl.N, L=wl.L, zeta=np.array(wl.zeta), coeff=wl.C, twist=tw[0], fj=fj)
+    lp, el, dl, de = orc.eval_configs_twist(osys, wl.R, X, tw)
+    assert np.all(np.abs(g["el"] - el) <= 1e-10 * np.maximum(np.abs(el), 1.0))
+    assert np.all(np.abs(g["lnpsi"] - lp) <= 1e-10 * np.maximum(np.abs(lp), 1.0))
+    assert np.all(_rel_vec(g["dlnpsi"], dl) < 1e-10)
+    assert np.all(_rel_vec(g["del_"], de) < 1e-10)
+
+
+def test_twisted_with_jastrow34_chain_reproduces_oracle():
+    wl = synth.workload("h16", walkers=4, sweeps=3, warmup=2)
+    tw = MP4[[9, 50]]
+    fj = _fj(wl.N)
+    sysg = q.QMCSystem(q.Config.from_workload(wl, twists=tw, fj=fj, recompute_every=100), wl.R)
+    res = sysg.energy_forces(wl.R)
+    osys = orc.System(N=wl.N, L=wl.L, zeta=np.array(wl.zeta), coeff=wl.C, twist=tw[0], fj=fj)
+    Xo, acco, ar, _ = orc.vmc_twists(osys, wl.R, tw, W=4, n_sweeps=3, n_warmup=2, sigma=wl.sigma, seed=wl.seed)
+    assert np.allclose(sysg.walkers(), Xo, atol=1e-9, rtol=0)
+    scale = np.maximum(np.abs(acco), 1.0)
+    assert np.max(np.abs(sysg.accumulators() - acco) / scale) < 1e-8
+    ro = orc.reduce_twists(acco, wl.N, 2)
+    assert abs(res["E"] - ro["E"]) < 1e-10 * max(abs(ro["E"]), 1.0)
+    assert np.max(np.abs(res["f"] - ro["f"])) < 1e-8 * np.max(np.abs(ro["f"]))
+    assert abs(res["accept"] - ar) < 1e-12
+
+
 def test_twist_average_of_single_twist_handles():
     """A two-twist handle equals the average of two one-twist handles that run
     the same walkers (the second one's Philox streams offset by W/K): E and f
