@@ -119,12 +119,27 @@ def workload(name: str, **over) -> Workload:
     return Workload(name=name, **kw)
 
 
-def monkhorst_pack(q: int) -> np.ndarray:
+def monkhorst_pack(q: int, time_reversal: bool = False) -> np.ndarray:
     """Twist vectors theta [q^3, 3] of the q x q x q Monkhorst-Pack mesh of a
     cubic cell (the main text's k-point sampling; q = 4 for the 64-atom runs):
-    theta_mu = 2 pi (2 r - q - 1) / (2 q), r = 1..q, i.e. k = theta / L."""
+    theta_mu = 2 pi (2 r - q - 1) / (2 q), r = 1..q, i.e. k = theta / L.
+    For even q no point is its own negative, and with time_reversal=True one
+    twist of each pair (theta, -theta) is kept (q^3 / 2 of them: the first in
+    mesh order), which gives the same equal-weight average because the spin
+    twists are opposite: psi(-theta) is the complex conjugate of psi(theta)."""
     u = (2.0 * np.arange(1, q + 1) - q - 1) / (2.0 * q)
     g = np.stack(np.meshgrid(u, u, u, indexing="ij"), -1).reshape(-1, 3)
+    if time_reversal:
+        if q % 2:
+            raise ValueError("the time-reversal halving needs an even mesh")
+        keep, seen = [], set()
+        for i, v in enumerate(g):
+            key = tuple(np.round(v * 2 * q).astype(int))
+            if tuple(-k for k in key) in seen:
+                continue
+            seen.add(key)
+            keep.append(i)
+        g = g[keep]
     return 2.0 * math.pi * g
 
 

@@ -227,3 +227,23 @@ def test_twisted_chain_samples_psi_squared_tiny_system():
     wn = w / w.mean()
     err_bf = math.sqrt(np.mean(wn ** 2 * (el - E_bf) ** 2) / len(w))
     assert abs(r["E"] - E_bf) < 3.5 * math.hypot(r["E_err"], err_bf), (r["E"], E_bf, r["E_err"], err_bf)
+
+
+def test_monkhorst_pack_mesh_and_its_time_reversal_half():
+    """The 4 x 4 x 4 mesh: 64 twists at 2 pi {-3/8, -1/8, 1/8, 3/8}^3, closed
+    under negation; its halving keeps one twist of each (theta, -theta) pair,
+    and every halved twist gives the oracle's E_L of its partner."""
+    full = synth.monkhorst_pack(4)
+    assert full.shape == (64, 3)
+    assert np.allclose(np.unique(np.round(full / (2 * math.pi) * 8)), [-3, -1, 1, 3])
+    half = synth.monkhorst_pack(4, time_reversal=True)
+    assert half.shape == (32, 3)
+    both = np.concatenate([half, -half])
+    key = lambda a: sorted(map(tuple, np.round(a / (2 * math.pi) * 8).astype(int)))
+    assert key(both) == key(full)
+    wl = synth.workload("h16")
+    X = synth.near_protons(1, wl.R, wl.N // 2, 0.6, wl.L, 4)[0]
+    for th in half[:3]:
+        a = orc.eval_config_twist(_system(wl, th), wl.R, X)
+        b = orc.eval_config_twist(_system(wl, -th), wl.R, X)
+        assert abs(a["el"] - b["el"]) < 1e-9 and abs(a["lnpsi"] - b["lnpsi"]) < 1e-11
