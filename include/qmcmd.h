@@ -93,8 +93,9 @@ typedef struct {
      * twist[3t..3t+2]; E_L and the estimators take real parts.  Each block is
      * reduced on its own and the results averaged with equal weights:
      * E, f and the acceptance are the means over the twists, n_samples the
-     * sum, E_err = sqrt(sum E_err_t^2) / K and S = sum S_t / K^2.  The served
-     * form and the walker-sharded calls reject twisted handles. */
+     * sum, E_err = sqrt(sum E_err_t^2) / K and S = sum S_t / K^2.  Served
+     * trajectories may be twisted; the walker-sharded calls reject twisted
+     * handles (the twists shard instead: qmc_twist_partial_device). */
     int32_t n_twist;          /* K, number of twists (0: Gamma point)                    */
     int32_t pad_twist;        /* unused, 0                                               */
     const double* twist;      /* [K][3] twist vectors theta, radians (copied), or NULL   */

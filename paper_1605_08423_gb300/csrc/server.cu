@@ -83,7 +83,7 @@ struct Arena {
 
 struct Traj {
     qmc_params p;
-    std::vector<double> zeta, coeff;
+    std::vector<double> zeta, coeff, twist;   // the parameter arrays, owned (twist: [K][3] or empty)
     int N = 0;
     size_t footprint = 0;             // handle + d_R + d_out, the arena block's size
     size_t handle_bytes = 0;          // the handle's part of the block
@@ -259,7 +259,7 @@ void qmc_server_destroy(qmc_server* s) {
 int qmc_server_add_trajectory(qmc_server* s, const qmc_params* p, const double* R0, double T_kelvin, double delta,
                               int s_mode, int* traj) {
     if (!s || !p || !R0 || !traj || !p->zeta || !p->coeff) return QMC_ERR_INVALID;
-    if (p->fj || p->n_twist) return QMC_ERR_INVALID;   // the served form: no e-e-n-n term, Gamma point only
+    if (p->fj) return QMC_ERR_INVALID;   // the served form carries no e-e-n-n Jastrow term
     if (s_mode != QMC_S_IDENTITY && s_mode != QMC_S_COV) return QMC_ERR_INVALID;
     const size_t fp = qmc_footprint_bytes(p);
     if (fp == 0) return QMC_ERR_INVALID;
@@ -268,6 +268,7 @@ int qmc_server_add_trajectory(qmc_server* s, const qmc_params* p, const double* 
     t.N = p->n_protons;
     t.zeta.assign(p->zeta, p->zeta + p->n_gauss);
     t.coeff.assign(p->coeff, p->coeff + (size_t)t.N * p->n_gauss * (t.N / 2));
+    if (p->n_twist > 0) t.twist.assign(p->twist, p->twist + 3 * (size_t)p->n_twist);
     t.handle_bytes = Arena::round(fp);
     t.footprint = t.handle_bytes + Arena::round(sizeof(double) * 3 * (size_t)t.N) +
                   Arena::round(sizeof(double) * t.out_len());
@@ -288,6 +289,7 @@ int qmc_server_add_trajectory(qmc_server* s, const qmc_params* p, const double* 
     Traj& tt = s->trajs.back();
     tt.p.zeta = tt.zeta.data();
     tt.p.coeff = tt.coeff.data();
+    tt.p.twist = tt.twist.empty() ? nullptr : tt.twist.data();
     *traj = (int)s->trajs.size() - 1;
     return QMC_OK;
 }

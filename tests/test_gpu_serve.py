@@ -163,3 +163,27 @@ def test_no_device_allocation_while_serving():
     srv.close()
     assert st["evictions"] > ev0 and st["admissions"] > 4
     assert free1 == free0, (free0, free1)
+
+
+def test_twisted_trajectory_served_alone_and_in_the_mix():
+    """A twisted FP64 trajectory (four twists, two walkers each, conventional
+    S = I steps: two walkers per twist give no full-rank covariance) gives the
+    same steps alone and among Gamma-point trajectories, and its first step's
+    energy is that of a standalone handle with the same parameters."""
+    wl = synth.workload("h16", walkers=8, sweeps=2, warmup=2)
+    tw = synth.monkhorst_pack(4)[[6, 25, 40, 59]]
+    cfg = q.Config.from_workload(wl, precision=q.QMC_FP64, warmup=2, warmup_cont=1, recompute_every=2, twists=tw)
+    big = 1 << 36
+    alone = q.Server(big, 1)
+    t0 = alone.add_trajectory(cfg, wl.R, 1000.0, 0.1, s_mode=q.QMC_S_IDENTITY)
+    res_alone = _run(alone, [t0], 2, [0, 0])[0]
+    alone.close()
+    others = [_traj(1, 16, 64, q.QMC_FP64), _traj(2, 16, 96, q.QMC_FP64)]
+    mix = q.Server(big, 2)
+    tids = [mix.add_trajectory(cfg, wl.R, 1000.0, 0.1, s_mode=q.QMC_S_IDENTITY)]
+    tids += [mix.add_trajectory(c, R, T, 0.1) for c, R, T in others]
+    res_mix = _run(mix, tids, 2, [0, 1, 2, 0, 1])
+    mix.close()
+    _same(res_alone, res_mix[0])
+    ref = q.QMCSystem(cfg, wl.R).energy_forces(wl.R)
+    assert abs(res_alone[0]["E"] - ref["E"]) <= 1e-12 * abs(ref["E"])
