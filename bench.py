@@ -427,6 +427,45 @@ def _twist_bench(stream, calls=5):
     return out
 
 
+def _empirical_bench(stream, steps=10):
+    """The Langevin step at N = 128 (3N = 384) with S = H + mu I built on the
+    device each step (QMC_S_EMPIRICAL: screened-Coulomb pair Hessian, then
+    the step's Cholesky and solves) beside the same step with S passed in
+    (QMC_S_COV); after 3 warm-up steps, `steps` steps timed one by one with
+    CUDA events on the handle's stream (median)."""
+    import numpy as np
+    import torch
+    from paper_1605_08423_gb300 import qmcmd as q
+    from paper_1605_08423_gb300 import synth
+    wl = synth.workload("h128", walkers=2)
+    n3 = 3 * wl.N
+    out = {"metric": "Langevin steps/s at N = 128", "config": {"workload": "h128 protons, T = 1500 K, Delta = 0.02, "
+                                                                          "lambda = Thomas-Fermi length, mu = 1.5 "
+                                                                          "(H's lowest eigenvalue here: -1.30)"}}
+    for tag, mode in (("empirical_S", q.QMC_S_EMPIRICAL), ("given_S", q.QMC_S_COV)):
+        sysq = q.QMCSystem(q.Config.from_workload(wl), wl.R)
+        sysq.set_stream(stream.cuda_stream)
+        sysq.set_empirical_s(0.0, 1.5)
+        R = torch.tensor(wl.R.ravel(), dtype=torch.float64, device="cuda")
+        f = torch.tensor(0.01 * np.random.default_rng(1).standard_normal(n3), dtype=torch.float64, device="cuda")
+        S = torch.tensor(sysq.empirical_s(wl.R), dtype=torch.float64, device="cuda")
+        ts = []
+        for k in range(3 + steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sysq.langevin_step_device(R, f, S if mode == q.QMC_S_COV else None, 1500.0, 0.02, mode, 0.0)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= 3:
+                ts.append(e0.elapsed_time(e1))
+        sysq.sync()
+        ts.sort()
+        out[tag] = {"ms_per_step_median": ts[len(ts) // 2], "ms_min": ts[0], "ms_max": ts[-1],
+                    "steps_per_s": 1e3 / ts[len(ts) // 2], "R_finite": bool(torch.isfinite(R).all().item())}
+        sysq.close()
+    return out
+
+
 def _toy_cpu_baseline():
     """The oracle's toy model on the host cores: 4096 trajectories x 20000 steps."""
     import numpy as np
@@ -823,6 +862,13 @@ def run_ours(args, ws, rank, local):
         except Exception as exc:   # a secondary leg: report, do not lose the headline line
             twl = {"error": f"{type(exc).__name__}: {exc}"}
 
+    emp = None
+    if not args.no_twist and rank == 0:
+        try:
+            emp = _empirical_bench(stream)
+        except Exception as exc:   # a secondary leg: report, do not lose the headline line
+            emp = {"error": f"{type(exc).__name__}: {exc}"}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = _cpu_baseline(wl)
@@ -862,6 +908,7 @@ def run_ours(args, ws, rank, local):
                "toy_langevin": toy,
                "jastrow34_fp64": j34,
                "twist_fp64": twl,
+               "empirical_s_langevin": emp,
                "peaks": peak_kind,
                "result": {"E": res["E"], "E_err": res["E_err"], "accept": res["accept"], "Nc": res["Nc"]}}
         print(json.dumps(out), flush=True)
