@@ -27,7 +27,10 @@
 //                          Metropolis delta against full evaluations
 //   langevin_step ........ harmonic closed forms (steepest descent, Newton step,
 //                          stationary covariance, autocorrelation); fast and
-//                          simple-rule variants against their closed forms
+//                          simple-rule variants against their closed forms; in
+//                          the periodic box, invariance under whole-box shifts
+//                          of R_prev and the canonical <cos 2 pi x / L> of a
+//                          periodic potential with position-dependent S
 //   twisted form ......... Bloch Gaussians against their Fourier series
 //                          (Poisson summation) and the Bloch property; psi's
 //                          Bloch phases and time reversal; the complex kinetic
