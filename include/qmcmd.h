@@ -304,7 +304,8 @@ int qmc_langevin_step_static(int n3, double* R, const double* Rprev, const doubl
  * Per-configuration evaluation (parity checks): for n_conf <= n_walkers
  * configurations X (host [n_conf][N][3]) at nuclei R, returns ln|psi|, E_L
  * and the R-derivatives d ln|psi|/dR, dE_L/dR ([n_conf][N][3]) from the same
- * kernels the sampler uses.  Overwrites the first n_conf walkers.
+ * kernels the sampler uses.  Overwrites the first n_conf walkers.  With
+ * twists, configuration c is evaluated as walker c: twist c / (n_walkers / K).
  */
 int qmc_eval_config(qmc_system* h, int n_conf, const double* X, const double* R,
                     double* logpsi, double* EL, double* dlogpsi_dR, double* dEL_dR);
