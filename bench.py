@@ -376,8 +376,10 @@ def _twist_bench(stream, calls=5):
     4 measured sweeps + 1 continuation per call, a sample every sweep, inverse
     recompute every 4 sweeps; after a warm-up call, `calls` calls timed one by
     one (median, min, max, median SM clock), then one profiled call for the
-    per-kernel split.  The Gamma-point FP64 form at the same size is timed the
-    same way beside it."""
+    per-kernel split.  The Gamma-point FP64 form at the same size, and the
+    twisted form with the e-e-n-n Jastrow term (the paper's production
+    wavefunction; synthetic symmetric U(-0.3, 0.3) coefficients), are timed
+    the same way beside it."""
     import torch
     from paper_1605_08423_gb300 import qmcmd as q
     from paper_1605_08423_gb300 import synth
@@ -388,9 +390,12 @@ def _twist_bench(stream, calls=5):
            "config": {"workload": f"h64: N=64 H, r_s=1.4, 2 s-Gaussians/proton, 4x4x4 Monkhorst-Pack twists, "
                                   f"{wl.walkers} walkers (16 per twist), 4 sweeps (+1 continuation) per call, "
                                   "sample every sweep, inverse recompute every 4 sweeps, FP64 form"}}
-    for tag, twists in (("twisted", tw), ("gamma", None)):
+    import numpy as np
+    A = np.random.default_rng(5).uniform(-0.3, 0.3, (wl.N, wl.N))
+    fj = 0.5 * (A + A.T)        # e-e-n-n Jastrow coefficients (synthetic, symmetric)
+    for tag, twists, f in (("twisted", tw, None), ("gamma", None, None), ("twisted_with_U34", tw, fj)):
         cfg = q.Config.from_workload(wl, precision=q.QMC_FP64, warmup=2, warmup_cont=1, measure_every=1,
-                                     recompute_every=4, twists=twists)
+                                     recompute_every=4, twists=twists, fj=f)
         sysq = q.QMCSystem(cfg, wl.R)
         sysq.set_stream(stream.cuda_stream)
         o = torch.zeros(4 + 3 * wl.N + 9 * wl.N * wl.N, dtype=torch.float64, device="cuda")
@@ -424,6 +429,8 @@ def _twist_bench(stream, calls=5):
                     "E": float(o[0].item()), "E_err": float(o[1].item())}
         sysq.close()
     out["twisted_over_gamma_time"] = out["twisted"]["ms_per_call_median"] / out["gamma"]["ms_per_call_median"]
+    out["with_U34_over_twisted_time"] = (out["twisted_with_U34"]["ms_per_call_median"]
+                                         / out["twisted"]["ms_per_call_median"])
     return out
 
 
