@@ -214,7 +214,8 @@ size_t footprint(const qmc_params* p) {
     b += 8 * (3 * 3 * N + 3 * 9 * N * N);           // Langevin
     b += 8 * (2 * 3 * N + 2 * 9 * N * N);           // first simplified scheme between its halves
     if (p->fj) b += (t == 4 ? 12 : 8) * N * N;       // e-e-n-n Jastrow coefficients (+ FP32 copy)
-    if (p->n_twist > 0) {   // twists, phase table, real D' / Lp' / unit rows / zero coefficients, E_L and ln|psi|, per-twist results
+    if (p->n_twist > 0) {
+        // twists, phase table, real D' / Lp' / unit rows / zero coefficients, E_L and ln|psi|, per-twist results
         const size_t K = p->n_twist, M = bloch_images(p);
         b += 8 * 3 * K + 16 * 3 * K * (2 * M + 1) + 8 * (W * N * 4 * n + 2 * W * n * n + B * n) + 8 * 2 * W +
              8 * K * (4 + 3 * N + 9 * N * N);
